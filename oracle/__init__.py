@@ -1,0 +1,147 @@
+"""FP64 CPU oracle for all-versus-all cRMSD (TEST INFRASTRUCTURE).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline /
+reference leg may import this package. It shares no code with the CUDA path:
+the C source ``crmsd_oracle.c`` is compiled on its own with gcc (OpenMP for
+timing only) and loaded through ctypes.
+
+Every function follows ClusCo's definition of cRMSD (section "Algorithms",
+eq. 1: RMS deviation of matched atoms after the optimal superposition, with the
+cited Kabsch method). ``crmsd_eq2_pair`` restates the paper's closed form
+(eq. 2: radii of gyration, eigenvalues of M^T M from a cubic, sign of det M)
+and serves as a pin and as a second CPU method; the oracle's answers never
+come from it.
+
+Parity pins: every function here is pinned by ``tests/test_oracle_pins.py``
+(closed forms, invariances, brute-force rotation search, eq. 2, finite
+differences); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "crmsd_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_f32p = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+
+
+def build(src: str = _SRC, out: str = _LIB, extra_flags=()) -> str:
+    """Compile the oracle with gcc (-O2, FP64, OpenMP). Returns the .so path."""
+    cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-fopenmp",
+           "-fno-fast-math", *extra_flags, src, "-o", out, "-lm"]
+    subprocess.run(cmd, check=True)
+    return out
+
+
+def load(path: str | None = None):
+    """Load (building first if missing or stale) and return the ctypes library."""
+    global _lib
+    if path is not None:
+        return _bind(ctypes.CDLL(path))
+    with _lock:
+        if _lib is None:
+            if (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+                build()
+            _lib = _bind(ctypes.CDLL(_LIB))
+    return _lib
+
+
+def _bind(lib):
+    i64 = ctypes.c_int64
+    lib.oracle_max_threads.restype = ctypes.c_int
+    lib.oracle_crmsd_pair.argtypes = [_f32p, _f32p, i64, ctypes.POINTER(ctypes.c_double), _f64p]
+    lib.oracle_crmsd_allpairs.argtypes = [_f32p, i64, i64, _f64p, ctypes.c_int]
+    lib.oracle_crmsd_pairs.argtypes = [_f32p, i64, i64, _i64p, _i64p, i64, _f64p, ctypes.c_int]
+    lib.oracle_crmsd_vs_ref.argtypes = [_f32p, i64, i64, _f32p, _f64p, ctypes.c_int]
+    lib.oracle_crmsd_grad.argtypes = [_f32p, i64, i64, _f64p, ctypes.c_double, _f64p, ctypes.c_int]
+    lib.oracle_crmsd_eq2.argtypes = [_f32p, _f32p, i64, ctypes.POINTER(ctypes.c_double)]
+    for f in ("oracle_crmsd_pair", "oracle_crmsd_allpairs", "oracle_crmsd_pairs",
+              "oracle_crmsd_vs_ref", "oracle_crmsd_grad", "oracle_crmsd_eq2"):
+        getattr(lib, f).restype = ctypes.c_int
+    return lib
+
+
+def _check(st, what):
+    if st != 0:
+        raise RuntimeError(f"oracle {what} failed with status {st}")
+
+
+def _f32(x):
+    return np.ascontiguousarray(x, dtype=np.float32)
+
+
+def max_threads() -> int:
+    return int(load().oracle_max_threads())
+
+
+def crmsd_pair(A, B, lib=None):
+    """(cRMSD, R) for one pair; R (3x3) maps centred B onto centred A."""
+    lib = lib or load()
+    A, B = _f32(A), _f32(B)
+    assert A.shape == B.shape and A.ndim == 2 and A.shape[1] == 3
+    c = ctypes.c_double()
+    R = np.zeros(9, dtype=np.float64)
+    _check(lib.oracle_crmsd_pair(A, B, A.shape[0], ctypes.byref(c), R), "pair")
+    return c.value, R.reshape(3, 3)
+
+
+def crmsd_allpairs(X, nthreads: int = 0, lib=None) -> np.ndarray:
+    """Condensed N(N-1)/2 FP64 matrix, row-major upper triangle (a < b)."""
+    lib = lib or load()
+    X = _f32(X)
+    N, L = X.shape[0], X.shape[1]
+    out = np.empty(N * (N - 1) // 2, dtype=np.float64)
+    _check(lib.oracle_crmsd_allpairs(X, N, L, out, nthreads), "allpairs")
+    return out
+
+
+def crmsd_pairs(X, ia, ib, nthreads: int = 0, lib=None) -> np.ndarray:
+    """cRMSD for the listed pairs (ia[k], ib[k])."""
+    lib = lib or load()
+    X = _f32(X)
+    ia = np.ascontiguousarray(ia, dtype=np.int64)
+    ib = np.ascontiguousarray(ib, dtype=np.int64)
+    out = np.empty(ia.shape[0], dtype=np.float64)
+    _check(lib.oracle_crmsd_pairs(X, X.shape[0], X.shape[1], ia, ib, ia.shape[0], out, nthreads), "pairs")
+    return out
+
+
+def crmsd_vs_ref(X, ref, nthreads: int = 0, lib=None) -> np.ndarray:
+    """out[a] = cRMSD(model a, ref) in FP64."""
+    lib = lib or load()
+    X, ref = _f32(X), _f32(ref)
+    out = np.empty(X.shape[0], dtype=np.float64)
+    _check(lib.oracle_crmsd_vs_ref(X, X.shape[0], X.shape[1], ref, out, nthreads), "vs_ref")
+    return out
+
+
+def crmsd_grad(X, w, eps: float = 1e-6, nthreads: int = 0, lib=None) -> np.ndarray:
+    """d/dX of sum_{a<b} w_ab cRMSD_ab, shape [N, L, 3] (FP64)."""
+    lib = lib or load()
+    X = _f32(X)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    N, L = X.shape[0], X.shape[1]
+    assert w.shape[0] == N * (N - 1) // 2
+    g = np.empty((N, L, 3), dtype=np.float64)
+    _check(lib.oracle_crmsd_grad(X, N, L, w, float(eps), g.reshape(-1), nthreads), "grad")
+    return g
+
+
+def crmsd_eq2_pair(A, B, lib=None) -> float:
+    """The paper's closed form (eq. 2) in FP64 for one pair."""
+    lib = lib or load()
+    A, B = _f32(A), _f32(B)
+    c = ctypes.c_double()
+    _check(lib.oracle_crmsd_eq2(A, B, A.shape[0], ctypes.byref(c)), "eq2")
+    return c.value
