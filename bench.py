@@ -1,0 +1,353 @@
+#!/usr/bin/env python3
+"""Benchmark: all-vs-all cRMSD pairs/s (forward, forward+backward) on one B300.
+
+Workload (default): N = 5,000 models x L = 300 atoms, 5 seeded natives x 1,000 models,
+sigma ~ U(0.5, 10) A, random rigid motions (the plain-method-at-scale ensemble). One step
+is one pass of the whole hot path over that ensemble:
+    pre-pass + all-pairs forward (12,497,500 pairs, condensed FP32 matrix)
+    + one-versus-native scoring of all 5,000 models
+    + the adjoint of sum_ab w_ab cRMSD_ab (w ~ U[0,1], fixed) to d/dcoords.
+``value`` is pairs per second of that step (P / step time, device time by CUDA events,
+inputs resident in HBM). L2 is flushed (a 512 MiB write) before every timed step, outside
+the events. ``e2e`` repeats the step through the public API with host buffers: the
+step's inputs go host->device from pinned memory and the matrix, the vs-native scores and
+the gradient come back device->host inside the timed region.
+
+``--impl reference`` times the FP64 CPU oracle (test infrastructure, the reference arm of
+this build) on a bounded sample of the same workload on the host cores.
+Under torchrun (N > 1 GPUs) every rank runs an independent replica (the path needs no
+exchange); value = pairs of all ranks / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "all-vs-all cRMSD pairs/s (fwd+bwd step) at max err <= 1e-3 A"
+UNIT = "pairs/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--form", default=None, help="fp32_simt | tf32 | bf16x3 | bf16_exact2 (default: best built)")
+    p.add_argument("--N", type=int, default=5000)
+    p.add_argument("--L", type=int, default=300)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-models", type=int, default=240, help="models in the oracle's timed sample")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(N, L):
+    from paper_1302_4000_b300 import ensembles as E
+    e = E.config1(N=N, L=L)
+    w = E.weights(N * (N - 1) // 2, E.SEED_BASE + 101)
+    native = e.natives[0].astype(np.float32)
+    return e, w, native
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], d["bf16_tflops"], d.get("bf16_tflops_sustained", d["bf16_tflops"]), "measured"
+    except Exception:
+        return 6400.0, 1800.0, 1400.0, "fallback"
+
+
+def cpu_baseline(e, w, native, n_models):
+    """The FP64 oracle as it stands, on all pairs among the first n_models models."""
+    import oracle
+    X = np.ascontiguousarray(e.coords[:n_models])
+    n = X.shape[0]
+    from paper_1302_4000_b300 import ensembles as E
+    ws = E.weights(n * (n - 1) // 2, 7).astype(np.float64)
+    cores = oracle.max_threads()
+    t0 = time.perf_counter()
+    oracle.crmsd_allpairs(X)
+    oracle.crmsd_vs_ref(X, native)
+    oracle.crmsd_grad(X, ws, 1e-6)
+    dt = time.perf_counter() - t0
+    P = n * (n - 1) // 2
+    return {"value": P / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"all {P} pairs among the first {n} models (fwd + vs-native + gradient), {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    e, w, native = workload(args.N, args.L)
+    import oracle
+    oracle.load()
+    times = []
+    n = args.cpu_models
+    for it in range(args.warmup + args.steps):
+        r = cpu_baseline(e, w, native, n)
+        if it >= args.warmup:
+            times.append(r)
+    v = statistics.mean(t["value"] for t in times)
+    P = n * (n - 1) // 2
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * P / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"decoy ensemble N={args.N} L={args.L} (bounded sample: {n} models per step)",
+                       "l2": "n/a (CPU)"},
+            "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": times[0]["cores"], "kind": "oracle",
+                             "sample": times[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1302_4000_b300 import clusco
+
+    ws_, rank, local = dist_env()
+    if ws_ > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    lib = clusco.load()
+
+    if args.form is None:
+        form_name = "bf16_exact2"
+        try:
+            Xt = torch.zeros((4, 8, 3), device=dev)
+            Xt[:, :, 0] = torch.arange(8, device=dev)
+            clusco.crmsd_allpairs(Xt, clusco.FORM_BF16_EXACT2)
+            torch.cuda.synchronize()
+        except clusco.ClusCoError:
+            form_name = "fp32_simt"
+    else:
+        form_name = args.form
+    form = clusco.FORMS[form_name]
+
+    e, w, native = workload(args.N, args.L)
+    N, L = e.N, e.L
+    P = N * (N - 1) // 2
+    X = torch.from_numpy(e.coords).to(dev)
+    W = torch.from_numpy(w).to(dev)
+    ref = torch.from_numpy(native).to(dev)
+    out = torch.empty(P, dtype=torch.float32, device=dev)
+    vs = torch.empty(N, dtype=torch.float32, device=dev)
+    grad = torch.empty_like(X)
+    ws_all = torch.empty(clusco.workspace_bytes(clusco.OP_ALLPAIRS, N, L, form), dtype=torch.uint8, device=dev)
+    ws_vs = torch.empty(clusco.workspace_bytes(clusco.OP_VS_REF, N, L, form), dtype=torch.uint8, device=dev)
+    ws_bw = torch.empty(clusco.workspace_bytes(clusco.OP_BACKWARD, N, L, form), dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def fwd():
+        clusco.crmsd_allpairs(X, form, out=out, workspace=ws_all)
+
+    def step():
+        clusco.crmsd_allpairs(X, form, out=out, workspace=ws_all)
+        clusco.crmsd_vs_ref(X, ref, out=vs, workspace=ws_vs)
+        clusco.crmsd_allpairs_backward(X, W, out, 1e-6, form, grad_coords=grad, workspace=ws_bw)
+
+    launches_per_step = 2 + 2 + 3
+
+    def timed(fn, k, w_):
+        for _ in range(w_):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        if ws_ > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for s_, t_ in ev:
+            flush.fill_(1)
+            s_.record(stream)
+            fn()
+            t_.record(stream)
+        torch.cuda.synchronize()
+        if ws_ > 1:
+            dist.barrier()
+        return [s_.elapsed_time(t_) for s_, t_ in ev]
+
+    clocks = Clocks(local if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    clocks.start()
+    step_ms = timed(step, args.steps, args.warmup)
+    clk = clocks.stop()
+    if clusco.sync_status() != 0:
+        raise RuntimeError("device status set during the timed steps: " + lib.clusco_last_error().decode())
+    fwd_ms = timed(fwd, args.steps, 2)
+    ms = statistics.mean(step_ms)
+    fms = statistics.mean(fwd_ms)
+    if ws_ > 1:
+        t = torch.tensor([ms, fms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, fms = float(t[0]), float(t[1])
+
+    # plain-form forward for the "vs plain FP32" ratio (same GPU, same inputs)
+    plain_fwd = None
+    if form != clusco.FORM_FP32_SIMT:
+        ws_p = torch.empty(clusco.workspace_bytes(clusco.OP_ALLPAIRS, N, L, 0), dtype=torch.uint8, device=dev)
+        out_p = torch.empty_like(out)
+
+        def pfwd():
+            clusco.crmsd_allpairs(X, clusco.FORM_FP32_SIMT, out=out_p, workspace=ws_p)
+        plain_fwd = statistics.mean(timed(pfwd, max(2, args.steps // 2), 1))
+        del ws_p, out_p
+
+    # accuracy of this run's output on sampled pairs against the oracle (outside timing)
+    max_err = None
+    if rank == 0:
+        import oracle
+        rng = np.random.default_rng(3)
+        ia = rng.integers(0, N, 4000)
+        ib = rng.integers(0, N, 4000)
+        keep = ia != ib
+        ia, ib = np.minimum(ia[keep], ib[keep]), np.maximum(ia[keep], ib[keep])
+        idx = ia * N - ia * (ia + 1) // 2 + (ib - ia - 1)
+        got = out.cpu().numpy()[idx].astype(np.float64)
+        want = oracle.crmsd_pairs(e.coords, ia, ib)
+        max_err = float(np.abs(got - want).max())
+
+    # e2e through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(e.coords).pin_memory()
+        Wh = torch.from_numpy(w).pin_memory()
+        Rh = torch.from_numpy(native).pin_memory()
+        out_h = torch.empty(P, dtype=torch.float32).pin_memory()
+        vs_h = torch.empty(N, dtype=torch.float32).pin_memory()
+        g_h = torch.empty(X.shape, dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            Xd = Xh.to(dev, non_blocking=True)
+            Wd = Wh.to(dev, non_blocking=True)
+            Rd = Rh.to(dev, non_blocking=True)
+            clusco.crmsd_allpairs(Xd, form, out=out, workspace=ws_all)
+            clusco.crmsd_vs_ref(Xd, Rd, out=vs, workspace=ws_vs)
+            clusco.crmsd_allpairs_backward(Xd, Wd, out, 1e-6, form, grad_coords=grad, workspace=ws_bw)
+            out_h.copy_(out, non_blocking=True)
+            vs_h.copy_(vs, non_blocking=True)
+            g_h.copy_(grad, non_blocking=True)
+
+        e_ms = statistics.mean(timed(e2e_step, args.steps, 1))
+        if ws_ > 1:
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t[0])
+        h2d = Xh.numel() * 4 + Wh.numel() * 4 + Rh.numel() * 4
+        d2h = out_h.numel() * 4 + vs_h.numel() * 4 + g_h.numel() * 4
+        e2e = {"value": ws_ * P / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    hbm, bf16, bf16_sus, pk_kind = peaks()
+    # roofline of the dominant kernel: the all-pairs forward covariance contraction,
+    # 18 L flops per pair (BASELINE's algorithmic count), against the measured bf16 peak.
+    fl = 18.0 * L * P
+    ach_tf = fl / (fms * 1e-3) / 1e12
+    line = {"metric": METRIC, "value": ws_ * P / (ms * 1e-3), "unit": UNIT, "n_gpus": ws_, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32_simt": "f32+f64", "tf32": "tf32+f32",
+                                           "bf16x3": "bf16+f32", "bf16_exact2": "bf16(exact int)+f32/f64"}[form_name],
+            "data": "synthetic",
+            "config": {"workload": f"decoy ensemble N={N} L={L}, 5 natives, sigma~U(0.5,10) A", "form": form_name,
+                       "pairs": P, "step": "prepass + all-pairs fwd + vs-native + backward",
+                       "l2": "flushed (512 MiB write) before each timed step", "parallelism": f"replicas x{ws_}"},
+            "fwd": {"value": ws_ * P / (fms * 1e-3), "unit": UNIT, "ms": fms},
+            "vs_plain_fp32_fwd": (plain_fwd / fms) if plain_fwd else 1.0,
+            "plain_fp32_fwd_ms": plain_fwd,
+            "max_err_sampled_A": max_err,
+            "roofline": {"bound": "tensor", "achieved": ach_tf, "peak": bf16, "unit": "TFLOP/s",
+                         "frac": ach_tf / bf16, "traffic": None,
+                         "kernel": "all-pairs forward (prepass + contraction + epilogue), 18 L flop/pair",
+                         "peak_kind": f"{pk_kind} bf16 burst"},
+            "clocks": clk, "gpu_launches": launches_per_step * args.steps}
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(e, w, native, args.cpu_models)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws_ > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

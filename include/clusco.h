@@ -1,0 +1,124 @@
+/*
+ * clusco.h -- C-ABI of libclusco: all-versus-all cRMSD on one B300 (sm_103a).
+ *
+ * The operation (ClusCo, section "Algorithms", eq. 1 and eq. 2): for models A
+ * and B of L matched atoms,
+ *     cRMSD = sqrt(R_A^2 + R_B^2 - 2 (sqrt(l1) + sqrt(l2) + S sqrt(l3)))
+ * where R_A, R_B are the radii of gyration, l1 >= l2 >= l3 the eigenvalues of
+ * M^T M for the 3x3 covariance M = (1/L) sum_i a_i b_i^T of the centred
+ * coordinates, found as roots of a cubic, and S = sign(det M). This equals the
+ * RMS deviation after the optimal superposition (eq. 1) without building the
+ * rotation. The all-versus-all matrix has N(N-1)/2 entries (section
+ * "Background"); scoring against a reference model is the second mode the
+ * paper names (section "Results and Discussion", first paragraph).
+ *
+ * Conventions shared by every call:
+ *  - Pointers named coords, ref, out, grad_out, grad_coords and crmsd are DEVICE pointers owned by
+ *    the caller; the library never frees or keeps them. coords is
+ *    float[N][L][3] (row-major, atom-major, xyz innermost), 4-byte aligned.
+ *  - Condensed output: out[idx(a,b)] for a < b with
+ *    idx(a,b) = a*N - a*(a+1)/2 + (b - a - 1)   (int64 arithmetic).
+ *  - workspace: optional device scratch of at least
+ *    clusco_workspace_bytes(op, N, L, form) bytes, 256-byte aligned. If it is
+ *    NULL the call allocates stream-ordered scratch (cudaMallocAsync) and
+ *    frees it on the same stream.
+ *  - stream: a cudaStream_t (NULL = legacy default stream). Every call only
+ *    enqueues work and returns; argument errors return at once and enqueue
+ *    nothing.
+ *  - Device-detected conditions (non-finite input, a bounded wait that gave
+ *    up) set a device status word; clusco_sync_status() synchronises the
+ *    stream, returns that status and clears it. A model with a non-finite
+ *    coordinate yields NaN for every pair it is in. No call traps the GPU.
+ *  - Return values are clusco_status codes; clusco_last_error() gives a
+ *    thread-local message for the last non-OK return.
+ */
+#ifndef CLUSCO_H
+#define CLUSCO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CLUSCO_OK = 0,
+    CLUSCO_EINVAL = 1,      /* bad argument: sizes, null or unaligned pointer, range */
+    CLUSCO_ENOMEM = 2,      /* scratch allocation failed / workspace too small */
+    CLUSCO_ECUDA = 3,       /* a CUDA runtime call failed (message has the name) */
+    CLUSCO_ETIMEOUT = 4,    /* a bounded device wait gave up (device status) */
+    CLUSCO_EOVERFLOW = 5,   /* N*L*3 or the condensed index would overflow int64 */
+    CLUSCO_ENONFINITE = 6,  /* an input coordinate was NaN or Inf (device status) */
+    CLUSCO_EUNSUPPORTED = 7 /* form not available for these sizes / this device */
+} clusco_status;
+
+/* Precision forms of the covariance contraction (the epilogue is fixed per form):
+ *  FP32_SIMT   -- plain form: FP32 CUDA-core GEMM, FP64 cubic (Viete) epilogue.
+ *  TF32        -- tcgen05 kind::tf32 on TF32-rounded centred coordinates.
+ *  BF16X3      -- tcgen05 bf16, classic split x = hi + lo, hi*hi + hi*lo + lo*hi
+ *                 in one FP32 accumulator.
+ *  BF16_EXACT2 -- tcgen05 bf16 on 16-bit fixed point coordinates split in two
+ *                 8-bit digits; all four digit products kept in separate FP32
+ *                 accumulators, exact for L <= 1024; FP32 epilogue with FP64
+ *                 refinement of the pairs whose FP32 error bound is too large. */
+typedef enum {
+    CLUSCO_FORM_FP32_SIMT = 0,
+    CLUSCO_FORM_TF32 = 1,
+    CLUSCO_FORM_BF16X3 = 2,
+    CLUSCO_FORM_BF16_EXACT2 = 3
+} clusco_form;
+
+typedef enum {
+    CLUSCO_OP_ALLPAIRS = 0,
+    CLUSCO_OP_VS_REF = 1,
+    CLUSCO_OP_BACKWARD = 2
+} clusco_op;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int clusco_version(void);
+
+/* Bytes of device workspace op needs for (N, L, form); 0 on invalid sizes. */
+size_t clusco_workspace_bytes(int op, int64_t N, int64_t L, int form);
+
+/* All-versus-all condensed cRMSD matrix (eq. 2 for every pair a < b).
+ * coords: float[N][L][3] device; out: float[N(N-1)/2] device, overwritten.
+ * N >= 2, L >= 1. Forms as above; FP32 output. */
+int clusco_crmsd_allpairs(const float *coords, int64_t N, int64_t L, float *out, int form,
+                          void *workspace, size_t workspace_bytes, void *stream);
+
+/* Row panel of the condensed matrix: rows a in [row_begin, row_end), all b > a.
+ * out_panel receives exactly those entries, in condensed order, starting at
+ * idx(row_begin, row_begin + 1). Panels are idempotent, so a long run can be
+ * resumed at any panel boundary. 0 <= row_begin < row_end <= N - 1. */
+int clusco_crmsd_allpairs_panel(const float *coords, int64_t N, int64_t L, int64_t row_begin,
+                                int64_t row_end, float *out_panel, int form, void *workspace,
+                                size_t workspace_bytes, void *stream);
+
+/* One-versus-reference: out[a] = cRMSD(model a, ref) for a in [0, N).
+ * ref: float[L][3] device; out: float[N] device. Exact-integer covariance on
+ * 24-bit fixed point coordinates, FP64 epilogue. N >= 1, L >= 1. */
+int clusco_crmsd_vs_ref(const float *coords, int64_t N, int64_t L, const float *ref, float *out,
+                        void *workspace, size_t workspace_bytes, void *stream);
+
+/* Adjoint of the all-pairs matrix for a loss with dLoss/dcRMSD_ab = grad_out[idx(a,b)]:
+ *   grad_coords[a][i] = sum_{b != a} grad_out_ab (a_i - R_ab b_i) / (L max(c_ab, eps))
+ * with R_ab the optimal rotation of centred b onto centred a (recomputed, never
+ * stored) and c_ab = crmsd[idx] (the forward output, reused). grad_coords is
+ * float[N][L][3], overwritten. eps > 0 guards cRMSD -> 0. Pairs with
+ * c_ab below the near-duplicate threshold use a direct FP64 residual path.
+ * No counterpart in the paper, which gives no gradient. */
+int clusco_crmsd_allpairs_backward(const float *coords, int64_t N, int64_t L, const float *grad_out,
+                                   const float *crmsd, float *grad_coords, float eps, int form,
+                                   void *workspace, size_t workspace_bytes, void *stream);
+
+/* Synchronise stream, return the device status word (CLUSCO_OK if clean) and clear it. */
+int clusco_sync_status(void *stream);
+
+/* Thread-local message for the last non-OK return of this thread ("" if none). */
+const char *clusco_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLUSCO_H */

@@ -1,0 +1,215 @@
+"""Thin Python binding of libclusco (argument marshalling only).
+
+Every function here has the name of its C entry point without the ``clusco_``
+prefix and does nothing but check shapes, allocate outputs with torch, pass raw
+device pointers and the current CUDA stream to the library, and raise on a
+non-OK status. All arithmetic runs in the library's CUDA kernels; there is no
+CPU fallback: if ``libclusco.so`` is missing or no CUDA device is present, the
+calls raise.
+
+The operation is ClusCo's cRMSD (section "Algorithms", eq. 1 / eq. 2) over the
+N(N-1)/2 pairs of an ensemble (section "Background").
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libclusco.so")
+
+FORM_FP32_SIMT = 0
+FORM_TF32 = 1
+FORM_BF16X3 = 2
+FORM_BF16_EXACT2 = 3
+FORMS = {"fp32_simt": FORM_FP32_SIMT, "tf32": FORM_TF32, "bf16x3": FORM_BF16X3, "bf16_exact2": FORM_BF16_EXACT2}
+
+OP_ALLPAIRS = 0
+OP_VS_REF = 1
+OP_BACKWARD = 2
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EOVERFLOW",
+          6: "ENONFINITE", 7: "EUNSUPPORTED"}
+
+EXPORTS = ("clusco_version", "clusco_workspace_bytes", "clusco_crmsd_allpairs", "clusco_crmsd_allpairs_panel",
+           "clusco_crmsd_vs_ref", "clusco_crmsd_allpairs_backward", "clusco_sync_status", "clusco_last_error")
+
+_lib = None
+_lock = threading.Lock()
+
+
+class ClusCoError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"clusco {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load(path: str = LIB_PATH):
+    """Load libclusco.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise ClusCoError(3, f"{path} not built; run paper_1302_4000_b300.build.build()")
+            lib = ctypes.CDLL(path)
+            vp, i64, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t
+            lib.clusco_version.restype = ctypes.c_int
+            lib.clusco_last_error.restype = ctypes.c_char_p
+            lib.clusco_workspace_bytes.restype = sz
+            lib.clusco_workspace_bytes.argtypes = [ctypes.c_int, i64, i64, ctypes.c_int]
+            lib.clusco_crmsd_allpairs.argtypes = [vp, i64, i64, vp, ctypes.c_int, vp, sz, vp]
+            lib.clusco_crmsd_allpairs_panel.argtypes = [vp, i64, i64, i64, i64, vp, ctypes.c_int, vp, sz, vp]
+            lib.clusco_crmsd_vs_ref.argtypes = [vp, i64, i64, vp, vp, vp, sz, vp]
+            lib.clusco_crmsd_allpairs_backward.argtypes = [vp, i64, i64, vp, vp, vp, ctypes.c_float, ctypes.c_int,
+                                                           vp, sz, vp]
+            lib.clusco_sync_status.argtypes = [vp]
+            for f in ("clusco_crmsd_allpairs", "clusco_crmsd_allpairs_panel", "clusco_crmsd_vs_ref",
+                      "clusco_crmsd_allpairs_backward", "clusco_sync_status"):
+                getattr(lib, f).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise ClusCoError(rc, load().clusco_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _coords(coords: torch.Tensor):
+    if not coords.is_cuda:
+        raise ValueError("coords must be a CUDA tensor (use *_host for host buffers)")
+    if coords.dtype != torch.float32 or coords.dim() != 3 or coords.shape[2] != 3:
+        raise ValueError("coords must be float32 [N, L, 3]")
+    return coords.contiguous()
+
+
+def version() -> int:
+    return load().clusco_version()
+
+
+def workspace_bytes(op: int, N: int, L: int, form: int = FORM_BF16_EXACT2) -> int:
+    return int(load().clusco_workspace_bytes(op, N, L, form))
+
+
+def _ws(workspace, op, N, L, form, device):
+    if workspace is not None:
+        return workspace, workspace.numel() * workspace.element_size()
+    nb = workspace_bytes(op, N, L, form)
+    return torch.empty(max(nb, 1), dtype=torch.uint8, device=device), nb
+
+
+def crmsd_allpairs(coords: torch.Tensor, form: int = FORM_BF16_EXACT2, out: torch.Tensor | None = None,
+                   workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Condensed all-versus-all cRMSD (float32, length N(N-1)/2) on coords' device."""
+    coords = _coords(coords)
+    N, L = coords.shape[0], coords.shape[1]
+    P = N * (N - 1) // 2
+    if out is None:
+        out = torch.empty(P, dtype=torch.float32, device=coords.device)
+    assert out.is_cuda and out.dtype == torch.float32 and out.numel() >= P and out.is_contiguous()
+    ws, nb = _ws(workspace, OP_ALLPAIRS, N, L, form, coords.device)
+    _check(load().clusco_crmsd_allpairs(coords.data_ptr(), N, L, out.data_ptr(), form, ws.data_ptr(), nb,
+                                        _stream(stream)))
+    return out
+
+
+def crmsd_allpairs_panel(coords: torch.Tensor, row_begin: int, row_end: int, form: int = FORM_BF16_EXACT2,
+                         out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                         stream=None) -> torch.Tensor:
+    """Rows [row_begin, row_end) of the condensed matrix (all b > a), in condensed order."""
+    coords = _coords(coords)
+    N, L = coords.shape[0], coords.shape[1]
+
+    def start(a):
+        return a * N - a * (a + 1) // 2
+
+    n = start(row_end) - start(row_begin)
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=coords.device)
+    ws, nb = _ws(workspace, OP_ALLPAIRS, N, L, form, coords.device)
+    _check(load().clusco_crmsd_allpairs_panel(coords.data_ptr(), N, L, row_begin, row_end, out.data_ptr(), form,
+                                              ws.data_ptr(), nb, _stream(stream)))
+    return out
+
+
+def crmsd_vs_ref(coords: torch.Tensor, ref: torch.Tensor, out: torch.Tensor | None = None,
+                 workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """cRMSD of every model against ref ([L, 3] float32, same device)."""
+    coords = _coords(coords)
+    N, L = coords.shape[0], coords.shape[1]
+    ref = ref.contiguous()
+    assert ref.is_cuda and ref.dtype == torch.float32 and tuple(ref.shape) == (L, 3)
+    if out is None:
+        out = torch.empty(N, dtype=torch.float32, device=coords.device)
+    ws, nb = _ws(workspace, OP_VS_REF, N, L, 0, coords.device)
+    _check(load().clusco_crmsd_vs_ref(coords.data_ptr(), N, L, ref.data_ptr(), out.data_ptr(), ws.data_ptr(), nb,
+                                      _stream(stream)))
+    return out
+
+
+def crmsd_allpairs_backward(coords: torch.Tensor, grad_out: torch.Tensor, crmsd: torch.Tensor, eps: float = 1e-6,
+                            form: int = FORM_BF16_EXACT2, grad_coords: torch.Tensor | None = None,
+                            workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """d Loss / d coords for dLoss/dcRMSD = grad_out (condensed), reusing the forward's crmsd."""
+    coords = _coords(coords)
+    N, L = coords.shape[0], coords.shape[1]
+    P = N * (N - 1) // 2
+    grad_out = grad_out.contiguous().to(torch.float32)
+    crmsd = crmsd.contiguous()
+    assert grad_out.numel() == P and crmsd.numel() == P and grad_out.is_cuda and crmsd.is_cuda
+    if grad_coords is None:
+        grad_coords = torch.empty_like(coords)
+    ws, nb = _ws(workspace, OP_BACKWARD, N, L, form, coords.device)
+    _check(load().clusco_crmsd_allpairs_backward(coords.data_ptr(), N, L, grad_out.data_ptr(), crmsd.data_ptr(),
+                                                 grad_coords.data_ptr(), float(eps), form, ws.data_ptr(), nb,
+                                                 _stream(stream)))
+    return grad_coords
+
+
+def sync_status(stream=None) -> int:
+    """Synchronise the stream and return the device status word (0 = clean); clears it."""
+    rc = load().clusco_sync_status(_stream(stream))
+    return rc
+
+
+class CRMSDAllPairs(torch.autograd.Function):
+    """Condensed all-pairs cRMSD with the library's hand-written adjoint."""
+
+    @staticmethod
+    def forward(ctx, coords, form: int, eps: float):
+        out = crmsd_allpairs(coords, form)
+        ctx.save_for_backward(coords, out)
+        ctx.form, ctx.eps = form, eps
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        coords, out = ctx.saved_tensors
+        g = crmsd_allpairs_backward(coords, grad_out, out, ctx.eps, ctx.form)
+        return g, None, None
+
+
+def crmsd_matrix(coords: torch.Tensor, form: int = FORM_BF16_EXACT2, eps: float = 1e-6) -> torch.Tensor:
+    """Differentiable condensed cRMSD matrix."""
+    return CRMSDAllPairs.apply(coords, form, eps)
+
+
+def crmsd_allpairs_host(coords_host: torch.Tensor, form: int = FORM_BF16_EXACT2, out_host: torch.Tensor | None = None,
+                        device="cuda", stream=None) -> torch.Tensor:
+    """End-to-end call with host buffers: H2D of coords, the all-pairs kernels, D2H of the matrix."""
+    assert not coords_host.is_cuda
+    d = coords_host.to(device, non_blocking=True)
+    out = crmsd_allpairs(d, form, stream=stream)
+    if out_host is None:
+        out_host = torch.empty(out.numel(), dtype=torch.float32, pin_memory=True)
+    out_host.copy_(out, non_blocking=True)
+    return out_host

@@ -1,0 +1,328 @@
+// clusco.cu -- C-ABI of libclusco (see include/clusco.h). Unity build: every kernel of the
+// library is included here so that the device status word lives in one translation unit.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <cstdarg>
+#include <string>
+
+#include "common.cuh"
+#include "epilogue.cuh"
+#include "pairs_simt.cuh"
+#include "pairs_tc.cuh"
+#include "prepass.cuh"
+#include "vsref.cuh"
+#include "backward.cuh"
+
+using namespace clusco;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) return fail(CLUSCO_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Sub-buffer carving of a workspace.
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *b) : base((char *)b) {}
+    template <typename T>
+    T *take(size_t count)
+    {
+        T *p = (T *)(base ? base + off : nullptr);
+        off = align256(off + count * sizeof(T));
+        return p;
+    }
+};
+
+bool valid_form(int form)
+{
+    return form == CLUSCO_FORM_FP32_SIMT || form == CLUSCO_FORM_TF32 || form == CLUSCO_FORM_BF16X3 ||
+           form == CLUSCO_FORM_BF16_EXACT2;
+}
+
+// Layout of the all-pairs workspace; also used (with base == nullptr) to size it.
+struct PairsWs {
+    // SIMT
+    float *Xk = nullptr;
+    double *G64 = nullptr;
+    // tcgen05
+    void *planes = nullptr;
+    float *scales = nullptr;
+    float *G32 = nullptr;
+    int64_t Lp = 0, Npad = 0, Rpad = 0;
+    size_t bytes = 0;
+};
+
+PairsWs carve_pairs(void *base, int64_t N, int64_t L, int form)
+{
+    PairsWs w;
+    Carver c(base);
+    if (form == CLUSCO_FORM_FP32_SIMT) {
+        w.Lp = round_up(L, SIMT_KC);
+        w.Npad = round_up(N, SIMT_TILE);
+        w.Xk = c.take<float>((size_t)(w.Lp * w.Npad * 3));
+        w.G64 = c.take<double>((size_t)w.Npad);
+    } else {
+        const int64_t kalign = (form == CLUSCO_FORM_TF32) ? 32 : 64;  // 128-byte rows
+        const size_t esize = (form == CLUSCO_FORM_TF32) ? 4 : 2;
+        const int nplanes = (form == CLUSCO_FORM_TF32) ? 1 : 2;
+        w.Lp = round_up(L, kalign);
+        w.Npad = round_up(N, TC_MA);
+        w.Rpad = (w.Npad / 10) * 32;
+        w.planes = c.take<char>((size_t)(nplanes * w.Rpad * w.Lp) * esize);
+        w.scales = c.take<float>((size_t)w.Npad * 3);
+        w.G64 = c.take<double>((size_t)w.Npad);
+        w.G32 = c.take<float>((size_t)w.Npad);
+    }
+    w.bytes = c.off;
+    return w;
+}
+
+int check_sizes(int64_t N, int64_t L, int64_t minN)
+{
+    if (N < minN) return fail(CLUSCO_EINVAL, "N=%lld must be >= %lld", (long long)N, (long long)minN);
+    if (L < 1) return fail(CLUSCO_EINVAL, "L=%lld must be >= 1", (long long)L);
+    if (L > (1 << 20)) return fail(CLUSCO_EINVAL, "L=%lld above the supported 2^20 atoms", (long long)L);
+    if (N > (int64_t)1 << 31) return fail(CLUSCO_EOVERFLOW, "N=%lld above 2^31 models", (long long)N);
+    // N*L*3 and N(N-1)/2 must fit int64 comfortably
+    if ((double)N * (double)L * 3.0 > 9.0e18 || (double)N * (double)N > 9.0e18)
+        return fail(CLUSCO_EOVERFLOW, "N*L*3 or N^2 overflows int64");
+    return CLUSCO_OK;
+}
+
+int check_ptr(const void *p, const char *name, size_t align)
+{
+    if (!p) return fail(CLUSCO_EINVAL, "%s is NULL", name);
+    if (((uintptr_t)p) % align) return fail(CLUSCO_EINVAL, "%s is not %zu-byte aligned", name, align);
+    return CLUSCO_OK;
+}
+
+// Scratch: the caller's workspace or a stream-ordered allocation freed after use.
+struct Scratch {
+    void *ptr = nullptr;
+    bool owned = false;
+    cudaStream_t st = nullptr;
+    ~Scratch()
+    {
+        if (owned && ptr) cudaFreeAsync(ptr, st);
+    }
+};
+
+int get_scratch(Scratch &s, void *ws, size_t ws_bytes, size_t need, cudaStream_t st)
+{
+    s.st = st;
+    if (need == 0) return CLUSCO_OK;
+    if (ws) {
+        if (ws_bytes < need)
+            return fail(CLUSCO_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed", ws_bytes, need);
+        if (((uintptr_t)ws) % 256) return fail(CLUSCO_EINVAL, "workspace is not 256-byte aligned");
+        s.ptr = ws;
+        return CLUSCO_OK;
+    }
+    cudaError_t e = cudaMallocAsync(&s.ptr, need, st);
+    if (e != cudaSuccess) {
+        s.ptr = nullptr;
+        return fail(CLUSCO_ENOMEM, "cudaMallocAsync(%zu): %s", need, cudaGetErrorString(e));
+    }
+    s.owned = true;
+    return CLUSCO_OK;
+}
+
+int run_prepass(const float *coords, int64_t N, int64_t L, int form, const PairsWs &w, cudaStream_t st)
+{
+    const unsigned blocks = (unsigned)((w.Npad + 7) / 8);
+    if (form == CLUSCO_FORM_FP32_SIMT) {
+        prepass_simt_kernel<<<blocks, 256, 0, st>>>(coords, N, (int)L, (int)w.Lp, w.Npad, w.Xk, w.G64);
+    } else if (form == CLUSCO_FORM_BF16_EXACT2) {
+        prepass_tc_kernel<TC_EXACT2><<<blocks, 256, 0, st>>>(coords, N, (int)L, (int)w.Lp, w.Npad, w.Rpad,
+                                                                w.planes, w.scales, w.G64, w.G32);
+    } else if (form == CLUSCO_FORM_BF16X3) {
+        prepass_tc_kernel<TC_BF16X3><<<blocks, 256, 0, st>>>(coords, N, (int)L, (int)w.Lp, w.Npad, w.Rpad,
+                                                                w.planes, w.scales, w.G64, w.G32);
+    } else {
+        prepass_tc_kernel<TC_TF32><<<blocks, 256, 0, st>>>(coords, N, (int)L, (int)w.Lp, w.Npad, w.Rpad,
+                                                              w.planes, w.scales, w.G64, w.G32);
+    }
+    CUDA_TRY(cudaGetLastError());
+    return CLUSCO_OK;
+}
+
+int allpairs_impl(const float *coords, int64_t N, int64_t L, int64_t row_begin, int64_t row_end, float *out,
+                  int form, void *ws, size_t ws_bytes, cudaStream_t st)
+{
+    int rc;
+    if ((rc = check_sizes(N, L, 2))) return rc;
+    if ((rc = check_ptr(coords, "coords", 4))) return rc;
+    if ((rc = check_ptr(out, "out", 4))) return rc;
+    if (!valid_form(form)) return fail(CLUSCO_EINVAL, "unknown form %d", form);
+    if (row_begin < 0 || row_end > N - 1 || row_begin >= row_end)
+        return fail(CLUSCO_EINVAL, "row range [%lld, %lld) outside [0, N-1=%lld)", (long long)row_begin,
+                    (long long)row_end, (long long)(N - 1));
+    if (form != CLUSCO_FORM_FP32_SIMT) {
+        if ((rc = tc_supported(form, L))) return rc;
+    }
+    const PairsWs sized = carve_pairs(nullptr, N, L, form);
+    Scratch s;
+    if ((rc = get_scratch(s, ws, ws_bytes, sized.bytes, st))) return rc;
+    const PairsWs w = carve_pairs(s.ptr, N, L, form);
+    if ((rc = run_prepass(coords, N, L, form, w, st))) return rc;
+    const int64_t out_base = condensed_idx(row_begin, row_begin + 1, N);
+    if (form == CLUSCO_FORM_FP32_SIMT) {
+        const int64_t T = w.Npad / SIMT_TILE;
+        const int64_t I0 = row_begin / SIMT_TILE, I1 = (row_end - 1) / SIMT_TILE + 1;
+        const int64_t t0 = tri_row_start(I0, T), nt = tri_row_start(I1, T) - t0;
+        pairs_simt_kernel<<<(unsigned)nt, 256, 0, st>>>(w.Xk, w.G64, N, w.Npad, (int)w.Lp, (int)L, T, t0,
+                                                        row_begin, row_end, out, out_base);
+        CUDA_TRY(cudaGetLastError());
+    } else {
+        TcArgs a;
+        a.form = form;
+        a.planes = w.planes;
+        a.scales = w.scales;
+        a.G64 = w.G64;
+        a.G32 = w.G32;
+        a.N = N;
+        a.L = L;
+        a.Lp = w.Lp;
+        a.Rpad = w.Rpad;
+        a.row_begin = row_begin;
+        a.row_end = row_end;
+        a.out = out;
+        a.out_base = out_base;
+        std::string err;
+        rc = tc_launch_allpairs(a, st, err);
+        if (rc) return fail(rc, "%s", err.c_str());
+    }
+    return CLUSCO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int clusco_version(void) { return 10000; }
+
+const char *clusco_last_error(void) { return g_last_error.c_str(); }
+
+size_t clusco_workspace_bytes(int op, int64_t N, int64_t L, int form)
+{
+    if (N < 1 || L < 1 || L > (1 << 20)) return 0;
+    if (op == CLUSCO_OP_ALLPAIRS) {
+        if (!valid_form(form) || N < 2) return 0;
+        return carve_pairs(nullptr, N, L, form).bytes;
+    }
+    if (op == CLUSCO_OP_VS_REF) {
+        Carver c(nullptr);
+        c.take<int>((size_t)L * 3);
+        c.take<RefInfo>(1);
+        return c.off;
+    }
+    if (op == CLUSCO_OP_BACKWARD) {
+        if (!valid_form(form) || N < 2) return 0;
+        return backward_ws_bytes(N, L, form);
+    }
+    return 0;
+}
+
+int clusco_crmsd_allpairs(const float *coords, int64_t N, int64_t L, float *out, int form, void *workspace,
+                          size_t workspace_bytes, void *stream)
+{
+    g_last_error.clear();
+    if (N < 2) return fail(CLUSCO_EINVAL, "N=%lld must be >= 2", (long long)N);
+    return allpairs_impl(coords, N, L, 0, N - 1, out, form, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+int clusco_crmsd_allpairs_panel(const float *coords, int64_t N, int64_t L, int64_t row_begin, int64_t row_end,
+                                float *out_panel, int form, void *workspace, size_t workspace_bytes, void *stream)
+{
+    g_last_error.clear();
+    return allpairs_impl(coords, N, L, row_begin, row_end, out_panel, form, workspace, workspace_bytes,
+                         (cudaStream_t)stream);
+}
+
+int clusco_crmsd_vs_ref(const float *coords, int64_t N, int64_t L, const float *ref, float *out, void *workspace,
+                        size_t workspace_bytes, void *stream)
+{
+    g_last_error.clear();
+    int rc;
+    if ((rc = check_sizes(N, L, 1))) return rc;
+    if ((rc = check_ptr(coords, "coords", 4))) return rc;
+    if ((rc = check_ptr(ref, "ref", 4))) return rc;
+    if ((rc = check_ptr(out, "out", 4))) return rc;
+    if (L > 18000) return fail(CLUSCO_EINVAL, "vs_ref supports L <= 18000 (reference staged in shared memory)");
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch s;
+    const size_t need = clusco_workspace_bytes(CLUSCO_OP_VS_REF, N, L, 0);
+    if ((rc = get_scratch(s, workspace, workspace_bytes, need, st))) return rc;
+    Carver c(s.ptr);
+    int *nref = c.take<int>((size_t)L * 3);
+    RefInfo *info = c.take<RefInfo>(1);
+    ref_prepass_kernel<<<1, 1024, 0, st>>>(ref, (int)L, nref, info);
+    CUDA_TRY(cudaGetLastError());
+    const size_t smem = (size_t)L * 3 * sizeof(int);
+    if (smem > 48 * 1024) CUDA_TRY(cudaFuncSetAttribute(vsref_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    vsref_kernel<<<(unsigned)((N + 7) / 8), 256, smem, st>>>(coords, N, (int)L, nref, info, out);
+    CUDA_TRY(cudaGetLastError());
+    return CLUSCO_OK;
+}
+
+int clusco_crmsd_allpairs_backward(const float *coords, int64_t N, int64_t L, const float *grad_out,
+                                   const float *crmsd, float *grad_coords, float eps, int form, void *workspace,
+                                   size_t workspace_bytes, void *stream)
+{
+    g_last_error.clear();
+    int rc;
+    if ((rc = check_sizes(N, L, 2))) return rc;
+    if ((rc = check_ptr(coords, "coords", 4))) return rc;
+    if ((rc = check_ptr(grad_out, "grad_out", 4))) return rc;
+    if ((rc = check_ptr(crmsd, "crmsd", 4))) return rc;
+    if ((rc = check_ptr(grad_coords, "grad_coords", 4))) return rc;
+    if (!(eps > 0.f) || !std::isfinite(eps)) return fail(CLUSCO_EINVAL, "eps=%g must be finite and > 0", (double)eps);
+    if (!valid_form(form)) return fail(CLUSCO_EINVAL, "unknown form %d", form);
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch s;
+    const size_t need = backward_ws_bytes(N, L, form);
+    if ((rc = get_scratch(s, workspace, workspace_bytes, need, st))) return rc;
+    std::string err;
+    rc = backward_launch(coords, N, L, grad_out, crmsd, grad_coords, eps, form, s.ptr, st, err);
+    if (rc) return fail(rc, "%s", err.c_str());
+    return CLUSCO_OK;
+}
+
+int clusco_sync_status(void *stream)
+{
+    g_last_error.clear();
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned int st = 0, zero = 0;
+    CUDA_TRY(cudaMemcpyFromSymbol(&st, g_clusco_status, sizeof st));
+    CUDA_TRY(cudaMemcpyToSymbol(g_clusco_status, &zero, sizeof zero));
+    if (st & CLUSCO_ST_TIMEOUT) return fail(CLUSCO_ETIMEOUT, "a bounded device wait gave up (status 0x%x)", st);
+    if (st & CLUSCO_ST_NONFINITE) return fail(CLUSCO_ENONFINITE, "non-finite input coordinate (status 0x%x)", st);
+    if (st & CLUSCO_ST_BOUNDS) return fail(CLUSCO_ECUDA, "device bounds check fired (status 0x%x)", st);
+    return CLUSCO_OK;
+}
+
+}  // extern "C"

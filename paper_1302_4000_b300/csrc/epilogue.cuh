@@ -1,0 +1,163 @@
+// epilogue.cuh -- per-pair cRMSD from a 3x3 covariance (eq. 2), FP32 and FP64 forms.
+//
+// For centred models A, B with H = sum_i a_i b_i^T and G_A = sum_i |a_i|^2,
+// G_B = sum_i |b_i|^2, eq. 2 reads
+//     L * cRMSD^2 = G_A + G_B - 2 (s1 + s2 + S s3)
+// with s_k the singular values of H (square roots of the eigenvalues of
+// H^T H, the roots of its characteristic cubic) and S = sign(det H).
+//
+// Everything here works in a normalised frame m = H * 2 / (G_A + G_B), so that
+// Sigma_hat = s1 + s2 + S s3 of m lies in [-1, 1] and
+//     L * cRMSD^2 = (G_A + G_B) (1 - Sigma_hat);
+// no intermediate can overflow whatever the coordinate scale, and the
+// cancellation sits in one subtraction 1 - Sigma_hat.
+//
+// Two refinements of Sigma_hat are used beside the cubic:
+//   Sigma = s1 + s2 + S s3 is the largest root of the quartic
+//     P(x) = x^4 - 2 I1 x^2 - 8 det(m) x + (I1^2 - 4 I2),
+//   I1 = |m|_F^2, I2 = sum of squared 2x2 minors of m (= e2 of m^T m by
+//   Cauchy-Binet); its roots are +-s1 +- s2 +- s3 with sign product S. P is
+//   convex right of its largest root, so Newton steps from the cubic's
+//   estimate converge to it quadratically.
+#pragma once
+#include <cuda_runtime.h>
+
+__device__ __forceinline__ void sincos_t(float x, float *s, float *c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_t(double x, double *s, double *c) { sincos(x, s, c); }
+
+// Invariants of the 3x3 matrix m (row-major): I1 = |m|^2, det, I2 = sum of squared 2x2 minors.
+template <typename T>
+__device__ __forceinline__ void invariants3(const T m[9], T &I1, T &det, T &I2)
+{
+    const T a01 = m[3] * m[7] - m[4] * m[6];  // rows 1,2 / cols 0,1
+    const T a02 = m[3] * m[8] - m[5] * m[6];  // rows 1,2 / cols 0,2
+    const T a12 = m[4] * m[8] - m[5] * m[7];  // rows 1,2 / cols 1,2
+    const T b01 = m[0] * m[7] - m[1] * m[6];  // rows 0,2
+    const T b02 = m[0] * m[8] - m[2] * m[6];
+    const T b12 = m[1] * m[8] - m[2] * m[7];
+    const T c01 = m[0] * m[4] - m[1] * m[3];  // rows 0,1
+    const T c02 = m[0] * m[5] - m[2] * m[3];
+    const T c12 = m[1] * m[5] - m[2] * m[4];
+    det = m[0] * a12 - m[1] * a02 + m[2] * a01;
+    I2 = a01 * a01 + a02 * a02 + a12 * a12 + b01 * b01 + b02 * b02 + b12 * b12
+       + c01 * c01 + c02 * c02 + c12 * c12;
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s += m[k] * m[k];
+    I1 = s;
+}
+
+// Eq. 2's route: eigenvalues l1 >= l2 >= l3 of m^T m as the roots of
+//   l^3 - I1 l^2 + I2 l - det^2 = 0
+// by the trigonometric (Viete) solution; returns sqrt(l1) + sqrt(l2) + S sqrt(l3).
+template <typename T>
+__device__ __forceinline__ T sigma_cubic(T I1, T det, T I2)
+{
+    const T mm = I1 / T(3);
+    const T p = I2 - T(3) * mm * mm;              // <= 0 for a real symmetric spectrum
+    const T q = (I2 - T(2) * mm * mm) * mm - det * det;
+    T l0, l1, l2;
+    if (!(p < T(0))) {
+        l0 = l1 = l2 = mm;
+    } else {
+        const T r = sqrt(-p / T(3));
+        T arg = (T(3) * q / (T(2) * p)) * sqrt(T(-3) / p);
+        arg = fmin(fmax(arg, T(-1)), T(1));
+        const T th = acos(arg) / T(3);
+        T sn, cs;
+        sincos_t(th, &sn, &cs);
+        const T h = T(0.86602540378443864676);  // sqrt(3)/2
+        l0 = mm + T(2) * r * cs;
+        l1 = mm + r * (-cs + T(2) * h * sn);
+        l2 = mm - r * (cs + T(2) * h * sn);
+    }
+    l0 = fmax(l0, T(0));
+    l1 = fmax(l1, T(0));
+    l2 = fmax(l2, T(0));
+    const T S = det < T(0) ? T(-1) : T(1);
+    return sqrt(l0) + sqrt(l1) + S * sqrt(l2);
+}
+
+// Newton steps on the quartic whose largest root is s1 + s2 + S s3.
+template <typename T>
+__device__ __forceinline__ T quartic_newton(T s, T I1, T det, T I2, int iters)
+{
+    const T c2 = T(-2) * I1;
+    const T c1 = T(-8) * det;
+    const T c0 = I1 * I1 - T(4) * I2;
+    for (int it = 0; it < iters; ++it) {
+        const T s2 = s * s;
+        const T P = (s2 + c2) * s2 + c1 * s + c0;
+        const T dP = (T(4) * s2 + T(2) * c2) * s + c1;
+        if (dP > T(0)) {
+            const T st = P / dP;
+            if (isfinite(st)) s -= st;
+        }
+    }
+    return s;
+}
+
+// The plain form's epilogue, FP64 throughout: cubic (Viete) roots only, no polish.
+// H is the raw covariance, Ga/Gb the raw sums of squares, invL = 1/L.
+__device__ __forceinline__ float crmsd_plain_fp64(const double H[9], double Ga, double Gb, double invL)
+{
+    const double Gs = Ga + Gb;
+    if (!(Gs > 0.0)) return 0.0f;
+    const double nrm = 2.0 / Gs;
+    double m[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m[k] = H[k] * nrm;
+    double I1, det, I2;
+    invariants3(m, I1, det, I2);
+    const double s = sigma_cubic(I1, det, I2);
+    const double c2 = Gs * invL * (1.0 - s);
+    return (float)sqrt(fmax(c2, 0.0));
+}
+
+// FP64 refinement: exact covariance in, cubic start (or a supplied start), Newton polish.
+// Returns L * cRMSD^2 / (G_A + G_B) = 1 - Sigma_hat through *one_minus and cRMSD as the result.
+__device__ __forceinline__ double crmsd_refined_fp64(const double H[9], double Ga, double Gb, double invL,
+                                                     double s_start, bool have_start)
+{
+    const double Gs = Ga + Gb;
+    if (!(Gs > 0.0)) return 0.0;
+    const double nrm = 2.0 / Gs;
+    double m[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m[k] = H[k] * nrm;
+    double I1, det, I2;
+    invariants3(m, I1, det, I2);
+    double s = have_start ? s_start : sigma_cubic(I1, det, I2);
+    s = quartic_newton(s, I1, det, I2, 3);
+    const double c2 = Gs * invL * (1.0 - s);
+    return sqrt(fmax(c2, 0.0));
+}
+
+// FP32 fast path on a rounded covariance: cubic + two Newton steps, all FP32.
+// Returns cRMSD and, through err_c2, a bound on the absolute error of cRMSD^2
+// coming from FP32 rounding (KERR ulps of the normalised Sigma, times (G_A+G_B)/L).
+#ifndef CLUSCO_KERR
+#define CLUSCO_KERR 16.0f
+#endif
+__device__ __forceinline__ float crmsd_fast_fp32(const float H[9], float Ga, float Gb, float invL,
+                                                 float *s_out, float *err_c2)
+{
+    const float Gs = Ga + Gb;
+    if (!(Gs > 0.0f)) {
+        *s_out = 1.0f;
+        *err_c2 = 0.0f;
+        return 0.0f;
+    }
+    const float nrm = 2.0f / Gs;
+    float m[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m[k] = H[k] * nrm;
+    float I1, det, I2;
+    invariants3(m, I1, det, I2);
+    float s = sigma_cubic(I1, det, I2);
+    s = quartic_newton(s, I1, det, I2, 2);
+    *s_out = s;
+    const float scale = Gs * invL;
+    *err_c2 = CLUSCO_KERR * 5.9604645e-8f * scale;
+    return sqrtf(fmaxf(scale * (1.0f - s), 0.0f));
+}

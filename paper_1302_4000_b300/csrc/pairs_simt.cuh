@@ -1,0 +1,108 @@
+// pairs_simt.cuh -- the plain form: FP32 CUDA-core covariance for 64x64-model tiles of the
+// upper triangle, FP64 eq. 2 epilogue (cubic roots), condensed FP32 output.
+#pragma once
+#include "common.cuh"
+#include "epilogue.cuh"
+#include "prepass.cuh"
+
+namespace clusco {
+
+// Tiles (I, J), I <= J < T, enumerated row by row; C(I) = I*T - I(I-1)/2 tiles precede row I.
+__host__ __device__ __forceinline__ int64_t tri_row_start(int64_t I, int64_t T) { return I * T - I * (I - 1) / 2; }
+
+__device__ __forceinline__ void tri_decode(int64_t t, int64_t T, int64_t *I, int64_t *J)
+{
+    const double b = 2.0 * (double)T + 1.0;
+    double disc = b * b - 8.0 * (double)t;
+    int64_t i = (int64_t)floor((b - sqrt(fmax(disc, 0.0))) * 0.5);
+    if (i < 0) i = 0;
+    if (i > T - 1) i = T - 1;
+    while (i > 0 && tri_row_start(i, T) > t) --i;
+    while (i + 1 < T && tri_row_start(i + 1, T) <= t) ++i;
+    *I = i;
+    *J = i + (t - tri_row_start(i, T));
+}
+
+// One CTA = one 64x64 model tile; 256 threads as 16x16, each 4 A-models x 4 B-models.
+// Xk: [Lp][Npad][3] centred FP32 (zero padded). Rows a outside [row_begin, row_end) are skipped;
+// out is indexed by condensed(a, b) - out_base.
+__global__ void __launch_bounds__(256, 1)
+    pairs_simt_kernel(const float *__restrict__ Xk, const double *__restrict__ G64, int64_t N, int64_t Npad, int Lp,
+                      int L, int64_t T, int64_t tile0, int64_t row_begin, int64_t row_end, float *__restrict__ out,
+                      int64_t out_base)
+{
+    __shared__ __align__(16) float As[SIMT_KC][SIMT_TILE * 3];
+    __shared__ __align__(16) float Bs[SIMT_KC][SIMT_TILE * 3];
+    int64_t I, J;
+    tri_decode(tile0 + blockIdx.x, T, &I, &J);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+
+    float acc[4][4][9];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 9; ++e) acc[i][j][e] = 0.f;
+
+    const int64_t a0 = I * SIMT_TILE, b0 = J * SIMT_TILE;
+    for (int k0 = 0; k0 < Lp; k0 += SIMT_KC) {
+        // cooperative load: 2 x 16 x 192 floats = 1536 float4, 6 per thread
+        for (int v = threadIdx.x; v < 2 * SIMT_KC * 48; v += 256) {
+            const int which = v / (SIMT_KC * 48);
+            const int rem = v % (SIMT_KC * 48);
+            const int k = rem / 48, q = rem % 48;
+            const int64_t base = which ? b0 : a0;
+            const float4 val = *reinterpret_cast<const float4 *>(Xk + ((int64_t)(k0 + k) * Npad + base) * 3 + 4 * q);
+            float *dst = which ? &Bs[k][4 * q] : &As[k][4 * q];
+            *reinterpret_cast<float4 *>(dst) = val;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < SIMT_KC; ++k) {
+            float av[12], bv[12];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float4 x = *reinterpret_cast<const float4 *>(&As[k][ty * 12 + 4 * q]);
+                const float4 y = *reinterpret_cast<const float4 *>(&Bs[k][tx * 12 + 4 * q]);
+                av[4 * q] = x.x; av[4 * q + 1] = x.y; av[4 * q + 2] = x.z; av[4 * q + 3] = x.w;
+                bv[4 * q] = y.x; bv[4 * q + 1] = y.y; bv[4 * q + 2] = y.z; bv[4 * q + 3] = y.w;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int al = 0; al < 3; ++al)
+#pragma unroll
+                        for (int be = 0; be < 3; ++be)
+                            acc[i][j][3 * al + be] = fmaf(av[3 * i + al], bv[3 * j + be], acc[i][j][3 * al + be]);
+        }
+        __syncthreads();
+    }
+
+    const double invL = 1.0 / (double)L;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t a = a0 + ty * 4 + i;
+        if (a < row_begin || a >= row_end || a >= N) continue;
+        const double Ga = G64[a];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t b = b0 + tx * 4 + j;
+            if (b <= a || b >= N) continue;
+            double H[9];
+#pragma unroll
+            for (int e = 0; e < 9; ++e) H[e] = (double)acc[i][j][e];
+            const double Gb = G64[b];
+            float c;
+            if (isnan(Ga) || isnan(Gb))
+                c = __int_as_float(0x7fc00000);
+            else
+                c = crmsd_plain_fp64(H, Ga, Gb, invL);
+            out[condensed_idx(a, b, N) - out_base] = c;
+        }
+    }
+}
+
+}  // namespace clusco

@@ -1,0 +1,174 @@
+// vsref.cuh -- one-versus-reference cRMSD (every model against one reference model).
+//
+// HBM-bound: each model's 12 L bytes are streamed once (one warp per model, three passes
+// that hit L1). The covariance is exact: centred coordinates are rounded to 24-bit fixed
+// point per model and axis (step max|x| / (2^23 - 1)), the 9 products and 3 squares are
+// accumulated in int64 (|n| < 2^23, so L < 2^17 cannot overflow), and the FP64 epilogue
+// (cubic start + quartic Newton polish) turns them into cRMSD.
+#pragma once
+#include "common.cuh"
+#include "epilogue.cuh"
+#include "prepass.cuh"
+
+namespace clusco {
+
+constexpr float Q24 = 8388607.f;  // 2^23 - 1
+
+struct RefInfo {
+    float scale[3];
+    float mu[3];
+    double G;
+    int finite;
+};
+
+// One block of 1024 threads (32 warps) quantises the reference: nref[i][axis] (int32).
+__global__ void __launch_bounds__(1024) ref_prepass_kernel(const float *__restrict__ ref, int L,
+                                                           int *__restrict__ nref, RefInfo *__restrict__ info)
+{
+    __shared__ double red[32][3];
+    __shared__ float mx[32][3];
+    __shared__ long long gred[32][3];
+    __shared__ int bad;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) bad = 0;
+    double s[3] = {0, 0, 0};
+    bool ok = true;
+    for (int i = threadIdx.x; i < L; i += 1024)
+        for (int ax = 0; ax < 3; ++ax) {
+            const float v = ref[3 * i + ax];
+            ok = ok && isfinite(v);
+            s[ax] += (double)v;
+        }
+    __syncthreads();
+    if (!ok) atomicOr(&bad, 1);
+    for (int ax = 0; ax < 3; ++ax) {
+        const double t = warp_sum_d(s[ax]);
+        if (lane == 0) red[w][ax] = t;
+    }
+    __syncthreads();
+    float mu[3];
+    for (int ax = 0; ax < 3; ++ax) {
+        double t = 0;
+        for (int k = 0; k < 32; ++k) t += red[k][ax];
+        mu[ax] = (float)(t / (double)L);
+    }
+    float m[3] = {0, 0, 0};
+    for (int i = threadIdx.x; i < L; i += 1024)
+        for (int ax = 0; ax < 3; ++ax) m[ax] = fmaxf(m[ax], fabsf(ref[3 * i + ax] - mu[ax]));
+    for (int ax = 0; ax < 3; ++ax) {
+        const float t = warp_max_f(m[ax]);
+        if (lane == 0) mx[w][ax] = t;
+    }
+    __syncthreads();
+    float sc[3], inv[3];
+    for (int ax = 0; ax < 3; ++ax) {
+        float t = 0.f;
+        for (int k = 0; k < 32; ++k) t = fmaxf(t, mx[k][ax]);
+        sc[ax] = (t > 0.f && isfinite(t)) ? t / Q24 : 1.f;
+        inv[ax] = (t > 0.f && isfinite(t)) ? Q24 / t : 1.f;
+    }
+    long long g[3] = {0, 0, 0};
+    for (int i = threadIdx.x; i < L; i += 1024)
+        for (int ax = 0; ax < 3; ++ax) {
+            const float v = ref[3 * i + ax] - mu[ax];
+            float n = rintf(v * inv[ax]);
+            n = isfinite(n) ? fminf(fmaxf(n, -Q24), Q24) : 0.f;
+            const int ni = (int)n;
+            nref[3 * i + ax] = ni;
+            g[ax] += (long long)ni * ni;
+        }
+    for (int ax = 0; ax < 3; ++ax) {
+        const long long t = warp_sum_ll(g[ax]);
+        if (lane == 0) gred[w][ax] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double G = 0;
+        for (int ax = 0; ax < 3; ++ax) {
+            long long t = 0;
+            for (int k = 0; k < 32; ++k) t += gred[k][ax];
+            G += (double)sc[ax] * (double)sc[ax] * (double)t;
+            info->scale[ax] = sc[ax];
+            info->mu[ax] = mu[ax];
+        }
+        info->G = G;
+        info->finite = bad ? 0 : 1;
+        if (bad) set_status(CLUSCO_ST_NONFINITE);
+    }
+}
+
+// One warp per model; nref staged in dynamic shared memory (12 L bytes).
+__global__ void __launch_bounds__(256) vsref_kernel(const float *__restrict__ coords, int64_t N, int L,
+                                                    const int *__restrict__ nref_g, const RefInfo *__restrict__ info,
+                                                    float *__restrict__ out)
+{
+    extern __shared__ int nref[];
+    for (int i = threadIdx.x; i < 3 * L; i += blockDim.x) nref[i] = nref_g[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t a = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (a >= N) return;
+    const float *x = coords + a * (int64_t)L * 3;
+    float mu[3];
+    bool finite;
+    model_centroid(x, L, lane, mu, &finite);
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+    for (int i = lane; i < L; i += 32) {
+        m0 = fmaxf(m0, fabsf(x[3 * i + 0] - mu[0]));
+        m1 = fmaxf(m1, fabsf(x[3 * i + 1] - mu[1]));
+        m2 = fmaxf(m2, fabsf(x[3 * i + 2] - mu[2]));
+    }
+    const float mx[3] = {warp_max_f(m0), warp_max_f(m1), warp_max_f(m2)};
+    float inv[3], sc[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const bool pos = mx[ax] > 0.f && isfinite(mx[ax]);
+        sc[ax] = pos ? mx[ax] / Q24 : 1.f;
+        inv[ax] = pos ? Q24 / mx[ax] : 1.f;
+    }
+    long long h[9], g[3];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) h[k] = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[k] = 0;
+    for (int i = lane; i < L; i += 32) {
+        int n[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            float v = rintf((x[3 * i + ax] - mu[ax]) * inv[ax]);
+            v = isfinite(v) ? fminf(fmaxf(v, -Q24), Q24) : 0.f;
+            n[ax] = (int)v;
+            g[ax] += (long long)n[ax] * n[ax];
+        }
+#pragma unroll
+        for (int al = 0; al < 3; ++al)
+#pragma unroll
+            for (int be = 0; be < 3; ++be) h[3 * al + be] += (long long)n[al] * nref[3 * i + be];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) h[k] = warp_sum_ll(h[k]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[k] = warp_sum_ll(g[k]);
+    if (lane == 0) {
+        const RefInfo ri = *info;
+        double H[9];
+        double Ga = 0.0;
+#pragma unroll
+        for (int al = 0; al < 3; ++al) {
+            Ga += (double)sc[al] * (double)sc[al] * (double)g[al];
+#pragma unroll
+            for (int be = 0; be < 3; ++be)
+                H[3 * al + be] = ((double)sc[al] * (double)ri.scale[be]) * (double)h[3 * al + be];
+        }
+        float c;
+        if (!finite || !ri.finite) {
+            c = __int_as_float(0x7fc00000);
+            if (!finite) set_status(CLUSCO_ST_NONFINITE);
+        } else {
+            c = (float)crmsd_refined_fp64(H, Ga, ri.G, 1.0 / (double)L, 0.0, false);
+        }
+        out[a] = c;
+    }
+}
+
+}  // namespace clusco

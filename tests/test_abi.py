@@ -1,0 +1,69 @@
+"""The C-ABI library builds, loads and exports every declared entry point (no GPU needed).
+
+Argument validation runs on the host before any CUDA call, so those checks run here too.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1302_4000_b300 import build, clusco
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return clusco.load()
+
+
+def declared_symbols():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(clusco_\w+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    syms = declared_symbols()
+    assert "clusco_crmsd_allpairs" in syms and "clusco_crmsd_allpairs_backward" in syms
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(clusco.EXPORTS) <= set(syms)
+
+
+def test_version_and_workspace(lib):
+    assert clusco.version() >= 10000
+    for form in clusco.FORMS.values():
+        assert clusco.workspace_bytes(clusco.OP_ALLPAIRS, 5000, 300, form) > 0
+        assert clusco.workspace_bytes(clusco.OP_ALLPAIRS, 1, 300, form) == 0
+    assert clusco.workspace_bytes(clusco.OP_VS_REF, 5000, 300, 0) > 0
+    assert clusco.workspace_bytes(clusco.OP_BACKWARD, 1024, 256, 0) > 0
+    assert clusco.workspace_bytes(99, 10, 10, 0) == 0
+
+
+def _call_allpairs(lib, ptr, N, L, out, form):
+    return lib.clusco_crmsd_allpairs(ptr, N, L, out, form, None, 0, None)
+
+
+def test_host_side_validation(lib):
+    fake = ctypes.c_void_p(0x1000)
+    assert _call_allpairs(lib, fake, 1, 10, fake, 0) == 1          # N < 2
+    assert _call_allpairs(lib, fake, 10, 0, fake, 0) == 1          # L < 1
+    assert _call_allpairs(lib, None, 10, 10, fake, 0) == 1         # null coords
+    assert _call_allpairs(lib, ctypes.c_void_p(0x1001), 10, 10, fake, 0) == 1  # unaligned
+    assert _call_allpairs(lib, fake, 10, 10, fake, 42) == 1        # unknown form
+    assert b"form" in lib.clusco_last_error()
+    assert _call_allpairs(lib, fake, 1 << 40, 10, fake, 0) == 5    # N overflow
+    assert lib.clusco_crmsd_allpairs_panel(fake, 10, 10, 5, 3, fake, 0, None, 0, None) == 1  # bad range
+    assert lib.clusco_crmsd_allpairs_panel(fake, 10, 10, 0, 10, fake, 0, None, 0, None) == 1  # row_end > N-1
+    assert lib.clusco_crmsd_vs_ref(fake, 10, 10, None, fake, None, 0, None) == 1
+    assert lib.clusco_crmsd_allpairs_backward(fake, 10, 10, fake, fake, fake, ctypes.c_float(0.0), 0,
+                                              None, 0, None) == 1  # eps must be > 0
+    # a workspace that is too small is refused before any launch
+    assert lib.clusco_crmsd_allpairs(fake, 10, 10, fake, 0, fake, 16, None) == 2

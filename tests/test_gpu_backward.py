@@ -1,0 +1,130 @@
+"""GPU parity of the hand-written adjoint against the oracle's analytic gradient and FD.
+
+Tolerance (the stated ``<= 1e-3 relative`` for gradients, read per model):
+    ||g_a - g_a^oracle||_2 <= 1e-3 ||g_a^oracle||_2 for every model a,
+and per coordinate |dg| <= 1e-3 |g^oracle| + 1e-5 max|g^oracle|.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1302_4000_b300 import build, clusco
+from paper_1302_4000_b300 import ensembles as E
+
+from _util import condensed_index
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    build.build()
+    return clusco.load()
+
+
+def gpu_grad(X, w, eps, form=clusco.FORM_FP32_SIMT):
+    Xd = torch.from_numpy(X).cuda()
+    wd = torch.from_numpy(w).cuda()
+    c = clusco.crmsd_allpairs(Xd, form)
+    g = clusco.crmsd_allpairs_backward(Xd, wd, c, eps, form)
+    assert clusco.sync_status() == 0
+    return g.cpu().numpy().astype(np.float64), c.cpu().numpy()
+
+
+def compare(g, gref, what):
+    na = np.linalg.norm((g - gref).reshape(g.shape[0], -1), axis=1)
+    nr = np.linalg.norm(gref.reshape(g.shape[0], -1), axis=1)
+    rel = na / np.maximum(nr, 1e-300)
+    coord = np.abs(g - gref) <= 1e-3 * np.abs(gref) + 1e-5 * np.abs(gref).max()
+    print(f"{what}: max per-model rel err {rel.max():.3e} (model {np.argmax(rel)}), coords ok {coord.mean():.6f}")
+    assert rel.max() <= 1e-3, what
+    assert coord.all(), what
+
+
+@pytest.fixture(scope="module")
+def cfg3():
+    e, w = E.config3()
+    return e, w
+
+
+def test_config3_gradient_vs_oracle(cfg3):
+    e, w = cfg3
+    eps = 1e-6
+    gref = oracle.crmsd_grad(e.coords, w.astype(np.float64), eps)
+    for form in (clusco.FORM_FP32_SIMT,):
+        g, c = gpu_grad(e.coords, w, eps, form)
+        compare(g, gref, f"config3 form {form}")
+    # the close pairs really sit below the guard scale
+    cp = e.extra["close_pairs"]
+    ia = np.array([p[0] for p in cp])
+    ib = np.array([p[1] for p in cp])
+    assert np.all(oracle.crmsd_pairs(e.coords, ia, ib) < 1e-3)
+
+
+def test_config3_eps_guard_active(cfg3):
+    """eps = 1e-3 A is above the close pairs' cRMSD: the guard clamps their denominators."""
+    e, w = cfg3
+    eps = 1e-3
+    gref = oracle.crmsd_grad(e.coords, w.astype(np.float64), eps)
+    g, _ = gpu_grad(e.coords, w, eps)
+    compare(g, gref, "config3 eps=1e-3")
+    g6 = oracle.crmsd_grad(e.coords, w.astype(np.float64), 1e-6)
+    a = e.extra["close_pairs"][0][0]
+    assert np.linalg.norm(g6[a] - gref[a]) > 1e-2 * np.linalg.norm(g6[a])  # the guard changes the answer
+
+
+def test_gradient_vs_central_differences(cfg3):
+    """GPU gradient vs FP64 central differences of the oracle loss (h ~ 1e-4 A) on 64 coordinates."""
+    e, w = cfg3
+    X = e.coords
+    N, L = X.shape[0], X.shape[1]
+    g, _ = gpu_grad(X, w, 1e-6)
+    close = {m for p in e.extra["close_pairs"] for m in p}
+    rng = np.random.default_rng(64)
+    done = 0
+    while done < 64:
+        a = int(rng.integers(N))
+        if a in close:
+            continue
+        i, k = int(rng.integers(L)), int(rng.integers(3))
+        others = np.array([b for b in range(N) if b != a], dtype=np.int64)
+        lo, hi = np.minimum(a, others), np.maximum(a, others)
+        wi = w[condensed_index(lo, hi, N)].astype(np.float64)
+        Xp, Xm = X.copy(), X.copy()
+        Xp[a, i, k] = np.float32(X[a, i, k] + np.float32(1e-4))
+        Xm[a, i, k] = np.float32(X[a, i, k] - np.float32(1e-4))
+        h = float(Xp[a, i, k]) - float(Xm[a, i, k])
+        fp = (wi * oracle.crmsd_pairs(Xp, np.full(N - 1, a), others)).sum()
+        fm = (wi * oracle.crmsd_pairs(Xm, np.full(N - 1, a), others)).sum()
+        fd = (fp - fm) / h
+        scale = np.abs(g[a]).max()
+        assert abs(fd - g[a, i, k]) <= 1e-3 * abs(fd) + 2e-3 * scale, (a, i, k, fd, g[a, i, k])
+        done += 1
+
+
+def test_identical_copy_is_finite():
+    e = E.decoy_ensemble(12, 40, 1, (0.5, 5.0), 3)
+    X = e.coords.copy()
+    X[5] = X[2]
+    N = X.shape[0]
+    w = np.ones(N * (N - 1) // 2, dtype=np.float32)
+    g, c = gpu_grad(X, w, 1e-6)
+    assert np.all(np.isfinite(g))
+    gref = oracle.crmsd_grad(X, w.astype(np.float64), 1e-6)
+    compare(g, gref, "identical copy")
+
+
+def test_autograd_function_matches_direct_call(cfg3):
+    e, w = cfg3
+    X = torch.from_numpy(e.coords[:200]).cuda().requires_grad_(True)
+    N = 200
+    wt = torch.from_numpy(w[: N * (N - 1) // 2]).cuda()
+    loss = (wt * clusco.crmsd_matrix(X, clusco.FORM_FP32_SIMT, 1e-6)).sum()
+    loss.backward()
+    c = clusco.crmsd_allpairs(X.detach(), clusco.FORM_FP32_SIMT)
+    g = clusco.crmsd_allpairs_backward(X.detach(), wt, c, 1e-6, clusco.FORM_FP32_SIMT)
+    torch.cuda.synchronize()
+    assert torch.allclose(X.grad, g, rtol=1e-5, atol=1e-6 * float(g.abs().max()))

@@ -1,0 +1,178 @@
+"""GPU parity: the CUDA all-pairs and one-vs-reference paths against the FP64 oracle.
+
+Every call goes through the C-ABI (the ctypes binding). Tolerances:
+
+* BF16_EXACT2 (split BF16, exact digit products): 1e-3 A absolute on every pair (the
+  tolerance stated for split-BF16 forms); the 16-bit fixed point grid itself moves cRMSD
+  by at most about 1e-4 A.
+* FP32_SIMT (plain form): 1e-4 A absolute where FP32 accumulation allows it; in general
+  |dc| <= dc2 / c with dc2 = 8 sqrt(L) eps32 (G_a + G_b) / L, the bound of FP32
+  accumulation of the covariance over L terms (random-walk growth, factor 8 margin)
+  pushed through the cancellation in D = R_A^2 + R_B^2 - 2 Sigma.
+* TF32 and BF16X3: their input rounding (2^-11 and 2^-17 relative) is not benign on
+  near-duplicates; bounds as FP32 with their own unit roundoff.
+* one-vs-reference (24-bit exact integers, FP64 epilogue): 1e-4 A.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1302_4000_b300 import build, clusco
+from paper_1302_4000_b300 import ensembles as E
+
+from _util import all_pairs, c_error_bound, condensed_index, gyration_sums, sample_pairs
+
+pytestmark = pytest.mark.gpu
+
+EPS32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    build.build()
+    return clusco.load()
+
+
+def tc_forms():
+    return [clusco.FORM_BF16_EXACT2, clusco.FORM_BF16X3, clusco.FORM_TF32]
+
+
+def forms_available():
+    out = [clusco.FORM_FP32_SIMT]
+    X = torch.zeros((4, 8, 3), device="cuda")
+    X[:, :, 0] = torch.arange(8, device="cuda")
+    for f in tc_forms():
+        try:
+            clusco.crmsd_allpairs(X, f)
+            torch.cuda.synchronize()
+            out.append(f)
+        except clusco.ClusCoError as e:
+            if e.code != 7:
+                raise
+    return out
+
+
+def bound_for(form, c_ref, Ga, Gb, L):
+    if form == clusco.FORM_BF16_EXACT2:
+        return np.full_like(np.asarray(c_ref, dtype=np.float64), 1e-3)
+    u = {clusco.FORM_FP32_SIMT: EPS32, clusco.FORM_TF32: 2.0 ** -11, clusco.FORM_BF16X3: 2.0 ** -17}[form]
+    rel = 8.0 * np.sqrt(L) * u
+    return np.maximum(c_error_bound(c_ref, Ga, Gb, L, rel), 1e-4)
+
+
+def run_allpairs(X, form):
+    Xd = torch.from_numpy(X).cuda()
+    out = clusco.crmsd_allpairs(Xd, form)
+    rc = clusco.sync_status()
+    assert rc == 0, clusco.load().clusco_last_error()
+    return out.cpu().numpy().astype(np.float64)
+
+
+def check(form, X, got, ia, ib, ref):
+    G = gyration_sums(X)
+    L = X.shape[1]
+    err = np.abs(got - ref)
+    bnd = bound_for(form, ref, G[ia], G[ib], L)
+    worst = np.argmax(err / bnd)
+    msg = (f"form={form} N={X.shape[0]} L={L}: max|d|={err.max():.3e} p99={np.percentile(err, 99):.3e} "
+           f"worst pair ({ia[worst]},{ib[worst]}) c={ref[worst]:.6f} got={got[worst]:.6f} bound={bnd[worst]:.3e}")
+    print(msg)
+    assert np.all(np.isfinite(got)), msg
+    assert np.all(err <= bnd), msg
+    return err
+
+
+@pytest.mark.parametrize("form", [0, 1, 2, 3])
+def test_config0_all_pairs(form):
+    if form not in forms_available():
+        pytest.skip("form not built")
+    e = E.config0()
+    ref = oracle.crmsd_allpairs(e.coords)
+    got = run_allpairs(e.coords, form)
+    ia, ib = all_pairs(e.N)
+    err = check(form, e.coords, got, ia, ib, ref)
+    if form in (clusco.FORM_FP32_SIMT, clusco.FORM_BF16_EXACT2):
+        assert err.max() <= (1e-4 if form == clusco.FORM_FP32_SIMT else 1e-3)
+
+
+@pytest.mark.parametrize("N", [2, 3, 5, 33, 129])
+@pytest.mark.parametrize("L", [1, 2, 3, 4, 7, 16, 17, 255])
+def test_tiny_shapes_every_pair(N, L):
+    e = E.decoy_ensemble(N, L, 1, (0.5, 6.0), 1000 + 7 * N + L)
+    ref = oracle.crmsd_allpairs(e.coords)
+    ia, ib = all_pairs(N)
+    for form in forms_available():
+        got = run_allpairs(e.coords, form)
+        check(form, e.coords, got, ia, ib, ref)
+
+
+def test_config1_sampled_at_bench_size():
+    """N=5000, L=300 (the bench workload): 20,000 sampled pairs, every form built."""
+    e = E.config1()
+    ia, ib = sample_pairs(e.N, 20000, 5)
+    ref = oracle.crmsd_pairs(e.coords, ia, ib)
+    idx = condensed_index(ia, ib, e.N)
+    for form in forms_available():
+        got = run_allpairs(e.coords, form)[idx]
+        check(form, e.coords, got, ia, ib, ref)
+
+
+def test_panels_equal_one_shot():
+    e = E.decoy_ensemble(301, 40, 2, (0.5, 6.0), 31)
+    X = torch.from_numpy(e.coords).cuda()
+    for form in forms_available():
+        full = clusco.crmsd_allpairs(X, form).cpu()
+        N = e.N
+        pieces = []
+        for r0, r1 in [(0, 37), (37, 128), (128, 299), (299, 300)]:
+            pieces.append(clusco.crmsd_allpairs_panel(X, r0, r1, form).cpu())
+        assert torch.equal(torch.cat(pieces), full)
+
+
+def test_output_canaries():
+    e = E.decoy_ensemble(70, 20, 1, (0.5, 6.0), 8)
+    X = torch.from_numpy(e.coords).cuda()
+    P = 70 * 69 // 2
+    for form in forms_available():
+        buf = torch.full((P + 4096,), 12345.0, device="cuda")
+        clusco.crmsd_allpairs(X, form, out=buf)
+        torch.cuda.synchronize()
+        assert torch.all(buf[P:] == 12345.0)
+        assert torch.all(buf[:P] != 12345.0)
+
+
+def test_vs_ref():
+    e = E.config1(N=2000)
+    ref_model = e.natives[0].astype(np.float32)
+    got = clusco.crmsd_vs_ref(torch.from_numpy(e.coords).cuda(), torch.from_numpy(ref_model).cuda()).cpu().numpy()
+    want = oracle.crmsd_vs_ref(e.coords, ref_model)
+    assert clusco.sync_status() == 0
+    err = np.abs(got - want)
+    print(f"vs_ref max|d|={err.max():.3e}")
+    assert err.max() <= 1e-4
+
+
+def test_vs_ref_tiny():
+    for L in (1, 2, 3, 5, 64, 1000):
+        e = E.decoy_ensemble(17, L, 1, (0.1, 4.0), 90 + L)
+        got = clusco.crmsd_vs_ref(torch.from_numpy(e.coords).cuda(), torch.from_numpy(e.coords[3]).cuda()).cpu().numpy()
+        want = oracle.crmsd_vs_ref(e.coords, e.coords[3])
+        assert np.abs(got - want).max() <= 1e-4, L
+
+
+def test_nonfinite_inputs_flagged():
+    e = E.decoy_ensemble(50, 30, 1, (0.5, 6.0), 12)
+    X = e.coords.copy()
+    X[7, 3, 1] = np.nan
+    Xd = torch.from_numpy(X).cuda()
+    for form in forms_available():
+        out = clusco.crmsd_allpairs(Xd, form).cpu().numpy()
+        assert clusco.sync_status() == 6
+        ia, ib = all_pairs(50)
+        bad = (ia == 7) | (ib == 7)
+        assert np.all(np.isnan(out[bad]))
+        assert np.all(np.isfinite(out[~bad]))
+    assert clusco.sync_status() == 0
