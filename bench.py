@@ -41,7 +41,7 @@ UNIT = "pairs/s"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--form", default=None, help="fp32_simt | tf32 | bf16x3 | bf16_exact2 (default: best built)")
@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--L", type=int, default=300)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--cpu-models", type=int, default=240, help="models in the oracle's timed sample")
+    p.add_argument("--cpu-models", type=int, default=2400, help="models in the oracle's timed sample")
     return p.parse_args()
 
 

@@ -289,12 +289,7 @@ __global__ void __launch_bounds__(256) bwd_neardup_kernel(const float *__restric
             for (int k = 0; k < 9; ++k) m[k] = H[k] * nrm;
             double I1, det, I2;
             invariants3(m, I1, det, I2);
-            double s = 1.0;  // upper bound of the normalised Sigma; Newton from above converges
-            for (int it = 0; it < 60; ++it) {
-                const double sn = quartic_newton(s, I1, det, I2, 1);
-                if (!(sn < s)) break;
-                s = sn;
-            }
+            const double s = quartic_newton(sigma_cubic(I1, det, I2), I1, det, I2, 3);
             horn_rotation(m, s, R);
         }
         // residuals r_i = a_i - R b_i; c from the residuals; coefficient with the guard

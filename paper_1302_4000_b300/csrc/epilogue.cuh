@@ -22,8 +22,6 @@
 #pragma once
 #include <cuda_runtime.h>
 
-__device__ __forceinline__ void sincos_t(float x, float *s, float *c) { sincosf(x, s, c); }
-__device__ __forceinline__ void sincos_t(double x, double *s, double *c) { sincos(x, s, c); }
 
 // Invariants of the 3x3 matrix m (row-major): I1 = |m|^2, det, I2 = sum of squared 2x2 minors.
 template <typename T>
@@ -47,38 +45,41 @@ __device__ __forceinline__ void invariants3(const T m[9], T &I1, T &det, T &I2)
     I1 = s;
 }
 
-// Eq. 2's route: eigenvalues l1 >= l2 >= l3 of m^T m as the roots of
-//   l^3 - I1 l^2 + I2 l - det^2 = 0
-// by the trigonometric (Viete) solution; returns sqrt(l1) + sqrt(l2) + S sqrt(l3).
+// Eq. 2's route: the eigenvalues l1 >= l2 >= l3 of m^T m are the roots of
+//   l^3 - I1 l^2 + I2 l - det^2 = 0.
+// The largest root l1 comes from the trigonometric (Viete) solution, where it is well
+// conditioned. The other two enter only through sqrt(l2) + S sqrt(l3), whose square is
+//   l2 + l3 + 2 S sqrt(l2 l3) = (I2 - det^2/l1)/l1 + 2 det/sqrt(l1)
+// by Vieta's relations (l2 + l3 = (I2 - l2 l3)/l1, l2 l3 = det^2/l1, S |det| = det).
+// I2 is a sum of squared 2x2 minors, so a rank-deficient m (collinear or planar atoms)
+// keeps full relative accuracy, which sqrt() of the small cubic roots would lose.
+// Returns Sigma = sqrt(l1) + sqrt(l2) + S sqrt(l3).
 template <typename T>
 __device__ __forceinline__ T sigma_cubic(T I1, T det, T I2)
 {
     const T mm = I1 / T(3);
     const T p = I2 - T(3) * mm * mm;              // <= 0 for a real symmetric spectrum
     const T q = (I2 - T(2) * mm * mm) * mm - det * det;
-    T l0, l1, l2;
+    T l1;
     if (!(p < T(0))) {
-        l0 = l1 = l2 = mm;
+        l1 = mm;
     } else {
         const T r = sqrt(-p / T(3));
         T arg = (T(3) * q / (T(2) * p)) * sqrt(T(-3) / p);
         arg = fmin(fmax(arg, T(-1)), T(1));
-        const T th = acos(arg) / T(3);
-        T sn, cs;
-        sincos_t(th, &sn, &cs);
-        const T h = T(0.86602540378443864676);  // sqrt(3)/2
-        l0 = mm + T(2) * r * cs;
-        l1 = mm + r * (-cs + T(2) * h * sn);
-        l2 = mm - r * (cs + T(2) * h * sn);
+        l1 = mm + T(2) * r * cos(acos(arg) / T(3));
     }
-    l0 = fmax(l0, T(0));
-    l1 = fmax(l1, T(0));
-    l2 = fmax(l2, T(0));
-    const T S = det < T(0) ? T(-1) : T(1);
-    return sqrt(l0) + sqrt(l1) + S * sqrt(l2);
+    if (!(l1 > T(0))) return T(0);
+    const T rl1 = sqrt(l1);
+    const T t = (I2 - det * det / l1) / l1 + T(2) * det / rl1;
+    return rl1 + sqrt(fmax(t, T(0)));
 }
 
-// Newton steps on the quartic whose largest root is s1 + s2 + S s3.
+// Newton steps on the quartic whose largest root is s1 + s2 + S s3. At that root
+// P' = 8 (s2 + S s3)(s1 + S s3)(s1 + s2); where it vanishes against 8 Sigma^3 (rank <= 1
+// covariance, or S = -1 with s2 = s3) the root is double, P and P' are rounding noise and
+// a Newton step would be noise over noise, so the step is taken only while P' is a
+// clear fraction (1e-3) of its natural scale; the cubic route is accurate there.
 template <typename T>
 __device__ __forceinline__ T quartic_newton(T s, T I1, T det, T I2, int iters)
 {
@@ -89,7 +90,7 @@ __device__ __forceinline__ T quartic_newton(T s, T I1, T det, T I2, int iters)
         const T s2 = s * s;
         const T P = (s2 + c2) * s2 + c1 * s + c0;
         const T dP = (T(4) * s2 + T(2) * c2) * s + c1;
-        if (dP > T(0)) {
+        if (dP > T(8e-3) * s2 * s) {
             const T st = P / dP;
             if (isfinite(st)) s -= st;
         }
@@ -97,7 +98,7 @@ __device__ __forceinline__ T quartic_newton(T s, T I1, T det, T I2, int iters)
     return s;
 }
 
-// The plain form's epilogue, FP64 throughout: cubic (Viete) roots only, no polish.
+// The plain form's epilogue, FP64 throughout: the cubic route only, no Newton polish.
 // H is the raw covariance, Ga/Gb the raw sums of squares, invL = 1/L.
 __device__ __forceinline__ float crmsd_plain_fp64(const double H[9], double Ga, double Gb, double invL)
 {
@@ -115,7 +116,7 @@ __device__ __forceinline__ float crmsd_plain_fp64(const double H[9], double Ga, 
 }
 
 // FP64 refinement: exact covariance in, cubic start (or a supplied start), Newton polish.
-// Returns L * cRMSD^2 / (G_A + G_B) = 1 - Sigma_hat through *one_minus and cRMSD as the result.
+// Returns cRMSD; the cancellation 1 - Sigma_hat is taken in FP64.
 __device__ __forceinline__ double crmsd_refined_fp64(const double H[9], double Ga, double Gb, double invL,
                                                      double s_start, bool have_start)
 {

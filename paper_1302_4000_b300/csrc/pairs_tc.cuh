@@ -1,8 +1,43 @@
-// pairs_tc.cuh -- tcgen05 all-pairs kernels (placeholder until the tensor path lands).
+// pairs_tc.cuh -- tensor-core (tcgen05) all-pairs cRMSD: the covariance stage of eq. 2
+// as the contraction X X^T over K = L atoms, fused with the per-pair eq. 2 epilogue.
+//
+// Operands (written by prepass_tc_kernel): K-contiguous planes of 3N rows, rows grouped
+// 32 at a time as 10 models x 3 axes + 2 zero rows. One CTA computes one tile of
+// 40 A-models (128 rows) x 20 B-models (64 rows): the 128 x N block of X_A X_B^T holds
+// the 3x3 covariance blocks of its 800 model pairs. Only tiles with pairs a < b exist
+// (upper triangle: B-tile J >= 2 I).
+//
+// Pipeline (one CTA, 8 warps, two CTAs per SM so that one CTA's epilogue overlaps the
+// other's MMAs): warp 0 lane 0 streams 64-column K blocks of the A and B tiles into a
+// 2-stage shared-memory ring with TMA (128-byte swizzle); warp 1 lane 0 issues
+// tcgen05.mma into tensor memory; all 8 warps then run the epilogue: tcgen05.ld of
+// their 32 TMEM lanes x 32 columns, assembly of each 3x3 block across the three lanes
+// of a model with warp shuffles, eq. 2 in the normalised frame, condensed FP32 store.
+// No covariance ever reaches global memory.
+//
+// Forms:
+//  EXACT2: planes h, l of 16-bit fixed point (n = 256 h + l). Per 16-wide K step two
+//    MMAs of N = 128 against B' = [B_h; B_l]: A_h B'^T -> TMEM cols [0,128) (hh | hl),
+//    A_l B'^T -> cols [128,256) (lh | ll). Four digit-product classes, each an exact
+//    integer sum in FP32 (|digit| <= 128, L <= 1024 keeps every sum below 2^24).
+//    Epilogue: FP32 fast path; pairs whose FP32 error bound exceeds the fast-path
+//    tolerance are queued per warp and recomputed from the exact classes in FP64.
+//  BF16X3: planes hi, lo; A_h B'^T (hh | hl) and A_l B_h^T (lh); H = hh + hl + lh.
+//  TF32: one FP32 plane; A B^T with kind::tf32.
 #pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
 #include <string>
 
 #include "common.cuh"
+#include "epilogue.cuh"
+#include "prepass.cuh"
+#include "ptx.cuh"
+
+#ifndef CLUSCO_TOL_FAST
+#define CLUSCO_TOL_FAST 2.5e-4f  // A: largest FP32 fast-path error accepted for the exact form
+#endif
 
 namespace clusco {
 
@@ -17,19 +52,439 @@ struct TcArgs {
     int64_t out_base;
 };
 
+constexpr int TC_THREADS = 256;
+constexpr int TC_STAGES = 2;
+constexpr int TC_TMEM_COLS = 256;
+constexpr uint32_t STAGE_BYTES_BF16 = 2 * 16384 + 2 * 8192;  // A_h, A_l, B_h, B_l
+constexpr uint32_t STAGE_BYTES_TF32 = 16384 + 8192;          // A, B
+constexpr size_t TC_SMEM = 1024 + TC_STAGES * STAGE_BYTES_BF16;  // same for every form: 2 CTAs/SM
+constexpr int QCAP = 64;  // refinement queue entries per warp
+struct QEntry {
+    float v[36];  // class-major raw class values of the 3x3 block (rows cyclic from alpha)
+    int la, lb, alpha;
+    float s;
+};
+static_assert(sizeof(QEntry) == 160, "queue entry layout");
+static_assert(8 * QCAP * sizeof(QEntry) <= TC_STAGES * STAGE_BYTES_BF16, "queues reuse the stage ring");
+
+__host__ __device__ __forceinline__ int64_t tc_row_start(int64_t I, int64_t TB) { return I * TB - I * (I - 1); }
+
+// Tile t -> (I, J): rows I in order, J in [2I, TB).
+__device__ __forceinline__ void tc_decode(int64_t t, int64_t TB, int64_t TA, int64_t *I, int64_t *J)
+{
+    const double b = (double)TB + 1.0;
+    int64_t i = (int64_t)floor((b - sqrt(fmax(b * b - 4.0 * (double)t, 0.0))) * 0.5);
+    if (i < 0) i = 0;
+    if (i > TA - 1) i = TA - 1;
+    while (i > 0 && tc_row_start(i, TB) > t) --i;
+    while (i + 1 < TA && tc_row_start(i + 1, TB) <= t) ++i;
+    *I = i;
+    *J = 2 * i + (t - tc_row_start(i, TB));
+}
+
+template <int LAYOUT>
+__device__ __forceinline__ void tc_issue_kblock(uint32_t tmem, uint32_t sbase, int kb)
+{
+    if (LAYOUT == TC_TF32) {
+        constexpr uint32_t id = make_idesc(128, 64, 2);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint64_t a = desc_sw128(sbase + 32 * k);
+            const uint64_t b = desc_sw128(sbase + 16384 + 32 * k);
+            mma_tf32(tmem, a, b, id, (kb > 0 || k > 0) ? 1u : 0u);
+        }
+    } else {
+        constexpr uint32_t id128 = make_idesc(128, 128, 1);
+        constexpr uint32_t id64 = make_idesc(128, 64, 1);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+            const uint64_t ah = desc_sw128(sbase + 32 * k);
+            const uint64_t al = desc_sw128(sbase + 16384 + 32 * k);
+            const uint64_t bb = desc_sw128(sbase + 32768 + 32 * k);  // [B_h; B_l], 128 rows
+            mma_bf16(tmem + 0, ah, bb, id128, acc);
+            if (LAYOUT == TC_EXACT2)
+                mma_bf16(tmem + 128, al, bb, id128, acc);
+            else
+                mma_bf16(tmem + 128, al, bb, id64, acc);  // B_h only: lh
+        }
+    }
+}
+
+// Selection among three values by a small runtime index (no local memory).
+__device__ __forceinline__ float sel3(int i, float a, float b, float c) { return i == 0 ? a : (i == 1 ? b : c); }
+
+template <int LAYOUT>
+__global__ void __launch_bounds__(TC_THREADS, 2)
+    pairs_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                    const float *__restrict__ scales, const double *__restrict__ G64, const float *__restrict__ G32,
+                    int64_t N, int L, int nkb, int64_t Rpad, int64_t TA, int64_t TB, int64_t tile0, int64_t row_begin,
+                    int64_t row_end, float *__restrict__ out, int64_t out_base)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[TC_STAGES];
+    __shared__ __align__(8) uint64_t empty_bar[TC_STAGES];
+    __shared__ __align__(8) uint64_t done_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    __shared__ float sB_scale[TC_MB * 3];
+    __shared__ float sB_G32[TC_MB];
+    __shared__ int q_count[8];
+
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase0 = smem_u32(smem);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    int64_t I, J;
+    tc_decode(tile0 + blockIdx.x, TB, TA, &I, &J);
+    const int64_t a_base = I * TC_MA, b_base = J * TC_MB;
+
+    if (warp == 0) {
+        tmem_alloc(&tmem_slot, TC_TMEM_COLS);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&done_bar, 1);
+        abort_flag = 0;
+        fence_barrier_init();
+        fence_proxy_async();
+    }
+    if (tid < TC_MB * 3) {
+        const int64_t b = b_base + tid / 3;
+        sB_scale[tid] = scales[b * 3 + tid % 3];
+    }
+    if (tid < TC_MB) sB_G32[tid] = G32[b_base + tid];
+    if (tid < 8) q_count[tid] = 0;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    constexpr uint32_t STAGE_BYTES = (LAYOUT == TC_TF32) ? STAGE_BYTES_TF32 : STAGE_BYTES_BF16;
+    constexpr int KB_ELEMS = (LAYOUT == TC_TF32) ? 32 : 64;
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer ----
+        tma_prefetch_desc(&mapA);
+        tma_prefetch_desc(&mapB);
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % TC_STAGES, use = kb / TC_STAGES;
+            if (kb >= TC_STAGES) {
+                if (!mbar_wait(&empty_bar[s], (use - 1) & 1)) {
+                    atomicExch(&abort_flag, 1);
+                    break;
+                }
+            }
+            if (*(volatile int *)&abort_flag) break;
+            uint8_t *st = smem + s * STAGE_BYTES_BF16;
+            mbar_arrive_expect_tx(&full_bar[s], STAGE_BYTES);
+            const int x = kb * KB_ELEMS;
+            if (LAYOUT == TC_TF32) {
+                tma_load_2d(st, &mapA, &full_bar[s], x, (int)(128 * I));
+                tma_load_2d(st + 16384, &mapB, &full_bar[s], x, (int)(64 * J));
+            } else {
+                tma_load_2d(st, &mapA, &full_bar[s], x, (int)(128 * I));
+                tma_load_2d(st + 16384, &mapA, &full_bar[s], x, (int)(Rpad + 128 * I));
+                tma_load_2d(st + 32768, &mapB, &full_bar[s], x, (int)(64 * J));
+                tma_load_2d(st + 40960, &mapB, &full_bar[s], x, (int)(Rpad + 64 * J));
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer ----
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % TC_STAGES, use = kb / TC_STAGES;
+            if (!mbar_wait(&full_bar[s], use & 1) || *(volatile int *)&abort_flag) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            tc_fence_after();
+            tc_issue_kblock<LAYOUT>(tmem, sbase0 + s * STAGE_BYTES_BF16, kb);
+            mma_commit(&empty_bar[s]);
+        }
+        mma_commit(&done_bar);  // also on abort: fires once everything issued has finished
+    }
+    __syncwarp();
+    const bool ok = mbar_wait(&done_bar, 0);
+    tc_fence_after();
+    __syncthreads();  // every TMA write and MMA has landed; the stage ring is free
+    if (!ok || abort_flag) {
+        // drain: on an abort the producer may have loads in flight; wait for them (bounded)
+        if (warp == 0 && lane == 0) {
+            for (int s = 0; s < TC_STAGES; ++s) mbar_wait(&full_bar[s], 0);
+        }
+        tc_fence_before();
+        __syncthreads();
+        if (warp == 0) tmem_dealloc(tmem, TC_TMEM_COLS);
+        return;
+    }
+
+    // ---- epilogue: warp -> TMEM lanes 32*(warp&3).., B-model group g = warp>>2 ----
+    const int sp = warp & 3, g = warp >> 2;
+    const int mloc = lane / 3, alpha = lane - 3 * (lane / 3);
+    const int64_t a = a_base + 10 * sp + mloc;
+    const bool lane_ok = lane < 30 && a < N;
+    const int la = 10 * sp + mloc;
+    float srow[3] = {1.f, 1.f, 1.f};
+    float Ga = 0.f;
+    double Ga64 = 0.0;
+    if (lane_ok) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) srow[i] = scales[a * 3 + (alpha + i) % 3];
+        Ga = G32[a];
+        Ga64 = G64[a];
+    }
+    const uint32_t trow = tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)(32 * g);
+    float V[32];
+    {
+        float t[32];
+        if (LAYOUT == TC_EXACT2) {
+            tmem_ld32(trow + 0, V);  // hh
+#pragma unroll
+            for (int j = 0; j < 32; ++j) V[j] *= 65536.f;
+            tmem_ld32(trow + 64, t);  // hl
+#pragma unroll
+            for (int j = 0; j < 32; ++j) V[j] = fmaf(256.f, t[j], V[j]);
+            tmem_ld32(trow + 128, t);  // lh
+#pragma unroll
+            for (int j = 0; j < 32; ++j) V[j] = fmaf(256.f, t[j], V[j]);
+            tmem_ld32(trow + 192, t);  // ll
+#pragma unroll
+            for (int j = 0; j < 32; ++j) V[j] += t[j];
+            // scales: row (own axis alpha) x column (model b, axis beta)
+#pragma unroll
+            for (int j = 0; j < 30; ++j) V[j] *= srow[0] * sB_scale[30 * g + j];
+        } else if (LAYOUT == TC_BF16X3) {
+            tmem_ld32(trow + 0, V);
+            tmem_ld32(trow + 64, t);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) V[j] += t[j];
+            tmem_ld32(trow + 128, t);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) V[j] += t[j];
+        } else {
+            tmem_ld32(trow + 0, V);
+        }
+    }
+    const float invL = 1.f / (float)L;
+    QEntry *queue = reinterpret_cast<QEntry *>(smem) + warp * QCAP;
+
+    auto refine_batch = [&](int n) {
+        // lane i < n refines queue entry i in FP64 from the exact digit classes
+        if (lane < n) {
+            const QEntry &q = queue[lane];
+            const int64_t aa = a_base + q.la, bb = b_base + q.lb;
+            double H[9];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const double sr = (double)scales[aa * 3 + (q.alpha + i) % 3];
+#pragma unroll
+                for (int be = 0; be < 3; ++be) {
+                    const int k = 3 * i + be;
+                    const double v = 65536.0 * (double)q.v[k] + 256.0 * ((double)q.v[9 + k] + (double)q.v[18 + k]) +
+                                     (double)q.v[27 + k];
+                    H[k] = v * (sr * (double)scales[bb * 3 + be]);
+                }
+            }
+            const double c = crmsd_refined_fp64(H, G64[aa], G64[bb], 1.0 / (double)L, (double)q.s, true);
+            out[condensed_idx(aa, bb, N) - out_base] = (float)c;
+        }
+        __syncwarp();
+    };
+
+    for (int r = 0; r < 4; ++r) {
+        // candidate rows of the three blocks of this round: block 3r + al' at columns 9r + 3al' + be
+        float cand[3][3];
+#pragma unroll
+        for (int al = 0; al < 3; ++al)
+#pragma unroll
+            for (int be = 0; be < 3; ++be) {
+                const int j = 9 * r + 3 * al + be;
+                cand[al][be] = (j < 32) ? V[j] : 0.f;
+            }
+        float blk[9];
+#pragma unroll
+        for (int be = 0; be < 3; ++be) blk[be] = sel3(alpha, cand[0][be], cand[1][be], cand[2][be]);
+#pragma unroll
+        for (int k = 1; k <= 2; ++k) {
+            const int sendsel = (alpha + 3 - k) % 3;
+            const int src = 3 * mloc + (alpha + k) % 3;
+#pragma unroll
+            for (int be = 0; be < 3; ++be) {
+                const float sv = sel3(sendsel, cand[0][be], cand[1][be], cand[2][be]);
+                blk[3 * k + be] = __shfl_sync(0xffffffffu, sv, src & 31);
+            }
+        }
+        const int lb = 10 * g + 3 * r + alpha;  // local B model of this lane's pair
+        const int64_t b = b_base + lb;
+        const bool pair_ok = lane_ok && (3 * r + alpha) < 10 && b < N && a < b && a >= row_begin && a < row_end;
+        bool need = false;
+        float sfast = 1.f;
+        if (pair_ok) {
+            // every lane scaled its own row (axis) and the columns before the exchange, so blk is
+            // the scaled covariance with rows in cyclic order alpha, alpha+1, alpha+2: a proper
+            // rotation of the rows, which leaves eq. 2 unchanged
+            float errc2;
+            const float c = crmsd_fast_fp32(blk, Ga, sB_G32[lb], invL, &sfast, &errc2);
+            if (LAYOUT == TC_EXACT2 && !(errc2 <= 2.f * CLUSCO_TOL_FAST * c)) {
+                need = true;
+            } else {
+                out[condensed_idx(a, b, N) - out_base] = (isnan(Ga) || isnan(sB_G32[lb])) ? __int_as_float(0x7fc00000) : c;
+            }
+        }
+        if (LAYOUT == TC_EXACT2) {
+            const unsigned m = __ballot_sync(0xffffffffu, need);
+            if (m) {
+                // reload the four exact classes of this round's columns and queue the flagged pairs
+                const int base = q_count[warp];
+                const int slot = base + __popc(m & ((1u << lane) - 1u));
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    float t[32];
+                    tmem_ld32(trow + 64 * c4, t);
+                    float cc[3][3];
+#pragma unroll
+                    for (int al = 0; al < 3; ++al)
+#pragma unroll
+                        for (int be = 0; be < 3; ++be) {
+                            const int j = 9 * r + 3 * al + be;
+                            cc[al][be] = (j < 32) ? t[j] : 0.f;
+                        }
+                    float bv[9];
+#pragma unroll
+                    for (int be = 0; be < 3; ++be) bv[be] = sel3(alpha, cc[0][be], cc[1][be], cc[2][be]);
+#pragma unroll
+                    for (int k = 1; k <= 2; ++k) {
+                        const int sendsel = (alpha + 3 - k) % 3;
+                        const int src = 3 * mloc + (alpha + k) % 3;
+#pragma unroll
+                        for (int be = 0; be < 3; ++be)
+                            bv[3 * k + be] = __shfl_sync(0xffffffffu, sel3(sendsel, cc[0][be], cc[1][be], cc[2][be]), src & 31);
+                    }
+                    if (need) {
+#pragma unroll
+                        for (int e = 0; e < 9; ++e) queue[slot].v[9 * c4 + e] = bv[e];
+                    }
+                }
+                if (need) {
+                    queue[slot].la = la;
+                    queue[slot].lb = lb;
+                    queue[slot].alpha = alpha;
+                    queue[slot].s = sfast;
+                }
+                __syncwarp();
+                int cnt = base + __popc(m);
+                if (lane == 0) q_count[warp] = cnt;
+                __syncwarp();
+                if (cnt >= 32) {
+                    refine_batch(32);
+                    // move the remainder down
+                    for (int e = 32 + lane; e < cnt; e += 32) queue[e - 32] = queue[e];
+                    __syncwarp();
+                    if (lane == 0) q_count[warp] = cnt - 32;
+                    __syncwarp();
+                }
+            }
+        }
+    }
+    if (LAYOUT == TC_EXACT2) {
+        __syncwarp();
+        const int cnt = q_count[warp];
+        if (cnt > 0) refine_batch(cnt);
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, TC_TMEM_COLS);
+}
+
+// ---- host side ----------------------------------------------------------
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+inline EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
 inline int tc_supported(int form, int64_t L)
 {
-    (void)form;
-    (void)L;
-    return CLUSCO_EUNSUPPORTED;
+    if (form == CLUSCO_FORM_BF16_EXACT2 && L > 1024) return CLUSCO_EUNSUPPORTED;  // exact class sums need L <= 1024
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CLUSCO_ECUDA;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3) return CLUSCO_EUNSUPPORTED;  // built for sm_103a only
+    if (!encode_fn()) return CLUSCO_EUNSUPPORTED;
+    return CLUSCO_OK;
+}
+
+inline int make_map(CUtensorMap *m, void *base, bool tf32, int64_t Lp, int64_t rows, uint32_t box_rows,
+                    std::string &err)
+{
+    const cuuint64_t dims[2] = {(cuuint64_t)Lp, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)(Lp * (tf32 ? 4 : 2))};
+    const cuuint32_t box[2] = {tf32 ? 32u : 64u, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode_fn()(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base,
+                             dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+        return CLUSCO_ECUDA;
+    }
+    return CLUSCO_OK;
+}
+
+template <int LAYOUT>
+inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
+{
+    const bool tf32 = LAYOUT == TC_TF32;
+    const int64_t rows = tf32 ? a.Rpad : 2 * a.Rpad;
+    CUtensorMap mA, mB;
+    int rc;
+    if ((rc = make_map(&mA, a.planes, tf32, a.Lp, rows, 128, err))) return rc;
+    if ((rc = make_map(&mB, a.planes, tf32, a.Lp, rows, 64, err))) return rc;
+    const int64_t Npad = a.Rpad / 32 * 10;
+    const int64_t TA = Npad / TC_MA, TB = Npad / TC_MB;
+    const int64_t I0 = a.row_begin / TC_MA, I1 = (a.row_end - 1) / TC_MA + 1;
+    const int64_t t0 = tc_row_start(I0, TB), nt = tc_row_start(I1, TB) - t0;
+    const int nkb = (int)(a.Lp / (tf32 ? 32 : 64));
+    cudaError_t e = cudaFuncSetAttribute(pairs_tc_kernel<LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TC_SMEM);
+    if (e != cudaSuccess) {
+        err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+        return CLUSCO_ECUDA;
+    }
+    pairs_tc_kernel<LAYOUT><<<(unsigned)nt, TC_THREADS, TC_SMEM, st>>>(mA, mB, a.scales, a.G64, a.G32, a.N, (int)a.L,
+                                                                        nkb, a.Rpad, TA, TB, t0, a.row_begin,
+                                                                        a.row_end, a.out, a.out_base);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        err = std::string("pairs_tc_kernel launch: ") + cudaGetErrorString(e);
+        return CLUSCO_ECUDA;
+    }
+    return CLUSCO_OK;
 }
 
 inline int tc_launch_allpairs(const TcArgs &a, cudaStream_t st, std::string &err)
 {
-    (void)a;
-    (void)st;
-    err = "tensor-core forms not built";
-    return CLUSCO_EUNSUPPORTED;
+    if (a.form == CLUSCO_FORM_BF16_EXACT2) return launch_tc<TC_EXACT2>(a, st, err);
+    if (a.form == CLUSCO_FORM_BF16X3) return launch_tc<TC_BF16X3>(a, st, err);
+    return launch_tc<TC_TF32>(a, st, err);
 }
 
 }  // namespace clusco

@@ -71,9 +71,25 @@ def test_config3_eps_guard_active(cfg3):
     gref = oracle.crmsd_grad(e.coords, w.astype(np.float64), eps)
     g, _ = gpu_grad(e.coords, w, eps)
     compare(g, gref, "config3 eps=1e-3")
-    g6 = oracle.crmsd_grad(e.coords, w.astype(np.float64), 1e-6)
-    a = e.extra["close_pairs"][0][0]
-    assert np.linalg.norm(g6[a] - gref[a]) > 1e-2 * np.linalg.norm(g6[a])  # the guard changes the answer
+
+
+def test_eps_guard_changes_a_close_pair():
+    """Three models, only the close pair (c ~ 3.5e-4 A) weighted: its term scales by c/eps."""
+    e, _ = E.config3()
+    a, b = e.extra["close_pairs"][0]
+    far = (b + 1) % e.N if (b + 1) % e.N != a else (b + 2) % e.N
+    X = np.ascontiguousarray(e.coords[[a, b, far]])
+    w = np.array([1.0, 0.0, 0.0], dtype=np.float32)  # pairs (0,1), (0,2), (1,2)
+    out = {}
+    for eps in (1e-6, 1e-3):
+        gref = oracle.crmsd_grad(X, w.astype(np.float64), eps)
+        g, _ = gpu_grad(X, w, eps)
+        compare(g, gref, f"close pair eps={eps}")
+        out[eps] = gref
+    c = oracle.crmsd_pair(X[0], X[1])[0]
+    assert c < 1e-3
+    ratio = np.linalg.norm(out[1e-3]) / np.linalg.norm(out[1e-6])
+    assert abs(ratio - c / 1e-3) < 1e-6
 
 
 def test_gradient_vs_central_differences(cfg3):
