@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-models", type=int, default=2400, help="models in the oracle's timed sample")
+    p.add_argument("--ref-models", type=int, default=800, help="models per step of the reference arm")
     return p.parse_args()
 
 
@@ -152,7 +153,7 @@ def run_reference(args):
     import oracle
     oracle.load()
     times = []
-    n = args.cpu_models
+    n = args.ref_models
     for it in range(args.warmup + args.steps):
         r = cpu_baseline(e, w, native, n)
         if it >= args.warmup:

@@ -289,7 +289,9 @@ __global__ void __launch_bounds__(256) bwd_neardup_kernel(const float *__restric
             for (int k = 0; k < 9; ++k) m[k] = H[k] * nrm;
             double I1, det, I2;
             invariants3(m, I1, det, I2);
-            const double s = quartic_newton(sigma_cubic(I1, det, I2), I1, det, I2, 3);
+            bool deg;
+            double s = quartic_newton(sigma_cubic_d(I1, det, I2), I1, det, I2, 3, &deg);
+            if (deg) s = sigma_cubic_d(I1, det, I2);
             horn_rotation(m, s, R);
         }
         // residuals r_i = a_i - R b_i; c from the residuals; coefficient with the guard

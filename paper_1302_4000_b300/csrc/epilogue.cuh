@@ -53,48 +53,93 @@ __device__ __forceinline__ void invariants3(const T m[9], T &I1, T &det, T &I2)
 // by Vieta's relations (l2 + l3 = (I2 - l2 l3)/l1, l2 l3 = det^2/l1, S |det| = det).
 // I2 is a sum of squared 2x2 minors, so a rank-deficient m (collinear or planar atoms)
 // keeps full relative accuracy, which sqrt() of the small cubic roots would lose.
-// Returns Sigma = sqrt(l1) + sqrt(l2) + S sqrt(l3).
-template <typename T>
-__device__ __forceinline__ T sigma_cubic(T I1, T det, T I2)
+// Returns Sigma = sqrt(l1) + sqrt(l2) + S sqrt(l3). FP64, IEEE operations.
+__device__ __forceinline__ double sigma_cubic_d(double I1, double det, double I2)
 {
-    const T mm = I1 / T(3);
-    const T p = I2 - T(3) * mm * mm;              // <= 0 for a real symmetric spectrum
-    const T q = (I2 - T(2) * mm * mm) * mm - det * det;
-    T l1;
-    if (!(p < T(0))) {
+    const double mm = I1 / 3.0;
+    const double p = I2 - 3.0 * mm * mm;  // <= 0 for a real symmetric spectrum
+    const double q = (I2 - 2.0 * mm * mm) * mm - det * det;
+    double l1;
+    if (!(p < 0.0)) {
         l1 = mm;
     } else {
-        const T r = sqrt(-p / T(3));
-        T arg = (T(3) * q / (T(2) * p)) * sqrt(T(-3) / p);
-        arg = fmin(fmax(arg, T(-1)), T(1));
-        l1 = mm + T(2) * r * cos(acos(arg) / T(3));
+        const double r = sqrt(-p / 3.0);
+        double arg = (3.0 * q / (2.0 * p)) * sqrt(-3.0 / p);
+        arg = fmin(fmax(arg, -1.0), 1.0);
+        l1 = mm + 2.0 * r * cos(acos(arg) / 3.0);
     }
-    if (!(l1 > T(0))) return T(0);
-    const T rl1 = sqrt(l1);
-    const T t = (I2 - det * det / l1) / l1 + T(2) * det / rl1;
-    return rl1 + sqrt(fmax(t, T(0)));
+    if (!(l1 > 0.0)) return 0.0;
+    const double rl1 = sqrt(l1);
+    const double t = (I2 - det * det / l1) / l1 + 2.0 * det / rl1;
+    return rl1 + sqrt(fmax(t, 0.0));
+}
+
+// The same in FP32 with hardware approximations (reciprocal, reciprocal square root,
+// cosine): a starting value for the FP32 Newton polish, accurate to about 1e-6.
+__device__ __forceinline__ float sigma_cubic_f(float I1, float det, float I2)
+{
+    const float mm = I1 * (1.f / 3.f);
+    const float p = I2 - 3.f * mm * mm;
+    const float q = (I2 - 2.f * mm * mm) * mm - det * det;
+    float l1 = mm;
+    if (p < 0.f) {
+        const float rp = rsqrtf(-p);             // 1/sqrt(-p)
+        const float r = -p * rp * 0.57735026919f;  // sqrt(-p/3)
+        float arg = 1.5f * q * __fdividef(1.f, p) * 1.73205080757f * rp;  // (3q/2p) sqrt(-3/p)
+        arg = fminf(fmaxf(arg, -1.f), 1.f);
+        l1 = fmaf(2.f * r, __cosf(acosf(arg) * (1.f / 3.f)), mm);
+    }
+    if (!(l1 > 0.f)) return 0.f;
+    const float rl1i = rsqrtf(l1);
+    const float il1 = rl1i * rl1i;
+    const float t = (I2 - det * det * il1) * il1 + 2.f * det * rl1i;
+    return l1 * rl1i + sqrtf(fmaxf(t, 0.f));
 }
 
 // Newton steps on the quartic whose largest root is s1 + s2 + S s3. At that root
 // P' = 8 (s2 + S s3)(s1 + S s3)(s1 + s2); where it vanishes against 8 Sigma^3 (rank <= 1
 // covariance, or S = -1 with s2 = s3) the root is double, P and P' are rounding noise and
-// a Newton step would be noise over noise, so the step is taken only while P' is a
-// clear fraction (1e-3) of its natural scale; the cubic route is accurate there.
+// a Newton step would be noise over noise, so no step is taken once P' falls below 1e-3
+// of its natural scale and *degenerate is set; the cubic route is the answer there.
 template <typename T>
-__device__ __forceinline__ T quartic_newton(T s, T I1, T det, T I2, int iters)
+__device__ __forceinline__ T quartic_newton(T s, T I1, T det, T I2, int iters, bool *degenerate)
 {
     const T c2 = T(-2) * I1;
     const T c1 = T(-8) * det;
     const T c0 = I1 * I1 - T(4) * I2;
+    bool deg = false;
     for (int it = 0; it < iters; ++it) {
         const T s2 = s * s;
         const T P = (s2 + c2) * s2 + c1 * s + c0;
         const T dP = (T(4) * s2 + T(2) * c2) * s + c1;
         if (dP > T(8e-3) * s2 * s) {
-            const T st = P / dP;
-            if (isfinite(st)) s -= st;
+            s -= P / dP;
+        } else {
+            deg = true;
         }
     }
+    *degenerate = deg;
+    return s;
+}
+
+__device__ __forceinline__ float quartic_newton_f(float s, float I1, float det, float I2, int iters, bool *degenerate)
+{
+    const float c2 = -2.f * I1;
+    const float c1 = -8.f * det;
+    const float c0 = I1 * I1 - 4.f * I2;
+    bool deg = false;
+#pragma unroll
+    for (int it = 0; it < iters; ++it) {
+        const float s2 = s * s;
+        const float P = fmaf(s2 + c2, s2, fmaf(c1, s, c0));
+        const float dP = fmaf(fmaf(4.f, s2, 2.f * c2), s, c1);
+        if (dP > 8e-3f * s2 * s) {
+            s -= __fdividef(P, dP);
+        } else {
+            deg = true;
+        }
+    }
+    *degenerate = deg;
     return s;
 }
 
@@ -110,13 +155,14 @@ __device__ __forceinline__ float crmsd_plain_fp64(const double H[9], double Ga, 
     for (int k = 0; k < 9; ++k) m[k] = H[k] * nrm;
     double I1, det, I2;
     invariants3(m, I1, det, I2);
-    const double s = sigma_cubic(I1, det, I2);
+    const double s = sigma_cubic_d(I1, det, I2);
     const double c2 = Gs * invL * (1.0 - s);
     return (float)sqrt(fmax(c2, 0.0));
 }
 
-// FP64 refinement: exact covariance in, cubic start (or a supplied start), Newton polish.
-// Returns cRMSD; the cancellation 1 - Sigma_hat is taken in FP64.
+// FP64 refinement: exact covariance in; start from s_start (an FP32 estimate) when given,
+// Newton polish; a degenerate (double) root falls back to the FP64 cubic route.
+// The cancellation 1 - Sigma_hat is taken in FP64. Returns cRMSD.
 __device__ __forceinline__ double crmsd_refined_fp64(const double H[9], double Ga, double Gb, double invL,
                                                      double s_start, bool have_start)
 {
@@ -128,20 +174,23 @@ __device__ __forceinline__ double crmsd_refined_fp64(const double H[9], double G
     for (int k = 0; k < 9; ++k) m[k] = H[k] * nrm;
     double I1, det, I2;
     invariants3(m, I1, det, I2);
-    double s = have_start ? s_start : sigma_cubic(I1, det, I2);
-    s = quartic_newton(s, I1, det, I2, 3);
+    double s = have_start ? s_start : sigma_cubic_d(I1, det, I2);
+    bool deg;
+    s = quartic_newton(s, I1, det, I2, 3, &deg);
+    if (deg) s = sigma_cubic_d(I1, det, I2);
     const double c2 = Gs * invL * (1.0 - s);
     return sqrt(fmax(c2, 0.0));
 }
 
-// FP32 fast path on a rounded covariance: cubic + two Newton steps, all FP32.
-// Returns cRMSD and, through err_c2, a bound on the absolute error of cRMSD^2
-// coming from FP32 rounding (KERR ulps of the normalised Sigma, times (G_A+G_B)/L).
+// FP32 fast path on a rounded covariance: cubic start + two Newton steps, all FP32.
+// Returns cRMSD and, through err_c2, a bound on the absolute error of cRMSD^2 coming from
+// FP32 rounding (KERR ulps of the normalised Sigma, times (G_A+G_B)/L); a degenerate root
+// returns err_c2 = +inf so that the caller refines the pair.
 #ifndef CLUSCO_KERR
 #define CLUSCO_KERR 16.0f
 #endif
-__device__ __forceinline__ float crmsd_fast_fp32(const float H[9], float Ga, float Gb, float invL,
-                                                 float *s_out, float *err_c2)
+__device__ __forceinline__ float crmsd_fast_fp32(const float H[9], float Ga, float Gb, float invL, float *s_out,
+                                                 float *err_c2)
 {
     const float Gs = Ga + Gb;
     if (!(Gs > 0.0f)) {
@@ -149,16 +198,16 @@ __device__ __forceinline__ float crmsd_fast_fp32(const float H[9], float Ga, flo
         *err_c2 = 0.0f;
         return 0.0f;
     }
-    const float nrm = 2.0f / Gs;
+    const float nrm = __fdividef(2.0f, Gs);
     float m[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) m[k] = H[k] * nrm;
     float I1, det, I2;
     invariants3(m, I1, det, I2);
-    float s = sigma_cubic(I1, det, I2);
-    s = quartic_newton(s, I1, det, I2, 2);
+    bool deg;
+    float s = quartic_newton_f(sigma_cubic_f(I1, det, I2), I1, det, I2, 2, &deg);
     *s_out = s;
     const float scale = Gs * invL;
-    *err_c2 = CLUSCO_KERR * 5.9604645e-8f * scale;
+    *err_c2 = deg ? __int_as_float(0x7f800000) : CLUSCO_KERR * 5.9604645e-8f * scale;
     return sqrtf(fmaxf(scale * (1.0f - s), 0.0f));
 }

@@ -294,6 +294,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         __syncwarp();
     };
 
+#pragma unroll
     for (int r = 0; r < 4; ++r) {
         // candidate rows of the three blocks of this round: block 3r + al' at columns 9r + 3al' + be
         float cand[3][3];
