@@ -101,6 +101,26 @@ int clusco_crmsd_allpairs_panel(const float *coords, int64_t N, int64_t L, int64
 int clusco_crmsd_vs_ref(const float *coords, int64_t N, int64_t L, const float *ref, float *out,
                         void *workspace, size_t workspace_bytes, void *stream);
 
+/* Largest reference (atoms) accepted by clusco_crmsd_vs_ref_noalloc. */
+#define CLUSCO_NOALLOC_MAX_L 16384
+
+/* One-versus-reference that allocates no device memory, for callers that cannot call
+ * cudaMalloc: code whose device memory belongs to another allocator or pool (a serving
+ * process or framework that reserved the GPU's memory up front), and latency-critical
+ * callers for whom cudaMalloc's possible device-wide synchronisation and variable latency
+ * are not acceptable. Same arguments, result and tolerance as clusco_crmsd_vs_ref, minus
+ * the workspace: the quantised reference lives in a fixed static device array of about
+ * 192 KB (references of up to CLUSCO_NOALLOC_MAX_L atoms) that every GPU loading the
+ * library keeps until the process exits. L above that maximum returns CLUSCO_EINVAL.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current, so make that first call before any stream capture.
+ * Every call shares the one array and overwrites all of it that it reads, so nothing
+ * needs clearing between calls, but two calls whose kernels can overlap on the GPU
+ * (unordered streams) race on it and may return wrong scores.
+ * The paper has no counterpart: this is a deployment variant of the call above. */
+int clusco_crmsd_vs_ref_noalloc(const float *coords, int64_t N, int64_t L, const float *ref, float *out,
+                                void *stream);
+
 /* Adjoint of the all-pairs matrix for a loss with dLoss/dcRMSD_ab = grad_out[idx(a,b)]:
  *   grad_coords[a][i] = sum_{b != a} grad_out_ab (a_i - R_ab b_i) / (L max(c_ab, eps))
  * with R_ab the optimal rotation of centred b onto centred a (recomputed, never

@@ -35,7 +35,9 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EOVE
           6: "ENONFINITE", 7: "EUNSUPPORTED"}
 
 EXPORTS = ("clusco_version", "clusco_workspace_bytes", "clusco_crmsd_allpairs", "clusco_crmsd_allpairs_panel",
-           "clusco_crmsd_vs_ref", "clusco_crmsd_allpairs_backward", "clusco_sync_status", "clusco_last_error")
+           "clusco_crmsd_vs_ref", "clusco_crmsd_vs_ref_noalloc", "clusco_crmsd_allpairs_backward",
+           "clusco_sync_status", "clusco_last_error")
+NOALLOC_MAX_L = 16384
 
 _lib = None
 _lock = threading.Lock()
@@ -63,10 +65,12 @@ def load(path: str = LIB_PATH):
             lib.clusco_crmsd_allpairs.argtypes = [vp, i64, i64, vp, ctypes.c_int, vp, sz, vp]
             lib.clusco_crmsd_allpairs_panel.argtypes = [vp, i64, i64, i64, i64, vp, ctypes.c_int, vp, sz, vp]
             lib.clusco_crmsd_vs_ref.argtypes = [vp, i64, i64, vp, vp, vp, sz, vp]
+            lib.clusco_crmsd_vs_ref_noalloc.argtypes = [vp, i64, i64, vp, vp, vp]
             lib.clusco_crmsd_allpairs_backward.argtypes = [vp, i64, i64, vp, vp, vp, ctypes.c_float, ctypes.c_int,
                                                            vp, sz, vp]
             lib.clusco_sync_status.argtypes = [vp]
             for f in ("clusco_crmsd_allpairs", "clusco_crmsd_allpairs_panel", "clusco_crmsd_vs_ref",
+                      "clusco_crmsd_vs_ref_noalloc",
                       "clusco_crmsd_allpairs_backward", "clusco_sync_status"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
@@ -153,6 +157,22 @@ def crmsd_vs_ref(coords: torch.Tensor, ref: torch.Tensor, out: torch.Tensor | No
     ws, nb = _ws(workspace, OP_VS_REF, N, L, 0, coords.device)
     _check(load().clusco_crmsd_vs_ref(coords.data_ptr(), N, L, ref.data_ptr(), out.data_ptr(), ws.data_ptr(), nb,
                                       _stream(stream)))
+    return out
+
+
+def crmsd_vs_ref_noalloc(coords: torch.Tensor, ref: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+    """One-versus-reference through the entry point that allocates no device memory.
+
+    For callers that cannot allocate (device memory owned by another pool, or no room for
+    cudaMalloc's synchronisation on a latency-critical path): the caller passes the output,
+    the library uses a fixed static device array (references up to NOALLOC_MAX_L atoms).
+    """
+    coords = _coords(coords)
+    N, L = coords.shape[0], coords.shape[1]
+    assert ref.is_cuda and ref.is_contiguous() and tuple(ref.shape) == (L, 3)
+    assert out.is_cuda and out.dtype == torch.float32 and out.numel() >= N
+    _check(load().clusco_crmsd_vs_ref_noalloc(coords.data_ptr(), N, L, ref.data_ptr(), out.data_ptr(),
+                                              _stream(stream)))
     return out
 
 

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <cstdarg>
+#include <mutex>
 #include <string>
 
 #include "common.cuh"
@@ -309,6 +310,68 @@ int clusco_crmsd_allpairs_backward(const float *coords, int64_t N, int64_t L, co
     std::string err;
     rc = backward_launch(coords, N, L, grad_out, crmsd, grad_coords, eps, form, s.ptr, st, err);
     if (rc) return fail(rc, "%s", err.c_str());
+    return CLUSCO_OK;
+}
+
+}  // extern "C"
+
+// ---- one-versus-reference without device allocation --------------------------
+// The scratch of clusco_crmsd_vs_ref_noalloc: the quantised reference (3 int32 per atom)
+// followed by its RefInfo. In host code g_vsref_scratch only names the symbol; its device
+// address is looked up per device with cudaGetSymbolAddress and passed to the kernels.
+namespace {
+constexpr size_t NOALLOC_REF_BYTES = ((size_t)CLUSCO_NOALLOC_MAX_L * 3 * sizeof(int) + 255) & ~(size_t)255;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_vsref_scratch[NOALLOC_REF_BYTES + 256];
+
+namespace {
+// Device address of g_vsref_scratch on the current device; looked up on the first call per device.
+int noalloc_scratch(void **out)
+{
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(CLUSCO_EUNSUPPORTED, "device %d beyond %d", dev, NOALLOC_MAX_DEVICES);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_vsref_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(CLUSCO_ECUDA, "cudaGetSymbolAddress(g_vsref_scratch): %s", cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return CLUSCO_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int clusco_crmsd_vs_ref_noalloc(const float *coords, int64_t N, int64_t L, const float *ref, float *out, void *stream)
+{
+    g_last_error.clear();
+    int rc;
+    if ((rc = check_sizes(N, L, 1))) return rc;
+    if ((rc = check_ptr(coords, "coords", 4))) return rc;
+    if ((rc = check_ptr(ref, "ref", 4))) return rc;
+    if ((rc = check_ptr(out, "out", 4))) return rc;
+    if (L > CLUSCO_NOALLOC_MAX_L)
+        return fail(CLUSCO_EINVAL, "L=%lld exceeds the %d-atom maximum of the no-allocation entry point",
+                    (long long)L, CLUSCO_NOALLOC_MAX_L);
+    void *scratch = nullptr;
+    if ((rc = noalloc_scratch(&scratch))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    int *nref = (int *)scratch;
+    RefInfo *info = (RefInfo *)((char *)scratch + NOALLOC_REF_BYTES);
+    ref_prepass_kernel<<<1, 1024, 0, st>>>(ref, (int)L, nref, info);
+    CUDA_TRY(cudaGetLastError());
+    const size_t smem = (size_t)L * 3 * sizeof(int);
+    if (smem > 48 * 1024) CUDA_TRY(cudaFuncSetAttribute(vsref_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    vsref_kernel<<<(unsigned)((N + 7) / 8), 256, smem, st>>>(coords, N, (int)L, nref, info, out);
+    CUDA_TRY(cudaGetLastError());
     return CLUSCO_OK;
 }
 
