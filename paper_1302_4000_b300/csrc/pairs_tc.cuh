@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         mma_commit(&done_bar);  // also on abort: fires once everything issued has finished
     }
     __syncwarp();
-    const bool ok = mbar_wait(&done_bar, 0);
+    const bool ok = mbar_wait_sleep(&done_bar, 0);
     tc_fence_after();
     __syncthreads();  // every TMA write and MMA has landed; the stage ring is free
     if (!ok || abort_flag) {
@@ -271,26 +271,27 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     const float invL = 1.f / (float)L;
     QEntry *queue = reinterpret_cast<QEntry *>(smem) + warp * QCAP;
 
-    auto refine_batch = [&](int n) {
-        // lane i < n refines queue entry i in FP64 from the exact digit classes
-        if (lane < n) {
-            const QEntry &q = queue[lane];
-            const int64_t aa = a_base + q.la, bb = b_base + q.lb;
-            double H[9];
+    // FP64 recomputation of one queued pair from its four exact digit classes.
+    auto refine_entry = [&](const QEntry &q) {
+        const int64_t aa = a_base + q.la, bb = b_base + q.lb;
+        double H[9];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const double sr = (double)scales[aa * 3 + (q.alpha + i) % 3];
+        for (int i = 0; i < 3; ++i) {
+            const double sr = (double)scales[aa * 3 + (q.alpha + i) % 3];
 #pragma unroll
-                for (int be = 0; be < 3; ++be) {
-                    const int k = 3 * i + be;
-                    const double v = 65536.0 * (double)q.v[k] + 256.0 * ((double)q.v[9 + k] + (double)q.v[18 + k]) +
-                                     (double)q.v[27 + k];
-                    H[k] = v * (sr * (double)scales[bb * 3 + be]);
-                }
+            for (int be = 0; be < 3; ++be) {
+                const int k = 3 * i + be;
+                const double v = 65536.0 * (double)q.v[k] + 256.0 * ((double)q.v[9 + k] + (double)q.v[18 + k]) +
+                                 (double)q.v[27 + k];
+                H[k] = v * (sr * (double)scales[bb * 3 + be]);
             }
-            const double c = crmsd_refined_fp64(H, G64[aa], G64[bb], 1.0 / (double)L, (double)q.s, true);
-            out[condensed_idx(aa, bb, N) - out_base] = (float)c;
         }
+        const double c = crmsd_refined_fp64(H, G64[aa], G64[bb], 1.0 / (double)L, (double)q.s, true);
+        out[condensed_idx(aa, bb, N) - out_base] = (float)c;
+    };
+    // a full batch: lane i refines entry i of this warp's queue
+    auto refine_batch = [&](int n) {
+        if (lane < n) refine_entry(queue[lane]);
         __syncwarp();
     };
 
@@ -391,9 +392,27 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         }
     }
     if (LAYOUT == TC_EXACT2) {
-        __syncwarp();
-        const int cnt = q_count[warp];
-        if (cnt > 0) refine_batch(cnt);
+        // The warps' leftovers (< 32 each) are refined together, 32 per warp, indexed through
+        // prefix offsets, so that the FP64 work runs in full warps instead of eight partial ones.
+        __shared__ int q_off[9];
+        __syncthreads();
+        if (tid == 0) {
+            int o = 0;
+            for (int w = 0; w < 8; ++w) {
+                q_off[w] = o;
+                o += q_count[w];
+            }
+            q_off[8] = o;
+        }
+        __syncthreads();
+        const int total = q_off[8];
+        const QEntry *qbase = reinterpret_cast<const QEntry *>(smem);
+        for (int gi = 32 * warp + lane; gi < total; gi += 256) {
+            int w = 0;
+#pragma unroll
+            for (int k = 1; k < 8; ++k) w += (gi >= q_off[k]) ? 1 : 0;
+            refine_entry(qbase[w * QCAP + (gi - q_off[w])]);
+        }
     }
 
     tc_fence_before();

@@ -63,6 +63,34 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
     }
 }
 
+// The same bounded wait, but each try sleeps up to hint_ns before giving the thread back:
+// for the long waits of warps that have nothing else to do (the epilogue warps during
+// the main loop), so that they do not take issue slots from the SM's other CTA.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t *bar, uint32_t parity)
+{
+    const uint64_t t0 = global_timer();
+    for (;;) {
+        if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+        if (global_timer() - t0 > CLUSCO_WAIT_NS) {
+            set_status(CLUSCO_ST_TIMEOUT);
+            return false;
+        }
+    }
+}
+
 __device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
 {
     asm volatile(
