@@ -66,11 +66,7 @@ inline BwWs carve_bw(void *base, int64_t N, int64_t L)
     return w;
 }
 
-inline size_t backward_ws_bytes(int64_t N, int64_t L, int form)
-{
-    (void)form;
-    return carve_bw(nullptr, N, L).bytes;
-}
+inline size_t backward_simt_ws_bytes(int64_t N, int64_t L) { return carve_bw(nullptr, N, L).bytes; }
 
 // grid: Npad/32 CTAs of 256 threads.
 __global__ void __launch_bounds__(256, 1)
@@ -328,7 +324,7 @@ __global__ void __launch_bounds__(256) bwd_neardup_kernel(const float *__restric
     }
 }
 
-inline int backward_launch(const float *coords, int64_t N, int64_t L, const float *grad_out, const float *crmsd,
+inline int backward_simt_launch(const float *coords, int64_t N, int64_t L, const float *grad_out, const float *crmsd,
                            float *grad, float eps, int form, void *ws, cudaStream_t st, std::string &err)
 {
     (void)form;

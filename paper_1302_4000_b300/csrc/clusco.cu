@@ -17,6 +17,7 @@
 #include "prepass.cuh"
 #include "vsref.cuh"
 #include "backward.cuh"
+#include "bwd_tc.cuh"
 
 using namespace clusco;
 
@@ -159,13 +160,13 @@ int run_prepass(const float *coords, int64_t N, int64_t L, int form, const Pairs
         prepass_simt_kernel<<<blocks, 256, 0, st>>>(coords, N, (int)L, (int)w.Lp, w.Npad, w.Xk, w.G64);
     } else if (form == CLUSCO_FORM_BF16_EXACT2) {
         prepass_tc_kernel<TC_EXACT2><<<blocks, 256, 0, st>>>(coords, N, (int)L, (int)w.Lp, w.Npad, w.Rpad,
-                                                                w.planes, w.scales, w.G64, w.G32);
+                                                                w.planes, w.scales, w.G64, w.G32, nullptr);
     } else if (form == CLUSCO_FORM_BF16X3) {
         prepass_tc_kernel<TC_BF16X3><<<blocks, 256, 0, st>>>(coords, N, (int)L, (int)w.Lp, w.Npad, w.Rpad,
-                                                                w.planes, w.scales, w.G64, w.G32);
+                                                                w.planes, w.scales, w.G64, w.G32, nullptr);
     } else {
         prepass_tc_kernel<TC_TF32><<<blocks, 256, 0, st>>>(coords, N, (int)L, (int)w.Lp, w.Npad, w.Rpad,
-                                                              w.planes, w.scales, w.G64, w.G32);
+                                                              w.planes, w.scales, w.G64, w.G32, nullptr);
     }
     CUDA_TRY(cudaGetLastError());
     return CLUSCO_OK;

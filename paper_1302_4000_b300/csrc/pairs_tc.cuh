@@ -207,10 +207,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         mma_commit(&done_bar);  // also on abort: fires once everything issued has finished
     }
     __syncwarp();
-    const bool ok = mbar_wait_sleep(&done_bar, 0);
+    if (!mbar_wait_sleep(&done_bar, 0)) atomicExch(&abort_flag, 1);
     tc_fence_after();
     __syncthreads();  // every TMA write and MMA has landed; the stage ring is free
-    if (!ok || abort_flag) {
+    if (*(volatile int *)&abort_flag) {  // read after the barrier: the same decision in every thread
         // drain: on an abort the producer may have loads in flight; wait for them (bounded)
         if (warp == 0 && lane == 0) {
             for (int s = 0; s < TC_STAGES; ++s) mbar_wait(&full_bar[s], 0);

@@ -16,6 +16,7 @@
 //      (exact in int64), so G and the covariance describe the same points.
 //    BF16X3: plane 0 = bf16(x), plane 1 = bf16(x - bf16(x)); G from hi + lo.
 //    TF32: one FP32 plane holding tf32-rounded x; G from those values.
+//    Optionally (xf != nullptr) the centred FP32 coordinates in the same row layout.
 //  The centroid is summed in FP32 per lane and combined in FP64 across lanes;
 //  its own rounding error only shifts the model by ~1e-6 A, which changes
 //  cRMSD at second order.
@@ -98,7 +99,7 @@ template <int LAYOUT>
 __global__ void __launch_bounds__(256) prepass_tc_kernel(const float *__restrict__ coords, int64_t N, int L, int Lp,
                                                          int64_t Npad, int64_t Rpad, void *__restrict__ planes,
                                                          float *__restrict__ scales, double *__restrict__ G64,
-                                                         float *__restrict__ G32)
+                                                         float *__restrict__ G32, float *__restrict__ xf)
 {
     const int lane = threadIdx.x & 31;
     const int64_t a = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -116,6 +117,7 @@ __global__ void __launch_bounds__(256) prepass_tc_kernel(const float *__restrict
                 p0[r * Lp + i] = __float2bfloat16_rn(0.f);
                 p1[r * Lp + i] = __float2bfloat16_rn(0.f);
             }
+            if (xf) xf[r * Lp + i] = 0.f;
         }
     };
     if (a % 10 == 9) {  // the two padding rows that close this model's 32-row group
@@ -158,6 +160,7 @@ __global__ void __launch_bounds__(256) prepass_tc_kernel(const float *__restrict
         for (int ax = 0; ax < 3; ++ax) {
             const int64_t off = (r0 + ax) * Lp + i;
             const float v = (i < L) ? (x[3 * i + ax] - mu[ax]) : 0.f;
+            if (xf) xf[off] = v;
             if (LAYOUT == TC_EXACT2) {
                 float n = rintf(v * inv[ax]);
                 n = fminf(fmaxf(n, -32767.f), 32767.f);

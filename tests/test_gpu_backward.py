@@ -2,7 +2,8 @@
 
 Tolerance (the stated ``<= 1e-3 relative`` for gradients, read per model):
     ||g_a - g_a^oracle||_2 <= 1e-3 ||g_a^oracle||_2 for every model a,
-and per coordinate |dg| <= 1e-3 |g^oracle| + 1e-5 max|g^oracle|.
+and per coordinate |dg_ai| <= 1e-3 (|g_ai^oracle| + rms(g_a^oracle)), so that a component
+near zero is held to the model's own gradient scale.
 """
 import numpy as np
 import pytest
@@ -38,7 +39,8 @@ def compare(g, gref, what):
     na = np.linalg.norm((g - gref).reshape(g.shape[0], -1), axis=1)
     nr = np.linalg.norm(gref.reshape(g.shape[0], -1), axis=1)
     rel = na / np.maximum(nr, 1e-300)
-    coord = np.abs(g - gref) <= 1e-3 * np.abs(gref) + 1e-5 * np.abs(gref).max()
+    rms = np.sqrt((gref.reshape(g.shape[0], -1) ** 2).mean(axis=1))[:, None, None]
+    coord = np.abs(g - gref) <= 1e-3 * (np.abs(gref) + rms)
     print(f"{what}: max per-model rel err {rel.max():.3e} (model {np.argmax(rel)}), coords ok {coord.mean():.6f}")
     assert rel.max() <= 1e-3, what
     assert coord.all(), what
@@ -134,6 +136,7 @@ def test_identical_copy_is_finite():
 
 
 def test_autograd_function_matches_direct_call(cfg3):
+    """The autograd Function routes to the same adjoint (up to the order of float atomics)."""
     e, w = cfg3
     X = torch.from_numpy(e.coords[:200]).cuda().requires_grad_(True)
     N = 200
@@ -143,4 +146,5 @@ def test_autograd_function_matches_direct_call(cfg3):
     c = clusco.crmsd_allpairs(X.detach(), clusco.FORM_FP32_SIMT)
     g = clusco.crmsd_allpairs_backward(X.detach(), wt, c, 1e-6, clusco.FORM_FP32_SIMT)
     torch.cuda.synchronize()
-    assert torch.allclose(X.grad, g, rtol=1e-5, atol=1e-6 * float(g.abs().max()))
+    d = (X.grad - g).reshape(N, -1).norm(dim=1) / g.reshape(N, -1).norm(dim=1)
+    assert float(d.max()) <= 1e-5
