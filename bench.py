@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--L", type=int, default=300)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--cpu-models", type=int, default=2400, help="models in the oracle's timed sample")
+    p.add_argument("--cpu-models", type=int, default=5000, help="models in the oracle's timed sample")
     p.add_argument("--ref-models", type=int, default=800, help="models per step of the reference arm")
     return p.parse_args()
 
