@@ -2,27 +2,29 @@
 //
 // g_a = (sum_b w~_ab) a - sum_b (w~_ab R_ab) b,  w~ = w / (L max(c, eps))   (see backward.cuh)
 //
-// One CTA (8 warps) owns one A tile I (40 models = 128 rows of the operand planes) and a
-// contiguous range of B tiles J over the full square (every b != a in both orders, so the
-// CTA owns its rows and needs no atomics). Tensor memory (512 columns) holds
+// One CTA owns one A tile I (40 models = 128 rows of the operand planes) and a contiguous
+// range of B tiles J over the full square (every b != a in both orders, so the CTA owns its
+// rows and needs no atomics). Tensor memory (512 columns) holds
 //   cols [0, 192)        the tile covariance in three exact digit classes (hh, hl + lh, ll);
 //   cols [192, 192 + Lp) the CTA's sum P.X over its column range (128 rows x Lp atoms,
 //                        FP32), accumulated over the whole sweep.
-// For every J:
-//   1. GEMM1: the exact-digit covariance of the 40 x 20 tile (TMA -> 2-stage ring ->
-//      tcgen05.mma kind::f16, as in the forward kernel, with hl and lh summed in one class:
-//      |hl + lh| <= 2^15 per atom keeps the sum exact for L <= 512);
-//   2. the warps read TMEM, assemble each 3x3 block (rows cyclic, as in the forward), take
-//      Sigma from the FP32 fast path and the rotation from Horn's quaternion form, undo the
-//      cyclic row order, and write w~ R as two TF32 parts (hi = rna(P), lo = rna(P - hi))
-//      into a shared 128 x 64 operand in the 128-byte-swizzled K-major layout; pairs below
-//      the near-duplicate threshold are queued for the FP64 direct kernel instead;
-//   3. GEMM2: sum += P . X_J on tcgen05 kind::tf32 in three passes (hi.hi + hi.lo + lo.hi,
-//      about 2^-21 relative per product), with X_J^T (atoms x 64) streamed by TMA from the
-//      transposed hi / lo FP32 planes into the freed ring, in two atom chunks when Lp > 160.
-// Rotations live only in shared memory. At the end the CTA reads the sum out of TMEM into
-// its partial-gradient slice (negated); bwd_reduce_kernel adds the partials of the S column
-// ranges, the diagonal term and the centring projection. Requires Lp = ceil(L/64)*64 <= 320.
+// Three roles run as a pipeline over the tiles J, synchronised by mbarriers:
+//   warp 0 (TMA): streams the covariance operands (2-stage ring, 128-byte swizzle) and, one
+//     tile behind, the transposed TF32 hi / lo coordinates X_J^T in 64-atom chunks (double
+//     buffer);
+//   warp 1 (MMA): GEMM1 = exact-digit covariance of tile J (tcgen05 kind::f16, hl and lh summed
+//     in one class: |hl + lh| <= 2^15 per atom keeps the sum exact for L <= 512), then
+//     GEMM2 of tile J-1 = sum += P . X (tcgen05 kind::tf32, three passes hi.hi + hi.lo + lo.hi,
+//     about 2^-21 relative per product);
+//   warps 2-9 (epilogue): read tile J's covariance from TMEM (then release it to GEMM1 of
+//     J+1), assemble each 3x3 block (rows cyclic, as in the forward), take Sigma from the
+//     FP32 fast path and the rotation from Horn's quaternion form, undo the cyclic order and
+//     write w~ R as two TF32 parts into a shared 128 x 64 operand in the 128-byte-swizzled
+//     K-major layout; pairs below the near-duplicate threshold go to the FP64 direct kernel.
+// So tile J's rotations overlap GEMM1 of J+1 and GEMM2 of J-1. Rotations live only in shared
+// memory. At the end the epilogue reads the sum out of TMEM into the CTA's partial-gradient
+// slice (negated); bwd_reduce_kernel adds the partials of the S column ranges, the diagonal
+// term and the centring projection. Requires Lp = ceil(L/64)*64 <= 320.
 #pragma once
 #include "backward.cuh"
 #include "pairs_tc.cuh"
@@ -30,17 +32,16 @@
 
 namespace clusco {
 
-constexpr int BT_THREADS = 256;
+constexpr int BT_THREADS = 320;                           // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int BT_MAXLP = 320;
 constexpr uint32_t BT_TMEM_COLS = 512;
 constexpr uint32_t BT_D2 = 192;                            // first TMEM column of the P.X sum
 constexpr size_t BT_RING = TC_STAGES * STAGE_BYTES_BF16;   // 96 KB; reused for X_J^T chunks
 constexpr size_t BT_A2 = 2 * 128 * 64 * 4;                 // hi, lo: 64 KB
-constexpr size_t BT_SMEM = 1024 + BT_RING + BT_A2;
-static_assert(4 * 160 * 128 <= BT_RING, "an X^T chunk of 160 atoms fits the ring");
-
-// Atoms per GEMM2 chunk: Lp itself up to 160, else Lp/2 (96, 128 or 160).
-__host__ __device__ __forceinline__ int bt_chunk(int Lp) { return Lp <= 160 ? Lp : Lp / 2; }
+constexpr int BT_XCH = 64;                                 // atoms per X^T chunk (GEMM2 N)
+constexpr size_t BT_XBUF = 4 * BT_XCH * 128;               // hi/lo x two 32-column blocks: 32 KB
+constexpr size_t BT_XT = 2 * BT_XBUF;                      // double buffer
+constexpr size_t BT_SMEM = 1024 + BT_RING + BT_XT + BT_A2;
 
 struct BtWs {
     void *planes = nullptr;  // EXACT2 digit planes [2][Rpad][Lp] bf16
@@ -138,11 +139,15 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
                   unsigned long long *__restrict__ nd_count, int64_t nd_cap)
 {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[TC_STAGES];
-    __shared__ __align__(8) uint64_t empty_bar[TC_STAGES];
-    __shared__ __align__(8) uint64_t done_bar;  // GEMM1 of the current J has landed in TMEM
-    __shared__ __align__(8) uint64_t xt_bar;    // an X^T chunk has landed in the ring
-    __shared__ __align__(8) uint64_t g2_bar;    // the GEMM2 MMAs of a chunk have finished
+    __shared__ __align__(8) uint64_t full_bar[TC_STAGES];   // GEMM1 ring: K block landed
+    __shared__ __align__(8) uint64_t empty_bar[TC_STAGES];  // GEMM1 ring: K block consumed
+    __shared__ __align__(8) uint64_t done1_bar;             // GEMM1 of a tile is in TMEM
+    __shared__ __align__(8) uint64_t tfree_bar;             // the epilogue has read that tile (8 arrivals)
+    __shared__ __align__(8) uint64_t a2full_bar;            // the rotation operand is written (8 arrivals)
+    __shared__ __align__(8) uint64_t a2empty_bar;           // GEMM2 has finished reading it
+    __shared__ __align__(8) uint64_t xfull_bar[2];          // an X^T chunk landed in buffer 0 / 1
+    __shared__ __align__(8) uint64_t xempty_bar[2];         // GEMM2 has finished reading buffer 0 / 1
+    __shared__ __align__(8) uint64_t d2_bar;                // the last GEMM2 has finished
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     __shared__ float sB_scale[TC_MB * 3];
@@ -151,8 +156,9 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
 
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase0 = smem_u32(smem);
-    uint8_t *A2 = smem + BT_RING;  // [hi 32 KB][lo 32 KB]
-    const uint32_t a2base = smem_u32(A2);
+    uint8_t *XT = smem + BT_RING;            // two X^T chunk buffers of BT_XBUF bytes
+    uint8_t *A2 = smem + BT_RING + BT_XT;    // [hi 32 KB][lo 32 KB]
+    const uint32_t xtbase = smem_u32(XT), a2base = smem_u32(A2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t I = blockIdx.x / S, sidx = blockIdx.x % S;
     const int64_t J0 = sidx * JC, J1 = (J0 + JC < TB) ? J0 + JC : TB;
@@ -174,9 +180,15 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
-        mbar_init(&done_bar, 1);
-        mbar_init(&xt_bar, 1);
-        mbar_init(&g2_bar, 1);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&xfull_bar[s], 1);
+            mbar_init(&xempty_bar[s], 1);
+        }
+        mbar_init(&done1_bar, 1);
+        mbar_init(&tfree_bar, 8);
+        mbar_init(&a2full_bar, 8);
+        mbar_init(&a2empty_bar, 1);
+        mbar_init(&d2_bar, 1);
         abort_flag = 0;
         fence_barrier_init();
         fence_proxy_async();
@@ -189,113 +201,194 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
+    const int64_t nJ = J1 - J0;
+    const int nch = Lp / BT_XCH;
+    volatile int *abort_v = &abort_flag;
 
-    const int sp = warp & 3, g = warp >> 2;
-    const int mloc = lane / 3, alpha = lane - 3 * (lane / 3);
-    const int la = 10 * sp + mloc;
-    const int64_t a = a_base + la;
-    const bool lane_ok = lane < 30 && a < N;
-    float srow0 = 1.f, Ga = 0.f;
-    if (lane_ok) {
-        srow0 = scales[a * 3 + alpha];
-        Ga = G32[a];
-    }
-    const uint32_t trow = tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)(32 * g);
-    const float invL = 1.f / (float)L;
-    const int chunk = bt_chunk(Lp);
-    const int nchunk = Lp / chunk;
-
-    int64_t kbt = 0;        // GEMM1 K blocks issued so far (ring phase)
-    uint32_t xt_count = 0;  // X^T chunks loaded so far (xt_bar and g2_bar phase)
-    bool alive = true;
-    for (int64_t J = J0; J < J1; ++J) {
-        const int64_t jt = J - J0;
-        const int64_t b_base = J * TC_MB;
-        if (tid < TC_MB * 3) sB_scale[tid] = scales[(b_base + tid / 3) * 3 + tid % 3];
-        if (tid < TC_MB) sB_G32[tid] = G32[b_base + tid];
-        // ---- 1. GEMM1: tile covariance in three exact classes ----
-        if (warp == 0 && lane == 0) {
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int64_t q = kbt + kb;
-                const int s = (int)(q % TC_STAGES);
-                const int64_t use = q / TC_STAGES;
-                if (q >= TC_STAGES && !mbar_wait(&empty_bar[s], (uint32_t)((use - 1) & 1))) {
-                    atomicExch(&abort_flag, 1);
-                    break;
+    if (warp == 0) {
+        // ================= TMA producer =================
+        if (lane == 0) {
+            int64_t q = 0, c = 0;
+            bool ok = true;
+            auto g1_loads = [&](int64_t J) {
+                for (int kb = 0; kb < nkb && ok; ++kb, ++q) {
+                    const int s = (int)(q % TC_STAGES);
+                    const int64_t use = q / TC_STAGES;
+                    if (q >= TC_STAGES && !mbar_wait(&empty_bar[s], (uint32_t)((use - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *st = smem + s * STAGE_BYTES_BF16;
+                    mbar_arrive_expect_tx(&full_bar[s], STAGE_BYTES_BF16);
+                    const int x = kb * 64;
+                    tma_load_2d(st, &mapA, &full_bar[s], x, (int)(128 * I));
+                    tma_load_2d(st + 16384, &mapA, &full_bar[s], x, (int)(Rpad + 128 * I));
+                    tma_load_2d(st + 32768, &mapB, &full_bar[s], x, (int)(64 * J));
+                    tma_load_2d(st + 40960, &mapB, &full_bar[s], x, (int)(Rpad + 64 * J));
                 }
-                uint8_t *st = smem + s * STAGE_BYTES_BF16;
-                mbar_arrive_expect_tx(&full_bar[s], STAGE_BYTES_BF16);
-                const int x = kb * 64;
-                tma_load_2d(st, &mapA, &full_bar[s], x, (int)(128 * I));
-                tma_load_2d(st + 16384, &mapA, &full_bar[s], x, (int)(Rpad + 128 * I));
-                tma_load_2d(st + 32768, &mapB, &full_bar[s], x, (int)(64 * J));
-                tma_load_2d(st + 40960, &mapB, &full_bar[s], x, (int)(Rpad + 64 * J));
+            };
+            auto xt_loads = [&](int64_t J) {
+                for (int ch = 0; ch < nch && ok; ++ch, ++c) {
+                    const int buf = (int)(c & 1);
+                    const int64_t use = c >> 1;
+                    if (c >= 2 && !mbar_wait(&xempty_bar[buf], (uint32_t)((use - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&xfull_bar[buf], (uint32_t)BT_XBUF);
+#pragma unroll
+                    for (int sp2 = 0; sp2 < 2; ++sp2)
+#pragma unroll
+                        for (int kb2 = 0; kb2 < 2; ++kb2)
+                            tma_load_2d(XT + buf * BT_XBUF + (2 * sp2 + kb2) * (BT_XCH * 128), &mapX,
+                                        &xfull_bar[buf], (int)(64 * J + 32 * kb2), (int)(sp2 * Lp + ch * BT_XCH));
+                }
+            };
+            for (int64_t j = 0; j < nJ && ok && !*abort_v; ++j) {
+                g1_loads(J0 + j);
+                if (j >= 1) xt_loads(J0 + j - 1);
             }
-        } else if (warp == 1 && lane == 0) {
+            if (ok && !*abort_v) xt_loads(J1 - 1);
+            if (!ok) atomicExch(&abort_flag, 1);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ================= MMA issuer =================
+        if (lane == 0) {
+            int64_t q = 0, c = 0;
+            bool ok = true;
             constexpr uint32_t id64 = make_idesc(128, 64, 1);
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int64_t q = kbt + kb;
-                const int s = (int)(q % TC_STAGES);
-                const int64_t use = q / TC_STAGES;
-                if (!mbar_wait(&full_bar[s], (uint32_t)(use & 1)) || *(volatile int *)&abort_flag) {
-                    atomicExch(&abort_flag, 1);
-                    break;
+            constexpr uint32_t idx = make_idesc(128, BT_XCH, 2);
+            auto g1 = [&]() {
+                for (int kb = 0; kb < nkb && ok; ++kb, ++q) {
+                    const int s = (int)(q % TC_STAGES);
+                    const int64_t use = q / TC_STAGES;
+                    if (!mbar_wait(&full_bar[s], (uint32_t)(use & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sb = sbase0 + s * STAGE_BYTES_BF16;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+                        const uint64_t ah = desc_sw128(sb + 32 * k), al = desc_sw128(sb + 16384 + 32 * k);
+                        const uint64_t bh = desc_sw128(sb + 32768 + 32 * k), bl = desc_sw128(sb + 40960 + 32 * k);
+                        mma_bf16(tmem + 0, ah, bh, id64, acc);
+                        mma_bf16(tmem + 64, ah, bl, id64, acc);
+                        mma_bf16(tmem + 64, al, bh, id64, 1u);
+                        mma_bf16(tmem + 128, al, bl, id64, acc);
+                    }
+                    mma_commit(&empty_bar[s]);
+                }
+                mma_commit(&done1_bar);
+            };
+            auto g2 = [&](int64_t jj) {
+                if (!mbar_wait(&a2full_bar, (uint32_t)(jj & 1))) {
+                    ok = false;
+                    return;
                 }
                 tc_fence_after();
-                const uint32_t sb = sbase0 + s * STAGE_BYTES_BF16;
+                for (int ch = 0; ch < nch && ok; ++ch, ++c) {
+                    const int buf = (int)(c & 1);
+                    if (!mbar_wait(&xfull_bar[buf], (uint32_t)((c >> 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t xb = xtbase + buf * BT_XBUF;
+                    const uint32_t d = tmem + BT_D2 + (uint32_t)(ch * BT_XCH);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
-                    const uint64_t ah = desc_sw128(sb + 32 * k), al = desc_sw128(sb + 16384 + 32 * k);
-                    const uint64_t bh = desc_sw128(sb + 32768 + 32 * k), bl = desc_sw128(sb + 40960 + 32 * k);
-                    mma_bf16(tmem + 0, ah, bh, id64, acc);
-                    mma_bf16(tmem + 64, ah, bl, id64, acc);
-                    mma_bf16(tmem + 64, al, bh, id64, 1u);
-                    mma_bf16(tmem + 128, al, bl, id64, acc);
+                    for (int kb2 = 0; kb2 < 2; ++kb2)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const uint64_t ahi = desc_sw128(a2base + kb2 * 16384 + 32 * k);
+                            const uint64_t alo = desc_sw128(a2base + 32768 + kb2 * 16384 + 32 * k);
+                            const uint64_t bhi = desc_sw128(xb + kb2 * (BT_XCH * 128) + 32 * k);
+                            const uint64_t blo = desc_sw128(xb + (2 + kb2) * (BT_XCH * 128) + 32 * k);
+                            // each chunk's first MMA of the sweep starts its columns from zero
+                            mma_tf32(d, ahi, bhi, idx, (jj == 0 && kb2 == 0 && k == 0) ? 0u : 1u);
+                            mma_tf32(d, ahi, blo, idx, 1u);
+                            mma_tf32(d, alo, bhi, idx, 1u);
+                        }
+                    mma_commit(&xempty_bar[buf]);
                 }
-                mma_commit(&empty_bar[s]);
+                mma_commit(&a2empty_bar);
+            };
+            for (int64_t j = 0; j < nJ && ok && !*abort_v; ++j) {
+                if (j >= 1 && !mbar_wait_sleep(&tfree_bar, (uint32_t)((j - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                g1();
+                if (j >= 1 && ok) g2(j - 1);
             }
-            mma_commit(&done_bar);
+            if (ok && !*abort_v) g2(nJ - 1);
+            mma_commit(&d2_bar);
+            if (!ok) atomicExch(&abort_flag, 1);
         }
-        kbt += nkb;
         __syncwarp();
-        if (!mbar_wait_sleep(&done_bar, (uint32_t)(jt & 1))) atomicExch(&abort_flag, 1);
-        tc_fence_after();
-        __syncthreads();
-        if (*(volatile int *)&abort_flag) {  // read after the barrier: a uniform decision
-            alive = false;
-            break;
+    } else {
+        // ================= epilogue warps 2..9 =================
+        const int etid = tid - 64;
+        const int sp = warp & 3, g = (warp - 2) >> 2;
+        const int mloc = lane / 3, alpha = lane - 3 * (lane / 3);
+        const int la = 10 * sp + mloc;
+        const int64_t a = a_base + la;
+        const bool lane_ok = lane < 30 && a < N;
+        float srow0 = 1.f, Ga = 0.f;
+        if (lane_ok) {
+            srow0 = scales[a * 3 + alpha];
+            Ga = G32[a];
         }
-        // The ring is free (GEMM1 has consumed it): start the first X^T chunk now, so that it
-        // lands while the rotations are computed.
-        auto load_chunk = [&](int ch) {
-            const uint32_t blk = (uint32_t)chunk * 128u;
-            mbar_arrive_expect_tx(&xt_bar, 4u * blk);
+        const uint32_t trow = tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)(32 * g);
+        const float invL = 1.f / (float)L;
+        bool alive = true;
+        for (int64_t j = 0; j < nJ; ++j) {
+            const int64_t J = J0 + j;
+            const int64_t b_base = J * TC_MB;
+            if (etid < TC_MB * 3) sB_scale[etid] = scales[(b_base + etid / 3) * 3 + etid % 3];
+            if (etid < TC_MB) sB_G32[etid] = G32[b_base + etid];
+            // forward outputs and weights of this lane's four pairs (issued early)
+            float cpre[4], wpre[4];
 #pragma unroll
-            for (int sp2 = 0; sp2 < 2; ++sp2)
-#pragma unroll
-                for (int kb2 = 0; kb2 < 2; ++kb2)
-                    tma_load_2d(smem + (2 * sp2 + kb2) * blk, &mapX, &xt_bar, (int)(64 * J + 32 * kb2),
-                                (int)(sp2 * Lp + ch * chunk));
-        };
-        if (warp == 0 && lane == 0) load_chunk(0);
-        // ---- 2. rotations: w~ R of every pair into the TF32 hi / lo operand ----
-        {
+            for (int r = 0; r < 4; ++r) {
+                cpre[r] = 0.f;
+                wpre[r] = 0.f;
+                const int bq = 3 * r + alpha;
+                const int64_t b = b_base + 10 * g + bq;
+                if (lane_ok && bq < 10 && b < N && b != a) {
+                    const int64_t lo = a < b ? a : b, hi = a < b ? b : a;
+                    const int64_t idx = condensed_idx(lo, hi, N);
+                    cpre[r] = crmsd[idx];
+                    wpre[r] = wvec[idx];
+                }
+            }
+            const bool ok1 = mbar_wait_sleep(&done1_bar, (uint32_t)(j & 1));
+            if (named_bar_or(1, 256, !ok1 || *abort_v)) {  // uniform across the epilogue warps
+                alive = false;
+                break;
+            }
+            tc_fence_after();
             float V[32];
             {
                 float t[32];
                 tmem_ld32(trow + 0, V);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) V[j] *= 65536.f;
+                for (int jj = 0; jj < 32; ++jj) V[jj] *= 65536.f;
                 tmem_ld32(trow + 64, t);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) V[j] = fmaf(256.f, t[j], V[j]);
+                for (int jj = 0; jj < 32; ++jj) V[jj] = fmaf(256.f, t[jj], V[jj]);
                 tmem_ld32(trow + 128, t);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) V[j] += t[j];
-#pragma unroll
-                for (int j = 0; j < 30; ++j) V[j] *= srow0 * sB_scale[30 * g + j];
+                for (int jj = 0; jj < 32; ++jj) V[jj] += t[jj];
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tfree_bar);  // TMEM cols 0..191 may be overwritten now
+#pragma unroll
+            for (int jj = 0; jj < 30; ++jj) V[jj] *= srow0 * sB_scale[30 * g + jj];
+            float Pall[4][9];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 float cand[3][3];
@@ -303,8 +396,8 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
                 for (int al = 0; al < 3; ++al)
 #pragma unroll
                     for (int be = 0; be < 3; ++be) {
-                        const int j = 9 * r + 3 * al + be;
-                        cand[al][be] = (j < 32) ? V[j] : 0.f;
+                        const int jj = 9 * r + 3 * al + be;
+                        cand[al][be] = (jj < 32) ? V[jj] : 0.f;
                     }
                 float blk[9];
 #pragma unroll
@@ -318,125 +411,96 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
                         blk[3 * k + be] = __shfl_sync(0xffffffffu, sel3(sendsel, cand[0][be], cand[1][be], cand[2][be]),
                                                       src & 31);
                 }
+#pragma unroll
+                for (int e = 0; e < 9; ++e) Pall[r][e] = 0.f;
+                const int bq = 3 * r + alpha;
+                const int lb = 10 * g + bq;
+                const int64_t b = b_base + lb;
+                if (lane_ok && bq < 10 && b < N && b != a) {
+                    const float c = cpre[r], w = wpre[r];
+                    if (!(c >= CLUSCO_NEARDUP)) {
+                        if (a < b && w != 0.f) {
+                            const unsigned long long slot = atomicAdd(nd_count, 1ull);
+                            if ((int64_t)slot < nd_cap) {
+                                nd_list[2 * slot] = a;
+                                nd_list[2 * slot + 1] = b;
+                            }
+                        }
+                    } else if (w != 0.f) {
+                        float sfast, errc2;
+                        const float Gb = sB_G32[lb];
+                        crmsd_fast_fp32(blk, Ga, Gb, invL, &sfast, &errc2);
+                        const float nrm = __fdividef(2.f, Ga + Gb);
+                        float Hn[9], Rp[9];
+#pragma unroll
+                        for (int e = 0; e < 9; ++e) Hn[e] = blk[e] * nrm;
+                        horn_rotation(Hn, sfast, Rp);
+                        const float coef = w / ((float)L * fmaxf(c, eps));
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            const int src_row = (i + 3 - alpha) % 3;
+#pragma unroll
+                            for (int be = 0; be < 3; ++be)
+                                Pall[r][3 * i + be] = coef * sel3(src_row, Rp[be], Rp[3 + be], Rp[6 + be]);
+                        }
+                        atomicAdd(&dsum[la], coef);
+                    }
+                }
+            }
+            // the operand is single-buffered: wait until GEMM2 of the previous tile has read it
+            bool ok2 = true;
+            if (j >= 1) ok2 = mbar_wait_sleep(&a2empty_bar, (uint32_t)((j - 1) & 1));
+            if (named_bar_or(1, 256, !ok2 || *abort_v)) {
+                alive = false;
+                break;
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
                 const int bq = 3 * r + alpha;
                 if (lane < 30 && bq < 10) {
-                    const int lb = 10 * g + bq;
-                    const int64_t b = b_base + lb;
-                    float P[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-                    if (lane_ok && b < N && b != a) {
-                        const int64_t lo = a < b ? a : b, hi = a < b ? b : a;
-                        const int64_t idx = condensed_idx(lo, hi, N);
-                        const float c = crmsd[idx];
-                        const float w = wvec[idx];
-                        if (!(c >= CLUSCO_NEARDUP)) {
-                            if (a < b && w != 0.f) {
-                                const unsigned long long slot = atomicAdd(nd_count, 1ull);
-                                if ((int64_t)slot < nd_cap) {
-                                    nd_list[2 * slot] = a;
-                                    nd_list[2 * slot + 1] = b;
-                                }
-                            }
-                        } else if (w != 0.f) {
-                            float sfast, errc2;
-                            const float Gb = sB_G32[lb];
-                            crmsd_fast_fp32(blk, Ga, Gb, invL, &sfast, &errc2);
-                            const float nrm = __fdividef(2.f, Ga + Gb);
-                            float Hn[9], Rp[9];
-#pragma unroll
-                            for (int e = 0; e < 9; ++e) Hn[e] = blk[e] * nrm;
-                            horn_rotation(Hn, sfast, Rp);
-                            const float coef = w / ((float)L * fmaxf(c, eps));
-#pragma unroll
-                            for (int i = 0; i < 3; ++i) {
-                                const int src_row = (i + 3 - alpha) % 3;
-#pragma unroll
-                                for (int be = 0; be < 3; ++be)
-                                    P[3 * i + be] = coef * sel3(src_row, Rp[be], Rp[3 + be], Rp[6 + be]);
-                            }
-                            atomicAdd(&dsum[la], coef);
-                        }
-                    }
 #pragma unroll
                     for (int i = 0; i < 3; ++i)
 #pragma unroll
                         for (int be = 0; be < 3; ++be) {
                             const uint32_t off = a2_offset(32 * sp + 3 * mloc + i, 32 * g + 3 * bq + be);
-                            const float v = P[3 * i + be];
+                            const float v = Pall[r][3 * i + be];
                             const float vh = tf32_rna(v);
                             *reinterpret_cast<float *>(A2 + off) = vh;
                             *reinterpret_cast<float *>(A2 + 32768 + off) = tf32_rna(v - vh);
                         }
                 }
             }
+            fence_proxy_async();  // generic-proxy stores to A2 must be visible to tcgen05.mma
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&a2full_bar);
+            named_bar_sync(1, 256);  // sB_* of this tile are no longer read
         }
-        fence_proxy_async();  // the generic-proxy stores to A2 must be visible to tcgen05.mma
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        // ---- 3. GEMM2: sum += P . X_J in three TF32 passes, atom chunks ----
-        if (warp == 0 && lane == 0) {
-            const uint32_t id = make_idesc(128, chunk, 2);
-            const uint32_t blk = (uint32_t)chunk * 128u;
-            for (int ch = 0; ch < nchunk; ++ch) {
-                if (ch > 0) load_chunk(ch);
-                if (!mbar_wait(&xt_bar, xt_count & 1)) {
-                    atomicExch(&abort_flag, 1);
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t d = tmem + BT_D2 + (uint32_t)(ch * chunk);
+        if (alive) {
+            const bool ok3 = mbar_wait_sleep(&d2_bar, 0);
+            if (named_bar_or(1, 256, !ok3 || *abort_v)) alive = false;
+        }
+        if (alive) {
+            tc_fence_after();
+            // read the P.X sum out of TMEM: warp (sp, g) takes lanes 32 sp.., half of the atoms
+            float *row = Gp + (sidx * Rpad + 128 * I + 32 * sp + lane) * (int64_t)Lp;
+            const int half = Lp / 2;
+            for (int c0 = g * half; c0 < (g + 1) * half; c0 += 32) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * sp) << 16) + BT_D2 + (uint32_t)c0, v);
 #pragma unroll
-                for (int kb2 = 0; kb2 < 2; ++kb2)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const uint64_t ahi = desc_sw128(a2base + kb2 * 16384 + 32 * k);
-                        const uint64_t alo = desc_sw128(a2base + 32768 + kb2 * 16384 + 32 * k);
-                        const uint64_t bhi = desc_sw128(sbase0 + kb2 * blk + 32 * k);
-                        const uint64_t blo = desc_sw128(sbase0 + (2 + kb2) * blk + 32 * k);
-                        // each chunk's first MMA of the sweep starts its columns from zero
-                        mma_tf32(d, ahi, bhi, id, (jt == 0 && kb2 == 0 && k == 0) ? 0u : 1u);
-                        mma_tf32(d, ahi, blo, id, 1u);
-                        mma_tf32(d, alo, bhi, id, 1u);
-                    }
-                mma_commit(&g2_bar);
-                // the ring is reused by the next chunk or the next J's GEMM1: wait for these MMAs
-                const bool ok = mbar_wait(&g2_bar, xt_count & 1);
-                ++xt_count;
-                if (!ok) {
-                    atomicExch(&abort_flag, 1);
-                    break;
-                }
+                for (int jj = 0; jj < 32; ++jj) row[c0 + jj] = -v[jj];
             }
-        }
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (*(volatile int *)&abort_flag) {
-            alive = false;
-            break;
-        }
-    }
-    float *gp = Gp + (sidx * Rpad + 128 * I) * (int64_t)Lp;
-    if (alive) {
-        // ---- read the sum out of TMEM: warp (sp, g) takes lanes 32 sp.., half of the atoms ----
-        const int half = Lp / 2;
-        float *row = gp + (32 * sp + lane) * (int64_t)Lp;
-        for (int c0 = g * half; c0 < (g + 1) * half; c0 += 32) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * sp) << 16) + BT_D2 + (uint32_t)c0, v);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) row[c0 + j] = -v[j];
-        }
-        if (tid < TC_MA) dp[sidx * Npad + a_base + tid] = dsum[tid];
-    } else {
-        if (warp == 0 && lane == 0) {
-            // drain (bounded) the loads this CTA issued before giving up
-            for (int64_t q = (kbt > TC_STAGES ? kbt - TC_STAGES : 0); q < kbt; ++q)
-                mbar_wait(&full_bar[q % TC_STAGES], (uint32_t)((q / TC_STAGES) & 1));
-            mbar_wait(&xt_bar, xt_count & 1);
+            if (etid < TC_MA) dp[sidx * Npad + a_base + etid] = dsum[etid];
+        } else {
+            atomicExch(&abort_flag, 1);
         }
     }
     tc_fence_before();
+    __syncthreads();
+    if (*abort_v && tid == 0) {
+        // drain (bounded) whatever TMA traffic may still be landing in this CTA's shared memory
+        for (int s = 0; s < TC_STAGES; ++s) mbar_wait(&full_bar[s], 0);
+    }
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, BT_TMEM_COLS);
 }
@@ -494,10 +558,10 @@ inline int bt_launch(const float *coords, int64_t N, int64_t L, const float *gra
     if ((rc = make_map(&mA, w.planes, false, w.Lp, 2 * w.Rpad, 128, err))) return rc;
     if ((rc = make_map(&mB, w.planes, false, w.Lp, 2 * w.Rpad, 64, err))) return rc;
     {
-        // X^T parts: FP32 [2 Lp][Rpad]; boxes of 32 columns (128 bytes) x one atom chunk
+        // X^T parts: FP32 [2 Lp][Rpad]; boxes of 32 columns (128 bytes) x 64 atoms
         const cuuint64_t dims[2] = {(cuuint64_t)w.Rpad, (cuuint64_t)(2 * w.Lp)};
         const cuuint64_t strides[1] = {(cuuint64_t)(w.Rpad * 4)};
-        const cuuint32_t box[2] = {32u, (cuuint32_t)bt_chunk((int)w.Lp)};
+        const cuuint32_t box[2] = {32u, (cuuint32_t)BT_XCH};
         const cuuint32_t estr[2] = {1, 1};
         CUresult r = encode_fn()(&mX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, w.xT, dims, strides, box, estr,
                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
