@@ -10,26 +10,44 @@
 #pragma once
 
 template <typename T>
-__device__ __forceinline__ T det3_rows(const T A[4][4], int r0, int r1, int r2, int c0, int c1, int c2)
+__device__ __forceinline__ T sel4(int i, T a, T b, T c, T d)
 {
-    return A[r0][c0] * (A[r1][c1] * A[r2][c2] - A[r1][c2] * A[r2][c1])
-         - A[r0][c1] * (A[r1][c0] * A[r2][c2] - A[r1][c2] * A[r2][c0])
-         + A[r0][c2] * (A[r1][c0] * A[r2][c1] - A[r1][c1] * A[r2][c0]);
+    return i == 0 ? a : (i == 1 ? b : (i == 2 ? c : d));
 }
 
-// Cofactor C_jk of the 4x4 matrix A.
+// Adjugate of a 4x4 matrix by Laplace expansion along rows (0,1) against rows (2,3):
+// twelve 2x2 minors, then each cofactor as three products. adj[i][j] = (-1)^(i+j) M_ji.
 template <typename T>
-__device__ __forceinline__ T cofactor4(const T A[4][4], int j, int k)
+__device__ __forceinline__ void adjugate4(const T A[4][4], T adj[4][4])
 {
-    int r[3], c[3];
-    int n = 0;
-    for (int i = 0; i < 4; ++i)
-        if (i != j) r[n++] = i;
-    n = 0;
-    for (int i = 0; i < 4; ++i)
-        if (i != k) c[n++] = i;
-    const T d = det3_rows(A, r[0], r[1], r[2], c[0], c[1], c[2]);
-    return ((j + k) & 1) ? -d : d;
+    const T s0 = A[0][0] * A[1][1] - A[1][0] * A[0][1];
+    const T s1 = A[0][0] * A[1][2] - A[1][0] * A[0][2];
+    const T s2 = A[0][0] * A[1][3] - A[1][0] * A[0][3];
+    const T s3 = A[0][1] * A[1][2] - A[1][1] * A[0][2];
+    const T s4 = A[0][1] * A[1][3] - A[1][1] * A[0][3];
+    const T s5 = A[0][2] * A[1][3] - A[1][2] * A[0][3];
+    const T c5 = A[2][2] * A[3][3] - A[3][2] * A[2][3];
+    const T c4 = A[2][1] * A[3][3] - A[3][1] * A[2][3];
+    const T c3 = A[2][1] * A[3][2] - A[3][1] * A[2][2];
+    const T c2 = A[2][0] * A[3][3] - A[3][0] * A[2][3];
+    const T c1 = A[2][0] * A[3][2] - A[3][0] * A[2][2];
+    const T c0 = A[2][0] * A[3][1] - A[3][0] * A[2][1];
+    adj[0][0] = A[1][1] * c5 - A[1][2] * c4 + A[1][3] * c3;
+    adj[0][1] = -A[0][1] * c5 + A[0][2] * c4 - A[0][3] * c3;
+    adj[0][2] = A[3][1] * s5 - A[3][2] * s4 + A[3][3] * s3;
+    adj[0][3] = -A[2][1] * s5 + A[2][2] * s4 - A[2][3] * s3;
+    adj[1][0] = -A[1][0] * c5 + A[1][2] * c2 - A[1][3] * c1;
+    adj[1][1] = A[0][0] * c5 - A[0][2] * c2 + A[0][3] * c1;
+    adj[1][2] = -A[3][0] * s5 + A[3][2] * s2 - A[3][3] * s1;
+    adj[1][3] = A[2][0] * s5 - A[2][2] * s2 + A[2][3] * s1;
+    adj[2][0] = A[1][0] * c4 - A[1][1] * c2 + A[1][3] * c0;
+    adj[2][1] = -A[0][0] * c4 + A[0][1] * c2 - A[0][3] * c0;
+    adj[2][2] = A[3][0] * s4 - A[3][1] * s2 + A[3][3] * s0;
+    adj[2][3] = -A[2][0] * s4 + A[2][1] * s2 - A[2][3] * s0;
+    adj[3][0] = -A[1][0] * c3 + A[1][1] * c1 - A[1][2] * c0;
+    adj[3][1] = A[0][0] * c3 - A[0][1] * c1 + A[0][2] * c0;
+    adj[3][2] = -A[3][0] * s3 + A[3][1] * s1 - A[3][2] * s0;
+    adj[3][3] = A[2][0] * s3 - A[2][1] * s1 + A[2][2] * s0;
 }
 
 // R (row-major) maximising sum_i a_i . R b_i, given H (row-major) and lam = largest
@@ -49,20 +67,23 @@ __device__ __forceinline__ bool horn_rotation(const T H[9], T lam, T R[9])
     A[1][2] = A[2][1] = H[1] + H[3];
     A[1][3] = A[3][1] = H[2] + H[6];
     A[2][3] = A[3][2] = H[5] + H[7];
-    // adj_jj = cofactor C_jj >= 0 up to rounding; pick the largest
+    // every column of adj(K - lam I) is proportional to q; take the one with the largest
+    // diagonal entry (all diagonal entries share one sign), selected without indexing
+    T adj[4][4];
+    adjugate4(A, adj);
     int jb = 0;
-    T best = cofactor4(A, 0, 0);
+    T best = fabs(adj[0][0]);
 #pragma unroll
     for (int j = 1; j < 4; ++j) {
-        const T v = cofactor4(A, j, j);
-        if (fabs(v) > fabs(best)) {
+        const T v = fabs(adj[j][j]);
+        if (v > best) {
             best = v;
             jb = j;
         }
     }
     T q[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) q[k] = (k == jb) ? best : cofactor4(A, jb, k);
+    for (int k = 0; k < 4; ++k) q[k] = sel4(jb, adj[k][0], adj[k][1], adj[k][2], adj[k][3]);
     const T n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
     if (!(n2 > T(0)) || !isfinite(n2)) {
         R[0] = R[4] = R[8] = T(1);
