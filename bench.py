@@ -118,6 +118,22 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def traffic_for(key):
+    """DRAM bytes per launch of a kernel from its committed ncu summary, or None once the
+    kernel's source has changed since the counters were taken (sha256 recorded beside them)."""
+    import hashlib
+    src = {"pairs_tc": "pairs_tc.cuh", "bwd_tc": "bwd_tc.cuh"}[key]
+    try:
+        h = hashlib.sha256(open(os.path.join(ROOT, "paper_1302_4000_b300", "csrc", src), "rb").read()).hexdigest()
+        for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
+            parts = line.split()
+            if len(parts) == 4 and parts[0] == key and parts[1] == h:
+                return float(parts[2])
+    except OSError:
+        pass
+    return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -213,47 +229,61 @@ def run_ours(args):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def fwd():
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
         clusco.crmsd_allpairs(X, form, out=out, workspace=ws_all)
-
-    def step():
-        clusco.crmsd_allpairs(X, form, out=out, workspace=ws_all)
+        if evs:
+            evs[1].record(stream)
         clusco.crmsd_vs_ref(X, ref, out=vs, workspace=ws_vs)
+        if evs:
+            evs[2].record(stream)
         clusco.crmsd_allpairs_backward(X, W, out, 1e-6, form, grad_coords=grad, workspace=ws_bw)
+        if evs:
+            evs[3].record(stream)
 
-    launches_per_step = 2 + 2 + 3
+    # our kernels per step: pre-pass + pairs; ref pre-pass + vs-ref; adjoint (pre-pass,
+    # transpose, sweep, reduce, near-duplicate pass; 3 kernels on the CUDA-core fallback)
+    tc_bwd = L <= 320 and form_name != "none"
+    launches_per_step = 2 + 2 + (5 if tc_bwd else 3)
 
-    def timed(fn, k, w_):
+    def timed(fn, k, w_, split=False):
         for _ in range(w_):
             fn()
         torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(k)]
         if ws_ > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        for s_, t_ in ev:
+        for e4 in ev:
             flush.fill_(1)
-            s_.record(stream)
-            fn()
-            t_.record(stream)
+            if split:
+                fn(e4)
+            else:
+                e4[0].record(stream)
+                fn()
+                e4[3].record(stream)
         torch.cuda.synchronize()
         if ws_ > 1:
             dist.barrier()
-        return [s_.elapsed_time(t_) for s_, t_ in ev]
+        tot = [e4[0].elapsed_time(e4[3]) for e4 in ev]
+        if not split:
+            return tot, None, None
+        return tot, [e4[0].elapsed_time(e4[1]) for e4 in ev], [e4[2].elapsed_time(e4[3]) for e4 in ev]
 
     clocks = Clocks(local if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
     clocks.start()
-    step_ms = timed(step, args.steps, args.warmup)
+    step_ms, fwd_list, bwd_list = timed(step, args.steps, args.warmup, split=True)
     clk = clocks.stop()
     if clusco.sync_status() != 0:
         raise RuntimeError("device status set during the timed steps: " + lib.clusco_last_error().decode())
-    fwd_ms = timed(fwd, args.steps, 2)
     ms = statistics.mean(step_ms)
-    fms = statistics.mean(fwd_ms)
+    fms = statistics.mean(fwd_list)
+    bms = statistics.mean(bwd_list)
     if ws_ > 1:
-        t = torch.tensor([ms, fms], device=dev)
+        t = torch.tensor([ms, fms, bms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, fms = float(t[0]), float(t[1])
+        ms, fms, bms = float(t[0]), float(t[1]), float(t[2])
 
     # plain-form forward for the "vs plain FP32" ratio (same GPU, same inputs)
     plain_fwd = None
@@ -263,7 +293,7 @@ def run_ours(args):
 
         def pfwd():
             clusco.crmsd_allpairs(X, clusco.FORM_FP32_SIMT, out=out_p, workspace=ws_p)
-        plain_fwd = statistics.mean(timed(pfwd, max(2, args.steps // 2), 1))
+        plain_fwd = statistics.mean(timed(pfwd, max(2, args.steps // 2), 1)[0])
         del ws_p, out_p
 
     # accuracy of this run's output on sampled pairs against the oracle (outside timing)
@@ -301,7 +331,7 @@ def run_ours(args):
             vs_h.copy_(vs, non_blocking=True)
             g_h.copy_(grad, non_blocking=True)
 
-        e_ms = statistics.mean(timed(e2e_step, args.steps, 1))
+        e_ms = statistics.mean(timed(e2e_step, args.steps, 1)[0])
         if ws_ > 1:
             t = torch.tensor([e_ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -311,10 +341,19 @@ def run_ours(args):
         e2e = {"value": ws_ * P / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     hbm, bf16, bf16_sus, pk_kind = peaks()
-    # roofline of the dominant kernel: the all-pairs forward covariance contraction,
-    # 18 L flops per pair (BASELINE's algorithmic count), against the measured bf16 peak.
-    fl = 18.0 * L * P
-    ach_tf = fl / (fms * 1e-3) / 1e12
+    # Rooflines. Algorithmic flop per pair: the forward contraction is 18 L (the 3x3 covariance
+    # over L atoms); the adjoint is 54 L (that covariance once, plus R x_b and R^T x_a over L
+    # atoms for the two gradients). Durations are the CUDA-event brackets of each call in the
+    # timed steps (the forward call includes its pre-pass, the adjoint call its pre-pass,
+    # transpose, reduction and near-duplicate pass).
+    def rf(flop, msec, kernel, hash_key):
+        ach = flop / (msec * 1e-3) / 1e12
+        tr = traffic_for(hash_key)
+        return {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
+                "traffic": tr, "kernel": kernel, "peak_kind": f"{pk_kind} bf16 burst"}
+    r_fwd = rf(18.0 * L * P, fms, "pairs_tc_kernel (forward, 18 L flop/pair)", "pairs_tc")
+    r_bwd = rf(54.0 * L * P, bms, "bwd_tc_kernel (adjoint, 54 L flop/pair)", "bwd_tc")
+    dominant, other = (r_bwd, r_fwd) if bms >= fms else (r_fwd, r_bwd)
     line = {"metric": METRIC, "value": ws_ * P / (ms * 1e-3), "unit": UNIT, "n_gpus": ws_, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp32_simt": "f32+f64", "tf32": "tf32+f32",
@@ -324,13 +363,11 @@ def run_ours(args):
                        "pairs": P, "step": "prepass + all-pairs fwd + vs-native + backward",
                        "l2": "flushed (512 MiB write) before each timed step", "parallelism": f"replicas x{ws_}"},
             "fwd": {"value": ws_ * P / (fms * 1e-3), "unit": UNIT, "ms": fms},
+            "bwd_ms": bms,
             "vs_plain_fp32_fwd": (plain_fwd / fms) if plain_fwd else 1.0,
             "plain_fp32_fwd_ms": plain_fwd,
             "max_err_sampled_A": max_err,
-            "roofline": {"bound": "tensor", "achieved": ach_tf, "peak": bf16, "unit": "TFLOP/s",
-                         "frac": ach_tf / bf16, "traffic": None,
-                         "kernel": "all-pairs forward (prepass + contraction + epilogue), 18 L flop/pair",
-                         "peak_kind": f"{pk_kind} bf16 burst"},
+            "roofline": dominant, "roofline_other": other,
             "clocks": clk, "gpu_launches": launches_per_step * args.steps}
     if e2e:
         line["e2e"] = e2e

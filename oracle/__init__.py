@@ -66,8 +66,9 @@ def _bind(lib):
     lib.oracle_crmsd_vs_ref.argtypes = [_f32p, i64, i64, _f32p, _f64p, ctypes.c_int]
     lib.oracle_crmsd_grad.argtypes = [_f32p, i64, i64, _f64p, ctypes.c_double, _f64p, ctypes.c_int]
     lib.oracle_crmsd_eq2.argtypes = [_f32p, _f32p, i64, ctypes.POINTER(ctypes.c_double)]
+    lib.oracle_crmsd_grad_rows.argtypes = [_f32p, i64, i64, _f64p, ctypes.c_double, _i64p, i64, _f64p, ctypes.c_int]
     for f in ("oracle_crmsd_pair", "oracle_crmsd_allpairs", "oracle_crmsd_pairs",
-              "oracle_crmsd_vs_ref", "oracle_crmsd_grad", "oracle_crmsd_eq2"):
+              "oracle_crmsd_vs_ref", "oracle_crmsd_grad", "oracle_crmsd_eq2", "oracle_crmsd_grad_rows"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -135,6 +136,19 @@ def crmsd_grad(X, w, eps: float = 1e-6, nthreads: int = 0, lib=None) -> np.ndarr
     assert w.shape[0] == N * (N - 1) // 2
     g = np.empty((N, L, 3), dtype=np.float64)
     _check(lib.oracle_crmsd_grad(X, N, L, w, float(eps), g.reshape(-1), nthreads), "grad")
+    return g
+
+
+def crmsd_grad_rows(X, w, rows, eps: float = 1e-6, nthreads: int = 0, lib=None) -> np.ndarray:
+    """Rows of d/dX sum_{a<b} w_ab cRMSD_ab for the listed models, shape [len(rows), L, 3]."""
+    lib = lib or load()
+    X = _f32(X)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    N, L = X.shape[0], X.shape[1]
+    g = np.empty((rows.shape[0], L, 3), dtype=np.float64)
+    _check(lib.oracle_crmsd_grad_rows(X, N, L, w, float(eps), rows, rows.shape[0], g.reshape(-1), nthreads),
+           "grad_rows")
     return g
 
 

@@ -364,6 +364,56 @@ int oracle_crmsd_grad(const float *X, int64_t N, int64_t L, const double *w, dou
     return bad ? ORACLE_ENOCONV : ORACLE_OK;
 }
 
+/* Gradient rows: the same as oracle_crmsd_grad but only for the listed models
+ * (rows[k], k < nrows), written to grad[k][L][3]; for spot checks at sizes where the full
+ * gradient would take O(N^2 L) time. */
+int oracle_crmsd_grad_rows(const float *X, int64_t N, int64_t L, const double *w, double eps,
+                           const int64_t *rows, int64_t nrows, double *grad, int nthreads)
+{
+    if (!X || !w || !rows || !grad || N < 2 || L < 1 || nrows < 0 || !(eps >= 0.0)) return ORACLE_EINVAL;
+    for (int64_t k = 0; k < nrows; ++k)
+        if (rows[k] < 0 || rows[k] >= N) return ORACLE_EINVAL;
+    int bad = 0;
+    set_threads(nthreads);
+    for (int64_t k = 0; k < nrows; ++k) {
+        const int64_t a = rows[k];
+        double *g = grad + 3 * L * k;
+        double *ac = (double *)malloc(sizeof(double) * 3 * L);
+        centre(X + 3 * L * a, L, ac);
+        for (int64_t j = 0; j < 3 * L; ++j) g[j] = 0.0;
+#pragma omp parallel reduction(| : bad)
+        {
+            double *bc = (double *)malloc(sizeof(double) * 3 * L);
+            double *gl = (double *)calloc((size_t)(3 * L), sizeof(double));
+#pragma omp for schedule(dynamic, 16)
+            for (int64_t b = 0; b < N; ++b) {
+                if (b == a) continue;
+                double R[3][3], c = NAN;
+                centre(X + 3 * L * b, L, bc);
+                bad |= pair_from_centred(ac, bc, L, &c, R);
+                double wab = (a < b) ? w[condensed(a, b, N)] : w[condensed(b, a, N)];
+                double coef = wab / ((double)L * fmax(c, eps));
+                for (int64_t i = 0; i < L; ++i)
+                    for (int r = 0; r < 3; ++r) {
+                        double rb = R[r][0] * bc[3 * i + 0] + R[r][1] * bc[3 * i + 1] + R[r][2] * bc[3 * i + 2];
+                        gl[3 * i + r] += coef * (ac[3 * i + r] - rb);
+                    }
+            }
+#pragma omp critical
+            for (int64_t j = 0; j < 3 * L; ++j) g[j] += gl[j];
+            free(bc);
+            free(gl);
+        }
+        double m[3] = {0.0, 0.0, 0.0};
+        for (int64_t i = 0; i < L; ++i)
+            for (int r = 0; r < 3; ++r) m[r] += g[3 * i + r];
+        for (int64_t i = 0; i < L; ++i)
+            for (int r = 0; r < 3; ++r) g[3 * i + r] -= m[r] / (double)L;
+        free(ac);
+    }
+    return bad ? ORACLE_ENOCONV : ORACLE_OK;
+}
+
 /* The paper's closed form (eq. 2), FP64: eigenvalues of M^T M as roots of the
  * characteristic cubic, trigonometric (Viete) solution, S = sign(det M)
  * (S = +1 when det M = 0), negative eigenvalues and negative D clamped to 0. */

@@ -107,11 +107,14 @@ class Ensemble:
         return self.coords.shape[1]
 
 
-def _finish(models, sigma, native_id, natives, rng, recipe, extra=None) -> Ensemble:
+def _finish(models, sigma, native_id, natives, rng, recipe, per_model=None) -> Ensemble:
+    """Rigid placement, seeded permutation of the model order, FP32 cast; per_model arrays
+    (provenance, e.g. cluster ids) are permuted with the models."""
     placed = rigid_place(models, rng)
     perm = rng.permutation(models.shape[0])
     coords = np.ascontiguousarray(placed[perm].astype(np.float32))
-    return Ensemble(coords, sigma[perm], native_id[perm], natives, recipe, extra or {})
+    extra = {k: np.asarray(v)[perm] for k, v in (per_model or {}).items()}
+    return Ensemble(coords, sigma[perm], native_id[perm], natives, recipe, extra)
 
 
 def decoy_ensemble(N: int, L: int, n_natives: int, sigma_range, seed: int) -> Ensemble:
@@ -166,7 +169,8 @@ def config2(seed: int = SEED_BASE + 2, N: int = 20000, L: int = 150, n_natives: 
     native_id = np.concatenate([nid_div, nid_c[cid]])
     recipe = (f"precision: N={N} L={L} natives={n_natives}; {n_div} diverse sigma~U(1,8); "
               f"{n_centres} centres x {per} members sigma~U(0.02,0.5) seed={seed}")
-    return _finish(models, sigma, native_id, natives, rng, recipe)
+    cluster = np.concatenate([np.full(n_div, -1), cid])  # near-duplicate cluster id, -1 for diverse models
+    return _finish(models, sigma, native_id, natives, rng, recipe, {"cluster": cluster})
 
 
 def config3(seed: int = SEED_BASE + 3, N: int = 1024, L: int = 256, n_close: int = 10):

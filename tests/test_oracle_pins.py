@@ -220,6 +220,17 @@ def test_gradient_matches_finite_differences():
         assert abs(fd - g[a, i, k]) <= 1e-6 * np.abs(g).max() + 1e-6 * abs(g[a, i, k])
 
 
+def test_gradient_rows_equal_full_gradient():
+    """The per-model gradient entry point returns exactly the rows of the full gradient."""
+    e = E.decoy_ensemble(9, 20, 2, (0.5, 5.0), 21)
+    N = e.N
+    w = E.weights(N * (N - 1) // 2, 22).astype(np.float64)
+    g = oracle.crmsd_grad(e.coords, w, eps=1e-6)
+    rows = np.array([0, 4, 8])
+    gr = oracle.crmsd_grad_rows(e.coords, w, rows, eps=1e-6)
+    assert np.abs(gr - g[rows]).max() <= 1e-12 * np.abs(g).max()
+
+
 def test_gradient_guard_identical_copies():
     """c = 0 exactly (bit-identical copy): the guarded term is finite and zero."""
     e = E.config0()
