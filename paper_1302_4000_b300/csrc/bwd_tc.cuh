@@ -32,11 +32,12 @@
 
 namespace clusco {
 
+constexpr int BT_STAGES = 2;
 constexpr int BT_THREADS = 320;                           // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int BT_MAXLP = 320;
 constexpr uint32_t BT_TMEM_COLS = 512;
 constexpr uint32_t BT_D2 = 192;                            // first TMEM column of the P.X sum
-constexpr size_t BT_RING = TC_STAGES * STAGE_BYTES_BF16;   // 96 KB; reused for X_J^T chunks
+constexpr size_t BT_RING = BT_STAGES * STAGE_BYTES_BF16;   // 96 KB; reused for X_J^T chunks
 constexpr size_t BT_A2 = 2 * 128 * 64 * 4;                 // hi, lo: 64 KB
 constexpr int BT_XCH = 64;                                 // atoms per X^T chunk (GEMM2 N)
 constexpr size_t BT_XBUF = 4 * BT_XCH * 128;               // hi/lo x two 32-column blocks: 32 KB
@@ -139,8 +140,8 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
                   unsigned long long *__restrict__ nd_count, int64_t nd_cap)
 {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[TC_STAGES];   // GEMM1 ring: K block landed
-    __shared__ __align__(8) uint64_t empty_bar[TC_STAGES];  // GEMM1 ring: K block consumed
+    __shared__ __align__(8) uint64_t full_bar[BT_STAGES];   // GEMM1 ring: K block landed
+    __shared__ __align__(8) uint64_t empty_bar[BT_STAGES];  // GEMM1 ring: K block consumed
     __shared__ __align__(8) uint64_t done1_bar;             // GEMM1 of a tile is in TMEM
     __shared__ __align__(8) uint64_t tfree_bar;             // the epilogue has read that tile (8 arrivals)
     __shared__ __align__(8) uint64_t a2full_bar;            // the rotation operand is written (8 arrivals)
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
         tmem_relinquish();
     }
     if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < BT_STAGES; ++s) {
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
@@ -212,9 +213,9 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
             bool ok = true;
             auto g1_loads = [&](int64_t J) {
                 for (int kb = 0; kb < nkb && ok; ++kb, ++q) {
-                    const int s = (int)(q % TC_STAGES);
-                    const int64_t use = q / TC_STAGES;
-                    if (q >= TC_STAGES && !mbar_wait(&empty_bar[s], (uint32_t)((use - 1) & 1))) {
+                    const int s = (int)(q % BT_STAGES);
+                    const int64_t use = q / BT_STAGES;
+                    if (q >= BT_STAGES && !mbar_wait(&empty_bar[s], (uint32_t)((use - 1) & 1))) {
                         ok = false;
                         break;
                     }
@@ -261,8 +262,8 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
             constexpr uint32_t idx = make_idesc(128, BT_XCH, 2);
             auto g1 = [&]() {
                 for (int kb = 0; kb < nkb && ok; ++kb, ++q) {
-                    const int s = (int)(q % TC_STAGES);
-                    const int64_t use = q / TC_STAGES;
+                    const int s = (int)(q % BT_STAGES);
+                    const int64_t use = q / BT_STAGES;
                     if (!mbar_wait(&full_bar[s], (uint32_t)(use & 1))) {
                         ok = false;
                         break;
@@ -342,7 +343,6 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
             Ga = G32[a];
         }
         const uint32_t trow = tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)(32 * g);
-        const float invL = 1.f / (float)L;
         bool alive = true;
         for (int64_t j = 0; j < nJ; ++j) {
             const int64_t J = J0 + j;
@@ -427,15 +427,12 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
                             }
                         }
                     } else if (w != 0.f) {
-                        float sfast, errc2;
-                        const float Gb = sB_G32[lb];
-                        crmsd_fast_fp32(blk, Ga, Gb, invL, &sfast, &errc2);
-                        const float nrm = __fdividef(2.f, Ga + Gb);
+                        const float nrm = __fdividef(2.f, Ga + sB_G32[lb]);
                         float Hn[9], Rp[9];
 #pragma unroll
                         for (int e = 0; e < 9; ++e) Hn[e] = blk[e] * nrm;
-                        horn_rotation(Hn, sfast, Rp);
-                        const float coef = w / ((float)L * fmaxf(c, eps));
+                        horn_rotation(Hn, sigma_hat_f32(Hn), Rp);
+                        const float coef = __fdividef(w, (float)L * fmaxf(c, eps));
 #pragma unroll
                         for (int i = 0; i < 3; ++i) {
                             const int src_row = (i + 3 - alpha) % 3;
@@ -499,7 +496,7 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
     __syncthreads();
     if (*abort_v && tid == 0) {
         // drain (bounded) whatever TMA traffic may still be landing in this CTA's shared memory
-        for (int s = 0; s < TC_STAGES; ++s) mbar_wait(&full_bar[s], 0);
+        for (int s = 0; s < BT_STAGES; ++s) mbar_wait(&full_bar[s], 0);
     }
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, BT_TMEM_COLS);

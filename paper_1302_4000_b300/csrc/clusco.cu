@@ -286,7 +286,7 @@ int clusco_crmsd_vs_ref(const float *coords, int64_t N, int64_t L, const float *
     CUDA_TRY(cudaGetLastError());
     const size_t smem = (size_t)L * 3 * sizeof(int);
     if (smem > 48 * 1024) CUDA_TRY(cudaFuncSetAttribute(vsref_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    vsref_kernel<<<(unsigned)((N + 7) / 8), 256, smem, st>>>(coords, N, (int)L, nref, info, out);
+    vsref_kernel<<<(unsigned)((N + VSREF_MODELS - 1) / VSREF_MODELS), 256, smem, st>>>(coords, N, (int)L, nref, info, out);
     CUDA_TRY(cudaGetLastError());
     return CLUSCO_OK;
 }
@@ -371,7 +371,7 @@ int clusco_crmsd_vs_ref_noalloc(const float *coords, int64_t N, int64_t L, const
     CUDA_TRY(cudaGetLastError());
     const size_t smem = (size_t)L * 3 * sizeof(int);
     if (smem > 48 * 1024) CUDA_TRY(cudaFuncSetAttribute(vsref_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    vsref_kernel<<<(unsigned)((N + 7) / 8), 256, smem, st>>>(coords, N, (int)L, nref, info, out);
+    vsref_kernel<<<(unsigned)((N + VSREF_MODELS - 1) / VSREF_MODELS), 256, smem, st>>>(coords, N, (int)L, nref, info, out);
     CUDA_TRY(cudaGetLastError());
     return CLUSCO_OK;
 }

@@ -185,6 +185,16 @@ __device__ __forceinline__ double crmsd_refined_fp64(const double H[9], double G
     return sqrt(fmax(c2, 0.0));
 }
 
+// Sigma_hat alone (FP32, cubic start + two Newton steps) for a normalised covariance m:
+// what the adjoint needs for the rotation, without cRMSD or its error bound.
+__device__ __forceinline__ float sigma_hat_f32(const float m[9])
+{
+    float I1, det, I2, dP;
+    bool deg;
+    invariants3(m, I1, det, I2);
+    return quartic_newton_f(sigma_cubic_f(I1, det, I2), I1, det, I2, 2, &deg, &dP);
+}
+
 // FP32 fast path on a rounded covariance: cubic start + two Newton steps, all FP32.
 // Returns cRMSD and, through err_c2, a bound on the absolute error of cRMSD^2 from FP32
 // rounding. The bound follows the root's conditioning: the quartic is evaluated with an

@@ -28,6 +28,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <string>
 
 #include "common.cuh"
@@ -52,20 +53,19 @@ struct TcArgs {
     int64_t out_base;
 };
 
-constexpr int TC_THREADS = 256;
-constexpr int TC_STAGES = 2;
-constexpr int TC_TMEM_COLS = 256;
 constexpr uint32_t STAGE_BYTES_BF16 = 2 * 16384 + 2 * 8192;  // A_h, A_l, B_h, B_l
 constexpr uint32_t STAGE_BYTES_TF32 = 16384 + 8192;          // A, B
-constexpr size_t TC_SMEM = 1024 + TC_STAGES * STAGE_BYTES_BF16;  // same for every form: 2 CTAs/SM
-constexpr int QCAP = 64;  // refinement queue entries per warp
+// Persistent forward kernel: 1 CTA per SM, warp 0 TMA, warp 1 MMA, warps 2-9 epilogue.
+constexpr int FW_THREADS = 320;
+constexpr int FW_STAGES = 3;
+constexpr int FW_QCAP = 64;  // refinement queue entries per epilogue warp (flushed at 32)
 struct QEntry {
     float v[36];  // class-major raw class values of the 3x3 block (rows cyclic from alpha)
-    int la, lb, alpha;
+    int a, b, alpha;
     float s;
 };
 static_assert(sizeof(QEntry) == 160, "queue entry layout");
-static_assert(8 * QCAP * sizeof(QEntry) <= TC_STAGES * STAGE_BYTES_BF16, "queues reuse the stage ring");
+constexpr size_t FW_SMEM = 1024 + FW_STAGES * STAGE_BYTES_BF16 + 8 * FW_QCAP * sizeof(QEntry);
 
 __host__ __device__ __forceinline__ int64_t tc_row_start(int64_t I, int64_t TB) { return I * TB - I * (I - 1); }
 
@@ -115,309 +115,305 @@ __device__ __forceinline__ void tc_issue_kblock(uint32_t tmem, uint32_t sbase, i
 __device__ __forceinline__ float sel3(int i, float a, float b, float c) { return i == 0 ? a : (i == 1 ? b : c); }
 
 template <int LAYOUT>
-__global__ void __launch_bounds__(TC_THREADS, 2)
+__global__ void __launch_bounds__(FW_THREADS, 1)
     pairs_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                     const float *__restrict__ scales, const double *__restrict__ G64, const float *__restrict__ G32,
-                    int64_t N, int L, int nkb, int64_t Rpad, int64_t TA, int64_t TB, int64_t tile0, int64_t row_begin,
-                    int64_t row_end, float *__restrict__ out, int64_t out_base)
+                    int64_t N, int L, int nkb, int64_t Rpad, int64_t TA, int64_t TB, int64_t tile0, int64_t ntiles,
+                    int64_t row_begin, int64_t row_end, float *__restrict__ out, int64_t out_base)
 {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[TC_STAGES];
-    __shared__ __align__(8) uint64_t empty_bar[TC_STAGES];
-    __shared__ __align__(8) uint64_t done_bar;
+    __shared__ __align__(8) uint64_t full_bar[FW_STAGES];   // ring: K block landed
+    __shared__ __align__(8) uint64_t empty_bar[FW_STAGES];  // ring: K block consumed by the MMAs
+    __shared__ __align__(8) uint64_t tfull_bar[2];          // accumulator buffer holds a finished tile
+    __shared__ __align__(8) uint64_t tempty_bar[2];         // the epilogue has drained the buffer (8 arrivals)
+    __shared__ __align__(8) uint64_t done_bar;              // every MMA this CTA issued has completed
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
-    __shared__ float sB_scale[TC_MB * 3];
-    __shared__ float sB_G32[TC_MB];
-    __shared__ int q_count[8];
 
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase0 = smem_u32(smem);
+    QEntry *queues = reinterpret_cast<QEntry *>(smem + FW_STAGES * STAGE_BYTES_BF16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-    int64_t I, J;
-    tc_decode(tile0 + blockIdx.x, TB, TA, &I, &J);
-    const int64_t a_base = I * TC_MA, b_base = J * TC_MB;
+    constexpr uint32_t STAGE_BYTES = (LAYOUT == TC_TF32) ? STAGE_BYTES_TF32 : STAGE_BYTES_BF16;
+    constexpr int KB_ELEMS = (LAYOUT == TC_TF32) ? 32 : 64;
 
     if (warp == 0) {
-        tmem_alloc(&tmem_slot, TC_TMEM_COLS);
+        tmem_alloc(&tmem_slot, 512);
         tmem_relinquish();
     }
     if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < FW_STAGES; ++s) {
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull_bar[b], 1);
+            mbar_init(&tempty_bar[b], 8);
         }
         mbar_init(&done_bar, 1);
         abort_flag = 0;
         fence_barrier_init();
         fence_proxy_async();
     }
-    if (tid < TC_MB * 3) {
-        const int64_t b = b_base + tid / 3;
-        sB_scale[tid] = scales[b * 3 + tid % 3];
-    }
-    if (tid < TC_MB) sB_G32[tid] = G32[b_base + tid];
-    if (tid < 8) q_count[tid] = 0;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
+    volatile int *abort_v = &abort_flag;
 
-    constexpr uint32_t STAGE_BYTES = (LAYOUT == TC_TF32) ? STAGE_BYTES_TF32 : STAGE_BYTES_BF16;
-    constexpr int KB_ELEMS = (LAYOUT == TC_TF32) ? 32 : 64;
-    if (warp == 0 && lane == 0) {
-        // ---- TMA producer ----
-        tma_prefetch_desc(&mapA);
-        tma_prefetch_desc(&mapB);
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb % TC_STAGES, use = kb / TC_STAGES;
-            if (kb >= TC_STAGES) {
-                if (!mbar_wait(&empty_bar[s], (use - 1) & 1)) {
+    if (warp == 0) {
+        // ================= TMA producer =================
+        if (lane == 0) {
+            tma_prefetch_desc(&mapA);
+            tma_prefetch_desc(&mapB);
+            int64_t q = 0;
+            for (int64_t t = blockIdx.x; t < ntiles && !*abort_v; t += gridDim.x) {
+                int64_t I, J;
+                tc_decode(tile0 + t, TB, TA, &I, &J);
+                for (int kb = 0; kb < nkb; ++kb, ++q) {
+                    const int s = (int)(q % FW_STAGES);
+                    const int64_t use = q / FW_STAGES;
+                    if (q >= FW_STAGES && !mbar_wait(&empty_bar[s], (uint32_t)((use - 1) & 1))) {
+                        atomicExch(&abort_flag, 1);
+                        break;
+                    }
+                    uint8_t *st = smem + s * STAGE_BYTES_BF16;
+                    mbar_arrive_expect_tx(&full_bar[s], STAGE_BYTES);
+                    const int x = kb * KB_ELEMS;
+                    if (LAYOUT == TC_TF32) {
+                        tma_load_2d(st, &mapA, &full_bar[s], x, (int)(128 * I));
+                        tma_load_2d(st + 16384, &mapB, &full_bar[s], x, (int)(64 * J));
+                    } else {
+                        tma_load_2d(st, &mapA, &full_bar[s], x, (int)(128 * I));
+                        tma_load_2d(st + 16384, &mapA, &full_bar[s], x, (int)(Rpad + 128 * I));
+                        tma_load_2d(st + 32768, &mapB, &full_bar[s], x, (int)(64 * J));
+                        tma_load_2d(st + 40960, &mapB, &full_bar[s], x, (int)(Rpad + 64 * J));
+                    }
+                }
+            }
+            if (*abort_v) {
+                // loads still in flight must land before the CTA leaves (bounded waits)
+                for (int64_t r = (q > FW_STAGES ? q - FW_STAGES : 0); r < q; ++r)
+                    mbar_wait(&full_bar[r % FW_STAGES], (uint32_t)((r / FW_STAGES) & 1));
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ================= MMA issuer =================
+        if (lane == 0) {
+            int64_t q = 0, k = 0;
+            for (int64_t t = blockIdx.x; t < ntiles && !*abort_v; t += gridDim.x, ++k) {
+                const int buf = (int)(k & 1);
+                const int64_t u = k >> 1;
+                if (k >= 2 && !mbar_wait_sleep(&tempty_bar[buf], (uint32_t)((u - 1) & 1))) {
+                    atomicExch(&abort_flag, 1);
+                    break;
+                }
+                tc_fence_after();
+                bool ok = true;
+                for (int kb = 0; kb < nkb; ++kb, ++q) {
+                    const int s = (int)(q % FW_STAGES);
+                    const int64_t use = q / FW_STAGES;
+                    if (!mbar_wait(&full_bar[s], (uint32_t)(use & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    tc_issue_kblock<LAYOUT>(tmem + 256u * buf, sbase0 + s * STAGE_BYTES_BF16, kb);
+                    mma_commit(&empty_bar[s]);
+                }
+                mma_commit(&tfull_bar[buf]);
+                if (!ok) {
                     atomicExch(&abort_flag, 1);
                     break;
                 }
             }
-            if (*(volatile int *)&abort_flag) break;
-            uint8_t *st = smem + s * STAGE_BYTES_BF16;
-            mbar_arrive_expect_tx(&full_bar[s], STAGE_BYTES);
-            const int x = kb * KB_ELEMS;
-            if (LAYOUT == TC_TF32) {
-                tma_load_2d(st, &mapA, &full_bar[s], x, (int)(128 * I));
-                tma_load_2d(st + 16384, &mapB, &full_bar[s], x, (int)(64 * J));
-            } else {
-                tma_load_2d(st, &mapA, &full_bar[s], x, (int)(128 * I));
-                tma_load_2d(st + 16384, &mapA, &full_bar[s], x, (int)(Rpad + 128 * I));
-                tma_load_2d(st + 32768, &mapB, &full_bar[s], x, (int)(64 * J));
-                tma_load_2d(st + 40960, &mapB, &full_bar[s], x, (int)(Rpad + 64 * J));
-            }
+            mma_commit(&done_bar);
+            if (!mbar_wait(&done_bar, 0)) atomicExch(&abort_flag, 1);
         }
-    } else if (warp == 1 && lane == 0) {
-        // ---- MMA issuer ----
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb % TC_STAGES, use = kb / TC_STAGES;
-            if (!mbar_wait(&full_bar[s], use & 1) || *(volatile int *)&abort_flag) {
+        __syncwarp();
+    } else {
+        // ================= epilogue warps 2..9 =================
+        const int ew = warp - 2;
+        const int sp = warp & 3, g = ew >> 2;
+        const int mloc = lane / 3, alpha = lane - 3 * (lane / 3);
+        const float invL = 1.f / (float)L;
+        QEntry *queue = queues + ew * FW_QCAP;
+        int qn = 0;  // entries in this warp's queue (warp-uniform)
+
+        // FP64 recomputation of one queued pair from its four exact digit classes
+        auto refine_entry = [&](const QEntry &qe) {
+            const int64_t aa = qe.a, bb = qe.b;
+            double H[9];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const double sr = (double)scales[aa * 3 + (qe.alpha + i) % 3];
+#pragma unroll
+                for (int be = 0; be < 3; ++be) {
+                    const int kk = 3 * i + be;
+                    const double v = 65536.0 * (double)qe.v[kk] +
+                                     256.0 * ((double)qe.v[9 + kk] + (double)qe.v[18 + kk]) + (double)qe.v[27 + kk];
+                    H[kk] = v * (sr * (double)scales[bb * 3 + be]);
+                }
+            }
+            const double c = crmsd_refined_fp64(H, G64[aa], G64[bb], 1.0 / (double)L, (double)qe.s, true);
+            out[condensed_idx(aa, bb, N) - out_base] = (float)c;
+        };
+
+        int64_t k = 0;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+            int64_t I, J;
+            tc_decode(tile0 + t, TB, TA, &I, &J);
+            const int64_t a_base = I * TC_MA, b_base = J * TC_MB;
+            const int64_t a = a_base + 10 * sp + mloc;
+            const bool lane_ok = lane < 30 && a < N;
+            float srow0 = 1.f, Ga = 0.f;
+            if (lane_ok) {
+                srow0 = scales[a * 3 + alpha];
+                Ga = G32[a];
+            }
+            const int buf = (int)(k & 1);
+            const bool okw = mbar_wait_sleep(&tfull_bar[buf], (uint32_t)((k >> 1) & 1));
+            if (__any_sync(0xffffffffu, !okw || *abort_v)) {
                 atomicExch(&abort_flag, 1);
                 break;
             }
             tc_fence_after();
-            tc_issue_kblock<LAYOUT>(tmem, sbase0 + s * STAGE_BYTES_BF16, kb);
-            mma_commit(&empty_bar[s]);
-        }
-        mma_commit(&done_bar);  // also on abort: fires once everything issued has finished
-    }
-    __syncwarp();
-    if (!mbar_wait_sleep(&done_bar, 0)) atomicExch(&abort_flag, 1);
-    tc_fence_after();
-    __syncthreads();  // every TMA write and MMA has landed; the stage ring is free
-    if (*(volatile int *)&abort_flag) {  // read after the barrier: the same decision in every thread
-        // drain: on an abort the producer may have loads in flight; wait for them (bounded)
-        if (warp == 0 && lane == 0) {
-            for (int s = 0; s < TC_STAGES; ++s) mbar_wait(&full_bar[s], 0);
-        }
-        tc_fence_before();
-        __syncthreads();
-        if (warp == 0) tmem_dealloc(tmem, TC_TMEM_COLS);
-        return;
-    }
-
-    // ---- epilogue: warp -> TMEM lanes 32*(warp&3).., B-model group g = warp>>2 ----
-    const int sp = warp & 3, g = warp >> 2;
-    const int mloc = lane / 3, alpha = lane - 3 * (lane / 3);
-    const int64_t a = a_base + 10 * sp + mloc;
-    const bool lane_ok = lane < 30 && a < N;
-    const int la = 10 * sp + mloc;
-    float srow[3] = {1.f, 1.f, 1.f};
-    float Ga = 0.f;
-    double Ga64 = 0.0;
-    if (lane_ok) {
+            const uint32_t trow = tmem + 256u * buf + ((uint32_t)(32 * sp) << 16) + (uint32_t)(32 * g);
+            float V[32];
+            {
+                float tt[32];
+                if (LAYOUT == TC_EXACT2) {
+                    tmem_ld32(trow + 0, V);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) srow[i] = scales[a * 3 + (alpha + i) % 3];
-        Ga = G32[a];
-        Ga64 = G64[a];
-    }
-    const uint32_t trow = tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)(32 * g);
-    float V[32];
-    {
-        float t[32];
-        if (LAYOUT == TC_EXACT2) {
-            tmem_ld32(trow + 0, V);  // hh
+                    for (int j = 0; j < 32; ++j) V[j] *= 65536.f;
+                    tmem_ld32(trow + 64, tt);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) V[j] *= 65536.f;
-            tmem_ld32(trow + 64, t);  // hl
+                    for (int j = 0; j < 32; ++j) V[j] = fmaf(256.f, tt[j], V[j]);
+                    tmem_ld32(trow + 128, tt);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) V[j] = fmaf(256.f, t[j], V[j]);
-            tmem_ld32(trow + 128, t);  // lh
+                    for (int j = 0; j < 32; ++j) V[j] = fmaf(256.f, tt[j], V[j]);
+                    tmem_ld32(trow + 192, tt);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) V[j] = fmaf(256.f, t[j], V[j]);
-            tmem_ld32(trow + 192, t);  // ll
+                    for (int j = 0; j < 32; ++j) V[j] += tt[j];
+                    // column j of this warp's 32 is (model b_base + 10 g + j / 3, axis j % 3)
+                    const float cs = (lane < 30) ? __ldg(scales + (b_base + 10 * g) * 3 + lane) : 1.f;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) V[j] += t[j];
-            // scales: row (own axis alpha) x column (model b, axis beta)
+                    for (int j = 0; j < 30; ++j) V[j] *= srow0 * __shfl_sync(0xffffffffu, cs, j);
+                } else if (LAYOUT == TC_BF16X3) {
+                    tmem_ld32(trow + 0, V);
+                    tmem_ld32(trow + 64, tt);
 #pragma unroll
-            for (int j = 0; j < 30; ++j) V[j] *= srow[0] * sB_scale[30 * g + j];
-        } else if (LAYOUT == TC_BF16X3) {
-            tmem_ld32(trow + 0, V);
-            tmem_ld32(trow + 64, t);
+                    for (int j = 0; j < 32; ++j) V[j] += tt[j];
+                    tmem_ld32(trow + 128, tt);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) V[j] += t[j];
-            tmem_ld32(trow + 128, t);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) V[j] += t[j];
-        } else {
-            tmem_ld32(trow + 0, V);
-        }
-    }
-    const float invL = 1.f / (float)L;
-    QEntry *queue = reinterpret_cast<QEntry *>(smem) + warp * QCAP;
-
-    // FP64 recomputation of one queued pair from its four exact digit classes.
-    auto refine_entry = [&](const QEntry &q) {
-        const int64_t aa = a_base + q.la, bb = b_base + q.lb;
-        double H[9];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const double sr = (double)scales[aa * 3 + (q.alpha + i) % 3];
-#pragma unroll
-            for (int be = 0; be < 3; ++be) {
-                const int k = 3 * i + be;
-                const double v = 65536.0 * (double)q.v[k] + 256.0 * ((double)q.v[9 + k] + (double)q.v[18 + k]) +
-                                 (double)q.v[27 + k];
-                H[k] = v * (sr * (double)scales[bb * 3 + be]);
+                    for (int j = 0; j < 32; ++j) V[j] += tt[j];
+                } else {
+                    tmem_ld32(trow + 0, V);
+                }
             }
-        }
-        const double c = crmsd_refined_fp64(H, G64[aa], G64[bb], 1.0 / (double)L, (double)q.s, true);
-        out[condensed_idx(aa, bb, N) - out_base] = (float)c;
-    };
-    // a full batch: lane i refines entry i of this warp's queue
-    auto refine_batch = [&](int n) {
-        if (lane < n) refine_entry(queue[lane]);
-        __syncwarp();
-    };
-
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        // candidate rows of the three blocks of this round: block 3r + al' at columns 9r + 3al' + be
-        float cand[3][3];
+            for (int r = 0; r < 4; ++r) {
+                float cand[3][3];
 #pragma unroll
-        for (int al = 0; al < 3; ++al)
+                for (int al = 0; al < 3; ++al)
 #pragma unroll
-            for (int be = 0; be < 3; ++be) {
-                const int j = 9 * r + 3 * al + be;
-                cand[al][be] = (j < 32) ? V[j] : 0.f;
-            }
-        float blk[9];
+                    for (int be = 0; be < 3; ++be) {
+                        const int j = 9 * r + 3 * al + be;
+                        cand[al][be] = (j < 32) ? V[j] : 0.f;
+                    }
+                float blk[9];
 #pragma unroll
-        for (int be = 0; be < 3; ++be) blk[be] = sel3(alpha, cand[0][be], cand[1][be], cand[2][be]);
+                for (int be = 0; be < 3; ++be) blk[be] = sel3(alpha, cand[0][be], cand[1][be], cand[2][be]);
 #pragma unroll
-        for (int k = 1; k <= 2; ++k) {
-            const int sendsel = (alpha + 3 - k) % 3;
-            const int src = 3 * mloc + (alpha + k) % 3;
+                for (int kk = 1; kk <= 2; ++kk) {
+                    const int sendsel = (alpha + 3 - kk) % 3;
+                    const int src = 3 * mloc + (alpha + kk) % 3;
 #pragma unroll
-            for (int be = 0; be < 3; ++be) {
-                const float sv = sel3(sendsel, cand[0][be], cand[1][be], cand[2][be]);
-                blk[3 * k + be] = __shfl_sync(0xffffffffu, sv, src & 31);
-            }
-        }
-        const int lb = 10 * g + 3 * r + alpha;  // local B model of this lane's pair
-        const int64_t b = b_base + lb;
-        const bool pair_ok = lane_ok && (3 * r + alpha) < 10 && b < N && a < b && a >= row_begin && a < row_end;
-        bool need = false;
-        float sfast = 1.f;
-        if (pair_ok) {
-            // every lane scaled its own row (axis) and the columns before the exchange, so blk is
-            // the scaled covariance with rows in cyclic order alpha, alpha+1, alpha+2: a proper
-            // rotation of the rows, which leaves eq. 2 unchanged
-            float errc2;
-            const float c = crmsd_fast_fp32(blk, Ga, sB_G32[lb], invL, &sfast, &errc2);
-            if (LAYOUT == TC_EXACT2 && !(errc2 <= 2.f * CLUSCO_TOL_FAST * c)) {
-                need = true;
-            } else {
-                out[condensed_idx(a, b, N) - out_base] = (isnan(Ga) || isnan(sB_G32[lb])) ? __int_as_float(0x7fc00000) : c;
-            }
-        }
-        if (LAYOUT == TC_EXACT2) {
-            const unsigned m = __ballot_sync(0xffffffffu, need);
-            if (m) {
-                // reload the four exact classes of this round's columns and queue the flagged pairs
-                const int base = q_count[warp];
-                const int slot = base + __popc(m & ((1u << lane) - 1u));
+                    for (int be = 0; be < 3; ++be)
+                        blk[3 * kk + be] = __shfl_sync(0xffffffffu, sel3(sendsel, cand[0][be], cand[1][be], cand[2][be]),
+                                                       src & 31);
+                }
+                const int bq = 3 * r + alpha;
+                const int64_t b = b_base + 10 * g + bq;
+                const bool pair_ok = lane_ok && bq < 10 && b < N && a < b && a >= row_begin && a < row_end;
+                bool need = false;
+                float sfast = 1.f;
+                if (pair_ok) {
+                    float errc2;
+                    const float Gb = __ldg(G32 + b);
+                    const float c = crmsd_fast_fp32(blk, Ga, Gb, invL, &sfast, &errc2);
+                    if (LAYOUT == TC_EXACT2 && !(errc2 <= 2.f * CLUSCO_TOL_FAST * c)) {
+                        need = true;
+                    } else {
+                        out[condensed_idx(a, b, N) - out_base] =
+                            (isnan(Ga) || isnan(Gb)) ? __int_as_float(0x7fc00000) : c;
+                    }
+                }
+                if (LAYOUT == TC_EXACT2) {
+                    const unsigned m = __ballot_sync(0xffffffffu, need);
+                    if (m) {
+                        // re-read the four exact classes of this round's columns; queue the flagged pairs
+                        const int slot = qn + __popc(m & ((1u << lane) - 1u));
 #pragma unroll
-                for (int c4 = 0; c4 < 4; ++c4) {
-                    float t[32];
-                    tmem_ld32(trow + 64 * c4, t);
-                    float cc[3][3];
+                        for (int c4 = 0; c4 < 4; ++c4) {
+                            float tt[32];
+                            tmem_ld32(trow + 64 * c4, tt);
+                            float cc[3][3];
 #pragma unroll
-                    for (int al = 0; al < 3; ++al)
+                            for (int al = 0; al < 3; ++al)
 #pragma unroll
-                        for (int be = 0; be < 3; ++be) {
-                            const int j = 9 * r + 3 * al + be;
-                            cc[al][be] = (j < 32) ? t[j] : 0.f;
+                                for (int be = 0; be < 3; ++be) {
+                                    const int j = 9 * r + 3 * al + be;
+                                    cc[al][be] = (j < 32) ? tt[j] : 0.f;
+                                }
+                            float bv[9];
+#pragma unroll
+                            for (int be = 0; be < 3; ++be) bv[be] = sel3(alpha, cc[0][be], cc[1][be], cc[2][be]);
+#pragma unroll
+                            for (int kk = 1; kk <= 2; ++kk) {
+                                const int sendsel = (alpha + 3 - kk) % 3;
+                                const int src = 3 * mloc + (alpha + kk) % 3;
+#pragma unroll
+                                for (int be = 0; be < 3; ++be)
+                                    bv[3 * kk + be] = __shfl_sync(
+                                        0xffffffffu, sel3(sendsel, cc[0][be], cc[1][be], cc[2][be]), src & 31);
+                            }
+                            if (need) {
+#pragma unroll
+                                for (int e = 0; e < 9; ++e) queue[slot].v[9 * c4 + e] = bv[e];
+                            }
                         }
-                    float bv[9];
-#pragma unroll
-                    for (int be = 0; be < 3; ++be) bv[be] = sel3(alpha, cc[0][be], cc[1][be], cc[2][be]);
-#pragma unroll
-                    for (int k = 1; k <= 2; ++k) {
-                        const int sendsel = (alpha + 3 - k) % 3;
-                        const int src = 3 * mloc + (alpha + k) % 3;
-#pragma unroll
-                        for (int be = 0; be < 3; ++be)
-                            bv[3 * k + be] = __shfl_sync(0xffffffffu, sel3(sendsel, cc[0][be], cc[1][be], cc[2][be]), src & 31);
+                        if (need) {
+                            queue[slot].a = (int)a;
+                            queue[slot].b = (int)b;
+                            queue[slot].alpha = alpha;
+                            queue[slot].s = sfast;
+                        }
+                        qn += __popc(m);
+                        if (qn >= 32) {  // a full batch: every FP64 instruction runs on 32 lanes
+                            __syncwarp();
+                            refine_entry(queue[qn - 32 + lane]);
+                            __syncwarp();
+                            qn -= 32;
+                        }
                     }
-                    if (need) {
-#pragma unroll
-                        for (int e = 0; e < 9; ++e) queue[slot].v[9 * c4 + e] = bv[e];
-                    }
-                }
-                if (need) {
-                    queue[slot].la = la;
-                    queue[slot].lb = lb;
-                    queue[slot].alpha = alpha;
-                    queue[slot].s = sfast;
-                }
-                __syncwarp();
-                int cnt = base + __popc(m);
-                if (lane == 0) q_count[warp] = cnt;
-                __syncwarp();
-                if (cnt >= 32) {
-                    refine_batch(32);
-                    // move the remainder down
-                    for (int e = 32 + lane; e < cnt; e += 32) queue[e - 32] = queue[e];
-                    __syncwarp();
-                    if (lane == 0) q_count[warp] = cnt - 32;
-                    __syncwarp();
                 }
             }
+            // the accumulator buffer is drained: hand it back to the MMA warp
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty_bar[buf]);
+        }
+        if (LAYOUT == TC_EXACT2 && qn > 0) {
+            __syncwarp();
+            if (lane < qn) refine_entry(queue[lane]);
+            __syncwarp();
         }
     }
-    if (LAYOUT == TC_EXACT2) {
-        // The warps' leftovers (< 32 each) are refined together, 32 per warp, indexed through
-        // prefix offsets, so that the FP64 work runs in full warps instead of eight partial ones.
-        __shared__ int q_off[9];
-        __syncthreads();
-        if (tid == 0) {
-            int o = 0;
-            for (int w = 0; w < 8; ++w) {
-                q_off[w] = o;
-                o += q_count[w];
-            }
-            q_off[8] = o;
-        }
-        __syncthreads();
-        const int total = q_off[8];
-        const QEntry *qbase = reinterpret_cast<const QEntry *>(smem);
-        for (int gi = 32 * warp + lane; gi < total; gi += 256) {
-            int w = 0;
-#pragma unroll
-            for (int k = 1; k < 8; ++k) w += (gi >= q_off[k]) ? 1 : 0;
-            refine_entry(qbase[w * QCAP + (gi - q_off[w])]);
-        }
-    }
-
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, TC_TMEM_COLS);
+    if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 // ---- host side ----------------------------------------------------------
@@ -483,15 +479,21 @@ inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
     const int64_t I0 = a.row_begin / TC_MA, I1 = (a.row_end - 1) / TC_MA + 1;
     const int64_t t0 = tc_row_start(I0, TB), nt = tc_row_start(I1, TB) - t0;
     const int nkb = (int)(a.Lp / (tf32 ? 32 : 64));
+    if (nt <= 0) return CLUSCO_OK;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e = cudaFuncSetAttribute(pairs_tc_kernel<LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)TC_SMEM);
+                                         (int)FW_SMEM);
     if (e != cudaSuccess) {
         err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
         return CLUSCO_ECUDA;
     }
-    pairs_tc_kernel<LAYOUT><<<(unsigned)nt, TC_THREADS, TC_SMEM, st>>>(mA, mB, a.scales, a.G64, a.G32, a.N, (int)a.L,
-                                                                        nkb, a.Rpad, TA, TB, t0, a.row_begin,
-                                                                        a.row_end, a.out, a.out_base);
+    // persistent: one CTA per SM, CTA x takes tiles x, x + grid, x + 2 grid, ...
+    const unsigned grid = (unsigned)std::min<int64_t>(nt, sms > 0 ? sms : 148);
+    pairs_tc_kernel<LAYOUT><<<grid, FW_THREADS, FW_SMEM, st>>>(mA, mB, a.scales, a.G64, a.G32, a.N, (int)a.L, nkb,
+                                                                a.Rpad, TA, TB, t0, nt, a.row_begin, a.row_end,
+                                                                a.out, a.out_base);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         err = std::string("pairs_tc_kernel launch: ") + cudaGetErrorString(e);

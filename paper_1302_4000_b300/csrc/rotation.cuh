@@ -9,6 +9,9 @@
 // largest diagonal entry is the best conditioned.
 #pragma once
 
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
+
 template <typename T>
 __device__ __forceinline__ T sel4(int i, T a, T b, T c, T d)
 {
@@ -90,7 +93,7 @@ __device__ __forceinline__ bool horn_rotation(const T H[9], T lam, T R[9])
         R[1] = R[2] = R[3] = R[5] = R[6] = R[7] = T(0);
         return false;
     }
-    const T inv = T(1) / sqrt(n2);
+    const T inv = rsqrt_t(n2);
     const T w = q[0] * inv, x = q[1] * inv, y = q[2] * inv, z = q[3] * inv;
     R[0] = w * w + x * x - y * y - z * z;
     R[1] = T(2) * (x * y - w * z);

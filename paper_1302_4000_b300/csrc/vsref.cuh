@@ -97,77 +97,102 @@ __global__ void __launch_bounds__(1024) ref_prepass_kernel(const float *__restri
     }
 }
 
-// One warp per model; nref staged in dynamic shared memory (12 L bytes).
+// A block of 8 warps scores 32 models: each warp reduces the exact integer sums of four
+// models (reference staged in dynamic shared memory, 12 L bytes), then warp 0 runs the 32
+// FP64 epilogues side by side, one model per lane.
+constexpr int VSREF_MODELS = 32;
+
 __global__ void __launch_bounds__(256) vsref_kernel(const float *__restrict__ coords, int64_t N, int L,
                                                     const int *__restrict__ nref_g, const RefInfo *__restrict__ info,
                                                     float *__restrict__ out)
 {
     extern __shared__ int nref[];
+    __shared__ long long sh[VSREF_MODELS][9];
+    __shared__ long long sg[VSREF_MODELS][3];
+    __shared__ float ssc[VSREF_MODELS][3];
+    __shared__ int sfin[VSREF_MODELS];
     for (int i = threadIdx.x; i < 3 * L; i += blockDim.x) nref[i] = nref_g[i];
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t a = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (a >= N) return;
-    const float *x = coords + a * (int64_t)L * 3;
-    float mu[3];
-    bool finite;
-    model_centroid(x, L, lane, mu, &finite);
-    float m0 = 0.f, m1 = 0.f, m2 = 0.f;
-    for (int i = lane; i < L; i += 32) {
-        m0 = fmaxf(m0, fabsf(x[3 * i + 0] - mu[0]));
-        m1 = fmaxf(m1, fabsf(x[3 * i + 1] - mu[1]));
-        m2 = fmaxf(m2, fabsf(x[3 * i + 2] - mu[2]));
-    }
-    const float mx[3] = {warp_max_f(m0), warp_max_f(m1), warp_max_f(m2)};
-    float inv[3], sc[3];
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-        const bool pos = mx[ax] > 0.f && isfinite(mx[ax]);
-        sc[ax] = pos ? mx[ax] / Q24 : 1.f;
-        inv[ax] = pos ? Q24 / mx[ax] : 1.f;
-    }
-    long long h[9], g[3];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) h[k] = 0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) g[k] = 0;
-    for (int i = lane; i < L; i += 32) {
-        int n[3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t m0 = (int64_t)blockIdx.x * VSREF_MODELS;
+    for (int mm = warp; mm < VSREF_MODELS; mm += 8) {
+        const int64_t a = m0 + mm;
+        if (a >= N) break;
+        const float *x = coords + a * (int64_t)L * 3;
+        float mu[3];
+        bool finite;
+        model_centroid(x, L, lane, mu, &finite);
+        float m0x = 0.f, m1x = 0.f, m2x = 0.f;
+        for (int i = lane; i < L; i += 32) {
+            m0x = fmaxf(m0x, fabsf(x[3 * i + 0] - mu[0]));
+            m1x = fmaxf(m1x, fabsf(x[3 * i + 1] - mu[1]));
+            m2x = fmaxf(m2x, fabsf(x[3 * i + 2] - mu[2]));
+        }
+        const float mx[3] = {warp_max_f(m0x), warp_max_f(m1x), warp_max_f(m2x)};
+        float inv[3], sc[3];
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
-            float v = rintf((x[3 * i + ax] - mu[ax]) * inv[ax]);
-            v = isfinite(v) ? fminf(fmaxf(v, -Q24), Q24) : 0.f;
-            n[ax] = (int)v;
-            g[ax] += (long long)n[ax] * n[ax];
+            const bool pos = mx[ax] > 0.f && isfinite(mx[ax]);
+            sc[ax] = pos ? mx[ax] / Q24 : 1.f;
+            inv[ax] = pos ? Q24 / mx[ax] : 1.f;
+        }
+        long long h[9], g[3];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) h[k] = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) g[k] = 0;
+        for (int i = lane; i < L; i += 32) {
+            int n[3];
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                float v = rintf((x[3 * i + ax] - mu[ax]) * inv[ax]);
+                v = isfinite(v) ? fminf(fmaxf(v, -Q24), Q24) : 0.f;
+                n[ax] = (int)v;
+                g[ax] += (long long)n[ax] * n[ax];
+            }
+#pragma unroll
+            for (int al = 0; al < 3; ++al)
+#pragma unroll
+                for (int be = 0; be < 3; ++be) h[3 * al + be] += (long long)n[al] * nref[3 * i + be];
         }
 #pragma unroll
-        for (int al = 0; al < 3; ++al)
+        for (int k = 0; k < 9; ++k) h[k] = warp_sum_ll(h[k]);
 #pragma unroll
-            for (int be = 0; be < 3; ++be) h[3 * al + be] += (long long)n[al] * nref[3 * i + be];
+        for (int k = 0; k < 3; ++k) g[k] = warp_sum_ll(g[k]);
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) sh[mm][k] = h[k];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                sg[mm][k] = g[k];
+                ssc[mm][k] = sc[k];
+            }
+            sfin[mm] = finite ? 1 : 0;
+        }
     }
+    __syncthreads();
+    if (warp == 0) {
+        const int64_t a = m0 + lane;
+        if (a < N) {
+            const RefInfo ri = *info;
+            double H[9];
+            double Ga = 0.0;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) h[k] = warp_sum_ll(h[k]);
+            for (int al = 0; al < 3; ++al) {
+                const double sa = (double)ssc[lane][al];
+                Ga += sa * sa * (double)sg[lane][al];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) g[k] = warp_sum_ll(g[k]);
-    if (lane == 0) {
-        const RefInfo ri = *info;
-        double H[9];
-        double Ga = 0.0;
-#pragma unroll
-        for (int al = 0; al < 3; ++al) {
-            Ga += (double)sc[al] * (double)sc[al] * (double)g[al];
-#pragma unroll
-            for (int be = 0; be < 3; ++be)
-                H[3 * al + be] = ((double)sc[al] * (double)ri.scale[be]) * (double)h[3 * al + be];
+                for (int be = 0; be < 3; ++be) H[3 * al + be] = (sa * (double)ri.scale[be]) * (double)sh[lane][3 * al + be];
+            }
+            float c;
+            if (!sfin[lane] || !ri.finite) {
+                c = __int_as_float(0x7fc00000);
+                if (!sfin[lane]) set_status(CLUSCO_ST_NONFINITE);
+            } else {
+                c = (float)crmsd_refined_fp64(H, Ga, ri.G, 1.0 / (double)L, 0.0, false);
+            }
+            out[a] = c;
         }
-        float c;
-        if (!finite || !ri.finite) {
-            c = __int_as_float(0x7fc00000);
-            if (!finite) set_status(CLUSCO_ST_NONFINITE);
-        } else {
-            c = (float)crmsd_refined_fp64(H, Ga, ri.G, 1.0 / (double)L, 0.0, false);
-        }
-        out[a] = c;
     }
 }
 
