@@ -78,22 +78,24 @@ __device__ __forceinline__ double sigma_cubic_d(double I1, double det, double I2
 // cosine): a starting value for the FP32 Newton polish, accurate to about 1e-6.
 __device__ __forceinline__ float sigma_cubic_f(float I1, float det, float I2)
 {
+    // branch-free (selects), so that independent pairs interleave
     const float mm = I1 * (1.f / 3.f);
     const float p = I2 - 3.f * mm * mm;
     const float q = (I2 - 2.f * mm * mm) * mm - det * det;
-    float l1 = mm;
-    if (p < 0.f) {
-        const float rp = rsqrtf(-p);             // 1/sqrt(-p)
-        const float r = -p * rp * 0.57735026919f;  // sqrt(-p/3)
-        float arg = 1.5f * q * __fdividef(1.f, p) * 1.73205080757f * rp;  // (3q/2p) sqrt(-3/p)
-        arg = fminf(fmaxf(arg, -1.f), 1.f);
-        l1 = fmaf(2.f * r, __cosf(acosf(arg) * (1.f / 3.f)), mm);
-    }
-    if (!(l1 > 0.f)) return 0.f;
-    const float rl1i = rsqrtf(l1);
+    const float pn = fminf(p, -1e-30f);
+    const float rp = rsqrtf(-pn);               // 1/sqrt(-p)
+    const float r = -pn * rp * 0.57735026919f;  // sqrt(-p/3)
+    float arg = 1.5f * q * __fdividef(1.f, pn) * 1.73205080757f * rp;  // (3q/2p) sqrt(-3/p)
+    arg = fminf(fmaxf(arg, -1.f), 1.f);
+    float l1 = fmaf(2.f * r, __cosf(acosf(arg) * (1.f / 3.f)), mm);
+    l1 = (p < 0.f) ? l1 : mm;
+    const bool pos = l1 > 0.f;
+    const float l1p = pos ? l1 : 1.f;
+    const float rl1i = rsqrtf(l1p);
     const float il1 = rl1i * rl1i;
-    const float t = (I2 - det * det * il1) * il1 + 2.f * det * rl1i;
-    return l1 * rl1i + sqrtf(fmaxf(t, 0.f));
+    const float t = fmaxf((I2 - det * det * il1) * il1 + 2.f * det * rl1i, 0.f);
+    const float st = (t > 0.f) ? t * rsqrtf(t) : 0.f;  // a start value: approximate sqrt is enough
+    return pos ? l1p * rl1i + st : 0.f;
 }
 
 // Newton steps on the quartic whose largest root is s1 + s2 + S s3. At that root
@@ -185,6 +187,48 @@ __device__ __forceinline__ double crmsd_refined_fp64(const double H[9], double G
     return sqrt(fmax(c2, 0.0));
 }
 
+// FP64 refinement of a pair the FP32 fast path flagged, from its exact covariance H (raw
+// units) and the fast path's estimate s_hat of Sigma_hat = 2 Sigma / (G_A + G_B).
+// m = H 2^-e with 2^e <= G_A + G_B < 2^(e+1): a power of two, so the normalisation is exact
+// and needs no division. Newton steps on the quartic take the correction P / P' with an
+// FP32 reciprocal of P': its relative error (2^-24) scales only the correction, so the
+// iteration still converges to the FP64 root (from an FP32 start, one step reaches about
+// 1e-14). A degenerate root (P' below 8e-3 s^3) takes the FP64 cubic route instead.
+// c^2 = (G_A + G_B - 2 Sigma) / L = 2^(e+1) (h - s) / L with h = (G_A + G_B) 2^-e / 2, the
+// cancellation taken in FP64. invL is 1/L in FP64. Returns cRMSD rounded to FP32.
+__device__ __forceinline__ float crmsd_refine_newton_fp64(const double H[9], double Ga, double Gb, double invL,
+                                                          float s_hat)
+{
+    const double Gs = Ga + Gb;
+    if (!(Gs > 1e-300)) return 0.f;  // c^2 <= Gs / L: zero in FP32
+    if (!(Gs < 1.7e308)) return __int_as_float(0x7fc00000);
+    const long long ebits = (__double_as_longlong(Gs) >> 52) & 0x7ff;  // biased exponent, 1..2046
+    const double p2 = __longlong_as_double((2046LL - ebits) << 52);     // 2^-e
+    const double ip2 = __longlong_as_double(ebits << 52);                // 2^e
+    double m[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m[k] = H[k] * p2;
+    double I1, det, I2;
+    invariants3(m, I1, det, I2);
+    const double h = 0.5 * (Gs * p2);  // in [0.5, 1)
+    const double c2c = -2.0 * I1, c1 = -8.0 * det, c0 = I1 * I1 - 4.0 * I2;
+    double s = (double)s_hat * h;
+    bool deg = false;
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+        const double s2 = s * s;
+        const double P = (s2 + c2c) * s2 + c1 * s + c0;
+        const double dP = (4.0 * s2 + 2.0 * c2c) * s + c1;
+        if (dP > fmax(8e-3 * s2 * s, 1e-30))
+            s -= P * (double)__frcp_rn((float)dP);
+        else
+            deg = true;
+    }
+    if (deg) s = sigma_cubic_d(I1, det, I2);
+    const double c2 = 2.0 * (h - s) * ip2 * invL;
+    return sqrtf((float)fmax(c2, 0.0));
+}
+
 // Sigma_hat alone (FP32, cubic start + two Newton steps) for a normalised covariance m:
 // what the adjoint needs for the rotation, without cRMSD or its error bound.
 __device__ __forceinline__ float sigma_hat_f32(const float m[9])
@@ -214,12 +258,8 @@ __device__ __forceinline__ float crmsd_fast_fp32(const float H[9], float Ga, flo
                                                  float *err_c2)
 {
     const float Gs = Ga + Gb;
-    if (!(Gs > 0.0f)) {
-        *s_out = 1.0f;
-        *err_c2 = 0.0f;
-        return 0.0f;
-    }
-    const float nrm = __fdividef(2.0f, Gs);
+    const bool pos = Gs > 0.0f;
+    const float nrm = __fdividef(2.0f, pos ? Gs : 1.0f);
     float m[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) m[k] = H[k] * nrm;
@@ -233,6 +273,7 @@ __device__ __forceinline__ float crmsd_fast_fp32(const float H[9], float Ga, flo
     const float s2 = s * s;
     const float Q = fmaf(s2 + 2.f * I1, s2, fmaf(8.f * fabsf(det), s, I1 * I1));
     const float kq = CLUSCO_KERR_A + CLUSCO_KERR_B * __fdividef(Q, dP);
-    *err_c2 = (deg || !(dP > 0.f)) ? __int_as_float(0x7f800000) : kq * 5.9604645e-8f * scale;
-    return sqrtf(fmaxf(scale * (1.0f - s), 0.0f));
+    const float e = (deg || !(dP > 0.f)) ? __int_as_float(0x7f800000) : kq * 5.9604645e-8f * scale;
+    *err_c2 = pos ? e : 0.0f;
+    return pos ? sqrtf(fmaxf(scale * (1.0f - s), 0.0f)) : 0.0f;
 }

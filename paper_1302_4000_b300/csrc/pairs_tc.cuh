@@ -82,6 +82,18 @@ __device__ __forceinline__ void tc_decode(int64_t t, int64_t TB, int64_t TA, int
     *J = 2 * i + (t - tc_row_start(i, TB));
 }
 
+// Advance (I, J) by `step` tiles in the row-major order of the upper-triangle tiles (row I
+// holds J = 2I .. TB-1): integer carries only, no square root after the first decode.
+__device__ __forceinline__ void tc_advance(int64_t &I, int64_t &J, int64_t step, int64_t TB, int64_t TA)
+{
+    J += step;
+    while (J >= TB && I + 1 < TA) {
+        J -= TB;
+        ++I;
+        J += 2 * I;
+    }
+}
+
 template <int LAYOUT>
 __device__ __forceinline__ void tc_issue_kblock(uint32_t tmem, uint32_t sbase, int kb)
 {
@@ -113,6 +125,104 @@ __device__ __forceinline__ void tc_issue_kblock(uint32_t tmem, uint32_t sbase, i
 
 // Selection among three values by a small runtime index (no local memory).
 __device__ __forceinline__ float sel3(int i, float a, float b, float c) { return i == 0 ? a : (i == 1 ? b : c); }
+
+// Block assembly for round r (0..3). Lane (mloc, alpha) holds row alpha of model mloc's
+// 3 x 32 strip (3 x 3 blocks of B models 0..9 at columns 3 b' + beta, plus 2 pad columns).
+// In round r it gathers the whole block of B model 3 r + alpha: its own row from column
+// group alpha and the two other rows by shuffles from the model's other two lanes, in the
+// cyclic row order alpha, alpha + 1, alpha + 2 (a proper rotation of the rows, which
+// leaves eq. 2 unchanged).
+__device__ __forceinline__ void assemble_from_cand(const float (&cand)[3][3], int alpha, int mloc, float blk[9])
+{
+#pragma unroll
+    for (int be = 0; be < 3; ++be) blk[be] = sel3(alpha, cand[0][be], cand[1][be], cand[2][be]);
+#pragma unroll
+    for (int kk = 1; kk <= 2; ++kk) {
+        const int sendsel = (alpha + 3 - kk) % 3;
+        const int src = 3 * mloc + (alpha + kk) % 3;
+#pragma unroll
+        for (int be = 0; be < 3; ++be)
+            blk[3 * kk + be] = __shfl_sync(0xffffffffu, sel3(sendsel, cand[0][be], cand[1][be], cand[2][be]), src & 31);
+    }
+}
+
+__device__ __forceinline__ void assemble_block(const float V[32], int r, int alpha, int mloc, float blk[9])
+{
+    float cand[3][3];
+#pragma unroll
+    for (int al = 0; al < 3; ++al)
+#pragma unroll
+        for (int be = 0; be < 3; ++be) {
+            const int j = 9 * r + 3 * al + be;
+            cand[al][be] = (j < 32) ? V[j] : 0.f;
+        }
+    assemble_from_cand(cand, alpha, mloc, blk);
+}
+
+// Queue the flagged pairs of round r (warp-uniform, runtime): the round's 9 columns of each
+// of the four exact classes (36 single-column TMEM loads, one wait), assembled like the
+// fast path's blocks; lanes with need set write their entry. Out of line: it runs in about
+// a quarter of the rounds and keeps the fast path's code small.
+__device__ __noinline__ void queue_round(uint32_t trow, int r, int alpha, int mloc, bool need, QEntry *e, int a, int b,
+                                         float s)
+{
+    uint32_t u[4][9];
+#pragma unroll
+    for (int c4 = 0; c4 < 4; ++c4)
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int col = 9 * r + k;
+            u[c4][k] = (col < 32) ? tmem_ld1_issue(trow + 64 * c4 + col) : 0u;
+        }
+    tmem_wait_ld();
+#pragma unroll
+    for (int c4 = 0; c4 < 4; ++c4) {
+        tmem_pin9(u[c4]);
+        float cand[3][3];
+#pragma unroll
+        for (int al = 0; al < 3; ++al)
+#pragma unroll
+            for (int be = 0; be < 3; ++be) cand[al][be] = __uint_as_float(u[c4][3 * al + be]);
+        float bv[9];
+        assemble_from_cand(cand, alpha, mloc, bv);
+        if (need) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) e->v[9 * c4 + k] = bv[k];
+        }
+    }
+    if (need) {
+        e->a = a;
+        e->b = b;
+        e->alpha = alpha;
+        e->s = s;
+    }
+}
+
+// FP64 recomputation of one queued pair from its four exact digit classes (kept out of
+// line: it runs for about one pair in a hundred and would otherwise crowd the
+// instruction cache of the fast path).
+__device__ __noinline__ void refine_queued(const QEntry *qe, const float *__restrict__ scales,
+                                           const double *__restrict__ G64, double invL, int64_t N,
+                                           float *__restrict__ out, int64_t out_base)
+{
+    const int64_t aa = qe->a, bb = qe->b;
+    const int al0 = qe->alpha;
+    double H[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int ax = al0 + i - (al0 + i >= 3 ? 3 : 0);
+        const double sr = (double)scales[aa * 3 + ax];
+#pragma unroll
+        for (int be = 0; be < 3; ++be) {
+            const int kk = 3 * i + be;
+            const double v = 65536.0 * (double)qe->v[kk] + 256.0 * ((double)qe->v[9 + kk] + (double)qe->v[18 + kk]) +
+                             (double)qe->v[27 + kk];
+            H[kk] = v * (sr * (double)scales[bb * 3 + be]);
+        }
+    }
+    const float c = crmsd_refine_newton_fp64(H, G64[aa], G64[bb], invL, qe->s);
+    out[condensed_idx(aa, bb, N) - out_base] = c;
+}
 
 template <int LAYOUT>
 __global__ void __launch_bounds__(FW_THREADS, 1)
@@ -167,13 +277,13 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
             tma_prefetch_desc(&mapA);
             tma_prefetch_desc(&mapB);
             int64_t q = 0;
-            for (int64_t t = blockIdx.x; t < ntiles && !*abort_v; t += gridDim.x) {
-                int64_t I, J;
-                tc_decode(tile0 + t, TB, TA, &I, &J);
+            int64_t I, J;
+            tc_decode(tile0 + blockIdx.x, TB, TA, &I, &J);
+            for (int64_t t = blockIdx.x; t < ntiles && !*abort_v; t += gridDim.x, tc_advance(I, J, gridDim.x, TB, TA)) {
                 for (int kb = 0; kb < nkb; ++kb, ++q) {
                     const int s = (int)(q % FW_STAGES);
                     const int64_t use = q / FW_STAGES;
-                    if (q >= FW_STAGES && !mbar_wait(&empty_bar[s], (uint32_t)((use - 1) & 1))) {
+                    if (q >= FW_STAGES && !mbar_wait_sleep(&empty_bar[s], (uint32_t)((use - 1) & 1))) {
                         atomicExch(&abort_flag, 1);
                         break;
                     }
@@ -214,7 +324,7 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                 for (int kb = 0; kb < nkb; ++kb, ++q) {
                     const int s = (int)(q % FW_STAGES);
                     const int64_t use = q / FW_STAGES;
-                    if (!mbar_wait(&full_bar[s], (uint32_t)(use & 1))) {
+                    if (!mbar_wait_sleep(&full_bar[s], (uint32_t)(use & 1))) {
                         ok = false;
                         break;
                     }
@@ -238,39 +348,31 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
         const int sp = warp & 3, g = ew >> 2;
         const int mloc = lane / 3, alpha = lane - 3 * (lane / 3);
         const float invL = 1.f / (float)L;
+        const double invL64 = 1.0 / (double)L;
         QEntry *queue = queues + ew * FW_QCAP;
         int qn = 0;  // entries in this warp's queue (warp-uniform)
 
-        // FP64 recomputation of one queued pair from its four exact digit classes
-        auto refine_entry = [&](const QEntry &qe) {
-            const int64_t aa = qe.a, bb = qe.b;
-            double H[9];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const double sr = (double)scales[aa * 3 + (qe.alpha + i) % 3];
-#pragma unroll
-                for (int be = 0; be < 3; ++be) {
-                    const int kk = 3 * i + be;
-                    const double v = 65536.0 * (double)qe.v[kk] +
-                                     256.0 * ((double)qe.v[9 + kk] + (double)qe.v[18 + kk]) + (double)qe.v[27 + kk];
-                    H[kk] = v * (sr * (double)scales[bb * 3 + be]);
-                }
-            }
-            const double c = crmsd_refined_fp64(H, G64[aa], G64[bb], 1.0 / (double)L, (double)qe.s, true);
-            out[condensed_idx(aa, bb, N) - out_base] = (float)c;
-        };
-
         int64_t k = 0;
-        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
-            int64_t I, J;
-            tc_decode(tile0 + t, TB, TA, &I, &J);
-            const int64_t a_base = I * TC_MA, b_base = J * TC_MB;
-            const int64_t a = a_base + 10 * sp + mloc;
-            const bool lane_ok = lane < 30 && a < N;
+        int64_t I, J;
+        tc_decode(tile0 + blockIdx.x, TB, TA, &I, &J);
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++k, tc_advance(I, J, gridDim.x, TB, TA)) {
+            // lane (mloc, alpha): row = axis alpha of A model a; in round r its pair is (a, b0 + 3 r)
+            const int64_t a = I * TC_MA + 10 * sp + mloc;
+            const int64_t b0 = J * TC_MB + 10 * g + alpha;
+            const bool lane_ok = lane < 30 && a < N && a >= row_begin && a < row_end;
+            const int64_t rowbase = a * N - a * (a + 1) / 2 - a - 1 - out_base;  // condensed index - b
             float srow0 = 1.f, Ga = 0.f;
             if (lane_ok) {
                 srow0 = scales[a * 3 + alpha];
                 Ga = G32[a];
+            }
+            bool pok[4];
+            float Gb[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int64_t b = b0 + 3 * r;
+                pok[r] = lane_ok && (3 * r + alpha) < 10 && b < N && a < b;
+                Gb[r] = pok[r] ? __ldg(G32 + b) : 0.f;
             }
             const int buf = (int)(k & 1);
             const bool okw = mbar_wait_sleep(&tfull_bar[buf], (uint32_t)((k >> 1) & 1));
@@ -284,20 +386,24 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
             {
                 float tt[32];
                 if (LAYOUT == TC_EXACT2) {
-                    tmem_ld32(trow + 0, V);
+                    // two classes per wait: hh and hl, then lh and ll
+                    uint32_t u0[32], u1[32];
+                    tmem_ld32_issue(trow + 0, u0);
+                    tmem_ld32_issue(trow + 64, u1);
+                    tmem_wait_ld();
+                    tmem_pin32(u0);
+                    tmem_pin32(u1);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) V[j] *= 65536.f;
-                    tmem_ld32(trow + 64, tt);
+                    for (int j = 0; j < 32; ++j) V[j] = fmaf(256.f, __uint_as_float(u1[j]), 65536.f * __uint_as_float(u0[j]));
+                    tmem_ld32_issue(trow + 128, u0);
+                    tmem_ld32_issue(trow + 192, u1);
+                    tmem_wait_ld();
+                    tmem_pin32(u0);
+                    tmem_pin32(u1);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) V[j] = fmaf(256.f, tt[j], V[j]);
-                    tmem_ld32(trow + 128, tt);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) V[j] = fmaf(256.f, tt[j], V[j]);
-                    tmem_ld32(trow + 192, tt);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) V[j] += tt[j];
+                    for (int j = 0; j < 32; ++j) V[j] = fmaf(256.f, __uint_as_float(u0[j]), V[j]) + __uint_as_float(u1[j]);
                     // column j of this warp's 32 is (model b_base + 10 g + j / 3, axis j % 3)
-                    const float cs = (lane < 30) ? __ldg(scales + (b_base + 10 * g) * 3 + lane) : 1.f;
+                    const float cs = (lane < 30) ? __ldg(scales + (J * TC_MB + 10 * g) * 3 + lane) : 1.f;
 #pragma unroll
                     for (int j = 0; j < 30; ++j) V[j] *= srow0 * __shfl_sync(0xffffffffu, cs, j);
                 } else if (LAYOUT == TC_BF16X3) {
@@ -312,92 +418,43 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                     tmem_ld32(trow + 0, V);
                 }
             }
-#pragma unroll
+            // one round at a time (a compact loop: the fast path's code size, not its latency,
+            // limits this kernel); after each round V shifts down by the round's 9 columns
+#pragma unroll 1
             for (int r = 0; r < 4; ++r) {
-                float cand[3][3];
-#pragma unroll
-                for (int al = 0; al < 3; ++al)
-#pragma unroll
-                    for (int be = 0; be < 3; ++be) {
-                        const int j = 9 * r + 3 * al + be;
-                        cand[al][be] = (j < 32) ? V[j] : 0.f;
-                    }
                 float blk[9];
-#pragma unroll
-                for (int be = 0; be < 3; ++be) blk[be] = sel3(alpha, cand[0][be], cand[1][be], cand[2][be]);
-#pragma unroll
-                for (int kk = 1; kk <= 2; ++kk) {
-                    const int sendsel = (alpha + 3 - kk) % 3;
-                    const int src = 3 * mloc + (alpha + kk) % 3;
-#pragma unroll
-                    for (int be = 0; be < 3; ++be)
-                        blk[3 * kk + be] = __shfl_sync(0xffffffffu, sel3(sendsel, cand[0][be], cand[1][be], cand[2][be]),
-                                                       src & 31);
-                }
-                const int bq = 3 * r + alpha;
-                const int64_t b = b_base + 10 * g + bq;
-                const bool pair_ok = lane_ok && bq < 10 && b < N && a < b && a >= row_begin && a < row_end;
+                assemble_block(V, 0, alpha, mloc, blk);
+                float sv, ev;
+                const float cv = crmsd_fast_fp32(blk, Ga, Gb[0], invL, &sv, &ev);
+                const int64_t b = b0 + 3 * r;
                 bool need = false;
-                float sfast = 1.f;
-                if (pair_ok) {
-                    float errc2;
-                    const float Gb = __ldg(G32 + b);
-                    const float c = crmsd_fast_fp32(blk, Ga, Gb, invL, &sfast, &errc2);
-                    if (LAYOUT == TC_EXACT2 && !(errc2 <= 2.f * CLUSCO_TOL_FAST * c)) {
+                if (pok[0]) {
+                    if (LAYOUT == TC_EXACT2 && !(ev <= 2.f * CLUSCO_TOL_FAST * cv)) {
                         need = true;
                     } else {
-                        out[condensed_idx(a, b, N) - out_base] =
-                            (isnan(Ga) || isnan(Gb)) ? __int_as_float(0x7fc00000) : c;
+                        out[rowbase + b] = (isnan(Ga) || isnan(Gb[0])) ? __int_as_float(0x7fc00000) : cv;
                     }
                 }
                 if (LAYOUT == TC_EXACT2) {
                     const unsigned m = __ballot_sync(0xffffffffu, need);
                     if (m) {
-                        // re-read the four exact classes of this round's columns; queue the flagged pairs
                         const int slot = qn + __popc(m & ((1u << lane) - 1u));
-#pragma unroll
-                        for (int c4 = 0; c4 < 4; ++c4) {
-                            float tt[32];
-                            tmem_ld32(trow + 64 * c4, tt);
-                            float cc[3][3];
-#pragma unroll
-                            for (int al = 0; al < 3; ++al)
-#pragma unroll
-                                for (int be = 0; be < 3; ++be) {
-                                    const int j = 9 * r + 3 * al + be;
-                                    cc[al][be] = (j < 32) ? tt[j] : 0.f;
-                                }
-                            float bv[9];
-#pragma unroll
-                            for (int be = 0; be < 3; ++be) bv[be] = sel3(alpha, cc[0][be], cc[1][be], cc[2][be]);
-#pragma unroll
-                            for (int kk = 1; kk <= 2; ++kk) {
-                                const int sendsel = (alpha + 3 - kk) % 3;
-                                const int src = 3 * mloc + (alpha + kk) % 3;
-#pragma unroll
-                                for (int be = 0; be < 3; ++be)
-                                    bv[3 * kk + be] = __shfl_sync(
-                                        0xffffffffu, sel3(sendsel, cc[0][be], cc[1][be], cc[2][be]), src & 31);
-                            }
-                            if (need) {
-#pragma unroll
-                                for (int e = 0; e < 9; ++e) queue[slot].v[9 * c4 + e] = bv[e];
-                            }
-                        }
-                        if (need) {
-                            queue[slot].a = (int)a;
-                            queue[slot].b = (int)b;
-                            queue[slot].alpha = alpha;
-                            queue[slot].s = sfast;
-                        }
+                        queue_round(trow, r, alpha, mloc, need, queue + slot, (int)a, (int)b, sv);
                         qn += __popc(m);
                         if (qn >= 32) {  // a full batch: every FP64 instruction runs on 32 lanes
                             __syncwarp();
-                            refine_entry(queue[qn - 32 + lane]);
+                            refine_queued(queue + (qn - 32 + lane), scales, G64, invL64, N, out, out_base);
                             __syncwarp();
                             qn -= 32;
                         }
                     }
+                }
+#pragma unroll
+                for (int j = 0; j < 32; ++j) V[j] = (j + 9 < 32) ? V[j + 9] : 0.f;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    Gb[i] = Gb[i + 1];
+                    pok[i] = pok[i + 1];
                 }
             }
             // the accumulator buffer is drained: hand it back to the MMA warp
@@ -407,7 +464,7 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
         }
         if (LAYOUT == TC_EXACT2 && qn > 0) {
             __syncwarp();
-            if (lane < qn) refine_entry(queue[lane]);
+            if (lane < qn) refine_queued(queue + lane, scales, G64, invL64, N, out, out_base);
             __syncwarp();
         }
     }
