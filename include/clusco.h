@@ -132,6 +132,18 @@ int clusco_crmsd_allpairs_backward(const float *coords, int64_t N, int64_t L, co
                                    const float *crmsd, float *grad_coords, float eps, int form,
                                    void *workspace, size_t workspace_bytes, void *stream);
 
+/* Kernel timing for benchmarks (no counterpart in the paper). While enabled, every launch
+ * of the all-pairs tensor-core kernel (CLUSCO_KERNEL_PAIRS) or of the adjoint kernel
+ * (CLUSCO_KERNEL_ADJOINT) is bracketed by two CUDA events recorded on the launch's own
+ * stream. clusco_profile_enable(1) starts a fresh window (unread brackets are dropped),
+ * clusco_profile_enable(0) stops recording. clusco_profile_read waits for the kernel's
+ * recorded brackets, returns their summed duration (ms) and count, and frees them.
+ * Host-side state shared by all threads; EINVAL for an unknown kernel id or null output. */
+#define CLUSCO_KERNEL_PAIRS 0
+#define CLUSCO_KERNEL_ADJOINT 1
+int clusco_profile_enable(int on);
+int clusco_profile_read(int kernel, double *total_ms, long long *launches);
+
 /* Synchronise stream, return the device status word (CLUSCO_OK if clean) and clear it. */
 int clusco_sync_status(void *stream);
 

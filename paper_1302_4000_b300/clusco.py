@@ -36,7 +36,9 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EOVE
 
 EXPORTS = ("clusco_version", "clusco_workspace_bytes", "clusco_crmsd_allpairs", "clusco_crmsd_allpairs_panel",
            "clusco_crmsd_vs_ref", "clusco_crmsd_vs_ref_noalloc", "clusco_crmsd_allpairs_backward",
-           "clusco_sync_status", "clusco_last_error")
+           "clusco_sync_status", "clusco_last_error", "clusco_profile_enable", "clusco_profile_read")
+KERNEL_PAIRS = 0
+KERNEL_ADJOINT = 1
 NOALLOC_MAX_L = 16384
 
 _lib = None
@@ -69,9 +71,12 @@ def load(path: str = LIB_PATH):
             lib.clusco_crmsd_allpairs_backward.argtypes = [vp, i64, i64, vp, vp, vp, ctypes.c_float, ctypes.c_int,
                                                            vp, sz, vp]
             lib.clusco_sync_status.argtypes = [vp]
+            lib.clusco_profile_enable.argtypes = [ctypes.c_int]
+            lib.clusco_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                                ctypes.POINTER(ctypes.c_longlong)]
             for f in ("clusco_crmsd_allpairs", "clusco_crmsd_allpairs_panel", "clusco_crmsd_vs_ref",
-                      "clusco_crmsd_vs_ref_noalloc",
-                      "clusco_crmsd_allpairs_backward", "clusco_sync_status"):
+                      "clusco_crmsd_vs_ref_noalloc", "clusco_crmsd_allpairs_backward", "clusco_sync_status",
+                      "clusco_profile_enable", "clusco_profile_read"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -98,6 +103,18 @@ def _coords(coords: torch.Tensor):
 
 def version() -> int:
     return load().clusco_version()
+
+
+def profile_enable(on: bool = True) -> None:
+    """Start (True) or stop (False) bracketing the tensor-core kernels' launches with events."""
+    _check(load().clusco_profile_enable(1 if on else 0))
+
+
+def profile_read(kernel: int):
+    """(total ms, launches) of the given kernel's bracketed launches since profile_enable(True)."""
+    ms, n = ctypes.c_double(), ctypes.c_longlong()
+    _check(load().clusco_profile_read(kernel, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
 
 
 def workspace_bytes(op: int, N: int, L: int, form: int = FORM_BF16_EXACT2) -> int:

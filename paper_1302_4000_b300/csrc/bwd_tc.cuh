@@ -18,9 +18,10 @@
 //     about 2^-21 relative per product);
 //   warps 2-9 (epilogue): read tile J's covariance from TMEM (then release it to GEMM1 of
 //     J+1), assemble each 3x3 block (rows cyclic, as in the forward), take Sigma from the
-//     FP32 fast path and the rotation from Horn's quaternion form, undo the cyclic order and
-//     write w~ R as two TF32 parts into a shared 128 x 64 operand in the 128-byte-swizzled
-//     K-major layout; pairs below the near-duplicate threshold go to the FP64 direct kernel.
+//     FP32 fast path and the rotation with it (dSigma/dM from the quartic, with Horn's
+//     quaternion form only near a double root), undo the cyclic order and write w~ R as two
+//     TF32 parts into a shared 128 x 64 operand in the 128-byte-swizzled K-major layout;
+//     pairs below the near-duplicate threshold go to the FP64 direct kernel.
 // So tile J's rotations overlap GEMM1 of J+1 and GEMM2 of J-1. Rotations live only in shared
 // memory. At the end the epilogue reads the sum out of TMEM into the CTA's partial-gradient
 // slice (negated); bwd_reduce_kernel adds the partials of the S column ranges, the diagonal
@@ -129,6 +130,17 @@ __global__ void __launch_bounds__(256) bt_transpose_kernel(const float *__restri
         xT[(int64_t)(i0 + k) * Rpad + r0 + tx] = hi;
         xT[((int64_t)Lp + i0 + k) * Rpad + r0 + tx] = tf32_rna(v - hi);
     }
+}
+
+// Horn's eigenvector route for the rare near-double-root blocks (out of line).
+__device__ __noinline__ void horn_rotation_ool(const float *Hn, float *R)
+{
+    float H[9], Rl[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) H[e] = Hn[e];
+    horn_rotation(H, sigma_hat_f32(H), Rl);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) R[e] = Rl[e];
 }
 
 __global__ void __launch_bounds__(BT_THREADS, 1)
@@ -431,7 +443,7 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
                         float Hn[9], Rp[9];
 #pragma unroll
                         for (int e = 0; e < 9; ++e) Hn[e] = blk[e] * nrm;
-                        horn_rotation(Hn, sigma_hat_f32(Hn), Rp);
+                        if (!sigma_rotation_f32(Hn, Rp)) horn_rotation_ool(Hn, Rp);
                         const float coef = __fdividef(w, (float)L * fmaxf(c, eps));
 #pragma unroll
                         for (int i = 0; i < 3; ++i) {
@@ -574,10 +586,12 @@ inline int bt_launch(const float *coords, int64_t N, int64_t L, const float *gra
     const unsigned grid = (unsigned)(TA * w.S);
     e = cudaFuncSetAttribute(bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BT_SMEM);
     if (e == cudaSuccess) {
+        prof_mark(PROF_ADJOINT, st);
         bwd_tc_kernel<<<grid, BT_THREADS, BT_SMEM, st>>>(mA, mB, mX, w.scales, w.G32, N, (int)L, (int)w.Lp, nkb,
                                                          w.Rpad, TB, w.S, JC, crmsd, grad_out, eps, w.Gp, w.dp,
                                                          w.nd_list, w.nd_count, w.nd_cap);
         e = cudaGetLastError();
+        prof_mark(PROF_ADJOINT, st);
     }
     if (e == cudaSuccess) {
         bwd_reduce_kernel<<<(unsigned)((N + 7) / 8), 256, 0, st>>>(w.Gp, w.dp, w.xf, N, (int)L, (int)w.Lp, w.Rpad,

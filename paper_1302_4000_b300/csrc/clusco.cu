@@ -376,6 +376,50 @@ int clusco_crmsd_vs_ref_noalloc(const float *coords, int64_t N, int64_t L, const
     return CLUSCO_OK;
 }
 
+int clusco_profile_enable(int on)
+{
+    g_last_error.clear();
+    clusco::ProfState &p = clusco::prof_state();
+    std::lock_guard<std::mutex> g(p.m);
+    if (on) {  // a fresh window: drop whatever an earlier window left unread
+        for (auto &v : p.ev) {
+            for (cudaEvent_t e : v) cudaEventDestroy(e);
+            v.clear();
+        }
+    }
+    p.on.store(on != 0);
+    return CLUSCO_OK;
+}
+
+int clusco_profile_read(int kernel, double *total_ms, long long *launches)
+{
+    g_last_error.clear();
+    if (kernel < 0 || kernel >= clusco::PROF_KINDS || !total_ms || !launches)
+        return fail(CLUSCO_EINVAL, "clusco_profile_read: bad kernel id or null output");
+    clusco::ProfState &p = clusco::prof_state();
+    std::lock_guard<std::mutex> g(p.m);
+    std::vector<cudaEvent_t> &v = p.ev[kernel];
+    double tot = 0.0;
+    long long n = 0;
+    int rc = CLUSCO_OK;
+    for (size_t i = 0; i + 1 < v.size(); i += 2) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(v[i + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, v[i], v[i + 1]);
+        if (e != cudaSuccess) {
+            rc = fail(CLUSCO_ECUDA, "clusco_profile_read: %s", cudaGetErrorString(e));
+            break;
+        }
+        tot += ms;
+        ++n;
+    }
+    for (cudaEvent_t e : v) cudaEventDestroy(e);
+    v.clear();
+    *total_ms = tot;
+    *launches = n;
+    return rc;
+}
+
 int clusco_sync_status(void *stream)
 {
     g_last_error.clear();

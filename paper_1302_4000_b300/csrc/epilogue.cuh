@@ -239,6 +239,63 @@ __device__ __forceinline__ float sigma_hat_f32(const float m[9])
     return quartic_newton_f(sigma_cubic_f(I1, det, I2), I1, det, I2, 2, &deg, &dP);
 }
 
+// Sigma and the optimal rotation together, FP32, for a normalised covariance m (row-major).
+// The rotation maximises <R, m> over SO(3) with maximum Sigma, so by the envelope theorem it
+// is dSigma/dm; Sigma is the largest root of P(x; I1, I2, det) = 0 (the quartic above), and
+// implicit differentiation with dI1/dm = 2 m, dI2/dm = 2 I1 m - 2 m m^T m, ddet/dm = cof(m)
+// gives
+//   R = [4 (I1 + Sigma^2) m - 8 m m^T m + 8 Sigma cof(m)] / P'(Sigma),
+//   P'(Sigma) = 4 Sigma^3 - 4 I1 Sigma - 8 det.
+// The cofactors are the 2x2 minors that I2 and det are built from. Returns false, leaving R
+// unset, where P' falls below 1e-2 of 8 Sigma^3 (near a double root, where this quotient
+// loses accuracy); the caller then takes Horn's eigenvector route.
+__device__ __forceinline__ bool sigma_rotation_f32(const float m[9], float R[9])
+{
+    const float a01 = m[3] * m[7] - m[4] * m[6];
+    const float a02 = m[3] * m[8] - m[5] * m[6];
+    const float a12 = m[4] * m[8] - m[5] * m[7];
+    const float b01 = m[0] * m[7] - m[1] * m[6];
+    const float b02 = m[0] * m[8] - m[2] * m[6];
+    const float b12 = m[1] * m[8] - m[2] * m[7];
+    const float c01 = m[0] * m[4] - m[1] * m[3];
+    const float c02 = m[0] * m[5] - m[2] * m[3];
+    const float c12 = m[1] * m[5] - m[2] * m[4];
+    const float det = m[0] * a12 - m[1] * a02 + m[2] * a01;
+    const float I2 = a01 * a01 + a02 * a02 + a12 * a12 + b01 * b01 + b02 * b02 + b12 * b12 + c01 * c01 +
+                     c02 * c02 + c12 * c12;
+    float I1 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) I1 = fmaf(m[k], m[k], I1);
+    bool deg;
+    float dPn;
+    const float s = quartic_newton_f(sigma_cubic_f(I1, det, I2), I1, det, I2, 2, &deg, &dPn);
+    const float s2 = s * s;
+    const float dP = fmaf(fmaf(4.f, s2, -4.f * I1), s, -8.f * det);
+    if (deg || !(dP > 8e-2f * s2 * s)) return false;
+    // cofactor matrix (signed minors), row-major
+    const float cf[9] = {a12, -a02, a01, -b12, b02, -b01, c12, -c02, c01};
+    // g = m^T m (symmetric)
+    const float g00 = m[0] * m[0] + m[3] * m[3] + m[6] * m[6];
+    const float g01 = m[0] * m[1] + m[3] * m[4] + m[6] * m[7];
+    const float g02 = m[0] * m[2] + m[3] * m[5] + m[6] * m[8];
+    const float g11 = m[1] * m[1] + m[4] * m[4] + m[7] * m[7];
+    const float g12 = m[1] * m[2] + m[4] * m[5] + m[7] * m[8];
+    const float g22 = m[2] * m[2] + m[5] * m[5] + m[8] * m[8];
+    const float inv = __fdividef(1.f, dP);
+    const float al = 4.f * (I1 + s2) * inv, be = 8.f * s * inv, ga = -8.f * inv;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float r0 = m[3 * i], r1 = m[3 * i + 1], r2 = m[3 * i + 2];
+        const float mg0 = r0 * g00 + r1 * g01 + r2 * g02;
+        const float mg1 = r0 * g01 + r1 * g11 + r2 * g12;
+        const float mg2 = r0 * g02 + r1 * g12 + r2 * g22;
+        R[3 * i + 0] = fmaf(al, r0, fmaf(ga, mg0, be * cf[3 * i + 0]));
+        R[3 * i + 1] = fmaf(al, r1, fmaf(ga, mg1, be * cf[3 * i + 1]));
+        R[3 * i + 2] = fmaf(al, r2, fmaf(ga, mg2, be * cf[3 * i + 2]));
+    }
+    return true;
+}
+
 // FP32 fast path on a rounded covariance: cubic start + two Newton steps, all FP32.
 // Returns cRMSD and, through err_c2, a bound on the absolute error of cRMSD^2 from FP32
 // rounding. The bound follows the root's conditioning: the quartic is evaluated with an

@@ -34,6 +34,7 @@
 #include "common.cuh"
 #include "epilogue.cuh"
 #include "prepass.cuh"
+#include "prof.cuh"
 #include "ptx.cuh"
 
 #ifndef CLUSCO_TOL_FAST
@@ -56,16 +57,25 @@ struct TcArgs {
 constexpr uint32_t STAGE_BYTES_BF16 = 2 * 16384 + 2 * 8192;  // A_h, A_l, B_h, B_l
 constexpr uint32_t STAGE_BYTES_TF32 = 16384 + 8192;          // A, B
 // Persistent forward kernel: 1 CTA per SM, warp 0 TMA, warp 1 MMA, warps 2-9 epilogue.
-constexpr int FW_THREADS = 320;
-constexpr int FW_STAGES = 3;
-constexpr int FW_QCAP = 64;  // refinement queue entries per epilogue warp (flushed at 32)
+#ifndef CLUSCO_FW_EGROUPS
+#define CLUSCO_FW_EGROUPS 1  // epilogue warp groups of 8; with 2, each group owns one TMEM buffer
+#endif
+constexpr int FW_EGROUPS = CLUSCO_FW_EGROUPS;
+constexpr int FW_THREADS = 64 + 256 * FW_EGROUPS;
+constexpr int FW_STAGES = FW_EGROUPS == 2 ? 2 : 3;
+constexpr int FW_QCAP = 62;  // refinement queue entries per epilogue warp: flushed at 32, a round adds <= 30
+// A queued pair: its 3x3 block's exact digit classes as integers (hh, hl + lh, ll; rows in
+// the cyclic order of the lane that owned the pair), the pair, that lane's axis and the
+// FP32 Sigma_hat.
 struct QEntry {
-    float v[36];  // class-major raw class values of the 3x3 block (rows cyclic from alpha)
+    int n[27];
     int a, b, alpha;
     float s;
+    int pad;
 };
-static_assert(sizeof(QEntry) == 160, "queue entry layout");
-constexpr size_t FW_SMEM = 1024 + FW_STAGES * STAGE_BYTES_BF16 + 8 * FW_QCAP * sizeof(QEntry);
+static_assert(sizeof(QEntry) == 128, "queue entry layout");
+constexpr size_t FW_SMEM = 1024 + FW_STAGES * STAGE_BYTES_BF16 + 8 * FW_EGROUPS * FW_QCAP * sizeof(QEntry);
+static_assert(FW_SMEM <= 227 * 1024, "shared memory per CTA");
 
 __host__ __device__ __forceinline__ int64_t tc_row_start(int64_t I, int64_t TB) { return I * TB - I * (I - 1); }
 
@@ -175,6 +185,7 @@ __device__ __noinline__ void queue_round(uint32_t trow, int r, int alpha, int ml
             u[c4][k] = (col < 32) ? tmem_ld1_issue(trow + 64 * c4 + col) : 0u;
         }
     tmem_wait_ld();
+    float bv[4][9];
 #pragma unroll
     for (int c4 = 0; c4 < 4; ++c4) {
         tmem_pin9(u[c4]);
@@ -183,14 +194,16 @@ __device__ __noinline__ void queue_round(uint32_t trow, int r, int alpha, int ml
         for (int al = 0; al < 3; ++al)
 #pragma unroll
             for (int be = 0; be < 3; ++be) cand[al][be] = __uint_as_float(u[c4][3 * al + be]);
-        float bv[9];
-        assemble_from_cand(cand, alpha, mloc, bv);
-        if (need) {
-#pragma unroll
-            for (int k = 0; k < 9; ++k) e->v[9 * c4 + k] = bv[k];
-        }
+        assemble_from_cand(cand, alpha, mloc, bv[c4]);
     }
     if (need) {
+        // every class value is an integer below 2^24 in magnitude, so these conversions are exact
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            e->n[k] = __float2int_rn(bv[0][k]);
+            e->n[9 + k] = __float2int_rn(bv[1][k]) + __float2int_rn(bv[2][k]);
+            e->n[18 + k] = __float2int_rn(bv[3][k]);
+        }
         e->a = a;
         e->b = b;
         e->alpha = alpha;
@@ -215,8 +228,7 @@ __device__ __noinline__ void refine_queued(const QEntry *qe, const float *__rest
 #pragma unroll
         for (int be = 0; be < 3; ++be) {
             const int kk = 3 * i + be;
-            const double v = 65536.0 * (double)qe->v[kk] + 256.0 * ((double)qe->v[9 + kk] + (double)qe->v[18 + kk]) +
-                             (double)qe->v[27 + kk];
+            const double v = 65536.0 * (double)qe->n[kk] + 256.0 * (double)qe->n[9 + kk] + (double)qe->n[18 + kk];
             H[kk] = v * (sr * (double)scales[bb * 3 + be]);
         }
     }
@@ -343,19 +355,24 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
         }
         __syncwarp();
     } else {
-        // ================= epilogue warps 2..9 =================
+        // ================= epilogue warps 2.. (FW_EGROUPS groups of 8) =================
+        // group gp takes the CTA's tiles k = gp, gp + FW_EGROUPS, ...; within a group warp w
+        // reads TMEM lanes 32 (w % 4) .. + 31 (its lane quadrant) and column half g
         const int ew = warp - 2;
-        const int sp = warp & 3, g = ew >> 2;
+        const int gp = ew >> 3;
+        const int sp = warp & 3, g = (ew & 7) >> 2;
         const int mloc = lane / 3, alpha = lane - 3 * (lane / 3);
         const float invL = 1.f / (float)L;
         const double invL64 = 1.0 / (double)L;
         QEntry *queue = queues + ew * FW_QCAP;
         int qn = 0;  // entries in this warp's queue (warp-uniform)
 
-        int64_t k = 0;
+        const int64_t gstep = (int64_t)FW_EGROUPS * gridDim.x;
+        int64_t k = gp;
         int64_t I, J;
-        tc_decode(tile0 + blockIdx.x, TB, TA, &I, &J);
-        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++k, tc_advance(I, J, gridDim.x, TB, TA)) {
+        tc_decode(tile0 + blockIdx.x + (int64_t)gp * gridDim.x, TB, TA, &I, &J);
+        for (int64_t t = blockIdx.x + (int64_t)gp * gridDim.x; t < ntiles;
+             t += gstep, k += FW_EGROUPS, tc_advance(I, J, gstep, TB, TA)) {
             // lane (mloc, alpha): row = axis alpha of A model a; in round r its pair is (a, b0 + 3 r)
             const int64_t a = I * TC_MA + 10 * sp + mloc;
             const int64_t b0 = J * TC_MB + 10 * g + alpha;
@@ -419,11 +436,16 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                 }
             }
             // one round at a time (a compact loop: the fast path's code size, not its latency,
-            // limits this kernel); after each round V shifts down by the round's 9 columns
+            // limits this kernel)
 #pragma unroll 1
             for (int r = 0; r < 4; ++r) {
                 float blk[9];
-                assemble_block(V, 0, alpha, mloc, blk);
+                switch (r) {  // warp-uniform; compile-time column offsets in each case
+                    case 0: assemble_block(V, 0, alpha, mloc, blk); break;
+                    case 1: assemble_block(V, 1, alpha, mloc, blk); break;
+                    case 2: assemble_block(V, 2, alpha, mloc, blk); break;
+                    default: assemble_block(V, 3, alpha, mloc, blk); break;
+                }
                 float sv, ev;
                 const float cv = crmsd_fast_fp32(blk, Ga, Gb[0], invL, &sv, &ev);
                 const int64_t b = b0 + 3 * r;
@@ -449,8 +471,6 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                         }
                     }
                 }
-#pragma unroll
-                for (int j = 0; j < 32; ++j) V[j] = (j + 9 < 32) ? V[j + 9] : 0.f;
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
                     Gb[i] = Gb[i + 1];
@@ -548,10 +568,12 @@ inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
     }
     // persistent: one CTA per SM, CTA x takes tiles x, x + grid, x + 2 grid, ...
     const unsigned grid = (unsigned)std::min<int64_t>(nt, sms > 0 ? sms : 148);
+    prof_mark(PROF_PAIRS, st);
     pairs_tc_kernel<LAYOUT><<<grid, FW_THREADS, FW_SMEM, st>>>(mA, mB, a.scales, a.G64, a.G32, a.N, (int)a.L, nkb,
                                                                 a.Rpad, TA, TB, t0, nt, a.row_begin, a.row_end,
                                                                 a.out, a.out_base);
     e = cudaGetLastError();
+    prof_mark(PROF_PAIRS, st);
     if (e != cudaSuccess) {
         err = std::string("pairs_tc_kernel launch: ") + cudaGetErrorString(e);
         return CLUSCO_ECUDA;
