@@ -41,7 +41,7 @@ UNIT = "pairs/s"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--form", default=None, help="fp32_simt | tf32 | bf16x3 | bf16_exact2 (default: best built)")
