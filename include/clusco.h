@@ -72,7 +72,9 @@ typedef enum {
 typedef enum {
     CLUSCO_OP_ALLPAIRS = 0,
     CLUSCO_OP_VS_REF = 1,
-    CLUSCO_OP_BACKWARD = 2
+    CLUSCO_OP_BACKWARD = 2,
+    CLUSCO_OP_BACKWARD_ROT = 3,
+    CLUSCO_OP_ALLPAIRS_ROT = 4
 } clusco_op;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -143,6 +145,28 @@ int clusco_crmsd_allpairs_backward(const float *coords, int64_t N, int64_t L, co
 #define CLUSCO_KERNEL_ADJOINT 1
 int clusco_profile_enable(int on);
 int clusco_profile_read(int kernel, double *total_ms, long long *launches);
+
+/* The all-pairs matrix as clusco_crmsd_allpairs, plus each pair's optimal rotation for the
+ * adjoint: rot is float[N(N-1)/2][9] (device, caller-owned, 4-byte aligned), in the output's
+ * condensed order; rot[idx*9 + 3*i + j] = R_ab[i][j], the rotation of centred b onto centred
+ * a (natural axis order), which maximises sum_i a_i . R b_i. R is dSigma/dM of the eq. 2 sum
+ * Sigma (see clusco_crmsd_allpairs_backward_rot), FP32. Tensor-core forms only
+ * (CLUSCO_EUNSUPPORTED for CLUSCO_FORM_FP32_SIMT); workspace: CLUSCO_OP_ALLPAIRS_ROT bytes
+ * (the all-pairs workspace plus a list of the ~0.5% of pairs whose rotation is solved by
+ * Jacobi sweeps after the main kernel).
+ * No counterpart in the paper, which needs no rotation. */
+int clusco_crmsd_allpairs_rot(const float *coords, int64_t N, int64_t L, float *out, float *rot, int form,
+                              void *workspace, size_t workspace_bytes, void *stream);
+
+/* The adjoint of clusco_crmsd_allpairs_backward from the rotations a clusco_crmsd_allpairs_rot
+ * call stored (rot, same ensemble and order): no covariance or rotation is recomputed, so the
+ * call only gathers R_ab, c_ab and grad_out_ab and contracts on the tensor cores. Same result,
+ * tolerance and near-duplicate handling as clusco_crmsd_allpairs_backward. L <= 512 and an
+ * sm_103 device (else CLUSCO_EUNSUPPORTED); workspace: CLUSCO_OP_BACKWARD_ROT bytes.
+ * No counterpart in the paper, which gives no gradient. */
+int clusco_crmsd_allpairs_backward_rot(const float *coords, int64_t N, int64_t L, const float *grad_out,
+                                       const float *crmsd, const float *rot, float *grad_coords, float eps,
+                                       void *workspace, size_t workspace_bytes, void *stream);
 
 /* Synchronise stream, return the device status word (CLUSCO_OK if clean) and clear it. */
 int clusco_sync_status(void *stream);

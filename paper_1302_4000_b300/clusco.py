@@ -30,13 +30,16 @@ FORMS = {"fp32_simt": FORM_FP32_SIMT, "tf32": FORM_TF32, "bf16x3": FORM_BF16X3, 
 OP_ALLPAIRS = 0
 OP_VS_REF = 1
 OP_BACKWARD = 2
+OP_BACKWARD_ROT = 3
+OP_ALLPAIRS_ROT = 4
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EOVERFLOW",
           6: "ENONFINITE", 7: "EUNSUPPORTED"}
 
 EXPORTS = ("clusco_version", "clusco_workspace_bytes", "clusco_crmsd_allpairs", "clusco_crmsd_allpairs_panel",
            "clusco_crmsd_vs_ref", "clusco_crmsd_vs_ref_noalloc", "clusco_crmsd_allpairs_backward",
-           "clusco_sync_status", "clusco_last_error", "clusco_profile_enable", "clusco_profile_read")
+           "clusco_sync_status", "clusco_last_error", "clusco_profile_enable", "clusco_profile_read",
+           "clusco_crmsd_allpairs_rot", "clusco_crmsd_allpairs_backward_rot")
 KERNEL_PAIRS = 0
 KERNEL_ADJOINT = 1
 NOALLOC_MAX_L = 16384
@@ -71,12 +74,16 @@ def load(path: str = LIB_PATH):
             lib.clusco_crmsd_allpairs_backward.argtypes = [vp, i64, i64, vp, vp, vp, ctypes.c_float, ctypes.c_int,
                                                            vp, sz, vp]
             lib.clusco_sync_status.argtypes = [vp]
+            lib.clusco_crmsd_allpairs_rot.argtypes = [vp, i64, i64, vp, vp, ctypes.c_int, vp, sz, vp]
+            lib.clusco_crmsd_allpairs_backward_rot.argtypes = [vp, i64, i64, vp, vp, vp, vp, ctypes.c_float, vp, sz,
+                                                               vp]
             lib.clusco_profile_enable.argtypes = [ctypes.c_int]
             lib.clusco_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(ctypes.c_longlong)]
             for f in ("clusco_crmsd_allpairs", "clusco_crmsd_allpairs_panel", "clusco_crmsd_vs_ref",
                       "clusco_crmsd_vs_ref_noalloc", "clusco_crmsd_allpairs_backward", "clusco_sync_status",
-                      "clusco_profile_enable", "clusco_profile_read"):
+                      "clusco_profile_enable", "clusco_profile_read", "clusco_crmsd_allpairs_rot",
+                      "clusco_crmsd_allpairs_backward_rot"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -141,6 +148,24 @@ def crmsd_allpairs(coords: torch.Tensor, form: int = FORM_BF16_EXACT2, out: torc
     _check(load().clusco_crmsd_allpairs(coords.data_ptr(), N, L, out.data_ptr(), form, ws.data_ptr(), nb,
                                         _stream(stream)))
     return out
+
+
+def crmsd_allpairs_rot(coords: torch.Tensor, form: int = FORM_BF16_EXACT2, out: torch.Tensor | None = None,
+                       rot: torch.Tensor | None = None, workspace: torch.Tensor | None = None, stream=None):
+    """(matrix, rotations): the condensed cRMSD and each pair's R_ab as float32 [P, 3, 3]."""
+    coords = _coords(coords)
+    N, L = coords.shape[0], coords.shape[1]
+    P = N * (N - 1) // 2
+    if out is None:
+        out = torch.empty(P, dtype=torch.float32, device=coords.device)
+    if rot is None:
+        rot = torch.empty((P, 3, 3), dtype=torch.float32, device=coords.device)
+    assert out.is_cuda and out.dtype == torch.float32 and out.numel() >= P and out.is_contiguous()
+    assert rot.is_cuda and rot.dtype == torch.float32 and rot.numel() >= 9 * P and rot.is_contiguous()
+    ws, nb = _ws(workspace, OP_ALLPAIRS_ROT, N, L, form, coords.device)
+    _check(load().clusco_crmsd_allpairs_rot(coords.data_ptr(), N, L, out.data_ptr(), rot.data_ptr(), form,
+                                            ws.data_ptr(), nb, _stream(stream)))
+    return out, rot
 
 
 def crmsd_allpairs_panel(coords: torch.Tensor, row_begin: int, row_end: int, form: int = FORM_BF16_EXACT2,
@@ -212,6 +237,27 @@ def crmsd_allpairs_backward(coords: torch.Tensor, grad_out: torch.Tensor, crmsd:
     return grad_coords
 
 
+def crmsd_allpairs_backward_rot(coords: torch.Tensor, grad_out: torch.Tensor, crmsd: torch.Tensor,
+                                rot: torch.Tensor, eps: float = 1e-6, grad_coords: torch.Tensor | None = None,
+                                workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """The adjoint from the rotations crmsd_allpairs_rot stored (no covariance recomputation)."""
+    coords = _coords(coords)
+    N, L = coords.shape[0], coords.shape[1]
+    P = N * (N - 1) // 2
+    grad_out = grad_out.contiguous().to(torch.float32)
+    crmsd = crmsd.contiguous()
+    rot = rot.contiguous()
+    assert grad_out.numel() == P and crmsd.numel() == P and rot.numel() == 9 * P
+    assert grad_out.is_cuda and crmsd.is_cuda and rot.is_cuda
+    if grad_coords is None:
+        grad_coords = torch.empty_like(coords)
+    ws, nb = _ws(workspace, OP_BACKWARD_ROT, N, L, FORM_BF16_EXACT2, coords.device)
+    _check(load().clusco_crmsd_allpairs_backward_rot(coords.data_ptr(), N, L, grad_out.data_ptr(), crmsd.data_ptr(),
+                                                     rot.data_ptr(), grad_coords.data_ptr(), float(eps),
+                                                     ws.data_ptr(), nb, _stream(stream)))
+    return grad_coords
+
+
 def sync_status(stream=None) -> int:
     """Synchronise the stream and return the device status word (0 = clean); clears it."""
     rc = load().clusco_sync_status(_stream(stream))
@@ -221,17 +267,29 @@ def sync_status(stream=None) -> int:
 class CRMSDAllPairs(torch.autograd.Function):
     """Condensed all-pairs cRMSD with the library's hand-written adjoint."""
 
+    # With a tensor-core form and L <= 512 the forward also stores each pair's rotation
+    # (36 bytes per pair) and the backward contracts from it; otherwise the backward
+    # recomputes the covariances.
     @staticmethod
     def forward(ctx, coords, form: int, eps: float):
-        out = crmsd_allpairs(coords, form)
-        ctx.save_for_backward(coords, out)
-        ctx.form, ctx.eps = form, eps
+        store = ctx.needs_input_grad[0] and form != FORM_FP32_SIMT and coords.shape[1] <= 512
+        if store:
+            out, rot = crmsd_allpairs_rot(coords, form)
+            ctx.save_for_backward(coords, out, rot)
+        else:
+            out = crmsd_allpairs(coords, form)
+            ctx.save_for_backward(coords, out)
+        ctx.form, ctx.eps, ctx.store = form, eps, store
         return out
 
     @staticmethod
     def backward(ctx, grad_out):
-        coords, out = ctx.saved_tensors
-        g = crmsd_allpairs_backward(coords, grad_out, out, ctx.eps, ctx.form)
+        if ctx.store:
+            coords, out, rot = ctx.saved_tensors
+            g = crmsd_allpairs_backward_rot(coords, grad_out, out, rot, ctx.eps)
+        else:
+            coords, out = ctx.saved_tensors
+            g = crmsd_allpairs_backward(coords, grad_out, out, ctx.eps, ctx.form)
         return g, None, None
 
 

@@ -8,13 +8,16 @@
 // a contraction of the 3N x 3N block matrix of w~ R with the 3N x L coordinates.
 //
 // Rotations are recomputed here, never stored. Each CTA owns 32 models (rows) and sweeps
-// all 32-model column tiles: FP32 CUDA-core covariance of the tile, per-pair Horn
-// rotation (FP32) scaled by w~ into shared memory, then the contraction into the row
+// all 32-model column tiles: FP32 CUDA-core covariance of the tile, per-pair rotation
+// (FP32, dSigma/dM; Horn's adjugate near a double root, Jacobi sweeps where that is degenerate)
+// scaled by w~ into
+// shared memory, then the contraction into the row
 // block's gradient (kept in the workspace; the row block is owned by one CTA, so there
 // are no atomics). Pairs with c below CLUSCO_NEARDUP (A) are left out of that path: the
 // GEMM form a - R b cancels like |x|/c there, so they are queued and handled by a direct
-// FP64 residual kernel (recentred from the FP32 input, FP64 covariance, Horn rotation
-// with a Newton-polished eigenvalue, c recomputed from the residuals).
+// FP64 residual kernel (recentred from the FP32 input, FP64 covariance, Horn rotation with a
+// Newton-polished eigenvalue, Jacobi sweeps where the top eigenvalue is repeated, c
+// recomputed from the residuals).
 #pragma once
 #include "common.cuh"
 #include "epilogue.cuh"
@@ -164,7 +167,8 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
                         for (int e = 0; e < 9; ++e) Hn[e] = acc[i][j][e] * nrm;
                         float R[9];
-                        horn_rotation(Hn, s, R);
+                        if (!rotation_from_sigma_f32(Hn, s, R) && !horn_rotation(Hn, s, 1e-5f, R))
+                            rotation_jacobi4<float, 8>(Hn, R);
                         coef = w / ((float)L * fmaxf(c, eps));
 #pragma unroll
                         for (int e = 0; e < 9; ++e) P[e] = coef * R[e];
@@ -288,7 +292,7 @@ __global__ void __launch_bounds__(256) bwd_neardup_kernel(const float *__restric
             bool deg;
             double s = quartic_newton(sigma_cubic_d(I1, det, I2), I1, det, I2, 3, &deg);
             if (deg) s = sigma_cubic_d(I1, det, I2);
-            horn_rotation(m, s, R);
+            if (!horn_rotation(m, s, 1e-12, R)) rotation_jacobi4<double, 10>(m, R);
         }
         // residuals r_i = a_i - R b_i; c from the residuals; coefficient with the guard
         double rr = 0.0;

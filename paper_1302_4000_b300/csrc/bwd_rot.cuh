@@ -1,0 +1,357 @@
+// bwd_rot.cuh -- adjoint of the all-pairs matrix from stored rotations (tcgen05 contraction only).
+//
+// g_a = (sum_b w~_ab) a - sum_b (w~_ab R_ab) b,  w~ = w / (L max(c, eps))   (see backward.cuh)
+//
+// The forward can store each pair's optimal rotation R_ab (pairs_tc_kernel with ROT); then the
+// adjoint needs no covariance and no rotation arithmetic: per tile it only gathers R_ab (or
+// R_ba^T for the lower triangle), c_ab and w_ab, scales, and contracts. Same tiling as
+// bwd_tc_kernel: a CTA owns one A tile I (40 models = 128 operand rows) and a contiguous range
+// of B tiles J over the full square (every b != a in both orders, so no atomics on the
+// gradient). Roles:
+//   warp 0 (TMA): X_J^T hi / lo TF32 chunks of 64 atoms into a 3-stage ring;
+//   warp 1 (MMA): sum += P_J . X_J (tcgen05 kind::tf32, three passes hi.hi + hi.lo + lo.hi)
+//     into a TMEM accumulator of Lp <= 512 columns;
+//   warps 2-9 (epilogue): gather, build w~ R (two TF32 parts) in one of two shared 128 x 64
+//     operands (128-byte swizzle, K-major), so that tile J+1's operand is written while
+//     GEMM2 reads tile J's. Pairs below the near-duplicate threshold go to the FP64 direct
+//     kernel, as in the recompute path.
+// At the end the CTA's sum goes out of TMEM into its partial slice; bwd_reduce_kernel adds the
+// partials, the diagonal term and the centring projection.
+#pragma once
+#include "bwd_tc.cuh"
+
+namespace clusco {
+
+constexpr int BR_THREADS = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int BR_XSTAGES = 3;
+constexpr int BR_MAXLP = 512;
+constexpr size_t BR_SMEM = 1024 + 2 * BT_A2 + BR_XSTAGES * BT_XBUF;  // 1 KB + 128 KB + 96 KB
+static_assert(BR_SMEM <= 227 * 1024, "shared memory per CTA");
+
+__global__ void __launch_bounds__(BR_THREADS, 1)
+    bwd_rot_kernel(const __grid_constant__ CUtensorMap mapX, int64_t N, int L, int Lp, uint32_t tmem_cols,
+                   int64_t Rpad, int64_t TB, int64_t S, int64_t JC, const float *__restrict__ crmsd,
+                   const float *__restrict__ wvec, const float *__restrict__ rot, float eps, float *__restrict__ Gp,
+                   float *__restrict__ dp, long long *__restrict__ nd_list, unsigned long long *__restrict__ nd_count,
+                   int64_t nd_cap)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t xfull_bar[BR_XSTAGES];   // an X^T chunk landed
+    __shared__ __align__(8) uint64_t xempty_bar[BR_XSTAGES];  // GEMM2 has finished reading it
+    __shared__ __align__(8) uint64_t a2full_bar[2];           // a rotation operand is written (8 arrivals)
+    __shared__ __align__(8) uint64_t a2empty_bar[2];          // GEMM2 has finished reading it
+    __shared__ __align__(8) uint64_t d2_bar;                  // the last GEMM2 has finished
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    __shared__ float dsum[TC_MA];
+
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *A2 = smem;                // two operands of BT_A2 bytes: [hi 32 KB][lo 32 KB] each
+    uint8_t *XT = smem + 2 * BT_A2;    // BR_XSTAGES chunk buffers of BT_XBUF bytes
+    const uint32_t a2base = smem_u32(A2), xtbase = smem_u32(XT);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t I = blockIdx.x / S, sidx = blockIdx.x % S;
+    const int64_t J0 = sidx * JC, J1 = (J0 + JC < TB) ? J0 + JC : TB;
+    const int64_t a_base = I * TC_MA;
+    const int64_t Npad = Rpad / 32 * 10;
+
+    if (J0 >= J1) {  // an empty column range still owns its (zero) partial slice
+        float *gp = Gp + (sidx * Rpad + 128 * I) * (int64_t)Lp;
+        for (int e = tid; e < 128 * Lp; e += BR_THREADS) gp[e] = 0.f;
+        if (tid < TC_MA) dp[sidx * Npad + a_base + tid] = 0.f;
+        return;
+    }
+    if (warp == 0) {
+        tmem_alloc(&tmem_slot, tmem_cols);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int s = 0; s < BR_XSTAGES; ++s) {
+            mbar_init(&xfull_bar[s], 1);
+            mbar_init(&xempty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&a2full_bar[b], 8);
+            mbar_init(&a2empty_bar[b], 1);
+        }
+        mbar_init(&d2_bar, 1);
+        abort_flag = 0;
+        fence_barrier_init();
+        fence_proxy_async();
+    }
+    // pad rows and columns of both operands stay zero for the whole sweep
+    for (int e = tid; e < (int)(2 * BT_A2 / 16); e += BR_THREADS)
+        reinterpret_cast<float4 *>(A2)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid < TC_MA) dsum[tid] = 0.f;
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const int64_t nJ = J1 - J0;
+    const int nch = Lp / BT_XCH;
+    volatile int *abort_v = &abort_flag;
+
+    if (warp == 0) {
+        // ================= TMA producer: X^T chunks =================
+        if (lane == 0) {
+            int64_t c = 0;
+            bool ok = true;
+            for (int64_t j = 0; j < nJ && ok && !*abort_v; ++j) {
+                const int64_t J = J0 + j;
+                for (int ch = 0; ch < nch && ok; ++ch, ++c) {
+                    const int st = (int)(c % BR_XSTAGES);
+                    const int64_t use = c / BR_XSTAGES;
+                    if (c >= BR_XSTAGES && !mbar_wait_sleep(&xempty_bar[st], (uint32_t)((use - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&xfull_bar[st], (uint32_t)BT_XBUF);
+#pragma unroll
+                    for (int sp2 = 0; sp2 < 2; ++sp2)
+#pragma unroll
+                        for (int kb2 = 0; kb2 < 2; ++kb2)
+                            tma_load_2d(XT + st * BT_XBUF + (2 * sp2 + kb2) * (BT_XCH * 128), &mapX, &xfull_bar[st],
+                                        (int)(64 * J + 32 * kb2), (int)(sp2 * Lp + ch * BT_XCH));
+                }
+            }
+            if (!ok) atomicExch(&abort_flag, 1);
+            if (*abort_v) {
+                // loads still in flight must land before the CTA leaves (bounded waits)
+                for (int64_t r = (c > BR_XSTAGES ? c - BR_XSTAGES : 0); r < c; ++r)
+                    mbar_wait(&xfull_bar[r % BR_XSTAGES], (uint32_t)((r / BR_XSTAGES) & 1));
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ================= MMA issuer: GEMM2 only =================
+        if (lane == 0) {
+            int64_t c = 0;
+            bool ok = true;
+            constexpr uint32_t idx = make_idesc(128, BT_XCH, 2);
+            for (int64_t j = 0; j < nJ && ok && !*abort_v; ++j) {
+                const int buf = (int)(j & 1);
+                if (!mbar_wait_sleep(&a2full_bar[buf], (uint32_t)((j >> 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t ab = a2base + (uint32_t)(buf * BT_A2);
+                for (int ch = 0; ch < nch && ok; ++ch, ++c) {
+                    const int st = (int)(c % BR_XSTAGES);
+                    if (!mbar_wait(&xfull_bar[st], (uint32_t)((c / BR_XSTAGES) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t xb = xtbase + st * BT_XBUF;
+                    const uint32_t d = tmem + (uint32_t)(ch * BT_XCH);
+#pragma unroll
+                    for (int kb2 = 0; kb2 < 2; ++kb2)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const uint64_t ahi = desc_sw128(ab + kb2 * 16384 + 32 * k);
+                            const uint64_t alo = desc_sw128(ab + 32768 + kb2 * 16384 + 32 * k);
+                            const uint64_t bhi = desc_sw128(xb + kb2 * (BT_XCH * 128) + 32 * k);
+                            const uint64_t blo = desc_sw128(xb + (2 + kb2) * (BT_XCH * 128) + 32 * k);
+                            // each chunk's first MMA of the sweep starts its columns from zero
+                            mma_tf32(d, ahi, bhi, idx, (j == 0 && kb2 == 0 && k == 0) ? 0u : 1u);
+                            mma_tf32(d, ahi, blo, idx, 1u);
+                            mma_tf32(d, alo, bhi, idx, 1u);
+                        }
+                    mma_commit(&xempty_bar[st]);
+                }
+                mma_commit(&a2empty_bar[buf]);
+            }
+            mma_commit(&d2_bar);  // also on abort: fires once everything issued has finished
+            if (!mbar_wait(&d2_bar, 0)) ok = false;
+            if (!ok) atomicExch(&abort_flag, 1);
+        }
+        __syncwarp();
+    } else {
+        // ================= epilogue warps 2..9 =================
+        const int etid = tid - 64;
+        const int sp = warp & 3, g = (warp - 2) >> 2;
+        const int mloc = lane / 3, alpha = lane - 3 * (lane / 3);
+        const int la = 10 * sp + mloc;
+        const int64_t a = a_base + la;
+        const bool lane_ok = lane < 30 && a < N;
+        const float fL = (float)L;
+        bool alive = true;
+        for (int64_t j = 0; j < nJ; ++j) {
+            const int64_t b_base = (J0 + j) * TC_MB;
+            const int buf = (int)(j & 1);
+            // gather this lane's four pairs: c, w and the stored rotation (issued together)
+            float cpre[4], wpre[4], Rg[4][9];
+            bool lower[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                cpre[r] = 0.f;
+                wpre[r] = 0.f;
+                lower[r] = false;
+#pragma unroll
+                for (int e = 0; e < 9; ++e) Rg[r][e] = 0.f;
+                const int bq = 3 * r + alpha;
+                const int64_t b = b_base + 10 * g + bq;
+                if (lane_ok && bq < 10 && b < N && b != a) {
+                    const int64_t lo = a < b ? a : b, hi = a < b ? b : a;
+                    const int64_t idx = condensed_idx(lo, hi, N);
+                    cpre[r] = crmsd[idx];
+                    wpre[r] = wvec[idx];
+                    lower[r] = a > b;
+                    const float *src = rot + idx * 9;
+#pragma unroll
+                    for (int e = 0; e < 9; ++e) Rg[r][e] = __ldg(src + e);
+                }
+            }
+            // w~ R blocks (R_ab, or R_ba^T when a > b), rows = a's axes, columns = b's axes
+            float Pall[4][9];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+#pragma unroll
+                for (int e = 0; e < 9; ++e) Pall[r][e] = 0.f;
+                const int bq = 3 * r + alpha;
+                const int64_t b = b_base + 10 * g + bq;
+                if (lane_ok && bq < 10 && b < N && b != a) {
+                    const float c = cpre[r], w = wpre[r];
+                    if (!(c >= CLUSCO_NEARDUP)) {
+                        if (a < b && w != 0.f) {
+                            const unsigned long long slot = atomicAdd(nd_count, 1ull);
+                            if ((int64_t)slot < nd_cap) {
+                                nd_list[2 * slot] = a;
+                                nd_list[2 * slot + 1] = b;
+                            }
+                        }
+                    } else if (w != 0.f) {
+                        const float coef = __fdividef(w, fL * fmaxf(c, eps));
+#pragma unroll
+                        for (int i = 0; i < 3; ++i)
+#pragma unroll
+                            for (int be = 0; be < 3; ++be)
+                                Pall[r][3 * i + be] = coef * (lower[r] ? Rg[r][3 * be + i] : Rg[r][3 * i + be]);
+                        atomicAdd(&dsum[la], coef);
+                    }
+                }
+            }
+            // the operand buffer is reused every other tile: wait until GEMM2 of tile j-2 read it
+            bool ok2 = true;
+            if (j >= 2) ok2 = mbar_wait_sleep(&a2empty_bar[buf], (uint32_t)(((j >> 1) - 1) & 1));
+            if (named_bar_or(1, 256, !ok2 || *abort_v)) {
+                alive = false;
+                break;
+            }
+            uint8_t *A2b = A2 + buf * BT_A2;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int bq = 3 * r + alpha;
+                if (lane < 30 && bq < 10) {
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+#pragma unroll
+                        for (int be = 0; be < 3; ++be) {
+                            const uint32_t off = a2_offset(32 * sp + 3 * mloc + i, 32 * g + 3 * bq + be);
+                            const float v = Pall[r][3 * i + be];
+                            const float vh = tf32_rna(v);
+                            *reinterpret_cast<float *>(A2b + off) = vh;
+                            *reinterpret_cast<float *>(A2b + 32768 + off) = tf32_rna(v - vh);
+                        }
+                }
+            }
+            fence_proxy_async();  // generic-proxy stores to the operand must be visible to tcgen05.mma
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&a2full_bar[buf]);
+        }
+        if (alive) {
+            const bool ok3 = mbar_wait_sleep(&d2_bar, 0);
+            if (named_bar_or(1, 256, !ok3 || *abort_v)) alive = false;
+        }
+        if (alive) {
+            tc_fence_after();
+            // read the P.X sum out of TMEM: warp (sp, g) takes lanes 32 sp.., half of the atoms
+            float *row = Gp + (sidx * Rpad + 128 * I + 32 * sp + lane) * (int64_t)Lp;
+            const int half = Lp / 2;
+            for (int c0 = g * half; c0 < (g + 1) * half; c0 += 32) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)c0, v);
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) row[c0 + jj] = -v[jj];
+            }
+            if (etid < TC_MA) dp[sidx * Npad + a_base + etid] = dsum[etid];
+        } else {
+            atomicExch(&abort_flag, 1);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, tmem_cols);
+}
+
+inline bool bwr_supported(int64_t L) { return (L + 63) / 64 * 64 <= BR_MAXLP; }
+
+// Host side: pre-pass (FP32 copy + transposed TF32 parts), the contraction sweep from stored
+// rotations, the reduction, and the FP64 near-duplicate kernel. Workspace: carve_bt's layout.
+inline int bwr_launch(const float *coords, int64_t N, int64_t L, const float *grad_out, const float *crmsd,
+                      const float *rot, float *grad, float eps, void *ws, cudaStream_t st, std::string &err)
+{
+    const BtWs w = carve_bt(ws, N, L);
+    const unsigned pblocks = (unsigned)((w.Npad + 7) / 8);
+    prepass_tc_kernel<TC_EXACT2><<<pblocks, 256, 0, st>>>(coords, N, (int)L, (int)w.Lp, w.Npad, w.Rpad, w.planes,
+                                                           w.scales, w.G64, w.G32, w.xf);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        bt_transpose_kernel<<<dim3((unsigned)(w.Rpad / 32), (unsigned)(w.Lp / 32)), 256, 0, st>>>(w.xf, w.Rpad,
+                                                                                                 (int)w.Lp, w.xT);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.nd_count, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) {
+        err = std::string("backward pre-pass: ") + cudaGetErrorString(e);
+        return CLUSCO_ECUDA;
+    }
+    CUtensorMap mX;
+    {
+        // X^T parts: FP32 [2 Lp][Rpad]; boxes of 32 columns (128 bytes) x 64 atoms
+        const cuuint64_t dims[2] = {(cuuint64_t)w.Rpad, (cuuint64_t)(2 * w.Lp)};
+        const cuuint64_t strides[1] = {(cuuint64_t)(w.Rpad * 4)};
+        const cuuint32_t box[2] = {32u, (cuuint32_t)BT_XCH};
+        const cuuint32_t estr[2] = {1, 1};
+        CUresult r = encode_fn()(&mX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, w.xT, dims, strides, box, estr,
+                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            err = "cuTensorMapEncodeTiled (X^T) failed (" + std::to_string((int)r) + ")";
+            return CLUSCO_ECUDA;
+        }
+    }
+    const int64_t TA = w.Npad / TC_MA, TB = w.Npad / TC_MB;
+    const int64_t JC = (TB + w.S - 1) / w.S;
+    uint32_t cols = 32;
+    while (cols < (uint32_t)w.Lp) cols <<= 1;  // TMEM allocations are powers of two
+    const unsigned grid = (unsigned)(TA * w.S);
+    e = cudaFuncSetAttribute(bwd_rot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BR_SMEM);
+    if (e == cudaSuccess) {
+        prof_mark(PROF_ADJOINT, st);
+        bwd_rot_kernel<<<grid, BR_THREADS, BR_SMEM, st>>>(mX, N, (int)L, (int)w.Lp, cols, w.Rpad, TB, w.S, JC, crmsd,
+                                                          grad_out, rot, eps, w.Gp, w.dp, w.nd_list, w.nd_count,
+                                                          w.nd_cap);
+        e = cudaGetLastError();
+        prof_mark(PROF_ADJOINT, st);
+    }
+    if (e == cudaSuccess) {
+        bwd_reduce_kernel<<<(unsigned)((N + 7) / 8), 256, 0, st>>>(w.Gp, w.dp, w.xf, N, (int)L, (int)w.Lp, w.Rpad,
+                                                                    w.S, grad);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        bwd_neardup_kernel<<<296, 256, 0, st>>>(coords, N, (int)L, grad_out, eps, w.nd_list, w.nd_count, w.nd_cap,
+                                                grad);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        err = std::string("backward from stored rotations: ") + cudaGetErrorString(e);
+        return CLUSCO_ECUDA;
+    }
+    return CLUSCO_OK;
+}
+
+}  // namespace clusco

@@ -18,8 +18,8 @@
 //     about 2^-21 relative per product);
 //   warps 2-9 (epilogue): read tile J's covariance from TMEM (then release it to GEMM1 of
 //     J+1), assemble each 3x3 block (rows cyclic, as in the forward), take Sigma from the
-//     FP32 fast path and the rotation with it (dSigma/dM from the quartic, with Horn's
-//     quaternion form only near a double root), undo the cyclic order and write w~ R as two
+//     FP32 fast path and the rotation with it (dSigma/dM from the quartic; Horn's adjugate,
+//     or Jacobi sweeps, only near a double root), undo the cyclic order and write w~ R as two
 //     TF32 parts into a shared 128 x 64 operand in the 128-byte-swizzled K-major layout;
 //     pairs below the near-duplicate threshold go to the FP64 direct kernel.
 // So tile J's rotations overlap GEMM1 of J+1 and GEMM2 of J-1. Rotations live only in shared
@@ -130,17 +130,6 @@ __global__ void __launch_bounds__(256) bt_transpose_kernel(const float *__restri
         xT[(int64_t)(i0 + k) * Rpad + r0 + tx] = hi;
         xT[((int64_t)Lp + i0 + k) * Rpad + r0 + tx] = tf32_rna(v - hi);
     }
-}
-
-// Horn's eigenvector route for the rare near-double-root blocks (out of line).
-__device__ __noinline__ void horn_rotation_ool(const float *Hn, float *R)
-{
-    float H[9], Rl[9];
-#pragma unroll
-    for (int e = 0; e < 9; ++e) H[e] = Hn[e];
-    horn_rotation(H, sigma_hat_f32(H), Rl);
-#pragma unroll
-    for (int e = 0; e < 9; ++e) R[e] = Rl[e];
 }
 
 __global__ void __launch_bounds__(BT_THREADS, 1)
@@ -443,7 +432,7 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
                         float Hn[9], Rp[9];
 #pragma unroll
                         for (int e = 0; e < 9; ++e) Hn[e] = blk[e] * nrm;
-                        if (!sigma_rotation_f32(Hn, Rp)) horn_rotation_ool(Hn, Rp);
+                        if (!sigma_rotation_f32(Hn, Rp)) rotation_robust_ool(Hn, Rp);
                         const float coef = __fdividef(w, (float)L * fmaxf(c, eps));
 #pragma unroll
                         for (int i = 0; i < 3; ++i) {

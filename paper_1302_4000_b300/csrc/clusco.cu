@@ -18,6 +18,7 @@
 #include "vsref.cuh"
 #include "backward.cuh"
 #include "bwd_tc.cuh"
+#include "bwd_rot.cuh"
 
 using namespace clusco;
 
@@ -75,10 +76,22 @@ struct PairsWs {
     float *scales = nullptr;
     float *G32 = nullptr;
     int64_t Lp = 0, Npad = 0, Rpad = 0;
+    // rotation entry point only: the deferred-rotation list
+    RotFix *fix = nullptr;
+    unsigned long long *fix_count = nullptr;
+    int64_t fix_cap = 0;
     size_t bytes = 0;
 };
 
-PairsWs carve_pairs(void *base, int64_t N, int64_t L, int form)
+// Capacity of the deferred-rotation list: about 0.5 % of a decoy ensemble's pairs need it;
+// pairs past the capacity are solved inside the forward kernel instead.
+inline int64_t rotfix_cap(int64_t N)
+{
+    const int64_t P = N * (N - 1) / 2, cap = (int64_t)1 << 22;
+    return P < cap ? P : cap;
+}
+
+PairsWs carve_pairs(void *base, int64_t N, int64_t L, int form, bool with_rot = false)
 {
     PairsWs w;
     Carver c(base);
@@ -98,6 +111,11 @@ PairsWs carve_pairs(void *base, int64_t N, int64_t L, int form)
         w.scales = c.take<float>((size_t)w.Npad * 3);
         w.G64 = c.take<double>((size_t)w.Npad);
         w.G32 = c.take<float>((size_t)w.Npad);
+        if (with_rot) {
+            w.fix_cap = rotfix_cap(N);
+            w.fix = c.take<RotFix>((size_t)w.fix_cap);
+            w.fix_count = c.take<unsigned long long>(1);
+        }
     }
     w.bytes = c.off;
     return w;
@@ -173,23 +191,25 @@ int run_prepass(const float *coords, int64_t N, int64_t L, int form, const Pairs
 }
 
 int allpairs_impl(const float *coords, int64_t N, int64_t L, int64_t row_begin, int64_t row_end, float *out,
-                  int form, void *ws, size_t ws_bytes, cudaStream_t st)
+                  int form, void *ws, size_t ws_bytes, cudaStream_t st, float *rot = nullptr)
 {
     int rc;
     if ((rc = check_sizes(N, L, 2))) return rc;
     if ((rc = check_ptr(coords, "coords", 4))) return rc;
     if ((rc = check_ptr(out, "out", 4))) return rc;
     if (!valid_form(form)) return fail(CLUSCO_EINVAL, "unknown form %d", form);
+    if (rot && form == CLUSCO_FORM_FP32_SIMT)
+        return fail(CLUSCO_EUNSUPPORTED, "rotations are produced by the tensor-core forms only");
     if (row_begin < 0 || row_end > N - 1 || row_begin >= row_end)
         return fail(CLUSCO_EINVAL, "row range [%lld, %lld) outside [0, N-1=%lld)", (long long)row_begin,
                     (long long)row_end, (long long)(N - 1));
     if (form != CLUSCO_FORM_FP32_SIMT) {
         if ((rc = tc_supported(form, L))) return rc;
     }
-    const PairsWs sized = carve_pairs(nullptr, N, L, form);
+    const PairsWs sized = carve_pairs(nullptr, N, L, form, rot != nullptr);
     Scratch s;
     if ((rc = get_scratch(s, ws, ws_bytes, sized.bytes, st))) return rc;
-    const PairsWs w = carve_pairs(s.ptr, N, L, form);
+    const PairsWs w = carve_pairs(s.ptr, N, L, form, rot != nullptr);
     if ((rc = run_prepass(coords, N, L, form, w, st))) return rc;
     const int64_t out_base = condensed_idx(row_begin, row_begin + 1, N);
     if (form == CLUSCO_FORM_FP32_SIMT) {
@@ -214,6 +234,10 @@ int allpairs_impl(const float *coords, int64_t N, int64_t L, int64_t row_begin, 
         a.row_end = row_end;
         a.out = out;
         a.out_base = out_base;
+        a.rot = rot;
+        a.fix = w.fix;
+        a.fix_count = w.fix_count;
+        a.fix_cap = w.fix_cap;
         std::string err;
         rc = tc_launch_allpairs(a, st, err);
         if (rc) return fail(rc, "%s", err.c_str());
@@ -245,6 +269,14 @@ size_t clusco_workspace_bytes(int op, int64_t N, int64_t L, int form)
     if (op == CLUSCO_OP_BACKWARD) {
         if (!valid_form(form) || N < 2) return 0;
         return backward_ws_bytes(N, L, form);
+    }
+    if (op == CLUSCO_OP_ALLPAIRS_ROT) {
+        if (!valid_form(form) || form == CLUSCO_FORM_FP32_SIMT || N < 2) return 0;
+        return carve_pairs(nullptr, N, L, form, true).bytes;
+    }
+    if (op == CLUSCO_OP_BACKWARD_ROT) {
+        if (N < 2 || !bwr_supported(L)) return 0;
+        return carve_bt(nullptr, N, L).bytes;
     }
     return 0;
 }
@@ -310,6 +342,41 @@ int clusco_crmsd_allpairs_backward(const float *coords, int64_t N, int64_t L, co
     if ((rc = get_scratch(s, workspace, workspace_bytes, need, st))) return rc;
     std::string err;
     rc = backward_launch(coords, N, L, grad_out, crmsd, grad_coords, eps, form, s.ptr, st, err);
+    if (rc) return fail(rc, "%s", err.c_str());
+    return CLUSCO_OK;
+}
+
+int clusco_crmsd_allpairs_rot(const float *coords, int64_t N, int64_t L, float *out, float *rot, int form,
+                              void *workspace, size_t workspace_bytes, void *stream)
+{
+    g_last_error.clear();
+    if (N < 2) return fail(CLUSCO_EINVAL, "N=%lld must be >= 2", (long long)N);
+    int rc;
+    if ((rc = check_ptr(rot, "rot", 4))) return rc;
+    return allpairs_impl(coords, N, L, 0, N - 1, out, form, workspace, workspace_bytes, (cudaStream_t)stream, rot);
+}
+
+int clusco_crmsd_allpairs_backward_rot(const float *coords, int64_t N, int64_t L, const float *grad_out,
+                                       const float *crmsd, const float *rot, float *grad_coords, float eps,
+                                       void *workspace, size_t workspace_bytes, void *stream)
+{
+    g_last_error.clear();
+    int rc;
+    if ((rc = check_sizes(N, L, 2))) return rc;
+    if ((rc = check_ptr(coords, "coords", 4))) return rc;
+    if ((rc = check_ptr(grad_out, "grad_out", 4))) return rc;
+    if ((rc = check_ptr(crmsd, "crmsd", 4))) return rc;
+    if ((rc = check_ptr(rot, "rot", 4))) return rc;
+    if ((rc = check_ptr(grad_coords, "grad_coords", 4))) return rc;
+    if (!(eps > 0.f) || !std::isfinite(eps)) return fail(CLUSCO_EINVAL, "eps=%g must be finite and > 0", (double)eps);
+    if (!bwr_supported(L)) return fail(CLUSCO_EUNSUPPORTED, "L=%lld above the 512 atoms of this path", (long long)L);
+    if ((rc = tc_supported(CLUSCO_FORM_BF16_EXACT2, L))) return fail(rc, "tensor-core path unavailable on this device");
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch s;
+    const size_t need = carve_bt(nullptr, N, L).bytes;
+    if ((rc = get_scratch(s, workspace, workspace_bytes, need, st))) return rc;
+    std::string err;
+    rc = bwr_launch(coords, N, L, grad_out, crmsd, rot, grad_coords, eps, s.ptr, st, err);
     if (rc) return fail(rc, "%s", err.c_str());
     return CLUSCO_OK;
 }

@@ -246,10 +246,11 @@ __device__ __forceinline__ float sigma_hat_f32(const float m[9])
 // gives
 //   R = [4 (I1 + Sigma^2) m - 8 m m^T m + 8 Sigma cof(m)] / P'(Sigma),
 //   P'(Sigma) = 4 Sigma^3 - 4 I1 Sigma - 8 det.
-// The cofactors are the 2x2 minors that I2 and det are built from. Returns false, leaving R
-// unset, where P' falls below 1e-2 of 8 Sigma^3 (near a double root, where this quotient
-// loses accuracy); the caller then takes Horn's eigenvector route.
-__device__ __forceinline__ bool sigma_rotation_f32(const float m[9], float R[9])
+// The cofactors are the 2x2 minors that I2 and det are built from. rotation_from_sigma_f32
+// takes Sigma (of m) as computed; both return false, leaving R unset, where P' falls below
+// 1e-2 of 8 Sigma^3 (near a double root, where this quotient loses accuracy); the caller then
+// takes the eigenvector route of rotation.cuh.
+__device__ __forceinline__ bool rotation_from_sigma_f32(const float m[9], float s, float R[9])
 {
     const float a01 = m[3] * m[7] - m[4] * m[6];
     const float a02 = m[3] * m[8] - m[5] * m[6];
@@ -261,17 +262,12 @@ __device__ __forceinline__ bool sigma_rotation_f32(const float m[9], float R[9])
     const float c02 = m[0] * m[5] - m[2] * m[3];
     const float c12 = m[1] * m[5] - m[2] * m[4];
     const float det = m[0] * a12 - m[1] * a02 + m[2] * a01;
-    const float I2 = a01 * a01 + a02 * a02 + a12 * a12 + b01 * b01 + b02 * b02 + b12 * b12 + c01 * c01 +
-                     c02 * c02 + c12 * c12;
     float I1 = 0.f;
 #pragma unroll
     for (int k = 0; k < 9; ++k) I1 = fmaf(m[k], m[k], I1);
-    bool deg;
-    float dPn;
-    const float s = quartic_newton_f(sigma_cubic_f(I1, det, I2), I1, det, I2, 2, &deg, &dPn);
     const float s2 = s * s;
     const float dP = fmaf(fmaf(4.f, s2, -4.f * I1), s, -8.f * det);
-    if (deg || !(dP > 8e-2f * s2 * s)) return false;
+    if (!(dP > 8e-2f * s2 * s)) return false;
     // cofactor matrix (signed minors), row-major
     const float cf[9] = {a12, -a02, a01, -b12, b02, -b01, c12, -c02, c01};
     // g = m^T m (symmetric)
@@ -293,7 +289,30 @@ __device__ __forceinline__ bool sigma_rotation_f32(const float m[9], float R[9])
         R[3 * i + 1] = fmaf(al, r1, fmaf(ga, mg1, be * cf[3 * i + 1]));
         R[3 * i + 2] = fmaf(al, r2, fmaf(ga, mg2, be * cf[3 * i + 2]));
     }
+    // The quotient inherits Sigma's FP32 error amplified by about Q/P', mostly as a departure
+    // from orthogonality; one Newton-Schulz step R <- R (3 I - R^T R) / 2 removes that to
+    // second order (the polar factor of R is the nearest rotation).
+    const float q00 = R[0] * R[0] + R[3] * R[3] + R[6] * R[6];
+    const float q01 = R[0] * R[1] + R[3] * R[4] + R[6] * R[7];
+    const float q02 = R[0] * R[2] + R[3] * R[5] + R[6] * R[8];
+    const float q11 = R[1] * R[1] + R[4] * R[4] + R[7] * R[7];
+    const float q12 = R[1] * R[2] + R[4] * R[5] + R[7] * R[8];
+    const float q22 = R[2] * R[2] + R[5] * R[5] + R[8] * R[8];
+    const float t00 = 1.5f - 0.5f * q00, t11 = 1.5f - 0.5f * q11, t22 = 1.5f - 0.5f * q22;
+    const float t01 = -0.5f * q01, t02 = -0.5f * q02, t12 = -0.5f * q12;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float r0 = R[3 * i], r1 = R[3 * i + 1], r2 = R[3 * i + 2];
+        R[3 * i + 0] = r0 * t00 + r1 * t01 + r2 * t02;
+        R[3 * i + 1] = r0 * t01 + r1 * t11 + r2 * t12;
+        R[3 * i + 2] = r0 * t02 + r1 * t12 + r2 * t22;
+    }
     return true;
+}
+
+__device__ __forceinline__ bool sigma_rotation_f32(const float m[9], float R[9])
+{
+    return rotation_from_sigma_f32(m, sigma_hat_f32(m), R);
 }
 
 // FP32 fast path on a rounded covariance: cubic start + two Newton steps, all FP32.

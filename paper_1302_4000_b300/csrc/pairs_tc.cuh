@@ -36,12 +36,24 @@
 #include "prepass.cuh"
 #include "prof.cuh"
 #include "ptx.cuh"
+#include "rotation.cuh"
 
 #ifndef CLUSCO_TOL_FAST
 #define CLUSCO_TOL_FAST 2.5e-4f  // A: largest FP32 fast-path error accepted for the exact form
 #endif
 
 namespace clusco {
+
+// A pair whose rotation the closed form cannot give accurately (P' below 0.08 Sigma^3, about
+// 0.5 % of the pairs of a decoy ensemble): the forward appends its normalised covariance
+// (natural axis order) and rot_fixup_kernel solves it by Jacobi sweeps afterwards, one pair per
+// thread, instead of a divergent slow path inside the epilogue's rounds.
+struct RotFix {
+    long long idx;  // condensed index relative to the output's base
+    float m[9];
+    float pad;
+};
+static_assert(sizeof(RotFix) == 48, "deferred rotation entry");
 
 struct TcArgs {
     int form;
@@ -52,7 +64,13 @@ struct TcArgs {
     int64_t N, L, Lp, Rpad, row_begin, row_end;
     float *out;
     int64_t out_base;
+    float *rot = nullptr;  // optional: R_ab per pair, [P][9] in the output's condensed order
+    RotFix *fix = nullptr;            // deferred rotations (see RotFix)
+    unsigned long long *fix_count = nullptr;
+    int64_t fix_cap = 0;
 };
+
+
 
 constexpr uint32_t STAGE_BYTES_BF16 = 2 * 16384 + 2 * 8192;  // A_h, A_l, B_h, B_l
 constexpr uint32_t STAGE_BYTES_TF32 = 16384 + 8192;          // A, B
@@ -236,12 +254,49 @@ __device__ __noinline__ void refine_queued(const QEntry *qe, const float *__rest
     out[condensed_idx(aa, bb, N) - out_base] = c;
 }
 
-template <int LAYOUT>
+// The rotation of a rare block whose quartic root is (nearly) double (out of line): Jacobi
+// sweeps for a rank-deficient block (I2 ~ 0, where an FP32 Sigma is least accurate), else
+// Horn's adjugate with the block's Sigma, and Jacobi sweeps where that is degenerate too.
+__device__ __noinline__ void rotation_robust_ool(const float *Hn, float *R)
+{
+    float H[9], Rl[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) H[e] = Hn[e];
+    float I1, det, I2;
+    invariants3(H, I1, det, I2);
+    if (!(I2 > 1e-8f * I1 * I1) || !horn_rotation(H, sigma_hat_f32(H), 1e-5f, Rl)) rotation_jacobi4<float, 8>(H, Rl);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) R[e] = Rl[e];
+}
+
+// Deferred rotations: Jacobi sweeps on each listed pair's covariance (one pair per thread).
+__global__ void __launch_bounds__(256) rot_fixup_kernel(const RotFix *__restrict__ list,
+                                                        const unsigned long long *__restrict__ count, int64_t cap,
+                                                        float *__restrict__ rot)
+{
+    const int64_t n = (int64_t)*count < cap ? (int64_t)*count : cap;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float m[9], R[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) m[e] = list[i].m[e];
+        rotation_jacobi4<float, 8>(m, R);
+        float *dst = rot + list[i].idx * 9;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) dst[e] = R[e];
+    }
+}
+
+// ROT: also write each pair's optimal rotation R_ab (b onto a, natural axis order, row-major)
+// to rot[(idx - out_base) * 9 ..], computed as dSigma/dM from the fast path's Sigma (Horn's
+// key matrix near a double root); the adjoint reads it instead of recomputing the covariance.
+template <int LAYOUT, bool ROT>
 __global__ void __launch_bounds__(FW_THREADS, 1)
     pairs_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                     const float *__restrict__ scales, const double *__restrict__ G64, const float *__restrict__ G32,
                     int64_t N, int L, int nkb, int64_t Rpad, int64_t TA, int64_t TB, int64_t tile0, int64_t ntiles,
-                    int64_t row_begin, int64_t row_end, float *__restrict__ out, int64_t out_base)
+                    int64_t row_begin, int64_t row_end, float *__restrict__ out, int64_t out_base,
+                    float *__restrict__ rot, RotFix *__restrict__ fix, unsigned long long *__restrict__ fix_count,
+                    int64_t fix_cap)
 {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[FW_STAGES];   // ring: K block landed
@@ -449,6 +504,46 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                 float sv, ev;
                 const float cv = crmsd_fast_fp32(blk, Ga, Gb[0], invL, &sv, &ev);
                 const int64_t b = b0 + 3 * r;
+                if (ROT) {
+                    const float Gs = Ga + Gb[0];
+                    const float nrm = __fdividef(2.0f, Gs > 0.f ? Gs : 1.0f);
+                    float m[9], R[9];
+#pragma unroll
+                    for (int e = 0; e < 9; ++e) m[e] = blk[e] * nrm;
+                    const bool okR = rotation_from_sigma_f32(m, sv, R);
+                    if (pok[0]) {
+                        // blk's rows are axes alpha, alpha + 1, alpha + 2: axis ax is row (ax - alpha) mod 3
+                        const int64_t ridx = rowbase + b;
+                        bool done = okR;
+                        if (!okR) {
+                            const unsigned long long slot = atomicAdd(fix_count, 1ull);
+                            if ((int64_t)slot < fix_cap) {
+                                RotFix *f = fix + slot;
+                                f->idx = ridx;
+#pragma unroll
+                                for (int ax = 0; ax < 3; ++ax) {
+                                    const int src = (ax + 3 - alpha) % 3;
+#pragma unroll
+                                    for (int be = 0; be < 3; ++be)
+                                        f->m[3 * ax + be] = sel3(src, m[be], m[3 + be], m[6 + be]);
+                                }
+                            } else {
+                                rotation_robust_ool(m, R);  // the list is full: solve it here
+                                done = true;
+                            }
+                        }
+                        if (done) {
+                            float *dst = rot + ridx * 9;
+#pragma unroll
+                            for (int ax = 0; ax < 3; ++ax) {
+                                const int src = (ax + 3 - alpha) % 3;
+#pragma unroll
+                                for (int be = 0; be < 3; ++be)
+                                    dst[3 * ax + be] = sel3(src, R[be], R[3 + be], R[6 + be]);
+                            }
+                        }
+                    }
+                }
                 bool need = false;
                 if (pok[0]) {
                     if (LAYOUT == TC_EXACT2 && !(ev <= 2.f * CLUSCO_TOL_FAST * cv)) {
@@ -560,8 +655,8 @@ inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaFuncSetAttribute(pairs_tc_kernel<LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)FW_SMEM);
+    auto kern = a.rot ? pairs_tc_kernel<LAYOUT, true> : pairs_tc_kernel<LAYOUT, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FW_SMEM);
     if (e != cudaSuccess) {
         err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
         return CLUSCO_ECUDA;
@@ -569,11 +664,22 @@ inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
     // persistent: one CTA per SM, CTA x takes tiles x, x + grid, x + 2 grid, ...
     const unsigned grid = (unsigned)std::min<int64_t>(nt, sms > 0 ? sms : 148);
     prof_mark(PROF_PAIRS, st);
-    pairs_tc_kernel<LAYOUT><<<grid, FW_THREADS, FW_SMEM, st>>>(mA, mB, a.scales, a.G64, a.G32, a.N, (int)a.L, nkb,
-                                                                a.Rpad, TA, TB, t0, nt, a.row_begin, a.row_end,
-                                                                a.out, a.out_base);
+    if (a.rot) {
+        e = cudaMemsetAsync(a.fix_count, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) {
+            err = std::string("rotation list reset: ") + cudaGetErrorString(e);
+            return CLUSCO_ECUDA;
+        }
+    }
+    kern<<<grid, FW_THREADS, FW_SMEM, st>>>(mA, mB, a.scales, a.G64, a.G32, a.N, (int)a.L, nkb, a.Rpad, TA, TB, t0,
+                                             nt, a.row_begin, a.row_end, a.out, a.out_base, a.rot, a.fix,
+                                             a.fix_count, a.fix_cap);
     e = cudaGetLastError();
     prof_mark(PROF_PAIRS, st);
+    if (e == cudaSuccess && a.rot) {
+        rot_fixup_kernel<<<4 * (sms > 0 ? sms : 148), 256, 0, st>>>(a.fix, a.fix_count, a.fix_cap, a.rot);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) {
         err = std::string("pairs_tc_kernel launch: ") + cudaGetErrorString(e);
         return CLUSCO_ECUDA;
