@@ -122,7 +122,7 @@ def traffic_for(key):
     """DRAM bytes per launch of a kernel from its committed ncu summary, or None once the
     kernel's source has changed since the counters were taken (sha256 recorded beside them)."""
     import hashlib
-    src = {"pairs_tc": "pairs_tc.cuh", "bwd_tc": "bwd_tc.cuh"}[key]
+    src = {"pairs_tc": "pairs_tc.cuh", "bwd_tc": "bwd_tc.cuh", "bwd_rot": "bwd_rot.cuh"}[key]
     try:
         h = hashlib.sha256(open(os.path.join(ROOT, "paper_1302_4000_b300", "csrc", src), "rb").read()).hexdigest()
         for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
@@ -223,29 +223,48 @@ def run_ours(args):
     out = torch.empty(P, dtype=torch.float32, device=dev)
     vs = torch.empty(N, dtype=torch.float32, device=dev)
     grad = torch.empty_like(X)
-    ws_all = torch.empty(clusco.workspace_bytes(clusco.OP_ALLPAIRS, N, L, form), dtype=torch.uint8, device=dev)
+    # the training step's path: with a tensor-core form and L <= 512 the forward stores each
+    # pair's rotation and the adjoint contracts from it; otherwise the adjoint recomputes
+    use_rot = form != clusco.FORM_FP32_SIMT and L <= 512
+    rot = torch.empty((P, clusco.ROT_STRIDE), dtype=torch.float32, device=dev) if use_rot else None
+    ws_all = torch.empty(clusco.workspace_bytes(clusco.OP_ALLPAIRS_ROT if use_rot else clusco.OP_ALLPAIRS, N, L,
+                                                form), dtype=torch.uint8, device=dev)
     ws_vs = torch.empty(clusco.workspace_bytes(clusco.OP_VS_REF, N, L, form), dtype=torch.uint8, device=dev)
-    ws_bw = torch.empty(clusco.workspace_bytes(clusco.OP_BACKWARD, N, L, form), dtype=torch.uint8, device=dev)
+    ws_bw = torch.empty(clusco.workspace_bytes(clusco.OP_BACKWARD_ROT if use_rot else clusco.OP_BACKWARD, N, L,
+                                               form), dtype=torch.uint8, device=dev)
+
+    def forward(Xd):
+        if use_rot:
+            clusco.crmsd_allpairs_rot(Xd, form, out=out, rot=rot, workspace=ws_all)
+        else:
+            clusco.crmsd_allpairs(Xd, form, out=out, workspace=ws_all)
+
+    def backward(Xd, Wd):
+        if use_rot:
+            clusco.crmsd_allpairs_backward_rot(Xd, Wd, out, rot, 1e-6, grad_coords=grad, workspace=ws_bw)
+        else:
+            clusco.crmsd_allpairs_backward(Xd, Wd, out, 1e-6, form, grad_coords=grad, workspace=ws_bw)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
     def step(evs=None):
         if evs:
             evs[0].record(stream)
-        clusco.crmsd_allpairs(X, form, out=out, workspace=ws_all)
+        forward(X)
         if evs:
             evs[1].record(stream)
         clusco.crmsd_vs_ref(X, ref, out=vs, workspace=ws_vs)
         if evs:
             evs[2].record(stream)
-        clusco.crmsd_allpairs_backward(X, W, out, 1e-6, form, grad_coords=grad, workspace=ws_bw)
+        backward(X, W)
         if evs:
             evs[3].record(stream)
 
-    # our kernels per step: pre-pass + pairs; ref pre-pass + vs-ref; adjoint (pre-pass,
-    # transpose, sweep, reduce, near-duplicate pass; 3 kernels on the CUDA-core fallback)
-    tc_bwd = L <= 320 and form_name != "none"
-    launches_per_step = 2 + 2 + (5 if tc_bwd else 3)
+    # our kernels per step: forward (pre-pass + pairs, + the deferred-rotation kernel when
+    # storing rotations); ref pre-pass + vs-ref; adjoint (pre-pass, transpose, sweep, reduce,
+    # near-duplicate pass; 3 kernels on the CUDA-core adjoint)
+    tc_bwd = use_rot or (L <= 320 and form != clusco.FORM_FP32_SIMT)
+    launches_per_step = (3 if use_rot else 2) + 2 + (5 if tc_bwd else 3)
 
     def timed(fn, k, w_, split=False, prof=False):
         for _ in range(w_):
@@ -297,7 +316,8 @@ def run_ours(args):
     # plain-form forward for the "vs plain FP32" ratio (same GPU, same inputs)
     plain_fwd = None
     if form != clusco.FORM_FP32_SIMT:
-        ws_p = torch.empty(clusco.workspace_bytes(clusco.OP_ALLPAIRS, N, L, 0), dtype=torch.uint8, device=dev)
+        ws_p = torch.empty(clusco.workspace_bytes(clusco.OP_ALLPAIRS, N, L, clusco.FORM_FP32_SIMT), dtype=torch.uint8,
+                           device=dev)
         out_p = torch.empty_like(out)
 
         def pfwd():
@@ -333,9 +353,9 @@ def run_ours(args):
             Xd = Xh.to(dev, non_blocking=True)
             Wd = Wh.to(dev, non_blocking=True)
             Rd = Rh.to(dev, non_blocking=True)
-            clusco.crmsd_allpairs(Xd, form, out=out, workspace=ws_all)
+            forward(Xd)
             clusco.crmsd_vs_ref(Xd, Rd, out=vs, workspace=ws_vs)
-            clusco.crmsd_allpairs_backward(Xd, Wd, out, 1e-6, form, grad_coords=grad, workspace=ws_bw)
+            backward(Xd, Wd)
             out_h.copy_(out, non_blocking=True)
             vs_h.copy_(vs, non_blocking=True)
             g_h.copy_(grad, non_blocking=True)
@@ -356,17 +376,30 @@ def run_ours(args):
     # of either kernel covers all P pairs. Duration: the kernel's own launch, bracketed by
     # events the library records on the launch stream during the timed steps (average over
     # the steps); the call bracket only where the kernel did not run (CUDA-core forms).
-    def rf(flop, kms, call_ms, kernel, hash_key):
+    def rf(flop, kms, call_ms, kernel, hash_key, hbm_bytes=None):
         msec = kms if kms else call_ms
-        ach = flop / (msec * 1e-3) / 1e12
-        tr = traffic_for(hash_key)
-        return {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
-                "traffic": tr, "kernel": kernel, "launch_ms": msec,
-                "timing": "kernel launch events" if kms else "API call bracket",
-                "peak_kind": f"{pk_kind} bf16 burst"}
+        r = {"kernel": kernel, "launch_ms": msec, "timing": "kernel launch events" if kms else "API call bracket",
+             "traffic": traffic_for(hash_key)}
+        if hbm_bytes is None:
+            ach = flop / (msec * 1e-3) / 1e12
+            r.update({"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
+                      "peak_kind": f"{pk_kind} bf16 burst"})
+        else:
+            ach = hbm_bytes / (msec * 1e-3) / 1e9
+            r.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                      "peak_kind": f"{pk_kind} HBM copy"})
+        return r
     kp, ka = kern["pairs"][0], kern["adjoint"][0]
-    r_fwd = rf(18.0 * L * P, kp, fms, "pairs_tc_kernel (forward, 18 L flop/pair)", "pairs_tc")
-    r_bwd = rf(54.0 * L * P, ka, bms, "bwd_tc_kernel (adjoint, 54 L flop/pair)", "bwd_tc")
+    r_fwd = rf(18.0 * L * P, kp, fms, "pairs_tc_kernel%s (forward, 18 L flop/pair)" % ("<ROT>" if use_rot else ""),
+               "pairs_tc")
+    if use_rot:
+        # from stored rotations the adjoint's contraction is 36 L flop per pair (R x_b and R^T x_a)
+        # against 44 bytes per pair of gathers (the nine floats of R_ab, c_ab, w_ab): the HBM
+        # term is the larger
+        r_bwd = rf(36.0 * L * P, ka, bms, "bwd_rot_kernel (adjoint from stored rotations, 44 B/pair)", "bwd_rot",
+                   hbm_bytes=44.0 * P)
+    else:
+        r_bwd = rf(54.0 * L * P, ka, bms, "bwd_tc_kernel (adjoint, 54 L flop/pair)", "bwd_tc")
     dominant, other = (r_bwd, r_fwd) if r_bwd["launch_ms"] >= r_fwd["launch_ms"] else (r_fwd, r_bwd)
     line = {"metric": METRIC, "value": ws_ * P / (ms * 1e-3), "unit": UNIT, "n_gpus": ws_, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -375,6 +408,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": f"decoy ensemble N={N} L={L}, 5 natives, sigma~U(0.5,10) A", "form": form_name,
                        "pairs": P, "step": "prepass + all-pairs fwd + vs-native + backward",
+                       "adjoint": "from stored rotations" if use_rot else "recomputed covariances",
                        "l2": "flushed (512 MiB write) before each timed step", "parallelism": f"replicas x{ws_}"},
             "fwd": {"value": ws_ * P / (fms * 1e-3), "unit": UNIT, "ms": fms},
             "bwd_ms": bms,

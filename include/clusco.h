@@ -147,14 +147,16 @@ int clusco_profile_enable(int on);
 int clusco_profile_read(int kernel, double *total_ms, long long *launches);
 
 /* The all-pairs matrix as clusco_crmsd_allpairs, plus each pair's optimal rotation for the
- * adjoint: rot is float[N(N-1)/2][9] (device, caller-owned, 4-byte aligned), in the output's
- * condensed order; rot[idx*9 + 3*i + j] = R_ab[i][j], the rotation of centred b onto centred
- * a (natural axis order), which maximises sum_i a_i . R b_i. R is dSigma/dM of the eq. 2 sum
+ * adjoint: rot is float[N(N-1)/2][CLUSCO_ROT_STRIDE] (device, caller-owned, 16-byte aligned),
+ * in the output's condensed order; rot[idx*CLUSCO_ROT_STRIDE + 3*i + j] = R_ab[i][j], the
+ * rotation of centred b onto centred a (natural axis order), which maximises
+ * sum_i a_i . R b_i; the record's last three floats are zero (48-byte records). R is dSigma/dM of the eq. 2 sum
  * Sigma (see clusco_crmsd_allpairs_backward_rot), FP32. Tensor-core forms only
  * (CLUSCO_EUNSUPPORTED for CLUSCO_FORM_FP32_SIMT); workspace: CLUSCO_OP_ALLPAIRS_ROT bytes
  * (the all-pairs workspace plus a list of the ~0.5% of pairs whose rotation is solved by
  * Jacobi sweeps after the main kernel).
  * No counterpart in the paper, which needs no rotation. */
+#define CLUSCO_ROT_STRIDE 12
 int clusco_crmsd_allpairs_rot(const float *coords, int64_t N, int64_t L, float *out, float *rot, int form,
                               void *workspace, size_t workspace_bytes, void *stream);
 

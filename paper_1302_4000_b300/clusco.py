@@ -150,18 +150,27 @@ def crmsd_allpairs(coords: torch.Tensor, form: int = FORM_BF16_EXACT2, out: torc
     return out
 
 
+ROT_STRIDE = 12
+
+
+def rotations_view(rot: torch.Tensor) -> torch.Tensor:
+    """The [P, 3, 3] rotations inside a stored-rotation buffer of [P, ROT_STRIDE] records."""
+    return rot[:, :9].reshape(-1, 3, 3)
+
+
 def crmsd_allpairs_rot(coords: torch.Tensor, form: int = FORM_BF16_EXACT2, out: torch.Tensor | None = None,
                        rot: torch.Tensor | None = None, workspace: torch.Tensor | None = None, stream=None):
-    """(matrix, rotations): the condensed cRMSD and each pair's R_ab as float32 [P, 3, 3]."""
+    """(matrix, rotation records): the condensed cRMSD and each pair's R_ab as float32
+    [P, ROT_STRIDE] records (R row-major in the first nine; rotations_view gives [P, 3, 3])."""
     coords = _coords(coords)
     N, L = coords.shape[0], coords.shape[1]
     P = N * (N - 1) // 2
     if out is None:
         out = torch.empty(P, dtype=torch.float32, device=coords.device)
     if rot is None:
-        rot = torch.empty((P, 3, 3), dtype=torch.float32, device=coords.device)
+        rot = torch.empty((P, ROT_STRIDE), dtype=torch.float32, device=coords.device)
     assert out.is_cuda and out.dtype == torch.float32 and out.numel() >= P and out.is_contiguous()
-    assert rot.is_cuda and rot.dtype == torch.float32 and rot.numel() >= 9 * P and rot.is_contiguous()
+    assert rot.is_cuda and rot.dtype == torch.float32 and rot.numel() >= ROT_STRIDE * P and rot.is_contiguous()
     ws, nb = _ws(workspace, OP_ALLPAIRS_ROT, N, L, form, coords.device)
     _check(load().clusco_crmsd_allpairs_rot(coords.data_ptr(), N, L, out.data_ptr(), rot.data_ptr(), form,
                                             ws.data_ptr(), nb, _stream(stream)))
@@ -247,7 +256,7 @@ def crmsd_allpairs_backward_rot(coords: torch.Tensor, grad_out: torch.Tensor, cr
     grad_out = grad_out.contiguous().to(torch.float32)
     crmsd = crmsd.contiguous()
     rot = rot.contiguous()
-    assert grad_out.numel() == P and crmsd.numel() == P and rot.numel() == 9 * P
+    assert grad_out.numel() == P and crmsd.numel() == P and rot.numel() == ROT_STRIDE * P
     assert grad_out.is_cuda and crmsd.is_cuda and rot.is_cuda
     if grad_coords is None:
         grad_coords = torch.empty_like(coords)

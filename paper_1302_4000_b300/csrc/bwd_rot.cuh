@@ -199,9 +199,17 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
                     cpre[r] = crmsd[idx];
                     wpre[r] = wvec[idx];
                     lower[r] = a > b;
-                    const float *src = rot + idx * 9;
-#pragma unroll
-                    for (int e = 0; e < 9; ++e) Rg[r][e] = __ldg(src + e);
+                    const float4 *src = reinterpret_cast<const float4 *>(rot + idx * ROT_STRIDE);
+                    const float4 r0 = __ldg(src), r1 = __ldg(src + 1), r2 = __ldg(src + 2);
+                    Rg[r][0] = r0.x;
+                    Rg[r][1] = r0.y;
+                    Rg[r][2] = r0.z;
+                    Rg[r][3] = r0.w;
+                    Rg[r][4] = r1.x;
+                    Rg[r][5] = r1.y;
+                    Rg[r][6] = r1.z;
+                    Rg[r][7] = r1.w;
+                    Rg[r][8] = r2.x;
                 }
             }
             // w~ R blocks (R_ab, or R_ba^T when a > b), rows = a's axes, columns = b's axes

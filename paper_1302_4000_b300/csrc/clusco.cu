@@ -352,7 +352,7 @@ int clusco_crmsd_allpairs_rot(const float *coords, int64_t N, int64_t L, float *
     g_last_error.clear();
     if (N < 2) return fail(CLUSCO_EINVAL, "N=%lld must be >= 2", (long long)N);
     int rc;
-    if ((rc = check_ptr(rot, "rot", 4))) return rc;
+    if ((rc = check_ptr(rot, "rot", 16))) return rc;
     return allpairs_impl(coords, N, L, 0, N - 1, out, form, workspace, workspace_bytes, (cudaStream_t)stream, rot);
 }
 
@@ -366,7 +366,7 @@ int clusco_crmsd_allpairs_backward_rot(const float *coords, int64_t N, int64_t L
     if ((rc = check_ptr(coords, "coords", 4))) return rc;
     if ((rc = check_ptr(grad_out, "grad_out", 4))) return rc;
     if ((rc = check_ptr(crmsd, "crmsd", 4))) return rc;
-    if ((rc = check_ptr(rot, "rot", 4))) return rc;
+    if ((rc = check_ptr(rot, "rot", 16))) return rc;
     if ((rc = check_ptr(grad_coords, "grad_coords", 4))) return rc;
     if (!(eps > 0.f) || !std::isfinite(eps)) return fail(CLUSCO_EINVAL, "eps=%g must be finite and > 0", (double)eps);
     if (!bwr_supported(L)) return fail(CLUSCO_EUNSUPPORTED, "L=%lld above the 512 atoms of this path", (long long)L);

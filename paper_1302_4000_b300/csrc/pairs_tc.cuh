@@ -44,6 +44,18 @@
 
 namespace clusco {
 
+// Stored rotations: one 48-byte record per pair, R_ab row-major in floats 0..8 and zeros in
+// 9..11, so that it moves as three 16-byte vectors.
+constexpr int ROT_STRIDE = 12;
+
+__device__ __forceinline__ void store_rot(float *dst, const float R[9])
+{
+    float4 *d = reinterpret_cast<float4 *>(dst);
+    d[0] = make_float4(R[0], R[1], R[2], R[3]);
+    d[1] = make_float4(R[4], R[5], R[6], R[7]);
+    d[2] = make_float4(R[8], 0.f, 0.f, 0.f);
+}
+
 // A pair whose rotation the closed form cannot give accurately (P' below 0.08 Sigma^3, about
 // 0.5 % of the pairs of a decoy ensemble): the forward appends its normalised covariance
 // (natural axis order) and rot_fixup_kernel solves it by Jacobi sweeps afterwards, one pair per
@@ -64,7 +76,7 @@ struct TcArgs {
     int64_t N, L, Lp, Rpad, row_begin, row_end;
     float *out;
     int64_t out_base;
-    float *rot = nullptr;  // optional: R_ab per pair, [P][9] in the output's condensed order
+    float *rot = nullptr;  // optional: R_ab per pair, [P][ROT_STRIDE] in the output's condensed order
     RotFix *fix = nullptr;            // deferred rotations (see RotFix)
     unsigned long long *fix_count = nullptr;
     int64_t fix_cap = 0;
@@ -280,14 +292,12 @@ __global__ void __launch_bounds__(256) rot_fixup_kernel(const RotFix *__restrict
 #pragma unroll
         for (int e = 0; e < 9; ++e) m[e] = list[i].m[e];
         rotation_jacobi4<float, 8>(m, R);
-        float *dst = rot + list[i].idx * 9;
-#pragma unroll
-        for (int e = 0; e < 9; ++e) dst[e] = R[e];
+        store_rot(rot + list[i].idx * ROT_STRIDE, R);
     }
 }
 
 // ROT: also write each pair's optimal rotation R_ab (b onto a, natural axis order, row-major)
-// to rot[(idx - out_base) * 9 ..], computed as dSigma/dM from the fast path's Sigma (Horn's
+// to rot[(idx - out_base) * ROT_STRIDE ..], computed as dSigma/dM from the fast path's Sigma (Horn's
 // key matrix near a double root); the adjoint reads it instead of recomputing the covariance.
 template <int LAYOUT, bool ROT>
 __global__ void __launch_bounds__(FW_THREADS, 1)
@@ -533,14 +543,14 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                             }
                         }
                         if (done) {
-                            float *dst = rot + ridx * 9;
+                            float Rn[9];
 #pragma unroll
                             for (int ax = 0; ax < 3; ++ax) {
                                 const int src = (ax + 3 - alpha) % 3;
 #pragma unroll
-                                for (int be = 0; be < 3; ++be)
-                                    dst[3 * ax + be] = sel3(src, R[be], R[3 + be], R[6 + be]);
+                                for (int be = 0; be < 3; ++be) Rn[3 * ax + be] = sel3(src, R[be], R[3 + be], R[6 + be]);
                             }
+                            store_rot(rot + ridx * ROT_STRIDE, Rn);
                         }
                     }
                 }

@@ -74,10 +74,11 @@ def test_rotations_every_pair_config0():
             d = (out - plain).abs().max().item()
             assert d <= 5e-4, d
             assert np.abs(out.double().cpu().numpy() - c_ref).max() <= 1e-3
-        R = rot.double().cpu().numpy()
+        assert torch.all(rot[:, 9:] == 0)
+        R = clusco.rotations_view(rot).double().cpu().numpy()
         check_rotations(e.coords, ia, ib, R, c_ref, f"config0 form {form}")
     # element-wise against the oracle's Kabsch rotation where the optimum is well separated
-    R = clusco.crmsd_allpairs_rot(X, clusco.FORM_BF16_EXACT2)[1].double().cpu().numpy()
+    R = clusco.rotations_view(clusco.crmsd_allpairs_rot(X, clusco.FORM_BF16_EXACT2)[1]).double().cpu().numpy()
     sel = np.random.default_rng(1).choice(len(ia), 400, replace=False)
     worst = 0.0
     for k in sel:
@@ -101,7 +102,7 @@ def test_rotations_bench_sample():
     assert clusco.sync_status() == 0
     ia, ib = sample_pairs(N, 5000, 11)
     idx = torch.from_numpy(condensed_index(ia, ib, N)).cuda()
-    R = rot[idx].double().cpu().numpy()
+    R = clusco.rotations_view(rot)[idx].double().cpu().numpy()
     check_rotations(e.coords, ia, ib, R, oracle.crmsd_pairs(e.coords, ia, ib), "5000 x 300 sample")
 
 
@@ -168,6 +169,6 @@ def test_rot_argument_errors():
     with pytest.raises(clusco.ClusCoError):  # the plain form produces no rotations
         clusco.crmsd_allpairs_rot(X, clusco.FORM_FP32_SIMT)
     out = torch.zeros(P, device="cuda")
-    rot = torch.zeros((P, 3, 3), device="cuda")
+    rot = torch.zeros((P, clusco.ROT_STRIDE), device="cuda")
     with pytest.raises(clusco.ClusCoError):  # above the 512 atoms of the stored-rotation adjoint
         clusco.crmsd_allpairs_backward_rot(X, torch.ones(P, device="cuda"), out, rot, 1e-6)
