@@ -8,9 +8,12 @@
 // bwd_tc_kernel: a CTA owns one A tile I (40 models = 128 operand rows) and a contiguous range
 // of B tiles J over the full square (every b != a in both orders, so no atomics on the
 // gradient). Roles:
-//   warp 0 (TMA): X_J^T hi / lo TF32 chunks of 64 atoms into a 3-stage ring;
-//   warp 1 (MMA): sum += P_J . X_J (tcgen05 kind::tf32, three passes hi.hi + hi.lo + lo.hi)
-//     into a TMEM accumulator of Lp <= 512 columns;
+//   warp 0 (TMA): X_J^T hi / lo TF32 chunks (128 atoms x 32 operand rows) into a 3-stage ring;
+//   warp 1 (MMA): the contraction transposed, sum^T += X_J^T . P_J^T (tcgen05 kind::tf32,
+//     M = 128 atoms, N = 128 rows of the A tile, three passes hi.hi + hi.lo + lo.hi): with the
+//     atoms as M the MMAs are 128 x 128 instead of 128 x 64, and the same shared P operand
+//     serves as the K-major B operand. The accumulator holds ceil(Lp/128) blocks of 128
+//     columns (TMEM lanes = atoms);
 //   warps 2-9 (epilogue): gather, build w~ R (two TF32 parts) in one of two shared 128 x 64
 //     operands (128-byte swizzle, K-major), so that tile J+1's operand is written while
 //     GEMM2 reads tile J's. Pairs below the near-duplicate threshold go to the FP64 direct
@@ -25,11 +28,14 @@ namespace clusco {
 constexpr int BR_THREADS = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int BR_XSTAGES = 3;
 constexpr int BR_MAXLP = 512;
-constexpr size_t BR_SMEM = 1024 + 2 * BT_A2 + BR_XSTAGES * BT_XBUF;  // 1 KB + 128 KB + 96 KB
+constexpr int BR_ABLK = 128;                      // atoms per accumulator block (MMA M)
+constexpr size_t BR_XBUF = 2 * 32 * BR_ABLK * 4;  // hi, lo: 32 operand rows x 128 atoms, 32 KB
+constexpr size_t BR_SMEM = 1024 + 2 * BT_A2 + BR_XSTAGES * BR_XBUF;  // 1 KB + 128 KB + 96 KB
 static_assert(BR_SMEM <= 227 * 1024, "shared memory per CTA");
 
 __global__ void __launch_bounds__(BR_THREADS, 1)
-    bwd_rot_kernel(const __grid_constant__ CUtensorMap mapX, int64_t N, int L, int Lp, uint32_t tmem_cols,
+    bwd_rot_kernel(const __grid_constant__ CUtensorMap mapXh, const __grid_constant__ CUtensorMap mapXl, int64_t N,
+                   int L, int Lp, uint32_t tmem_cols,
                    int64_t Rpad, int64_t TB, int64_t S, int64_t JC, const float *__restrict__ crmsd,
                    const float *__restrict__ wvec, const float *__restrict__ rot, float eps, float *__restrict__ Gp,
                    float *__restrict__ dp, long long *__restrict__ nd_list, unsigned long long *__restrict__ nd_count,
@@ -89,7 +95,8 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     const int64_t nJ = J1 - J0;
-    const int nch = Lp / BT_XCH;
+    const int nblk = (Lp + BR_ABLK - 1) / BR_ABLK;
+    const int nch = 2 * nblk;  // per tile: atom blocks x the two 32-row halves of the B tile
     volatile int *abort_v = &abort_flag;
 
     if (warp == 0) {
@@ -106,13 +113,11 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(&xfull_bar[st], (uint32_t)BT_XBUF);
-#pragma unroll
-                    for (int sp2 = 0; sp2 < 2; ++sp2)
-#pragma unroll
-                        for (int kb2 = 0; kb2 < 2; ++kb2)
-                            tma_load_2d(XT + st * BT_XBUF + (2 * sp2 + kb2) * (BT_XCH * 128), &mapX, &xfull_bar[st],
-                                        (int)(64 * J + 32 * kb2), (int)(sp2 * Lp + ch * BT_XCH));
+                    // chunk ch = (atom block ch / 2, operand-row half ch % 2); atoms past Lp read zeros
+                    const int x = (int)(64 * J + 32 * (ch & 1)), y = (ch >> 1) * BR_ABLK;
+                    mbar_arrive_expect_tx(&xfull_bar[st], (uint32_t)BR_XBUF);
+                    tma_load_2d(XT + st * BR_XBUF, &mapXh, &xfull_bar[st], x, y);
+                    tma_load_2d(XT + st * BR_XBUF + BR_XBUF / 2, &mapXl, &xfull_bar[st], x, y);
                 }
             }
             if (!ok) atomicExch(&abort_flag, 1);
@@ -128,7 +133,7 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
         if (lane == 0) {
             int64_t c = 0;
             bool ok = true;
-            constexpr uint32_t idx = make_idesc(128, BT_XCH, 2);
+            constexpr uint32_t idx = make_idesc(BR_ABLK, 128, 2);
             for (int64_t j = 0; j < nJ && ok && !*abort_v; ++j) {
                 const int buf = (int)(j & 1);
                 if (!mbar_wait_sleep(&a2full_bar[buf], (uint32_t)((j >> 1) & 1))) {
@@ -144,21 +149,21 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t xb = xtbase + st * BT_XBUF;
-                    const uint32_t d = tmem + (uint32_t)(ch * BT_XCH);
+                    const uint32_t xb = xtbase + st * BR_XBUF;
+                    const int kh = ch & 1;
+                    const uint32_t d = tmem + (uint32_t)((ch >> 1) * 128);
 #pragma unroll
-                    for (int kb2 = 0; kb2 < 2; ++kb2)
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const uint64_t ahi = desc_sw128(ab + kb2 * 16384 + 32 * k);
-                            const uint64_t alo = desc_sw128(ab + 32768 + kb2 * 16384 + 32 * k);
-                            const uint64_t bhi = desc_sw128(xb + kb2 * (BT_XCH * 128) + 32 * k);
-                            const uint64_t blo = desc_sw128(xb + (2 + kb2) * (BT_XCH * 128) + 32 * k);
-                            // each chunk's first MMA of the sweep starts its columns from zero
-                            mma_tf32(d, ahi, bhi, idx, (j == 0 && kb2 == 0 && k == 0) ? 0u : 1u);
-                            mma_tf32(d, ahi, blo, idx, 1u);
-                            mma_tf32(d, alo, bhi, idx, 1u);
-                        }
+                    for (int k = 0; k < 4; ++k) {
+                        // A = X^T (atoms x operand rows), B = P (A-tile rows x operand rows), both K-major
+                        const uint64_t xhi = desc_sw128(xb + 32 * k);
+                        const uint64_t xlo = desc_sw128(xb + BR_XBUF / 2 + 32 * k);
+                        const uint64_t phi = desc_sw128(ab + kh * 16384 + 32 * k);
+                        const uint64_t plo = desc_sw128(ab + 32768 + kh * 16384 + 32 * k);
+                        // each block's first MMA of the sweep starts its columns from zero
+                        mma_tf32(d, xhi, phi, idx, (j == 0 && kh == 0 && k == 0) ? 0u : 1u);
+                        mma_tf32(d, xhi, plo, idx, 1u);
+                        mma_tf32(d, xlo, phi, idx, 1u);
+                    }
                     mma_commit(&xempty_bar[st]);
                 }
                 mma_commit(&a2empty_bar[buf]);
@@ -275,14 +280,21 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
         }
         if (alive) {
             tc_fence_after();
-            // read the P.X sum out of TMEM: warp (sp, g) takes lanes 32 sp.., half of the atoms
-            float *row = Gp + (sidx * Rpad + 128 * I + 32 * sp + lane) * (int64_t)Lp;
-            const int half = Lp / 2;
-            for (int c0 = g * half; c0 < (g + 1) * half; c0 += 32) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)c0, v);
+            // read the transposed sum out of TMEM: warp (sp, g) takes TMEM lanes 32 sp.. (atoms)
+            // and half g of each block's 128 columns (rows of the A tile)
+            float *gbase = Gp + (sidx * Rpad + 128 * I) * (int64_t)Lp;
+            for (int blk = 0; blk < nblk; ++blk) {
+                const int atom = blk * BR_ABLK + 32 * sp + lane;
 #pragma unroll
-                for (int jj = 0; jj < 32; ++jj) row[c0 + jj] = -v[jj];
+                for (int h = 0; h < 2; ++h) {
+                    const int r0 = 64 * g + 32 * h;
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)(blk * 128 + r0), v);
+                    if (atom < Lp) {
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) gbase[(int64_t)(r0 + jj) * Lp + atom] = -v[jj];
+                    }
+                }
             }
             if (etid < TC_MA) dp[sidx * Npad + a_base + etid] = dsum[etid];
         } else {
@@ -316,15 +328,16 @@ inline int bwr_launch(const float *coords, int64_t N, int64_t L, const float *gr
         err = std::string("backward pre-pass: ") + cudaGetErrorString(e);
         return CLUSCO_ECUDA;
     }
-    CUtensorMap mX;
-    {
-        // X^T parts: FP32 [2 Lp][Rpad]; boxes of 32 columns (128 bytes) x 64 atoms
-        const cuuint64_t dims[2] = {(cuuint64_t)w.Rpad, (cuuint64_t)(2 * w.Lp)};
+    CUtensorMap mXh, mXl;
+    for (int part = 0; part < 2; ++part) {
+        // X^T hi / lo parts: FP32 [Lp][Rpad] each; boxes of 32 operand rows (128 bytes) x 128
+        // atoms; atoms past Lp read as zeros
+        const cuuint64_t dims[2] = {(cuuint64_t)w.Rpad, (cuuint64_t)w.Lp};
         const cuuint64_t strides[1] = {(cuuint64_t)(w.Rpad * 4)};
-        const cuuint32_t box[2] = {32u, (cuuint32_t)BT_XCH};
+        const cuuint32_t box[2] = {32u, (cuuint32_t)BR_ABLK};
         const cuuint32_t estr[2] = {1, 1};
-        CUresult r = encode_fn()(&mX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, w.xT, dims, strides, box, estr,
-                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+        CUresult r = encode_fn()(part ? &mXl : &mXh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, w.xT + part * w.Lp * w.Rpad,
+                                 dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
             err = "cuTensorMapEncodeTiled (X^T) failed (" + std::to_string((int)r) + ")";
@@ -334,12 +347,13 @@ inline int bwr_launch(const float *coords, int64_t N, int64_t L, const float *gr
     const int64_t TA = w.Npad / TC_MA, TB = w.Npad / TC_MB;
     const int64_t JC = (TB + w.S - 1) / w.S;
     uint32_t cols = 32;
-    while (cols < (uint32_t)w.Lp) cols <<= 1;  // TMEM allocations are powers of two
+    const uint32_t need_cols = (uint32_t)((w.Lp + BR_ABLK - 1) / BR_ABLK * 128);
+    while (cols < need_cols) cols <<= 1;  // TMEM allocations are powers of two
     const unsigned grid = (unsigned)(TA * w.S);
     e = cudaFuncSetAttribute(bwd_rot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BR_SMEM);
     if (e == cudaSuccess) {
         prof_mark(PROF_ADJOINT, st);
-        bwd_rot_kernel<<<grid, BR_THREADS, BR_SMEM, st>>>(mX, N, (int)L, (int)w.Lp, cols, w.Rpad, TB, w.S, JC, crmsd,
+        bwd_rot_kernel<<<grid, BR_THREADS, BR_SMEM, st>>>(mXh, mXl, N, (int)L, (int)w.Lp, cols, w.Rpad, TB, w.S, JC, crmsd,
                                                           grad_out, rot, eps, w.Gp, w.dp, w.nd_list, w.nd_count,
                                                           w.nd_cap);
         e = cudaGetLastError();
