@@ -503,7 +503,12 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
     if (warp == 0) tmem_dealloc(tmem, BT_TMEM_COLS);
 }
 
-// g_a = sum_s Gp[s] + (sum_s dp[s][a]) x_a, minus its atom mean; one warp per model.
+// g_a = sum_s Gp[s] + (sum_s dp[s][a]) x_a, minus its atom mean; one warp per model, one pass
+// over memory: every lane keeps its atoms' three axis values in registers (Lp <= 512), the S
+// partial slices of each value are independent loads, and the interleaved (x, y, z) output is
+// written once the per-axis means are known.
+constexpr int BRED_MAXC = 16;  // atoms per lane: Lp / 32 <= 16
+
 __global__ void __launch_bounds__(256) bwd_reduce_kernel(const float *__restrict__ Gp, const float *__restrict__ dp,
                                                          const float *__restrict__ xf, int64_t N, int L, int Lp,
                                                          int64_t Rpad, int64_t S, float *__restrict__ grad)
@@ -514,19 +519,32 @@ __global__ void __launch_bounds__(256) bwd_reduce_kernel(const float *__restrict
     const int64_t Npad = Rpad / 32 * 10;
     float d = 0.f;
     for (int64_t s = 0; s < S; ++s) d += dp[s * Npad + a];
+    float v[3][BRED_MAXC];
+    float m[3] = {0.f, 0.f, 0.f};
+#pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         const int64_t row = tc_row(a, ax);
-        float m = 0.f;
-        for (int i = lane; i < L; i += 32) {
-            float v = d * xf[row * Lp + i];
-            for (int64_t s = 0; s < S; ++s) v += Gp[(s * Rpad + row) * Lp + i];
-            m += v;
+#pragma unroll
+        for (int c = 0; c < BRED_MAXC; ++c) {
+            const int i = lane + 32 * c;
+            float t = 0.f;
+            if (i < L) {
+                t = d * xf[row * Lp + i];
+#pragma unroll 4
+                for (int64_t s = 0; s < S; ++s) t += Gp[(s * Rpad + row) * Lp + i];
+            }
+            v[ax][c] = t;
+            m[ax] += t;
         }
-        m = warp_sum_f(m) / (float)L;
-        for (int i = lane; i < L; i += 32) {
-            float v = d * xf[row * Lp + i];
-            for (int64_t s = 0; s < S; ++s) v += Gp[(s * Rpad + row) * Lp + i];
-            grad[(a * L + i) * 3 + ax] = v - m;
+        m[ax] = warp_sum_f(m[ax]) / (float)L;
+    }
+#pragma unroll
+    for (int c = 0; c < BRED_MAXC; ++c) {
+        const int i = lane + 32 * c;
+        if (i < L) {
+            float *gdst = grad + (a * L + i) * 3;
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) gdst[ax] = v[ax][c] - m[ax];
         }
     }
 }
