@@ -14,10 +14,12 @@
 //     atoms as M the MMAs are 128 x 128 instead of 128 x 64, and the same shared P operand
 //     serves as the K-major B operand. The accumulator holds ceil(Lp/128) blocks of 128
 //     columns (TMEM lanes = atoms);
-//   warps 2-9 (epilogue): gather, build w~ R (two TF32 parts) in one of two shared 128 x 64
-//     operands (128-byte swizzle, K-major), so that tile J+1's operand is written while
-//     GEMM2 reads tile J's. Pairs below the near-duplicate threshold go to the FP64 direct
-//     kernel, as in the recompute path.
+//   warps 2-9 (epilogue): each lane owns one row (model a, axis alpha) of the tile's 128 x 64
+//     operand: it gathers row alpha of R_ab (or column alpha of R_ba) and c, w for its ten
+//     B models, scales, and stores the row as two TF32 parts with 16-byte stores into one of
+//     two shared operands (128-byte swizzle, K-major), so that tile J+1's operand is written
+//     while GEMM2 reads tile J's. Pairs below the near-duplicate threshold go to the FP64
+//     direct kernel, as in the recompute path.
 // At the end the CTA's sum goes out of TMEM into its partial slice; bwd_reduce_kernel adds the
 // partials, the diagonal term and the centring projection.
 #pragma once
@@ -186,49 +188,39 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
         for (int64_t j = 0; j < nJ; ++j) {
             const int64_t b_base = (J0 + j) * TC_MB;
             const int buf = (int)(j & 1);
-            // gather this lane's four pairs: c, w and the stored rotation (issued together)
-            float cpre[4], wpre[4], Rg[4][9];
-            bool lower[4];
+            // This lane owns row (a, alpha) of the tile's operand: for each of its half's 10 B
+            // models b, row alpha of w~ R_ab (or column alpha of R_ba when a > b). Gather them all
+            // first (c, w and three floats of each record), then build and store the row.
+            float cg[10], wg[10], rg[10][3];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                cpre[r] = 0.f;
-                wpre[r] = 0.f;
-                lower[r] = false;
-#pragma unroll
-                for (int e = 0; e < 9; ++e) Rg[r][e] = 0.f;
-                const int bq = 3 * r + alpha;
+            for (int bq = 0; bq < 10; ++bq) {
                 const int64_t b = b_base + 10 * g + bq;
-                if (lane_ok && bq < 10 && b < N && b != a) {
+                cg[bq] = 0.f;
+                wg[bq] = 0.f;
+                rg[bq][0] = rg[bq][1] = rg[bq][2] = 0.f;
+                if (lane_ok && b < N && b != a) {
                     const int64_t lo = a < b ? a : b, hi = a < b ? b : a;
                     const int64_t idx = condensed_idx(lo, hi, N);
-                    cpre[r] = crmsd[idx];
-                    wpre[r] = wvec[idx];
-                    lower[r] = a > b;
-                    const float4 *src = reinterpret_cast<const float4 *>(rot + idx * ROT_STRIDE);
-                    const float4 r0 = __ldg(src), r1 = __ldg(src + 1), r2 = __ldg(src + 2);
-                    Rg[r][0] = r0.x;
-                    Rg[r][1] = r0.y;
-                    Rg[r][2] = r0.z;
-                    Rg[r][3] = r0.w;
-                    Rg[r][4] = r1.x;
-                    Rg[r][5] = r1.y;
-                    Rg[r][6] = r1.z;
-                    Rg[r][7] = r1.w;
-                    Rg[r][8] = r2.x;
+                    cg[bq] = __ldg(crmsd + idx);
+                    wg[bq] = __ldg(wvec + idx);
+                    const float *rec = rot + idx * ROT_STRIDE;
+                    // R_ab row alpha = rec[3 alpha + be]; R_ba^T row alpha = rec[3 be + alpha]
+                    const int o0 = a < b ? 3 * alpha : alpha, st = a < b ? 1 : 3;
+                    rg[bq][0] = __ldg(rec + o0);
+                    rg[bq][1] = __ldg(rec + o0 + st);
+                    rg[bq][2] = __ldg(rec + o0 + 2 * st);
                 }
             }
-            // w~ R blocks (R_ab, or R_ba^T when a > b), rows = a's axes, columns = b's axes
-            float Pall[4][9];
+            float v[32];
+            float csum = 0.f;
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-#pragma unroll
-                for (int e = 0; e < 9; ++e) Pall[r][e] = 0.f;
-                const int bq = 3 * r + alpha;
+            for (int bq = 0; bq < 10; ++bq) {
                 const int64_t b = b_base + 10 * g + bq;
-                if (lane_ok && bq < 10 && b < N && b != a) {
-                    const float c = cpre[r], w = wpre[r];
+                float coef = 0.f;
+                if (lane_ok && b < N && b != a) {
+                    const float c = cg[bq], w = wg[bq];
                     if (!(c >= CLUSCO_NEARDUP)) {
-                        if (a < b && w != 0.f) {
+                        if (alpha == 0 && a < b && w != 0.f) {  // one lane per pair queues it
                             const unsigned long long slot = atomicAdd(nd_count, 1ull);
                             if ((int64_t)slot < nd_cap) {
                                 nd_list[2 * slot] = a;
@@ -236,16 +228,15 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
                             }
                         }
                     } else if (w != 0.f) {
-                        const float coef = __fdividef(w, fL * fmaxf(c, eps));
-#pragma unroll
-                        for (int i = 0; i < 3; ++i)
-#pragma unroll
-                            for (int be = 0; be < 3; ++be)
-                                Pall[r][3 * i + be] = coef * (lower[r] ? Rg[r][3 * be + i] : Rg[r][3 * i + be]);
-                        atomicAdd(&dsum[la], coef);
+                        coef = __fdividef(w, fL * fmaxf(c, eps));
                     }
                 }
+                csum += coef;
+#pragma unroll
+                for (int be = 0; be < 3; ++be) v[3 * bq + be] = coef * rg[bq][be];
             }
+            v[30] = v[31] = 0.f;
+            if (alpha == 0 && lane_ok) atomicAdd(&dsum[la], csum);
             // the operand buffer is reused every other tile: wait until GEMM2 of tile j-2 read it
             bool ok2 = true;
             if (j >= 2) ok2 = mbar_wait_sleep(&a2empty_bar[buf], (uint32_t)(((j >> 1) - 1) & 1));
@@ -253,21 +244,22 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
                 alive = false;
                 break;
             }
-            uint8_t *A2b = A2 + buf * BT_A2;
+            // the row, as two TF32 parts, into the 128-byte-swizzled K-major operand: row
+            // 32 sp + lane of column block g, eight 16-byte chunks at (chunk ^ (row mod 8))
+            if (lane < 30) {
+                const int row = 32 * sp + lane;
+                uint8_t *base = A2 + buf * BT_A2 + g * 16384 + row * 128;
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int bq = 3 * r + alpha;
-                if (lane < 30 && bq < 10) {
+                for (int c16 = 0; c16 < 8; ++c16) {
+                    float h[4], l[4];
 #pragma unroll
-                    for (int i = 0; i < 3; ++i)
-#pragma unroll
-                        for (int be = 0; be < 3; ++be) {
-                            const uint32_t off = a2_offset(32 * sp + 3 * mloc + i, 32 * g + 3 * bq + be);
-                            const float v = Pall[r][3 * i + be];
-                            const float vh = tf32_rna(v);
-                            *reinterpret_cast<float *>(A2b + off) = vh;
-                            *reinterpret_cast<float *>(A2b + 32768 + off) = tf32_rna(v - vh);
-                        }
+                    for (int e = 0; e < 4; ++e) {
+                        h[e] = tf32_rna(v[4 * c16 + e]);
+                        l[e] = tf32_rna(v[4 * c16 + e] - h[e]);
+                    }
+                    const int off = ((c16 ^ (row & 7)) & 7) << 4;
+                    *reinterpret_cast<float4 *>(base + off) = make_float4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<float4 *>(base + 32768 + off) = make_float4(l[0], l[1], l[2], l[3]);
                 }
             }
             fence_proxy_async();  // generic-proxy stores to the operand must be visible to tcgen05.mma
