@@ -352,7 +352,7 @@ inline int bwr_launch(const float *coords, int64_t N, int64_t L, const float *gr
         prof_mark(PROF_ADJOINT, st);
     }
     if (e == cudaSuccess) {
-        bwd_reduce_kernel<<<(unsigned)((N + 7) / 8), 256, 0, st>>>(w.Gp, w.dp, w.xf, N, (int)L, (int)w.Lp, w.Rpad,
+        bwd_reduce_kernel<<<(unsigned)((3 * N + 7) / 8), 256, 0, st>>>(w.Gp, w.dp, w.xf, N, (int)L, (int)w.Lp, w.Rpad,
                                                                     w.S, grad);
         e = cudaGetLastError();
     }

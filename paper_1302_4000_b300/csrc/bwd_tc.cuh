@@ -503,49 +503,46 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
     if (warp == 0) tmem_dealloc(tmem, BT_TMEM_COLS);
 }
 
-// g_a = sum_s Gp[s] + (sum_s dp[s][a]) x_a, minus its atom mean; one warp per model, one pass
-// over memory: every lane keeps its atoms' three axis values in registers (Lp <= 512), the S
-// partial slices of each value are independent loads, and the interleaved (x, y, z) output is
-// written once the per-axis means are known.
-constexpr int BRED_MAXC = 16;  // atoms per lane: Lp / 32 <= 16
+// g_a = sum_s Gp[s] + (sum_s dp[s][a]) x_a, minus its atom mean. One warp per (model, axis):
+// the lane's atoms (Lp <= 512, at most 16 per lane) stay in registers, every partial slice of
+// every atom is an independent load, the axis mean
+// is a warp reduction, and the gradient's axis is written once.
+constexpr int BRED_MAXC = 16;
 
-__global__ void __launch_bounds__(256) bwd_reduce_kernel(const float *__restrict__ Gp, const float *__restrict__ dp,
+__global__ void __launch_bounds__(256, 3) bwd_reduce_kernel(const float *__restrict__ Gp, const float *__restrict__ dp,
                                                          const float *__restrict__ xf, int64_t N, int L, int Lp,
                                                          int64_t Rpad, int64_t S, float *__restrict__ grad)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t a = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int64_t wg = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int64_t a = wg / 3;
+    const int ax = (int)(wg - 3 * a);
     if (a >= N) return;
     const int64_t Npad = Rpad / 32 * 10;
+    const int64_t row = tc_row(a, ax);
+    const int64_t slice = Rpad * (int64_t)Lp;
+    const float *g0 = Gp + row * Lp, *x0 = xf + row * Lp;
     float d = 0.f;
     for (int64_t s = 0; s < S; ++s) d += dp[s * Npad + a];
-    float v[3][BRED_MAXC];
-    float m[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-        const int64_t row = tc_row(a, ax);
-#pragma unroll
-        for (int c = 0; c < BRED_MAXC; ++c) {
-            const int i = lane + 32 * c;
-            float t = 0.f;
-            if (i < L) {
-                t = d * xf[row * Lp + i];
-#pragma unroll 4
-                for (int64_t s = 0; s < S; ++s) t += Gp[(s * Rpad + row) * Lp + i];
-            }
-            v[ax][c] = t;
-            m[ax] += t;
-        }
-        m[ax] = warp_sum_f(m[ax]) / (float)L;
-    }
+    float v[BRED_MAXC];
+    float m = 0.f;
 #pragma unroll
     for (int c = 0; c < BRED_MAXC; ++c) {
         const int i = lane + 32 * c;
+        float t = 0.f;
         if (i < L) {
-            float *gdst = grad + (a * L + i) * 3;
-#pragma unroll
-            for (int ax = 0; ax < 3; ++ax) gdst[ax] = v[ax][c] - m[ax];
+            t = d * x0[i];
+#pragma unroll 4
+            for (int64_t s = 0; s < S; ++s) t += g0[s * slice + i];
         }
+        v[c] = t;
+        m += t;
+    }
+    m = warp_sum_f(m) / (float)L;
+#pragma unroll
+    for (int c = 0; c < BRED_MAXC; ++c) {
+        const int i = lane + 32 * c;
+        if (i < L) grad[(a * L + i) * 3 + ax] = v[c] - m;
     }
 }
 
@@ -601,7 +598,7 @@ inline int bt_launch(const float *coords, int64_t N, int64_t L, const float *gra
         prof_mark(PROF_ADJOINT, st);
     }
     if (e == cudaSuccess) {
-        bwd_reduce_kernel<<<(unsigned)((N + 7) / 8), 256, 0, st>>>(w.Gp, w.dp, w.xf, N, (int)L, (int)w.Lp, w.Rpad,
+        bwd_reduce_kernel<<<(unsigned)((3 * N + 7) / 8), 256, 0, st>>>(w.Gp, w.dp, w.xf, N, (int)L, (int)w.Lp, w.Rpad,
                                                                     w.S, grad);
         e = cudaGetLastError();
     }

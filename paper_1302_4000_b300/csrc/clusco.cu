@@ -314,7 +314,7 @@ int clusco_crmsd_vs_ref(const float *coords, int64_t N, int64_t L, const float *
     Carver c(s.ptr);
     int *nref = c.take<int>((size_t)L * 3);
     RefInfo *info = c.take<RefInfo>(1);
-    ref_prepass_kernel<<<1, 1024, 0, st>>>(ref, (int)L, nref, info);
+    ref_prepass_kernel<<<1, RP_THREADS, 0, st>>>(ref, (int)L, nref, info);
     CUDA_TRY(cudaGetLastError());
     const size_t smem = (size_t)L * 3 * sizeof(int);
     if (smem > 48 * 1024) CUDA_TRY(cudaFuncSetAttribute(vsref_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -434,7 +434,7 @@ int clusco_crmsd_vs_ref_noalloc(const float *coords, int64_t N, int64_t L, const
     cudaStream_t st = (cudaStream_t)stream;
     int *nref = (int *)scratch;
     RefInfo *info = (RefInfo *)((char *)scratch + NOALLOC_REF_BYTES);
-    ref_prepass_kernel<<<1, 1024, 0, st>>>(ref, (int)L, nref, info);
+    ref_prepass_kernel<<<1, RP_THREADS, 0, st>>>(ref, (int)L, nref, info);
     CUDA_TRY(cudaGetLastError());
     const size_t smem = (size_t)L * 3 * sizeof(int);
     if (smem > 48 * 1024) CUDA_TRY(cudaFuncSetAttribute(vsref_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

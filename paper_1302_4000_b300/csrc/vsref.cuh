@@ -21,19 +21,23 @@ struct RefInfo {
     int finite;
 };
 
-// One block of 1024 threads (32 warps) quantises the reference: nref[i][axis] (int32).
-__global__ void __launch_bounds__(1024) ref_prepass_kernel(const float *__restrict__ ref, int L,
-                                                           int *__restrict__ nref, RefInfo *__restrict__ info)
+// One block of RP_THREADS threads quantises the reference: nref[i][axis] (int32). Eight warps
+// keep the FP64 block reductions (centroid, G) short: the FP64 pipe is 1/64 of FP32 here.
+constexpr int RP_THREADS = 256;
+constexpr int RP_WARPS = RP_THREADS / 32;
+
+__global__ void __launch_bounds__(RP_THREADS) ref_prepass_kernel(const float *__restrict__ ref, int L,
+                                                                 int *__restrict__ nref, RefInfo *__restrict__ info)
 {
-    __shared__ double red[32][3];
-    __shared__ float mx[32][3];
-    __shared__ long long gred[32][3];
+    __shared__ double red[RP_WARPS][3];
+    __shared__ float mx[RP_WARPS][3];
+    __shared__ long long gred[RP_WARPS][3];
     __shared__ int bad;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x == 0) bad = 0;
     double s[3] = {0, 0, 0};
     bool ok = true;
-    for (int i = threadIdx.x; i < L; i += 1024)
+    for (int i = threadIdx.x; i < L; i += RP_THREADS)
         for (int ax = 0; ax < 3; ++ax) {
             const float v = ref[3 * i + ax];
             ok = ok && isfinite(v);
@@ -49,11 +53,11 @@ __global__ void __launch_bounds__(1024) ref_prepass_kernel(const float *__restri
     float mu[3];
     for (int ax = 0; ax < 3; ++ax) {
         double t = 0;
-        for (int k = 0; k < 32; ++k) t += red[k][ax];
+        for (int k = 0; k < RP_WARPS; ++k) t += red[k][ax];
         mu[ax] = (float)(t / (double)L);
     }
     float m[3] = {0, 0, 0};
-    for (int i = threadIdx.x; i < L; i += 1024)
+    for (int i = threadIdx.x; i < L; i += RP_THREADS)
         for (int ax = 0; ax < 3; ++ax) m[ax] = fmaxf(m[ax], fabsf(ref[3 * i + ax] - mu[ax]));
     for (int ax = 0; ax < 3; ++ax) {
         const float t = warp_max_f(m[ax]);
@@ -63,12 +67,12 @@ __global__ void __launch_bounds__(1024) ref_prepass_kernel(const float *__restri
     float sc[3], inv[3];
     for (int ax = 0; ax < 3; ++ax) {
         float t = 0.f;
-        for (int k = 0; k < 32; ++k) t = fmaxf(t, mx[k][ax]);
+        for (int k = 0; k < RP_WARPS; ++k) t = fmaxf(t, mx[k][ax]);
         sc[ax] = (t > 0.f && isfinite(t)) ? t / Q24 : 1.f;
         inv[ax] = (t > 0.f && isfinite(t)) ? Q24 / t : 1.f;
     }
     long long g[3] = {0, 0, 0};
-    for (int i = threadIdx.x; i < L; i += 1024)
+    for (int i = threadIdx.x; i < L; i += RP_THREADS)
         for (int ax = 0; ax < 3; ++ax) {
             const float v = ref[3 * i + ax] - mu[ax];
             float n = rintf(v * inv[ax]);
@@ -86,7 +90,7 @@ __global__ void __launch_bounds__(1024) ref_prepass_kernel(const float *__restri
         double G = 0;
         for (int ax = 0; ax < 3; ++ax) {
             long long t = 0;
-            for (int k = 0; k < 32; ++k) t += gred[k][ax];
+            for (int k = 0; k < RP_WARPS; ++k) t += gred[k][ax];
             G += (double)sc[ax] * (double)sc[ax] * (double)t;
             info->scale[ax] = sc[ax];
             info->mu[ax] = mu[ax];
