@@ -185,16 +185,16 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
         const bool lane_ok = lane < 30 && a < N;
         const float fL = (float)L;
         bool alive = true;
-        for (int64_t j = 0; j < nJ; ++j) {
-            const int64_t b_base = (J0 + j) * TC_MB;
-            const int buf = (int)(j & 1);
-            // This lane owns row (a, alpha) of the tile's operand: for each of its half's 10 B
-            // models b, row alpha of w~ R_ab (or column alpha of R_ba when a > b). Gather them all
-            // first (c, w and three floats of each record), then build and store the row.
-            float cg[10], wg[10], rg[10][3];
+        // This lane owns row (a, alpha) of each tile's operand: for each of its half's 10 B
+        // models b, row alpha of w~ R_ab (or column alpha of R_ba when a > b). The gathers (c, w
+        // and three floats of each record) are software-pipelined: tile j+1's are issued before
+        // tile j's operand is stored, so their latency overlaps the wait and the stores.
+        float cg[10], wg[10], rg[10][3];
+        auto gather = [&](int64_t jj) {
+            const int64_t gb = (J0 + jj) * TC_MB + 10 * g;
 #pragma unroll
             for (int bq = 0; bq < 10; ++bq) {
-                const int64_t b = b_base + 10 * g + bq;
+                const int64_t b = gb + bq;
                 cg[bq] = 0.f;
                 wg[bq] = 0.f;
                 rg[bq][0] = rg[bq][1] = rg[bq][2] = 0.f;
@@ -211,6 +211,11 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
                     rg[bq][2] = __ldg(rec + o0 + 2 * st);
                 }
             }
+        };
+        gather(0);
+        for (int64_t j = 0; j < nJ; ++j) {
+            const int64_t b_base = (J0 + j) * TC_MB;
+            const int buf = (int)(j & 1);
             float v[32];
             float csum = 0.f;
 #pragma unroll
@@ -237,6 +242,7 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
             }
             v[30] = v[31] = 0.f;
             if (alpha == 0 && lane_ok) atomicAdd(&dsum[la], csum);
+            if (j + 1 < nJ) gather(j + 1);  // consumed by the next iteration
             // the operand buffer is reused every other tile: wait until GEMM2 of tile j-2 read it
             bool ok2 = true;
             if (j >= 2) ok2 = mbar_wait_sleep(&a2empty_bar[buf], (uint32_t)(((j >> 1) - 1) & 1));
