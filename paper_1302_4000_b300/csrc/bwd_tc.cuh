@@ -56,6 +56,7 @@ struct BtWs {
     float *dp = nullptr;     // [S][Npad] partial row sums of w~
     long long *nd_list = nullptr;
     unsigned long long *nd_count = nullptr;
+    unsigned *scl = nullptr;  // stored-rotation adjoint: max |centred x|, max |w| (float bits)
     int64_t S = 1, nd_cap = 0, Lp = 0, Npad = 0, Rpad = 0;
     size_t bytes = 0;
 };
@@ -94,6 +95,7 @@ inline BtWs carve_bt(void *base, int64_t N, int64_t L)
     w.nd_cap = P < (int64_t)(1 << 22) ? P : (int64_t)(1 << 22);
     w.nd_list = (long long *)take(sizeof(long long) * 2 * w.nd_cap);
     w.nd_count = (unsigned long long *)take(sizeof(unsigned long long));
+    w.scl = (unsigned *)take(2 * sizeof(unsigned));
     w.bytes = off;
     return w;
 }

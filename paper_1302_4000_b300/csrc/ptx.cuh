@@ -135,6 +135,19 @@ __device__ __forceinline__ void bulk_load(void *smem_dst, const void *gsrc, uint
                  : "memory");
 }
 
+// Four-byte asynchronous copy global -> shared (no register staging), grouped per thread:
+// commit closes a group, wait<n> returns once at most n of this thread's groups are pending.
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem_dst)), "l"((uint64_t)gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int n>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(n) : "memory");
+}
+
 __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap *map)
 {
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
@@ -167,6 +180,13 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
         : "memory");
+}
+
+// The same instruction with FP16 operands (the format is in the instruction descriptor).
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                        uint32_t accumulate)
+{
+    mma_bf16(d_tmem, a_desc, b_desc, idesc, accumulate);
 }
 
 // Same with tf32 operands.
@@ -261,7 +281,7 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
     return d;
 }
 
-// Instruction descriptor: FP32 accumulator, A/B format (1 = bf16 for kind::f16,
+// Instruction descriptor: FP32 accumulator, A/B format (0 = fp16 or 1 = bf16 for kind::f16,
 // 2 = tf32 for kind::tf32), both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t make_idesc(int M, int N, uint32_t ab_format)
 {
