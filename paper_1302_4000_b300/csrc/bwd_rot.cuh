@@ -33,6 +33,8 @@
 #pragma once
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "bwd_tc.cuh"
 
 namespace clusco {
@@ -338,16 +340,17 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
                     const float *src = alpha ? wvec : crmsd;
                     float *d = cw + alpha * 100 + mloc * 10;
                     if (mode == 0) {
-                        const int64_t i0 = condensed_idx(a, b0, N);
-#pragma unroll 1
-                        for (int bq = 0; bq < nb; ++bq) cp_async4(d + bq, src + i0 + bq);
+                        const float *s0 = src + condensed_idx(a, b0, N);
+#pragma unroll
+                        for (int bq = 0; bq < 10; ++bq)
+                            if (bq < nb) cp_async4(d + bq, s0 + bq);
                     } else {
-                        int64_t i = condensed_idx(b0, a, N);  // idx(b + 1, a) = idx(b, a) + N - b - 2
-#pragma unroll 1
-                        for (int bq = 0; bq < nb; ++bq) {
-                            cp_async4(d + bq, src + i);
-                            i += N - (b0 + bq) - 2;
-                        }
+                        // idx(b + 1, a) = idx(b, a) + N - b - 2
+                        const float *s0 = src + condensed_idx(b0, a, N);
+                        const int64_t step0 = N - b0 - 2;
+#pragma unroll
+                        for (int bq = 0; bq < 10; ++bq)
+                            if (bq < nb) cp_async4(d + bq, s0 + (bq * step0 - (int64_t)(bq * (bq - 1) / 2)));
                     }
                 }
             }
@@ -370,37 +373,50 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
             const int mode = br_mode(a0, b0);
             const uint8_t *rw = REC + buf * BR_REC + ew * BR_RECW;
             const float *cw = CW + (buf * 8 + ew) * BR_CWW;
+            // pair (a, b0 + bq) is valid for bq < nbv, bq != self (b == a only straddling the diagonal)
+            const int nbv = lane_ok ? (int)(N - b0 < 0 ? 0 : (N - b0 > 10 ? 10 : N - b0)) : 0;
+            const int self = (int)(a - b0);
             float v[32];
             float csum = 0.f;
+            uint32_t ndm = 0;  // pairs below the near-duplicate threshold, queued after the loop
+            // One straight-line pass over the ten B models: row alpha of R_ab from record (a, b)
+            // along row a (mode 0, and the diagonal blocks' gathered rows), or column alpha of
+            // R_ba from record (b, a) along row b (mode 1).
+            auto consume = [&](auto below) {
+                constexpr bool M1 = decltype(below)::value;
 #pragma unroll
-            for (int bq = 0; bq < 10; ++bq) {
-                const int64_t b = b0 + bq;
-                const bool valid = lane_ok && b < N && b != a;
-                const float c = cw[ml * 10 + bq], w = cw[100 + ml * 10 + bq];
-                // row alpha of R_ab: record (a, b) along row a; column alpha of R_ba below
-                const float *r = mode == 1 ? reinterpret_cast<const float *>(rw + bq * BR_SEG + ml * 48) + alpha
-                                           : reinterpret_cast<const float *>(rw + ml * BR_SEG + bq * 48) + 3 * alpha;
-                const int st = mode == 1 ? 3 : 1;
-                const float r0 = r[0], r1 = r[st], r2 = r[2 * st];
-                float coef = 0.f;
-                if (valid) {
-                    if (!(c >= CLUSCO_NEARDUP)) {
-                        if (alpha == 0 && a < b && w != 0.f) {  // one lane per pair queues it
-                            const unsigned long long slot = atomicAdd(nd_count, 1ull);
-                            if ((int64_t)slot < nd_cap) {
-                                nd_list[2 * slot] = a;
-                                nd_list[2 * slot + 1] = b;
-                            }
+                for (int bq = 0; bq < 10; ++bq) {
+                    const bool valid = bq < nbv && bq != self;
+                    const float c = cw[ml * 10 + bq], w = cw[100 + ml * 10 + bq];
+                    const float *r = M1 ? reinterpret_cast<const float *>(rw + bq * BR_SEG + ml * 48) + alpha
+                                        : reinterpret_cast<const float *>(rw + ml * BR_SEG + bq * 48) + 3 * alpha;
+                    constexpr int st = M1 ? 3 : 1;
+                    const float r0 = r[0], r1 = r[st], r2 = r[2 * st];
+                    const bool far = c >= CLUSCO_NEARDUP;
+                    ndm |= (valid && !far && w != 0.f) ? (1u << bq) : 0u;
+                    const float coef = (valid && far) ? __fdividef(w, fL * fmaxf(c, eps)) : 0.f;
+                    csum += coef;
+                    const float cs = coef * sP;
+                    v[3 * bq + 0] = valid ? cs * r0 : 0.f;
+                    v[3 * bq + 1] = valid ? cs * r1 : 0.f;
+                    v[3 * bq + 2] = valid ? cs * r2 : 0.f;
+                }
+            };
+            if (mode == 1)
+                consume(std::true_type{});
+            else
+                consume(std::false_type{});
+            if (ndm != 0u && alpha == 0) {  // rare: one lane per pair queues it, from the a < b side
+                for (int bq = 0; bq < 10; ++bq) {
+                    const int64_t b = b0 + bq;
+                    if (((ndm >> bq) & 1u) && a < b) {
+                        const unsigned long long slot = atomicAdd(nd_count, 1ull);
+                        if ((int64_t)slot < nd_cap) {
+                            nd_list[2 * slot] = a;
+                            nd_list[2 * slot + 1] = b;
                         }
-                    } else if (w != 0.f) {
-                        coef = __fdividef(w, fL * fmaxf(c, eps));
                     }
                 }
-                csum += coef;
-                const float cs = coef * sP;
-                v[3 * bq + 0] = valid ? cs * r0 : 0.f;
-                v[3 * bq + 1] = valid ? cs * r1 : 0.f;
-                v[3 * bq + 2] = valid ? cs * r2 : 0.f;
             }
             v[30] = v[31] = 0.f;
             if (alpha == 0 && lane_ok) atomicAdd(&dsum[la], csum);

@@ -172,3 +172,30 @@ def test_rot_argument_errors():
     rot = torch.zeros((P, clusco.ROT_STRIDE), device="cuda")
     with pytest.raises(clusco.ClusCoError):  # above the 512 atoms of the stored-rotation adjoint
         clusco.crmsd_allpairs_backward_rot(X, torch.ones(P, device="cuda"), out, rot, 1e-6)
+
+
+@pytest.mark.parametrize("which", ["bench 5000 x 300", "large 8192 x 500"])
+def test_backward_rot_full_size_rows(which):
+    """The bench's workload (and the large forward+backward size) in the launch configuration
+    the bench times: sampled rows of the gradient against the oracle's per-row FP64 gradient."""
+    if which.startswith("bench"):
+        e = E.config1()
+        w = E.weights(e.N * (e.N - 1) // 2, E.SEED_BASE + 101)
+    else:
+        e = E.config4(N=8192, L=500)
+        w = E.weights(e.N * (e.N - 1) // 2, 505)
+    N = e.N
+    X = torch.from_numpy(e.coords).cuda()
+    out, rot = clusco.crmsd_allpairs_rot(X, clusco.FORM_BF16_EXACT2)
+    g = clusco.crmsd_allpairs_backward_rot(X, torch.from_numpy(w).cuda(), out, rot, 1e-6)
+    assert clusco.sync_status() == 0
+    rows = np.unique(np.concatenate([[0, 1, 39, 40, N // 2, N - 1],
+                                     np.random.default_rng(5).integers(0, N, 3)]))
+    gref = oracle.crmsd_grad_rows(e.coords, w.astype(np.float64), rows, 1e-6)
+    gg = g[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+    rel = np.linalg.norm((gg - gref).reshape(len(rows), -1), axis=1) / np.linalg.norm(gref.reshape(len(rows), -1), axis=1)
+    rms = np.sqrt((gref.reshape(len(rows), -1) ** 2).mean(axis=1))[:, None, None]
+    coord = np.abs(gg - gref) <= 1e-3 * (np.abs(gref) + rms)
+    print(f"\n{which}: per-model rel err {rel.max():.3e}, coords ok {coord.mean():.6f}")
+    assert rel.max() <= 1e-3
+    assert coord.all()
