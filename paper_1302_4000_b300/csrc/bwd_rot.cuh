@@ -422,7 +422,10 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
             if (alpha == 0 && lane_ok) atomicAdd(&dsum[la], csum);
             // the operand buffer is reused every other tile: wait until the MMAs of tile j-2 read it
             if (j >= 2) ok = mbar_wait_sleep(&a2empty_bar[buf], (uint32_t)(((j >> 1) - 1) & 1)) && ok;
-            if (named_bar_or(1, 256, !ok || *abort_v)) {
+            // each warp decides for itself (no barrier per tile); a warp that stops raises the
+            // flag, and the others' bounded waits end their sweeps
+            if (__any_sync(0xffffffffu, !ok || *abort_v)) {
+                if (lane == 0) atomicExch(&abort_flag, 1);
                 alive = false;
                 jfail = j;
                 break;
@@ -460,9 +463,9 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
             if (jfail + 1 < nJ) mbar_wait(&rec_bar[(jfail + 1) & 1][ew], (uint32_t)(((jfail + 1) >> 1) & 1));
             cp_async_wait<0>();
         }
-        if (alive) {
-            const bool ok3 = mbar_wait_sleep(&d2_bar, 0);
-            if (named_bar_or(1, 256, !ok3 || *abort_v)) alive = false;
+        {  // every epilogue warp, stopped or not, meets the others here once
+            const bool ok3 = alive && mbar_wait_sleep(&d2_bar, 0);
+            alive = !named_bar_or(1, 256, !ok3 || *abort_v);
         }
         if (alive) {
             tc_fence_after();
