@@ -555,9 +555,7 @@ inline int bwr_launch(const float *coords, int64_t N, int64_t L, const float *gr
         prof_mark(PROF_ADJOINT, st);
     }
     if (e == cudaSuccess) {
-        bwd_reduce_kernel<<<(unsigned)((3 * N + 7) / 8), 256, 0, st>>>(w.Gp, w.dp, w.xf, N, (int)L, (int)w.Lp, w.Rpad,
-                                                                    w.S, grad);
-        e = cudaGetLastError();
+        e = launch_bwd_reduce(w, N, L, grad, st);
     }
     if (e == cudaSuccess) {
         bwd_neardup_kernel<<<296, 256, 0, st>>>(coords, N, (int)L, grad_out, eps, w.nd_list, w.nd_count, w.nd_cap,

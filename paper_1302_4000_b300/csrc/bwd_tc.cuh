@@ -505,47 +505,71 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
     if (warp == 0) tmem_dealloc(tmem, BT_TMEM_COLS);
 }
 
-// g_a = sum_s Gp[s] + (sum_s dp[s][a]) x_a, minus its atom mean. One warp per (model, axis):
-// the lane's atoms (Lp <= 512, at most 16 per lane) stay in registers, every partial slice of
-// every atom is an independent load, the axis mean
-// is a warp reduction, and the gradient's axis is written once.
-constexpr int BRED_MAXC = 16;
+// g_a = sum_s Gp[s] + (sum_s dp[s][a]) x_a, minus its atom mean. One block of three warps per
+// model, warp = axis: each lane holds up to four float4 columns of its row (Lp <= 512), every
+// partial slice is an independent 16-byte load, the axis mean is a warp reduction, and the
+// model's gradient goes out through shared memory as one contiguous [L][3] run. Columns past L
+// are zero in every input, so the row sum over Lp is the sum over L.
+constexpr int BRED_THREADS = 96;
+constexpr int BRED_MAXQ = 4;
 
-__global__ void __launch_bounds__(256, 3) bwd_reduce_kernel(const float *__restrict__ Gp, const float *__restrict__ dp,
-                                                         const float *__restrict__ xf, int64_t N, int L, int Lp,
-                                                         int64_t Rpad, int64_t S, float *__restrict__ grad)
+__global__ void __launch_bounds__(BRED_THREADS) bwd_reduce_kernel(const float *__restrict__ Gp,
+                                                                  const float *__restrict__ dp,
+                                                                  const float *__restrict__ xf, int64_t N, int L,
+                                                                  int Lp, int64_t Rpad, int64_t S,
+                                                                  float *__restrict__ grad)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t wg = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int64_t a = wg / 3;
-    const int ax = (int)(wg - 3 * a);
-    if (a >= N) return;
+    extern __shared__ float sg[];  // [L][3], as in grad
+    const int lane = threadIdx.x & 31, ax = threadIdx.x >> 5;
+    const int64_t a = blockIdx.x;
     const int64_t Npad = Rpad / 32 * 10;
     const int64_t row = tc_row(a, ax);
-    const int64_t slice = Rpad * (int64_t)Lp;
-    const float *g0 = Gp + row * Lp, *x0 = xf + row * Lp;
+    const int64_t qslice = Rpad * (int64_t)Lp / 4;
+    const float4 *g0 = reinterpret_cast<const float4 *>(Gp + row * Lp);
+    const float4 *x0 = reinterpret_cast<const float4 *>(xf + row * Lp);
+    const int nq = Lp / 4;
     float d = 0.f;
     for (int64_t s = 0; s < S; ++s) d += dp[s * Npad + a];
-    float v[BRED_MAXC];
+    float4 v[BRED_MAXQ];
     float m = 0.f;
 #pragma unroll
-    for (int c = 0; c < BRED_MAXC; ++c) {
-        const int i = lane + 32 * c;
-        float t = 0.f;
-        if (i < L) {
-            t = d * x0[i];
+    for (int c = 0; c < BRED_MAXQ; ++c) {
+        const int q = lane + 32 * c;
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (q < nq) {
+            const float4 x = __ldg(x0 + q);
+            t = make_float4(d * x.x, d * x.y, d * x.z, d * x.w);
 #pragma unroll 4
-            for (int64_t s = 0; s < S; ++s) t += g0[s * slice + i];
+            for (int64_t s = 0; s < S; ++s) {
+                const float4 gv = __ldg(g0 + s * qslice + q);
+                t.x += gv.x;
+                t.y += gv.y;
+                t.z += gv.z;
+                t.w += gv.w;
+            }
         }
         v[c] = t;
-        m += t;
+        m += (t.x + t.y) + (t.z + t.w);
     }
     m = warp_sum_f(m) / (float)L;
 #pragma unroll
-    for (int c = 0; c < BRED_MAXC; ++c) {
-        const int i = lane + 32 * c;
-        if (i < L) grad[(a * L + i) * 3 + ax] = v[c] - m;
+    for (int c = 0; c < BRED_MAXQ; ++c) {
+        const int i = 4 * (lane + 32 * c);
+        if (i + 0 < L) sg[3 * (i + 0) + ax] = v[c].x - m;
+        if (i + 1 < L) sg[3 * (i + 1) + ax] = v[c].y - m;
+        if (i + 2 < L) sg[3 * (i + 2) + ax] = v[c].z - m;
+        if (i + 3 < L) sg[3 * (i + 3) + ax] = v[c].w - m;
     }
+    __syncthreads();
+    float *ga = grad + a * (int64_t)L * 3;
+    for (int e = threadIdx.x; e < 3 * L; e += BRED_THREADS) ga[e] = sg[e];
+}
+
+inline cudaError_t launch_bwd_reduce(const BtWs &w, int64_t N, int64_t L, float *grad, cudaStream_t st)
+{
+    bwd_reduce_kernel<<<(unsigned)N, BRED_THREADS, (size_t)(3 * L * sizeof(float)), st>>>(
+        w.Gp, w.dp, w.xf, N, (int)L, (int)w.Lp, w.Rpad, w.S, grad);
+    return cudaGetLastError();
 }
 
 // Host side: pre-pass (digits + FP32 copy + transposed TF32 parts), the tensor-core sweep,
@@ -600,9 +624,7 @@ inline int bt_launch(const float *coords, int64_t N, int64_t L, const float *gra
         prof_mark(PROF_ADJOINT, st);
     }
     if (e == cudaSuccess) {
-        bwd_reduce_kernel<<<(unsigned)((3 * N + 7) / 8), 256, 0, st>>>(w.Gp, w.dp, w.xf, N, (int)L, (int)w.Lp, w.Rpad,
-                                                                    w.S, grad);
-        e = cudaGetLastError();
+        e = launch_bwd_reduce(w, N, L, grad, st);
     }
     if (e == cudaSuccess) {
         bwd_neardup_kernel<<<296, 256, 0, st>>>(coords, N, (int)L, grad_out, eps, w.nd_list, w.nd_count, w.nd_cap,

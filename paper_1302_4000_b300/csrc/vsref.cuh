@@ -4,7 +4,7 @@
 // that hit L1). The covariance is exact: centred coordinates are rounded to 24-bit fixed
 // point per model and axis (step max|x| / (2^23 - 1)), the 9 products and 3 squares are
 // accumulated in int64 (|n| < 2^23, so L < 2^17 cannot overflow), and the FP64 epilogue
-// (cubic start + quartic Newton polish) turns them into cRMSD.
+// (an FP32 start polished by FP64 Newton on the quartic) turns them into cRMSD.
 #pragma once
 #include "common.cuh"
 #include "epilogue.cuh"
@@ -193,7 +193,14 @@ __global__ void __launch_bounds__(256) vsref_kernel(const float *__restrict__ co
                 c = __int_as_float(0x7fc00000);
                 if (!sfin[lane]) set_status(CLUSCO_ST_NONFINITE);
             } else {
-                c = (float)crmsd_refined_fp64(H, Ga, ri.G, 1.0 / (double)L, 0.0, false);
+                // FP32 start (cubic + two Newton steps on the normalised covariance), then FP64
+                // Newton on the exact covariance: no FP64 trigonometry unless the root is degenerate
+                const double Gs = Ga + ri.G;
+                const double nrm = Gs > 0.0 ? 2.0 / Gs : 0.0;
+                float mf[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) mf[k] = (float)(H[k] * nrm);
+                c = crmsd_refine_newton_fp64(H, Ga, ri.G, 1.0 / (double)L, sigma_hat_f32(mf));
             }
             out[a] = c;
         }
