@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
                         float Hn[9], Rp[9];
 #pragma unroll
                         for (int e = 0; e < 9; ++e) Hn[e] = blk[e] * nrm;
-                        if (!sigma_rotation_f32(Hn, Rp)) rotation_robust_ool(Hn, Rp);
+                        if (!sigma_rotation_f32(Hn, Rp)) rotation_robust_ptr(Hn, Rp);
                         const float coef = __fdividef(w, (float)L * fmaxf(c, eps));
 #pragma unroll
                         for (int i = 0; i < 3; ++i) {

@@ -269,9 +269,31 @@ __device__ __noinline__ void refine_queued(const QEntry *qe, const float *__rest
 // The rotation of a rare block whose quartic root is (nearly) double (out of line): Jacobi
 // sweeps for a rank-deficient block (I2 ~ 0, where an FP32 Sigma is least accurate), else
 // Horn's adjugate with the block's Sigma, and Jacobi sweeps where that is degenerate too.
-__device__ __noinline__ void rotation_robust_ool(const float *Hn, float *R)
+// (By value: an address taken in the caller would keep its matrices in local memory on every
+// pass of the fast path, not only on the rare call.)
+struct Mat3 {
+    float e[9];
+};
+
+__device__ __noinline__ Mat3 rotation_robust_ool(Mat3 Hn)
 {
-    float H[9], Rl[9];
+    float Rl[9];
+    float I1, det, I2;
+    invariants3(Hn.e, I1, det, I2);
+    if (!(I2 > 1e-8f * I1 * I1) || !horn_rotation(Hn.e, sigma_hat_f32(Hn.e), 1e-5f, Rl))
+        rotation_jacobi4<float, 8>(Hn.e, Rl);
+    Mat3 R;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) R.e[e] = Rl[e];
+    return R;
+}
+
+// Pointer form, for callers whose matrices already live in memory or whose registers are
+// scarcer than their stack (the recompute adjoint).
+__device__ __noinline__ void rotation_robust_ptr(const float *Hn, float *R)
+{
+    float Rl[9];
+    float H[9];
 #pragma unroll
     for (int e = 0; e < 9; ++e) H[e] = Hn[e];
     float I1, det, I2;
@@ -279,6 +301,16 @@ __device__ __noinline__ void rotation_robust_ool(const float *Hn, float *R)
     if (!(I2 > 1e-8f * I1 * I1) || !horn_rotation(H, sigma_hat_f32(H), 1e-5f, Rl)) rotation_jacobi4<float, 8>(H, Rl);
 #pragma unroll
     for (int e = 0; e < 9; ++e) R[e] = Rl[e];
+}
+
+__device__ __forceinline__ void rotation_robust(const float Hn[9], float R[9])
+{
+    Mat3 h;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) h.e[e] = Hn[e];
+    const Mat3 r = rotation_robust_ool(h);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) R[e] = r.e[e];
 }
 
 // Deferred rotations: Jacobi sweeps on each listed pair's covariance (one pair per thread).
@@ -538,7 +570,7 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                                         f->m[3 * ax + be] = sel3(src, m[be], m[3 + be], m[6 + be]);
                                 }
                             } else {
-                                rotation_robust_ool(m, R);  // the list is full: solve it here
+                                rotation_robust(m, R);  // the list is full: solve it here
                                 done = true;
                             }
                         }
