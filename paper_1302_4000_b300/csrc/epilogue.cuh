@@ -23,26 +23,42 @@
 #include <cuda_runtime.h>
 
 
-// Invariants of the 3x3 matrix m (row-major): I1 = |m|^2, det, I2 = sum of squared 2x2 minors.
+// The nine 2x2 minors of m (row-major), mn = {a01, a02, a12, b01, b02, b12, c01, c02, c12}:
+// a.. from rows 1,2, b.. from rows 0,2, c.. from rows 0,1; the digits name the columns.
 template <typename T>
-__device__ __forceinline__ void invariants3(const T m[9], T &I1, T &det, T &I2)
+__device__ __forceinline__ void minors3(const T m[9], T mn[9])
 {
-    const T a01 = m[3] * m[7] - m[4] * m[6];  // rows 1,2 / cols 0,1
-    const T a02 = m[3] * m[8] - m[5] * m[6];  // rows 1,2 / cols 0,2
-    const T a12 = m[4] * m[8] - m[5] * m[7];  // rows 1,2 / cols 1,2
-    const T b01 = m[0] * m[7] - m[1] * m[6];  // rows 0,2
-    const T b02 = m[0] * m[8] - m[2] * m[6];
-    const T b12 = m[1] * m[8] - m[2] * m[7];
-    const T c01 = m[0] * m[4] - m[1] * m[3];  // rows 0,1
-    const T c02 = m[0] * m[5] - m[2] * m[3];
-    const T c12 = m[1] * m[5] - m[2] * m[4];
-    det = m[0] * a12 - m[1] * a02 + m[2] * a01;
-    I2 = a01 * a01 + a02 * a02 + a12 * a12 + b01 * b01 + b02 * b02 + b12 * b12
-       + c01 * c01 + c02 * c02 + c12 * c12;
+    mn[0] = m[3] * m[7] - m[4] * m[6];
+    mn[1] = m[3] * m[8] - m[5] * m[6];
+    mn[2] = m[4] * m[8] - m[5] * m[7];
+    mn[3] = m[0] * m[7] - m[1] * m[6];
+    mn[4] = m[0] * m[8] - m[2] * m[6];
+    mn[5] = m[1] * m[8] - m[2] * m[7];
+    mn[6] = m[0] * m[4] - m[1] * m[3];
+    mn[7] = m[0] * m[5] - m[2] * m[3];
+    mn[8] = m[1] * m[5] - m[2] * m[4];
+}
+
+// Invariants of the 3x3 matrix m from its minors: I1 = |m|^2, det, I2 = sum of squared minors.
+template <typename T>
+__device__ __forceinline__ void invariants_from_minors(const T m[9], const T mn[9], T &I1, T &det, T &I2)
+{
+    det = m[0] * mn[2] - m[1] * mn[1] + m[2] * mn[0];
+    I2 = mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2] + mn[3] * mn[3] + mn[4] * mn[4] + mn[5] * mn[5]
+       + mn[6] * mn[6] + mn[7] * mn[7] + mn[8] * mn[8];
     T s = T(0);
 #pragma unroll
     for (int k = 0; k < 9; ++k) s += m[k] * m[k];
     I1 = s;
+}
+
+// Invariants of the 3x3 matrix m (row-major): I1 = |m|^2, det, I2 = sum of squared 2x2 minors.
+template <typename T>
+__device__ __forceinline__ void invariants3(const T m[9], T &I1, T &det, T &I2)
+{
+    T mn[9];
+    minors3(m, mn);
+    invariants_from_minors(m, mn, I1, det, I2);
 }
 
 // Eq. 2's route: the eigenvalues l1 >= l2 >= l3 of m^T m are the roots of
@@ -250,26 +266,15 @@ __device__ __forceinline__ float sigma_hat_f32(const float m[9])
 // takes Sigma (of m) as computed; both return false, leaving R unset, where P' falls below
 // 1e-2 of 8 Sigma^3 (near a double root, where this quotient loses accuracy); the caller then
 // takes the eigenvector route of rotation.cuh.
-__device__ __forceinline__ bool rotation_from_sigma_f32(const float m[9], float s, float R[9])
+// The rotation from m, its minors mn (minors3), det, I1 and Sigma s.
+__device__ __forceinline__ bool rotation_core_f32(const float m[9], const float mn[9], float det, float I1, float s,
+                                                  float R[9])
 {
-    const float a01 = m[3] * m[7] - m[4] * m[6];
-    const float a02 = m[3] * m[8] - m[5] * m[6];
-    const float a12 = m[4] * m[8] - m[5] * m[7];
-    const float b01 = m[0] * m[7] - m[1] * m[6];
-    const float b02 = m[0] * m[8] - m[2] * m[6];
-    const float b12 = m[1] * m[8] - m[2] * m[7];
-    const float c01 = m[0] * m[4] - m[1] * m[3];
-    const float c02 = m[0] * m[5] - m[2] * m[3];
-    const float c12 = m[1] * m[5] - m[2] * m[4];
-    const float det = m[0] * a12 - m[1] * a02 + m[2] * a01;
-    float I1 = 0.f;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) I1 = fmaf(m[k], m[k], I1);
     const float s2 = s * s;
     const float dP = fmaf(fmaf(4.f, s2, -4.f * I1), s, -8.f * det);
     if (!(dP > 8e-2f * s2 * s)) return false;
     // cofactor matrix (signed minors), row-major
-    const float cf[9] = {a12, -a02, a01, -b12, b02, -b01, c12, -c02, c01};
+    const float cf[9] = {mn[2], -mn[1], mn[0], -mn[5], mn[4], -mn[3], mn[8], -mn[7], mn[6]};
     // g = m^T m (symmetric)
     const float g00 = m[0] * m[0] + m[3] * m[3] + m[6] * m[6];
     const float g01 = m[0] * m[1] + m[3] * m[4] + m[6] * m[7];
@@ -308,6 +313,17 @@ __device__ __forceinline__ bool rotation_from_sigma_f32(const float m[9], float 
         R[3 * i + 2] = r0 * t02 + r1 * t12 + r2 * t22;
     }
     return true;
+}
+
+__device__ __forceinline__ bool rotation_from_sigma_f32(const float m[9], float s, float R[9])
+{
+    float mn[9];
+    minors3(m, mn);
+    const float det = m[0] * mn[2] - m[1] * mn[1] + m[2] * mn[0];
+    float I1 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) I1 = fmaf(m[k], m[k], I1);
+    return rotation_core_f32(m, mn, det, I1, s, R);
 }
 
 __device__ __forceinline__ bool sigma_rotation_f32(const float m[9], float R[9])
@@ -351,5 +367,34 @@ __device__ __forceinline__ float crmsd_fast_fp32(const float H[9], float Ga, flo
     const float kq = CLUSCO_KERR_A + CLUSCO_KERR_B * __fdividef(Q, dP);
     const float e = (deg || !(dP > 0.f)) ? __int_as_float(0x7f800000) : kq * 5.9604645e-8f * scale;
     *err_c2 = pos ? e : 0.0f;
+    return pos ? sqrtf(fmaxf(scale * (1.0f - s), 0.0f)) : 0.0f;
+}
+
+// crmsd_fast_fp32 and the rotation of the same pair together: one set of minors serves I2,
+// det and the rotation's cofactor term. m receives the normalised block (the rotation's
+// input, for callers that defer the rare pairs whose quotient is ill-conditioned: *okR false).
+__device__ __forceinline__ float crmsd_fast_rot_fp32(const float H[9], float Ga, float Gb, float invL, float *s_out,
+                                                     float *err_c2, float m[9], float R[9], bool *okR)
+{
+    const float Gs = Ga + Gb;
+    const bool pos = Gs > 0.0f;
+    const float nrm = __fdividef(2.0f, pos ? Gs : 1.0f);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m[k] = H[k] * nrm;
+    float mn[9];
+    minors3(m, mn);
+    float I1, det, I2;
+    invariants_from_minors(m, mn, I1, det, I2);
+    bool deg;
+    float dP;
+    const float s = quartic_newton_f(sigma_cubic_f(I1, det, I2), I1, det, I2, 2, &deg, &dP);
+    *s_out = s;
+    const float scale = Gs * invL;
+    const float s2 = s * s;
+    const float Q = fmaf(s2 + 2.f * I1, s2, fmaf(8.f * fabsf(det), s, I1 * I1));
+    const float kq = CLUSCO_KERR_A + CLUSCO_KERR_B * __fdividef(Q, dP);
+    const float e = (deg || !(dP > 0.f)) ? __int_as_float(0x7f800000) : kq * 5.9604645e-8f * scale;
+    *err_c2 = pos ? e : 0.0f;
+    *okR = rotation_core_f32(m, mn, det, I1, s, R);
     return pos ? sqrtf(fmaxf(scale * (1.0f - s), 0.0f)) : 0.0f;
 }

@@ -544,15 +544,12 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                     default: assemble_block(V, 3, alpha, mloc, blk); break;
                 }
                 float sv, ev;
-                const float cv = crmsd_fast_fp32(blk, Ga, Gb[0], invL, &sv, &ev);
+                float m[9], R[9];
+                bool okR = false;
+                const float cv = ROT ? crmsd_fast_rot_fp32(blk, Ga, Gb[0], invL, &sv, &ev, m, R, &okR)
+                                     : crmsd_fast_fp32(blk, Ga, Gb[0], invL, &sv, &ev);
                 const int64_t b = b0 + 3 * r;
                 if (ROT) {
-                    const float Gs = Ga + Gb[0];
-                    const float nrm = __fdividef(2.0f, Gs > 0.f ? Gs : 1.0f);
-                    float m[9], R[9];
-#pragma unroll
-                    for (int e = 0; e < 9; ++e) m[e] = blk[e] * nrm;
-                    const bool okR = rotation_from_sigma_f32(m, sv, R);
                     if (pok[0]) {
                         // blk's rows are axes alpha, alpha + 1, alpha + 2: axis ax is row (ax - alpha) mod 3
                         const int64_t ridx = rowbase + b;
