@@ -118,13 +118,24 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_for(key):
-    """DRAM bytes per launch of a kernel from its committed ncu summary, or None once the
-    kernel's source has changed since the counters were taken (sha256 recorded beside them)."""
+def csrc_hash():
+    """sha256 over every source file of the library (names and contents, sorted by name): a
+    kernel's counters stand only for the sources they were taken from, headers included."""
+    import glob
     import hashlib
-    src = {"pairs_tc": "pairs_tc.cuh", "bwd_tc": "bwd_tc.cuh", "bwd_rot": "bwd_rot.cuh"}[key]
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1302_4000_b300", "csrc", "*"))):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def traffic_for(key):
+    """DRAM bytes per launch of a kernel from its committed ncu summary, or None once any
+    library source has changed since the counters were taken (csrc_hash recorded beside them)."""
     try:
-        h = hashlib.sha256(open(os.path.join(ROOT, "paper_1302_4000_b300", "csrc", src), "rb").read()).hexdigest()
+        h = csrc_hash()
         for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
             parts = line.split()
             if len(parts) == 4 and parts[0] == key and parts[1] == h:
@@ -264,10 +275,11 @@ def run_ours(args):
             evs[3].record(stream)
 
     # our kernels per step: forward (pre-pass + pairs, + the deferred-rotation kernel when
-    # storing rotations); ref pre-pass + vs-ref; adjoint (pre-pass, transpose, sweep, reduce,
-    # near-duplicate pass; 3 kernels on the CUDA-core adjoint)
-    tc_bwd = use_rot or (L <= 320 and form != clusco.FORM_FP32_SIMT)
-    launches_per_step = (3 if use_rot else 2) + 2 + (5 if tc_bwd else 3)
+    # storing rotations); ref pre-pass + vs-ref; adjoint from stored rotations (pre-pass, FP16
+    # split, max |w|, sweep, reduce, near-duplicate pass), or recomputing (pre-pass, transpose,
+    # sweep, reduce, near-duplicate pass; 3 kernels on the CUDA-core adjoint)
+    tc_bwd = L <= 320 and form != clusco.FORM_FP32_SIMT
+    launches_per_step = (3 if use_rot else 2) + 2 + (6 if use_rot else (5 if tc_bwd else 3))
 
     def timed(fn, k, w_, split=False, prof=False):
         for _ in range(w_):
@@ -428,8 +440,13 @@ def run_ours(args):
                       "peak_kind": f"{pk_kind} HBM copy"})
         return r
     kp, ka = kern["pairs"][0], kern["adjoint"][0]
-    r_fwd = rf(18.0 * L * P, kp, fms, "pairs_tc_kernel%s (forward, 18 L flop/pair)" % ("<ROT>" if use_rot else ""),
-               "pairs_tc")
+    if use_rot:
+        # storing rotations, the forward writes 52 bytes per pair (the 48-byte rotation record and
+        # the 4-byte cRMSD) against 18 L flop: at this L the HBM term of the roofline is the larger
+        r_fwd = rf(18.0 * L * P, kp, fms, "pairs_tc_kernel<ROT> (forward storing rotations, 52 B/pair)",
+                   "pairs_tc_rot", hbm_bytes=52.0 * P)
+    else:
+        r_fwd = rf(18.0 * L * P, kp, fms, "pairs_tc_kernel (forward, 18 L flop/pair)", "pairs_tc")
     if use_rot:
         # from stored rotations the adjoint's contraction is 36 L flop per pair (R x_b and R^T x_a)
         # against 44 bytes per pair of gathers (the nine floats of R_ab, c_ab, w_ab): the HBM

@@ -101,15 +101,11 @@ __global__ void __launch_bounds__(256) bwr_prepass_kernel(const float *__restric
     if (lane == 0 && finite && m > 0.f) atomicMax(xmax, __float_as_uint(m));
 }
 
-// xT[part][i][r] = FP16 part (hi, lo) of xf[r][i] 2^kx, 32 x 32 tiles through shared memory;
-// every block also folds a grid-stride slice of |w| into wmax.
+// xT[part][i][r] = FP16 part (hi, lo) of xf[r][i] 2^kx, 32 x 32 tiles through shared memory.
 __global__ void __launch_bounds__(256) bwr_split_kernel(const float *__restrict__ xf, int64_t Rpad, int Lp,
-                                                        const unsigned *__restrict__ xmax, __half *__restrict__ xT,
-                                                        const float *__restrict__ w, int64_t P,
-                                                        unsigned *__restrict__ wmax)
+                                                        const unsigned *__restrict__ xmax, __half *__restrict__ xT)
 {
     __shared__ float t[32][33];
-    __shared__ float red[8];
     const int64_t r0 = (int64_t)blockIdx.x * 32;
     const int i0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -122,12 +118,28 @@ __global__ void __launch_bounds__(256) bwr_split_kernel(const float *__restrict_
         xT[(int64_t)(i0 + k) * Rpad + r0 + tx] = hi;
         xT[((int64_t)Lp + i0 + k) * Rpad + r0 + tx] = __float2half_rn(v - __half2float(hi));
     }
-    const int64_t nthr = (int64_t)gridDim.x * gridDim.y * 256;
+}
+
+// wmax = max |w| over the P weights (NaN ignored), 16-byte loads where w is 16-byte aligned.
+__global__ void __launch_bounds__(256) bwr_absmax_kernel(const float *__restrict__ w, int64_t P,
+                                                         unsigned *__restrict__ wmax)
+{
+    __shared__ float red[8];
+    const int64_t nthr = (int64_t)gridDim.x * 256, tid = (int64_t)blockIdx.x * 256 + threadIdx.x;
     float m = 0.f;
-    for (int64_t p = ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * 256 + threadIdx.x; p < P; p += nthr)
-        m = fmaxf(m, fabsf(w[p]));
+    int64_t head = 0;
+    if (((uintptr_t)w & 15) == 0) {
+        const float4 *w4 = reinterpret_cast<const float4 *>(w);
+        const int64_t n4 = P / 4;
+        for (int64_t q = tid; q < n4; q += nthr) {
+            const float4 v = __ldg(w4 + q);
+            m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+        }
+        head = 4 * n4;
+    }
+    for (int64_t p = head + tid; p < P; p += nthr) m = fmaxf(m, fabsf(w[p]));
     m = warp_max_f(m);
-    if (tx == 0) red[ty] = m;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int k = 1; k < 8; ++k) m = fmaxf(m, red[k]);
@@ -515,8 +527,12 @@ inline int bwr_launch(const float *coords, int64_t N, int64_t L, const float *gr
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        bwr_split_kernel<<<dim3((unsigned)(w.Rpad / 32), (unsigned)(w.Lp / 32)), 256, 0, st>>>(
-            w.xf, w.Rpad, (int)w.Lp, w.scl, xT, grad_out, P, w.scl + 1);
+        bwr_split_kernel<<<dim3((unsigned)(w.Rpad / 32), (unsigned)(w.Lp / 32)), 256, 0, st>>>(w.xf, w.Rpad, (int)w.Lp,
+                                                                                              w.scl, xT);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        bwr_absmax_kernel<<<4 * 148, 256, 0, st>>>(grad_out, P, w.scl + 1);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {
