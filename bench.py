@@ -274,12 +274,13 @@ def run_ours(args):
         if evs:
             evs[3].record(stream)
 
-    # our kernels per step: forward (pre-pass + pairs, + the deferred-rotation kernel when
-    # storing rotations); ref pre-pass + vs-ref; adjoint from stored rotations (pre-pass, FP16
+    # our kernels per step: forward (pre-pass + pairs, + the refinement of flagged pairs in the
+    # exact-digit form, + the deferred-rotation kernel when storing rotations); ref pre-pass + vs-ref; adjoint from stored rotations (pre-pass, FP16
     # split, max |w|, sweep, reduce, near-duplicate pass), or recomputing (pre-pass, transpose,
     # sweep, reduce, near-duplicate pass; 3 kernels on the CUDA-core adjoint)
     tc_bwd = L <= 320 and form != clusco.FORM_FP32_SIMT
-    launches_per_step = (3 if use_rot else 2) + 2 + (6 if use_rot else (5 if tc_bwd else 3))
+    exact2 = form == clusco.FORM_BF16_EXACT2  # its forward adds the refinement of flagged pairs
+    launches_per_step = (3 if use_rot else 2) + int(exact2) + 2 + (6 if use_rot else (5 if tc_bwd else 3))
 
     def timed(fn, k, w_, split=False, prof=False):
         for _ in range(w_):

@@ -21,7 +21,8 @@
 //    A_l B'^T -> cols [128,256) (lh | ll). Four digit-product classes, each an exact
 //    integer sum in FP32 (|digit| <= 128, L <= 1024 keeps every sum below 2^24).
 //    Epilogue: FP32 fast path; pairs whose FP32 error bound exceeds the fast-path
-//    tolerance are queued per warp and recomputed from the exact classes in FP64.
+//    tolerance get a bit in a mask and are recomputed after the sweep, exactly from the
+//    16-bit coordinates and in FP64 (refine_flagged_kernel).
 //  BF16X3: planes hi, lo; A_h B'^T (hh | hl) and A_l B_h^T (lh); H = hh + hl + lh.
 //  TF32: one FP32 plane; A B^T with kind::tf32.
 #pragma once
@@ -80,6 +81,8 @@ struct TcArgs {
     RotFix *fix = nullptr;            // deferred rotations (see RotFix)
     unsigned long long *fix_count = nullptr;
     int64_t fix_cap = 0;
+    uint32_t *flags = nullptr;  // EXACT2: one bit per output pair, set where the FP32 bound fails
+    int16_t *nplane = nullptr;  // EXACT2: the 16-bit fixed-point coordinates, for the refinement
 };
 
 
@@ -93,18 +96,7 @@ constexpr uint32_t STAGE_BYTES_TF32 = 16384 + 8192;          // A, B
 constexpr int FW_EGROUPS = CLUSCO_FW_EGROUPS;
 constexpr int FW_THREADS = 64 + 256 * FW_EGROUPS;
 constexpr int FW_STAGES = FW_EGROUPS == 2 ? 2 : 3;
-constexpr int FW_QCAP = 62;  // refinement queue entries per epilogue warp: flushed at 32, a round adds <= 30
-// A queued pair: its 3x3 block's exact digit classes as integers (hh, hl + lh, ll; rows in
-// the cyclic order of the lane that owned the pair), the pair, that lane's axis and the
-// FP32 Sigma_hat.
-struct QEntry {
-    int n[27];
-    int a, b, alpha;
-    float s;
-    int pad;
-};
-static_assert(sizeof(QEntry) == 128, "queue entry layout");
-constexpr size_t FW_SMEM = 1024 + FW_STAGES * STAGE_BYTES_BF16 + 8 * FW_EGROUPS * FW_QCAP * sizeof(QEntry);
+constexpr size_t FW_SMEM = 1024 + FW_STAGES * STAGE_BYTES_BF16;
 static_assert(FW_SMEM <= 227 * 1024, "shared memory per CTA");
 
 __host__ __device__ __forceinline__ int64_t tc_row_start(int64_t I, int64_t TB) { return I * TB - I * (I - 1); }
@@ -199,73 +191,6 @@ __device__ __forceinline__ void assemble_block(const float V[32], int r, int alp
     assemble_from_cand(cand, alpha, mloc, blk);
 }
 
-// Queue the flagged pairs of round r (warp-uniform, runtime): the round's 9 columns of each
-// of the four exact classes (36 single-column TMEM loads, one wait), assembled like the
-// fast path's blocks; lanes with need set write their entry. Out of line: it runs in about
-// a quarter of the rounds and keeps the fast path's code small.
-__device__ __noinline__ void queue_round(uint32_t trow, int r, int alpha, int mloc, bool need, QEntry *e, int a, int b,
-                                         float s)
-{
-    uint32_t u[4][9];
-#pragma unroll
-    for (int c4 = 0; c4 < 4; ++c4)
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const int col = 9 * r + k;
-            u[c4][k] = (col < 32) ? tmem_ld1_issue(trow + 64 * c4 + col) : 0u;
-        }
-    tmem_wait_ld();
-    float bv[4][9];
-#pragma unroll
-    for (int c4 = 0; c4 < 4; ++c4) {
-        tmem_pin9(u[c4]);
-        float cand[3][3];
-#pragma unroll
-        for (int al = 0; al < 3; ++al)
-#pragma unroll
-            for (int be = 0; be < 3; ++be) cand[al][be] = __uint_as_float(u[c4][3 * al + be]);
-        assemble_from_cand(cand, alpha, mloc, bv[c4]);
-    }
-    if (need) {
-        // every class value is an integer below 2^24 in magnitude, so these conversions are exact
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            e->n[k] = __float2int_rn(bv[0][k]);
-            e->n[9 + k] = __float2int_rn(bv[1][k]) + __float2int_rn(bv[2][k]);
-            e->n[18 + k] = __float2int_rn(bv[3][k]);
-        }
-        e->a = a;
-        e->b = b;
-        e->alpha = alpha;
-        e->s = s;
-    }
-}
-
-// FP64 recomputation of one queued pair from its four exact digit classes (kept out of
-// line: it runs for about one pair in a hundred and would otherwise crowd the
-// instruction cache of the fast path).
-__device__ __noinline__ void refine_queued(const QEntry *qe, const float *__restrict__ scales,
-                                           const double *__restrict__ G64, double invL, int64_t N,
-                                           float *__restrict__ out, int64_t out_base)
-{
-    const int64_t aa = qe->a, bb = qe->b;
-    const int al0 = qe->alpha;
-    double H[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const int ax = al0 + i - (al0 + i >= 3 ? 3 : 0);
-        const double sr = (double)scales[aa * 3 + ax];
-#pragma unroll
-        for (int be = 0; be < 3; ++be) {
-            const int kk = 3 * i + be;
-            const double v = 65536.0 * (double)qe->n[kk] + 256.0 * (double)qe->n[9 + kk] + (double)qe->n[18 + kk];
-            H[kk] = v * (sr * (double)scales[bb * 3 + be]);
-        }
-    }
-    const float c = crmsd_refine_newton_fp64(H, G64[aa], G64[bb], invL, qe->s);
-    out[condensed_idx(aa, bb, N) - out_base] = c;
-}
-
 // The rotation of a rare block whose quartic root is (nearly) double (out of line): Jacobi
 // sweeps for a rank-deficient block (I2 ~ 0, where an FP32 Sigma is least accurate), else
 // Horn's adjugate with the block's Sigma, and Jacobi sweeps where that is degenerate too.
@@ -334,11 +259,11 @@ __global__ void __launch_bounds__(256) rot_fixup_kernel(const RotFix *__restrict
 template <int LAYOUT, bool ROT>
 __global__ void __launch_bounds__(FW_THREADS, 1)
     pairs_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                    const float *__restrict__ scales, const double *__restrict__ G64, const float *__restrict__ G32,
+                    const float *__restrict__ scales, const float *__restrict__ G32,
                     int64_t N, int L, int nkb, int64_t Rpad, int64_t TA, int64_t TB, int64_t tile0, int64_t ntiles,
                     int64_t row_begin, int64_t row_end, float *__restrict__ out, int64_t out_base,
                     float *__restrict__ rot, RotFix *__restrict__ fix, unsigned long long *__restrict__ fix_count,
-                    int64_t fix_cap)
+                    int64_t fix_cap, uint32_t *__restrict__ flags)
 {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[FW_STAGES];   // ring: K block landed
@@ -351,7 +276,6 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
 
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase0 = smem_u32(smem);
-    QEntry *queues = reinterpret_cast<QEntry *>(smem + FW_STAGES * STAGE_BYTES_BF16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr uint32_t STAGE_BYTES = (LAYOUT == TC_TF32) ? STAGE_BYTES_TF32 : STAGE_BYTES_BF16;
     constexpr int KB_ELEMS = (LAYOUT == TC_TF32) ? 32 : 64;
@@ -460,9 +384,6 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
         const int sp = warp & 3, g = (ew & 7) >> 2;
         const int mloc = lane / 3, alpha = lane - 3 * (lane / 3);
         const float invL = 1.f / (float)L;
-        const double invL64 = 1.0 / (double)L;
-        QEntry *queue = queues + ew * FW_QCAP;
-        int qn = 0;  // entries in this warp's queue (warp-uniform)
 
         const int64_t gstep = (int64_t)FW_EGROUPS * gridDim.x;
         int64_t k = gp;
@@ -583,26 +504,13 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                         }
                     }
                 }
-                bool need = false;
                 if (pok[0]) {
                     if (LAYOUT == TC_EXACT2 && !(ev <= 2.f * CLUSCO_TOL_FAST * cv)) {
-                        need = true;
+                        // the bound fails: refine_flagged_kernel writes this pair's value
+                        const int64_t li = rowbase + b;
+                        atomicOr(flags + (li >> 5), 1u << (li & 31));
                     } else {
                         out[rowbase + b] = (isnan(Ga) || isnan(Gb[0])) ? __int_as_float(0x7fc00000) : cv;
-                    }
-                }
-                if (LAYOUT == TC_EXACT2) {
-                    const unsigned m = __ballot_sync(0xffffffffu, need);
-                    if (m) {
-                        const int slot = qn + __popc(m & ((1u << lane) - 1u));
-                        queue_round(trow, r, alpha, mloc, need, queue + slot, (int)a, (int)b, sv);
-                        qn += __popc(m);
-                        if (qn >= 32) {  // a full batch: every FP64 instruction runs on 32 lanes
-                            __syncwarp();
-                            refine_queued(queue + (qn - 32 + lane), scales, G64, invL64, N, out, out_base);
-                            __syncwarp();
-                            qn -= 32;
-                        }
                     }
                 }
 #pragma unroll
@@ -615,11 +523,6 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty_bar[buf]);
-        }
-        if (LAYOUT == TC_EXACT2 && qn > 0) {
-            __syncwarp();
-            if (lane < qn) refine_queued(queue + lane, scales, G64, invL64, N, out, out_base);
-            __syncwarp();
         }
     }
     tc_fence_before();
@@ -676,6 +579,122 @@ inline int make_map(CUtensorMap *m, void *base, bool tf32, int64_t Lp, int64_t r
     return CLUSCO_OK;
 }
 
+// Row a of condensed index idx (the largest a with condensed_idx(a, a + 1, N) <= idx). The
+// start counts from the nearer end of the triangle, where the quadratic's root is well
+// conditioned: from the top, a = (t - sqrt(t^2 - 8 idx)) / 2 with t = 2N - 1; from the bottom,
+// the r = N - 1 - a last rows hold r (r + 1) / 2 pairs, so r = ceil((sqrt(8 R + 1) - 1) / 2)
+// for the R = P - idx pairs from idx on. In FP32 (N <= 2^22) either start is within a row;
+// exact integer corrections follow.
+__device__ __forceinline__ int64_t condensed_row(int64_t idx, int64_t N)
+{
+    const int64_t P = N * (N - 1) / 2;
+    int64_t a;
+    if (N <= ((int64_t)1 << 22)) {
+        if (2 * idx < P) {
+            const float t = 2.f * (float)N - 1.f;
+            a = (int64_t)floorf(0.5f * (t - sqrtf(fmaxf(t * t - 8.f * (float)idx, 0.f))));
+        } else {
+            const float R = (float)(P - idx);
+            a = N - 1 - (int64_t)ceilf(0.5f * (sqrtf(8.f * R + 1.f) - 1.f));
+        }
+    } else {
+        const double t = 2.0 * (double)N - 1.0;
+        a = (int64_t)floor(0.5 * (t - sqrt(fmax(t * t - 8.0 * (double)idx, 0.0))));
+    }
+    a = a < 0 ? 0 : (a > N - 2 ? N - 2 : a);
+    while (a > 0 && condensed_idx(a, a + 1, N) > idx) --a;
+    while (a < N - 2 && condensed_idx(a + 1, a + 2, N) <= idx) ++a;
+    return a;
+}
+
+// The pairs the fast path flagged (their bits set in flags, indices relative to out_base):
+// each one's covariance recomputed exactly from the 16-bit fixed-point coordinates n (int16
+// plane, rows in the tensor-core layout, zero past L) as nine integer sums, then scaled to
+// FP64, and cRMSD by FP64 Newton from an FP32 start (crmsd_refine_newton_fp64). Flagged pairs
+// cluster (close decoys of one native), so warps take single mask words (32 pairs)
+// round-robin; lanes split the atoms of each pair (per-lane sums below 2^46 in int64, reduced
+// exactly as two 32-bit halves), and pairs are batched 32 at a time so that every FP64
+// instruction runs on 32 lanes.
+__global__ void __launch_bounds__(256, 3) refine_flagged_kernel(const int16_t *__restrict__ nplane,
+                                                             const float *__restrict__ scales,
+                                                             const double *__restrict__ G64, int64_t N, int L, int Lp,
+                                                             int64_t npairs, int64_t out_base,
+                                                             const uint32_t *__restrict__ flags,
+                                                             float *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nwords = (npairs + 31) / 32;
+    const double invL = 1.0 / (double)L;
+    // this lane's batch slot: the pair's exact integer sums, its models and output index; the
+    // FP64 work waits for the batch, where every FP64 instruction serves 32 pairs
+    long long v[9];
+    int64_t sa = 0, sb = 0, oidx = -1;
+    int cnt = 0;
+    auto flush = [&]() {
+        if (lane < cnt) {
+            double H[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                H[k] = (double)v[k] * ((double)scales[sa * 3 + k / 3] * (double)scales[sb * 3 + k % 3]);
+            const double Ga = G64[sa], Gb = G64[sb];
+            const double Gs = Ga + Gb;
+            const double nrm = Gs > 0.0 ? 2.0 / Gs : 0.0;
+            float mf[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) mf[k] = (float)(H[k] * nrm);
+            out[oidx] = crmsd_refine_newton_fp64(H, Ga, Gb, invL, sigma_hat_f32(mf));
+        }
+        cnt = 0;
+    };
+    for (int64_t wi = w0; wi < nwords; wi += nwarps) {
+        uint32_t wd = flags[wi];
+        if (wi == nwords - 1 && (npairs & 31)) wd &= ~0u >> (32 - (int)(npairs & 31));
+        while (wd) {
+            const int bit = __ffs(wd) - 1;
+            wd &= wd - 1;
+            const int64_t li = wi * 32 + bit;
+            const int64_t idx = li + out_base;
+            const int64_t a = condensed_row(idx, N);
+            const int64_t b = idx - condensed_idx(a, a + 1, N) + a + 1;
+            const int16_t *pa = nplane + tc_row(a, 0) * Lp;
+            const int16_t *pb = nplane + tc_row(b, 0) * Lp;
+            long long acc[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) acc[k] = 0;
+#pragma unroll 4
+            for (int i = lane; i < L; i += 32) {
+                const int x0 = pa[i], x1 = pa[Lp + i], x2 = pa[2 * Lp + i];
+                const int y0 = pb[i], y1 = pb[Lp + i], y2 = pb[2 * Lp + i];
+                acc[0] += x0 * y0;
+                acc[1] += x0 * y1;
+                acc[2] += x0 * y2;
+                acc[3] += x1 * y0;
+                acc[4] += x1 * y1;
+                acc[5] += x1 * y2;
+                acc[6] += x2 * y0;
+                acc[7] += x2 * y1;
+                acc[8] += x2 * y2;
+            }
+            const int slot = cnt;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const int hi = __reduce_add_sync(0xffffffffu, (int)(acc[k] >> 20));
+                const int lo = __reduce_add_sync(0xffffffffu, (int)(acc[k] & 0xFFFFF));
+                if (lane == slot) v[k] = ((long long)hi << 20) + (long long)lo;
+            }
+            if (lane == slot) {
+                sa = a;
+                sb = b;
+                oidx = li;
+            }
+            if (++cnt == 32) flush();
+        }
+    }
+    flush();
+}
+
 template <int LAYOUT>
 inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
 {
@@ -702,6 +721,14 @@ inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
     }
     // persistent: one CTA per SM, CTA x takes tiles x, x + grid, x + 2 grid, ...
     const unsigned grid = (unsigned)std::min<int64_t>(nt, sms > 0 ? sms : 148);
+    const int64_t npairs = condensed_idx(a.row_end - 1, a.N - 1, a.N) + 1 - a.out_base;
+    if (LAYOUT == TC_EXACT2) {
+        e = cudaMemsetAsync(a.flags, 0, (size_t)((npairs + 31) / 32) * sizeof(uint32_t), st);
+        if (e != cudaSuccess) {
+            err = std::string("flag mask reset: ") + cudaGetErrorString(e);
+            return CLUSCO_ECUDA;
+        }
+    }
     prof_mark(PROF_PAIRS, st);
     if (a.rot) {
         e = cudaMemsetAsync(a.fix_count, 0, sizeof(unsigned long long), st);
@@ -710,11 +737,17 @@ inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
             return CLUSCO_ECUDA;
         }
     }
-    kern<<<grid, FW_THREADS, FW_SMEM, st>>>(mA, mB, a.scales, a.G64, a.G32, a.N, (int)a.L, nkb, a.Rpad, TA, TB, t0,
-                                             nt, a.row_begin, a.row_end, a.out, a.out_base, a.rot, a.fix,
-                                             a.fix_count, a.fix_cap);
+    kern<<<grid, FW_THREADS, FW_SMEM, st>>>(mA, mB, a.scales, a.G32, a.N, (int)a.L, nkb, a.Rpad, TA, TB, t0, nt,
+                                             a.row_begin, a.row_end, a.out, a.out_base, a.rot, a.fix, a.fix_count,
+                                             a.fix_cap, a.flags);
     e = cudaGetLastError();
     prof_mark(PROF_PAIRS, st);
+    if (e == cudaSuccess && LAYOUT == TC_EXACT2) {
+        refine_flagged_kernel<<<4 * (sms > 0 ? sms : 148), 256, 0, st>>>(a.nplane, a.scales, a.G64, a.N, (int)a.L,
+                                                                          (int)a.Lp, npairs, a.out_base, a.flags,
+                                                                          a.out);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess && a.rot) {
         rot_fixup_kernel<<<4 * (sms > 0 ? sms : 148), 256, 0, st>>>(a.fix, a.fix_count, a.fix_cap, a.rot);
         e = cudaGetLastError();

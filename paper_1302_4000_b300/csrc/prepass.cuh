@@ -94,12 +94,14 @@ enum TcLayout { TC_EXACT2 = 0, TC_BF16X3 = 1, TC_TF32 = 2 };
 
 // tcgen05 operand planes. Grid: ceil(Npad40/8) blocks of 256 threads.
 // planes: element type bf16 (EXACT2, BF16X3; two planes) or float (TF32; one plane),
-// plane stride Rpad*Lp elements.
+// plane stride Rpad*Lp elements. nplane (EXACT2, optional): the same 16-bit fixed-point
+// coordinates n = 256 h + l as int16, for the exact recomputation of flagged pairs.
 template <int LAYOUT>
 __global__ void __launch_bounds__(256) prepass_tc_kernel(const float *__restrict__ coords, int64_t N, int L, int Lp,
                                                          int64_t Npad, int64_t Rpad, void *__restrict__ planes,
                                                          float *__restrict__ scales, double *__restrict__ G64,
-                                                         float *__restrict__ G32, float *__restrict__ xf)
+                                                         float *__restrict__ G32, float *__restrict__ xf,
+                                                         int16_t *__restrict__ nplane = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const int64_t a = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -118,6 +120,7 @@ __global__ void __launch_bounds__(256) prepass_tc_kernel(const float *__restrict
                 p1[r * Lp + i] = __float2bfloat16_rn(0.f);
             }
             if (xf) xf[r * Lp + i] = 0.f;
+            if (nplane) nplane[r * Lp + i] = 0;
         }
     };
     if (a % 10 == 9) {  // the two padding rows that close this model's 32-row group
@@ -170,6 +173,7 @@ __global__ void __launch_bounds__(256) prepass_tc_kernel(const float *__restrict
                 p0[off] = __float2bfloat16_rn(h);
                 p1[off] = __float2bfloat16_rn(l);
                 const int ni = (int)n;
+                if (nplane) nplane[off] = (int16_t)ni;
                 gi[ax] += (long long)ni * ni;
             } else if (LAYOUT == TC_BF16X3) {
                 const __nv_bfloat16 h = __float2bfloat16_rn(v);
