@@ -77,7 +77,8 @@ struct PairsWs {
     float *G32 = nullptr;
     int64_t Lp = 0, Npad = 0, Rpad = 0;
     // EXACT2: the 16-bit coordinates and the mask of pairs the fast path flags
-    int16_t *nplane = nullptr;
+    int8_t *hplane = nullptr;
+    uint8_t *lplane = nullptr;
     uint32_t *flags = nullptr;
     // rotation entry point only: the deferred-rotation list
     RotFix *fix = nullptr;
@@ -116,7 +117,8 @@ PairsWs carve_pairs(void *base, int64_t N, int64_t L, int form, bool with_rot = 
         w.G32 = c.take<float>((size_t)w.Npad);
         if (form == CLUSCO_FORM_BF16_EXACT2) {
             const int64_t P = N * (N - 1) / 2;
-            w.nplane = c.take<int16_t>((size_t)(w.Rpad * w.Lp));
+            w.hplane = c.take<int8_t>((size_t)(w.Rpad * w.Lp));
+            w.lplane = c.take<uint8_t>((size_t)(w.Rpad * w.Lp));
             w.flags = c.take<uint32_t>((size_t)((P + 31) / 32));
         }
         if (with_rot) {
@@ -186,7 +188,8 @@ int run_prepass(const float *coords, int64_t N, int64_t L, int form, const Pairs
         prepass_simt_kernel<<<blocks, 256, 0, st>>>(coords, N, (int)L, (int)w.Lp, w.Npad, w.Xk, w.G64);
     } else if (form == CLUSCO_FORM_BF16_EXACT2) {
         prepass_tc_kernel<TC_EXACT2><<<blocks, 256, 0, st>>>(coords, N, (int)L, (int)w.Lp, w.Npad, w.Rpad,
-                                                                w.planes, w.scales, w.G64, w.G32, nullptr, w.nplane);
+                                                                w.planes, w.scales, w.G64, w.G32, nullptr, w.hplane,
+                                                                w.lplane);
     } else if (form == CLUSCO_FORM_BF16X3) {
         prepass_tc_kernel<TC_BF16X3><<<blocks, 256, 0, st>>>(coords, N, (int)L, (int)w.Lp, w.Npad, w.Rpad,
                                                                 w.planes, w.scales, w.G64, w.G32, nullptr);
@@ -247,7 +250,8 @@ int allpairs_impl(const float *coords, int64_t N, int64_t L, int64_t row_begin, 
         a.fix_count = w.fix_count;
         a.fix_cap = w.fix_cap;
         a.flags = w.flags;
-        a.nplane = w.nplane;
+        a.hplane = w.hplane;
+        a.lplane = w.lplane;
         std::string err;
         rc = tc_launch_allpairs(a, st, err);
         if (rc) return fail(rc, "%s", err.c_str());

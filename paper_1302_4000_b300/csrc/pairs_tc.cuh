@@ -82,7 +82,8 @@ struct TcArgs {
     unsigned long long *fix_count = nullptr;
     int64_t fix_cap = 0;
     uint32_t *flags = nullptr;  // EXACT2: one bit per output pair, set where the FP32 bound fails
-    int16_t *nplane = nullptr;  // EXACT2: the 16-bit fixed-point coordinates, for the refinement
+    int8_t *hplane = nullptr;   // EXACT2: the 16-bit fixed-point coordinates as bytes (h, l), for
+    uint8_t *lplane = nullptr;  // the refinement of flagged pairs
 };
 
 
@@ -607,25 +608,57 @@ __device__ __forceinline__ int64_t condensed_row(int64_t idx, int64_t N)
     return a;
 }
 
+// 4-way byte dot products with a 32-bit accumulator: signed x signed, signed x unsigned,
+// unsigned x signed, unsigned x unsigned bytes.
+__device__ __forceinline__ int dp4a_ss(int a, int b, int c)
+{
+    int d;
+    asm("dp4a.s32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ int dp4a_su(int a, int b, int c)
+{
+    int d;
+    asm("dp4a.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ int dp4a_us(int a, int b, int c)
+{
+    int d;
+    asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned dp4a_uu(unsigned a, unsigned b, unsigned c)
+{
+    unsigned d;
+    asm("dp4a.u32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
 // The pairs the fast path flagged (their bits set in flags, indices relative to out_base):
-// each one's covariance recomputed exactly from the 16-bit fixed-point coordinates n (int16
-// plane, rows in the tensor-core layout, zero past L) as nine integer sums, then scaled to
-// FP64, and cRMSD by FP64 Newton from an FP32 start (crmsd_refine_newton_fp64). Flagged pairs
-// cluster (close decoys of one native), so warps take single mask words (32 pairs)
-// round-robin; lanes split the atoms of each pair (per-lane sums below 2^46 in int64, reduced
-// exactly as two 32-bit halves), and pairs are batched 32 at a time so that every FP64
-// instruction runs on 32 lanes.
-__global__ void __launch_bounds__(256, 3) refine_flagged_kernel(const int16_t *__restrict__ nplane,
-                                                             const float *__restrict__ scales,
-                                                             const double *__restrict__ G64, int64_t N, int L, int Lp,
-                                                             int64_t npairs, int64_t out_base,
-                                                             const uint32_t *__restrict__ flags,
-                                                             float *__restrict__ out)
+// each one's covariance recomputed exactly from the 16-bit fixed-point coordinates
+// n = 256 h + l (byte planes, h signed and l unsigned; rows in the tensor-core layout, zero
+// past L) as three digit classes of nine sums, hh, hl + lh and ll, each an exact 32-bit
+// integer (4-way byte dot products over atom quads: per atom |hh| <= 2^14, |hl + lh| < 2^16,
+// ll < 2^16, so over L <= 1024 atoms every class stays below 2^26), then
+// H = 65536 hh + 256 (hl + lh) + ll in int64, scaled to FP64, and cRMSD by FP64 Newton from an
+// FP32 start (crmsd_refine_newton_fp64). Flagged pairs cluster (close decoys of one native),
+// so warps take single mask words (32 pairs) round-robin; lanes split the atom quads of each
+// pair, and pairs are batched 32 at a time so that every FP64 instruction runs on 32 lanes.
+__global__ void __launch_bounds__(256, 2) refine_flagged_kernel(const int8_t *__restrict__ hplane,
+                                                                const uint8_t *__restrict__ lplane,
+                                                                const float *__restrict__ scales,
+                                                                const double *__restrict__ G64, int64_t N, int L,
+                                                                int Lp, int64_t npairs, int64_t out_base,
+                                                                const uint32_t *__restrict__ flags,
+                                                                float *__restrict__ out)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t nwords = (npairs + 31) / 32;
+    const int nq = (L + 3) / 4;  // atom quads (bytes past L are zero)
+    const int rq = Lp / 4;       // quads per row
     const double invL = 1.0 / (double)L;
     // this lane's batch slot: the pair's exact integer sums, its models and output index; the
     // FP64 work waits for the batch, where every FP64 instruction serves 32 pairs
@@ -658,31 +691,45 @@ __global__ void __launch_bounds__(256, 3) refine_flagged_kernel(const int16_t *_
             const int64_t idx = li + out_base;
             const int64_t a = condensed_row(idx, N);
             const int64_t b = idx - condensed_idx(a, a + 1, N) + a + 1;
-            const int16_t *pa = nplane + tc_row(a, 0) * Lp;
-            const int16_t *pb = nplane + tc_row(b, 0) * Lp;
-            long long acc[9];
+            const int *ha = reinterpret_cast<const int *>(hplane + tc_row(a, 0) * Lp);
+            const unsigned *la = reinterpret_cast<const unsigned *>(lplane + tc_row(a, 0) * Lp);
+            const int *hb = reinterpret_cast<const int *>(hplane + tc_row(b, 0) * Lp);
+            const unsigned *lb = reinterpret_cast<const unsigned *>(lplane + tc_row(b, 0) * Lp);
+            int hh[9], hx[9];
+            unsigned ll[9];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) acc[k] = 0;
-#pragma unroll 4
-            for (int i = lane; i < L; i += 32) {
-                const int x0 = pa[i], x1 = pa[Lp + i], x2 = pa[2 * Lp + i];
-                const int y0 = pb[i], y1 = pb[Lp + i], y2 = pb[2 * Lp + i];
-                acc[0] += x0 * y0;
-                acc[1] += x0 * y1;
-                acc[2] += x0 * y2;
-                acc[3] += x1 * y0;
-                acc[4] += x1 * y1;
-                acc[5] += x1 * y2;
-                acc[6] += x2 * y0;
-                acc[7] += x2 * y1;
-                acc[8] += x2 * y2;
+            for (int k = 0; k < 9; ++k) {
+                hh[k] = 0;
+                hx[k] = 0;
+                ll[k] = 0u;
+            }
+            for (int q = lane; q < nq; q += 32) {
+                int A[3], B[3];
+                unsigned Al[3], Bl[3];
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) {
+                    A[ax] = __ldg(ha + ax * rq + q);
+                    Al[ax] = __ldg(la + ax * rq + q);
+                    B[ax] = __ldg(hb + ax * rq + q);
+                    Bl[ax] = __ldg(lb + ax * rq + q);
+                }
+#pragma unroll
+                for (int al = 0; al < 3; ++al)
+#pragma unroll
+                    for (int be = 0; be < 3; ++be) {
+                        const int k = 3 * al + be;
+                        hh[k] = dp4a_ss(A[al], B[be], hh[k]);
+                        hx[k] = dp4a_us((int)Al[al], B[be], dp4a_su(A[al], (int)Bl[be], hx[k]));
+                        ll[k] = dp4a_uu(Al[al], Bl[be], ll[k]);
+                    }
             }
             const int slot = cnt;
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
-                const int hi = __reduce_add_sync(0xffffffffu, (int)(acc[k] >> 20));
-                const int lo = __reduce_add_sync(0xffffffffu, (int)(acc[k] & 0xFFFFF));
-                if (lane == slot) v[k] = ((long long)hi << 20) + (long long)lo;
+                const long long shh = __reduce_add_sync(0xffffffffu, hh[k]);
+                const long long shx = __reduce_add_sync(0xffffffffu, hx[k]);
+                const long long sll = (long long)__reduce_add_sync(0xffffffffu, ll[k]);
+                if (lane == slot) v[k] = 65536LL * shh + 256LL * shx + sll;
             }
             if (lane == slot) {
                 sa = a;
@@ -743,9 +790,9 @@ inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
     e = cudaGetLastError();
     prof_mark(PROF_PAIRS, st);
     if (e == cudaSuccess && LAYOUT == TC_EXACT2) {
-        refine_flagged_kernel<<<4 * (sms > 0 ? sms : 148), 256, 0, st>>>(a.nplane, a.scales, a.G64, a.N, (int)a.L,
-                                                                          (int)a.Lp, npairs, a.out_base, a.flags,
-                                                                          a.out);
+        refine_flagged_kernel<<<4 * (sms > 0 ? sms : 148), 256, 0, st>>>(a.hplane, a.lplane, a.scales, a.G64, a.N,
+                                                                          (int)a.L, (int)a.Lp, npairs, a.out_base,
+                                                                          a.flags, a.out);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && a.rot) {

@@ -94,14 +94,16 @@ enum TcLayout { TC_EXACT2 = 0, TC_BF16X3 = 1, TC_TF32 = 2 };
 
 // tcgen05 operand planes. Grid: ceil(Npad40/8) blocks of 256 threads.
 // planes: element type bf16 (EXACT2, BF16X3; two planes) or float (TF32; one plane),
-// plane stride Rpad*Lp elements. nplane (EXACT2, optional): the same 16-bit fixed-point
-// coordinates n = 256 h + l as int16, for the exact recomputation of flagged pairs.
+// plane stride Rpad*Lp elements. hplane / lplane (EXACT2, optional): the same 16-bit
+// fixed-point coordinates as bytes, n = 256 h + l with h = n >> 8 signed and l = n & 255
+// unsigned, for the exact recomputation of flagged pairs with 4-way byte dot products.
 template <int LAYOUT>
 __global__ void __launch_bounds__(256) prepass_tc_kernel(const float *__restrict__ coords, int64_t N, int L, int Lp,
                                                          int64_t Npad, int64_t Rpad, void *__restrict__ planes,
                                                          float *__restrict__ scales, double *__restrict__ G64,
                                                          float *__restrict__ G32, float *__restrict__ xf,
-                                                         int16_t *__restrict__ nplane = nullptr)
+                                                         int8_t *__restrict__ hplane = nullptr,
+                                                         uint8_t *__restrict__ lplane = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const int64_t a = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -120,7 +122,10 @@ __global__ void __launch_bounds__(256) prepass_tc_kernel(const float *__restrict
                 p1[r * Lp + i] = __float2bfloat16_rn(0.f);
             }
             if (xf) xf[r * Lp + i] = 0.f;
-            if (nplane) nplane[r * Lp + i] = 0;
+            if (hplane) {
+                hplane[r * Lp + i] = 0;
+                lplane[r * Lp + i] = 0;
+            }
         }
     };
     if (a % 10 == 9) {  // the two padding rows that close this model's 32-row group
@@ -173,7 +178,10 @@ __global__ void __launch_bounds__(256) prepass_tc_kernel(const float *__restrict
                 p0[off] = __float2bfloat16_rn(h);
                 p1[off] = __float2bfloat16_rn(l);
                 const int ni = (int)n;
-                if (nplane) nplane[off] = (int16_t)ni;
+                if (hplane) {
+                    hplane[off] = (int8_t)(ni >> 8);     // n = 256 h + l, h in [-128, 127]
+                    lplane[off] = (uint8_t)(ni & 255);  // l in [0, 255]
+                }
                 gi[ax] += (long long)ni * ni;
             } else if (LAYOUT == TC_BF16X3) {
                 const __nv_bfloat16 h = __float2bfloat16_rn(v);
