@@ -667,16 +667,23 @@ __global__ void __launch_bounds__(256, 2) refine_flagged_kernel(const int8_t *__
     int cnt = 0;
     auto flush = [&]() {
         if (lane < cnt) {
+            float s3a[3], s3b[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                s3a[k] = scales[sa * 3 + k];
+                s3b[k] = scales[sb * 3 + k];
+            }
+            const double Ga = G64[sa], Gb = G64[sb];
+            // the FP32 start from the same sums in FP32 (it only has to be close: Newton in FP64
+            // polishes it), the exact covariance in FP64 (each scale product is exact in FP64)
+            const float nrmf = __fdividef(2.f, (float)(Ga + Gb));
+            float mf[9];
             double H[9];
 #pragma unroll
-            for (int k = 0; k < 9; ++k)
-                H[k] = (double)v[k] * ((double)scales[sa * 3 + k / 3] * (double)scales[sb * 3 + k % 3]);
-            const double Ga = G64[sa], Gb = G64[sb];
-            const double Gs = Ga + Gb;
-            const double nrm = Gs > 0.0 ? 2.0 / Gs : 0.0;
-            float mf[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) mf[k] = (float)(H[k] * nrm);
+            for (int k = 0; k < 9; ++k) {
+                mf[k] = (float)v[k] * (s3a[k / 3] * s3b[k % 3]) * nrmf;
+                H[k] = (double)v[k] * ((double)s3a[k / 3] * (double)s3b[k % 3]);
+            }
             out[oidx] = crmsd_refine_newton_fp64(H, Ga, Gb, invL, sigma_hat_f32(mf));
         }
         cnt = 0;
@@ -703,6 +710,7 @@ __global__ void __launch_bounds__(256, 2) refine_flagged_kernel(const int8_t *__
                 hx[k] = 0;
                 ll[k] = 0u;
             }
+#pragma unroll 4
             for (int q = lane; q < nq; q += 32) {
                 int A[3], B[3];
                 unsigned Al[3], Bl[3];
