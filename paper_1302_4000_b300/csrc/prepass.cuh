@@ -56,6 +56,39 @@ __device__ __forceinline__ void model_centroid(const float *__restrict__ x, int 
     *finite = __all_sync(0xffffffffu, ok);
 }
 
+// model_centroid plus the largest |x - mu| per axis, without a second pass: rounding is
+// monotonic, so max_i fl(|x_i - mu|) = max(fl(max_i x_i - mu), fl(mu - min_i x_i)) exactly.
+__device__ __forceinline__ void model_centroid_absmax(const float *__restrict__ x, int L, int lane, float mu[3],
+                                                      float mx[3], bool *finite)
+{
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    float lo[3] = {3.4e38f, 3.4e38f, 3.4e38f}, hi[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+    bool ok = true;
+    for (int i = lane; i < L; i += 32) {
+        const float v0 = x[3 * i + 0], v1 = x[3 * i + 1], v2 = x[3 * i + 2];
+        ok = ok && isfinite(v0) && isfinite(v1) && isfinite(v2);
+        s0 += v0;
+        s1 += v1;
+        s2 += v2;
+        lo[0] = fminf(lo[0], v0);
+        lo[1] = fminf(lo[1], v1);
+        lo[2] = fminf(lo[2], v2);
+        hi[0] = fmaxf(hi[0], v0);
+        hi[1] = fmaxf(hi[1], v1);
+        hi[2] = fmaxf(hi[2], v2);
+    }
+    const double invL = 1.0 / (double)L;
+    mu[0] = (float)(warp_sum_d((double)s0) * invL);
+    mu[1] = (float)(warp_sum_d((double)s1) * invL);
+    mu[2] = (float)(warp_sum_d((double)s2) * invL);
+    *finite = __all_sync(0xffffffffu, ok);
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const float l = -warp_max_f(-lo[ax]), h = warp_max_f(hi[ax]);
+        mx[ax] = fmaxf(fmaxf(h - mu[ax], mu[ax] - l), 0.f);
+    }
+}
+
 // FP32-SIMT layout. Grid: ceil(Npad/8) blocks of 256 threads (8 warps = 8 model slots).
 __global__ void __launch_bounds__(256) prepass_simt_kernel(const float *__restrict__ coords, int64_t N, int L, int Lp,
                                                            int64_t Npad, float *__restrict__ Xk,
@@ -142,19 +175,15 @@ __global__ void __launch_bounds__(256) prepass_tc_kernel(const float *__restrict
         return;
     }
     const float *x = coords + a * (int64_t)L * 3;
-    float mu[3];
+    float mu[3], mx[3];
     bool finite;
-    model_centroid(x, L, lane, mu, &finite);
+    if (LAYOUT == TC_EXACT2)
+        model_centroid_absmax(x, L, lane, mu, mx, &finite);
+    else
+        model_centroid(x, L, lane, mu, &finite);
 
     float inv[3] = {1.f, 1.f, 1.f}, sc[3] = {1.f, 1.f, 1.f};
     if (LAYOUT == TC_EXACT2) {
-        float mx0 = 0.f, mx1 = 0.f, mx2 = 0.f;
-        for (int i = lane; i < L; i += 32) {
-            mx0 = fmaxf(mx0, fabsf(x[3 * i + 0] - mu[0]));
-            mx1 = fmaxf(mx1, fabsf(x[3 * i + 1] - mu[1]));
-            mx2 = fmaxf(mx2, fabsf(x[3 * i + 2] - mu[2]));
-        }
-        float mx[3] = {warp_max_f(mx0), warp_max_f(mx1), warp_max_f(mx2)};
         for (int ax = 0; ax < 3; ++ax) {
             if (mx[ax] > 0.f && isfinite(mx[ax])) {
                 sc[ax] = mx[ax] / 32767.f;

@@ -101,10 +101,11 @@ __global__ void __launch_bounds__(RP_THREADS) ref_prepass_kernel(const float *__
     }
 }
 
-// A block of 8 warps scores 32 models: each warp reduces the exact integer sums of four
-// models (reference staged in dynamic shared memory, 12 L bytes), then warp 0 runs the 32
-// FP64 epilogues side by side, one model per lane.
-constexpr int VSREF_MODELS = 32;
+// A block of 8 warps scores 8 models: each warp reduces the exact integer sums of one model
+// (reference staged in dynamic shared memory, 12 L bytes), then warp 0 runs the 8 FP64
+// epilogues side by side, one model per lane. (With 32 models per block, four per warp, the
+// grid was about one block per SM and the integer sums' load latency dominated.)
+constexpr int VSREF_MODELS = 8;
 
 __global__ void __launch_bounds__(256) vsref_kernel(const float *__restrict__ coords, int64_t N, int L,
                                                     const int *__restrict__ nref_g, const RefInfo *__restrict__ info,
@@ -123,16 +124,9 @@ __global__ void __launch_bounds__(256) vsref_kernel(const float *__restrict__ co
         const int64_t a = m0 + mm;
         if (a >= N) break;
         const float *x = coords + a * (int64_t)L * 3;
-        float mu[3];
+        float mu[3], mx[3];
         bool finite;
-        model_centroid(x, L, lane, mu, &finite);
-        float m0x = 0.f, m1x = 0.f, m2x = 0.f;
-        for (int i = lane; i < L; i += 32) {
-            m0x = fmaxf(m0x, fabsf(x[3 * i + 0] - mu[0]));
-            m1x = fmaxf(m1x, fabsf(x[3 * i + 1] - mu[1]));
-            m2x = fmaxf(m2x, fabsf(x[3 * i + 2] - mu[2]));
-        }
-        const float mx[3] = {warp_max_f(m0x), warp_max_f(m1x), warp_max_f(m2x)};
+        model_centroid_absmax(x, L, lane, mu, mx, &finite);
         float inv[3], sc[3];
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
@@ -175,7 +169,7 @@ __global__ void __launch_bounds__(256) vsref_kernel(const float *__restrict__ co
         }
     }
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 0 && lane < VSREF_MODELS) {
         const int64_t a = m0 + lane;
         if (a < N) {
             const RefInfo ri = *info;

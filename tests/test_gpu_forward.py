@@ -176,3 +176,27 @@ def test_nonfinite_inputs_flagged():
         assert np.all(np.isnan(out[bad]))
         assert np.all(np.isfinite(out[~bad]))
     assert clusco.sync_status() == 0
+
+
+def test_refinement_of_flagged_pairs_in_panels():
+    """Near-duplicate models (sigma 0.01-0.1 A): nearly every pair fails the FP32 bound and is
+    recomputed by the refinement kernel from the exact fixed-point coordinates. The one-shot
+    matrix is held to the exact-digit tolerance against the oracle, and row panels whose pair
+    ranges start inside a 32-pair mask word (and a pair count that is not a multiple of 32)
+    reproduce it bit for bit."""
+    if clusco.FORM_BF16_EXACT2 not in forms_available():
+        pytest.skip("exact-digit form unavailable")
+    e = E.decoy_ensemble(151, 64, 2, (0.01, 0.1), 77)
+    N = e.N
+    assert (N * (N - 1) // 2) % 32 != 0
+    X = torch.from_numpy(e.coords).cuda()
+    full = clusco.crmsd_allpairs(X, clusco.FORM_BF16_EXACT2)
+    assert clusco.sync_status() == 0
+    ia, ib = np.triu_indices(N, 1)
+    ref = oracle.crmsd_pairs(e.coords, ia, ib)
+    err = np.abs(full.double().cpu().numpy() - ref)
+    print(f"near-duplicate ensemble: c in [{ref.min():.3f}, {ref.max():.3f}] A, max |d| {err.max():.2e}")
+    assert err.max() <= 1e-3
+    pieces = [clusco.crmsd_allpairs_panel(X, r0, r1, clusco.FORM_BF16_EXACT2).cpu()
+              for r0, r1 in [(0, 1), (1, 37), (37, 101), (101, 149), (149, 150)]]
+    assert torch.equal(torch.cat(pieces), full.cpu())
