@@ -643,8 +643,9 @@ __device__ __forceinline__ unsigned dp4a_uu(unsigned a, unsigned b, unsigned c)
 // ll < 2^16, so over L <= 1024 atoms every class stays below 2^26), then
 // H = 65536 hh + 256 (hl + lh) + ll in int64, scaled to FP64, and cRMSD by FP64 Newton from an
 // FP32 start (crmsd_refine_newton_fp64). Flagged pairs cluster (close decoys of one native),
-// so warps take single mask words (32 pairs) round-robin; lanes split the atom quads of each
-// pair, and pairs are batched 32 at a time so that every FP64 instruction runs on 32 lanes.
+// so warps take single mask words (32 pairs) round-robin (loading 32 of their words at a
+// time); lanes split the atom quads of each pair, and pairs are batched 32 at a time so that
+// every FP64 instruction runs on 32 lanes.
 __global__ void __launch_bounds__(256, 2) refine_flagged_kernel(const int8_t *__restrict__ hplane,
                                                                 const uint8_t *__restrict__ lplane,
                                                                 const float *__restrict__ scales,
@@ -688,63 +689,77 @@ __global__ void __launch_bounds__(256, 2) refine_flagged_kernel(const int8_t *__
         }
         cnt = 0;
     };
-    for (int64_t wi = w0; wi < nwords; wi += nwarps) {
-        uint32_t wd = flags[wi];
-        if (wi == nwords - 1 && (npairs & 31)) wd &= ~0u >> (32 - (int)(npairs & 31));
-        while (wd) {
-            const int bit = __ffs(wd) - 1;
-            wd &= wd - 1;
-            const int64_t li = wi * 32 + bit;
-            const int64_t idx = li + out_base;
-            const int64_t a = condensed_row(idx, N);
-            const int64_t b = idx - condensed_idx(a, a + 1, N) + a + 1;
-            const int *ha = reinterpret_cast<const int *>(hplane + tc_row(a, 0) * Lp);
-            const unsigned *la = reinterpret_cast<const unsigned *>(lplane + tc_row(a, 0) * Lp);
-            const int *hb = reinterpret_cast<const int *>(hplane + tc_row(b, 0) * Lp);
-            const unsigned *lb = reinterpret_cast<const unsigned *>(lplane + tc_row(b, 0) * Lp);
-            int hh[9], hx[9];
-            unsigned ll[9];
+    // one flagged pair: its nine exact sums reduced across the warp into lane cnt's slot
+    auto pair = [&](int64_t li) {
+        const int64_t idx = li + out_base;
+        const int64_t a = condensed_row(idx, N);
+        const int64_t b = idx - condensed_idx(a, a + 1, N) + a + 1;
+        const int *ha = reinterpret_cast<const int *>(hplane + tc_row(a, 0) * Lp);
+        const unsigned *la = reinterpret_cast<const unsigned *>(lplane + tc_row(a, 0) * Lp);
+        const int *hb = reinterpret_cast<const int *>(hplane + tc_row(b, 0) * Lp);
+        const unsigned *lb = reinterpret_cast<const unsigned *>(lplane + tc_row(b, 0) * Lp);
+        int hh[9], hx[9];
+        unsigned ll[9];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                hh[k] = 0;
-                hx[k] = 0;
-                ll[k] = 0u;
-            }
+        for (int k = 0; k < 9; ++k) {
+            hh[k] = 0;
+            hx[k] = 0;
+            ll[k] = 0u;
+        }
 #pragma unroll 4
-            for (int q = lane; q < nq; q += 32) {
-                int A[3], B[3];
-                unsigned Al[3], Bl[3];
+        for (int q = lane; q < nq; q += 32) {
+            int A[3], B[3];
+            unsigned Al[3], Bl[3];
 #pragma unroll
-                for (int ax = 0; ax < 3; ++ax) {
-                    A[ax] = __ldg(ha + ax * rq + q);
-                    Al[ax] = __ldg(la + ax * rq + q);
-                    B[ax] = __ldg(hb + ax * rq + q);
-                    Bl[ax] = __ldg(lb + ax * rq + q);
+            for (int ax = 0; ax < 3; ++ax) {
+                A[ax] = __ldg(ha + ax * rq + q);
+                Al[ax] = __ldg(la + ax * rq + q);
+                B[ax] = __ldg(hb + ax * rq + q);
+                Bl[ax] = __ldg(lb + ax * rq + q);
+            }
+#pragma unroll
+            for (int al = 0; al < 3; ++al)
+#pragma unroll
+                for (int be = 0; be < 3; ++be) {
+                    const int k = 3 * al + be;
+                    hh[k] = dp4a_ss(A[al], B[be], hh[k]);
+                    hx[k] = dp4a_us((int)Al[al], B[be], dp4a_su(A[al], (int)Bl[be], hx[k]));
+                    ll[k] = dp4a_uu(Al[al], Bl[be], ll[k]);
                 }
+        }
+        const int slot = cnt;
 #pragma unroll
-                for (int al = 0; al < 3; ++al)
-#pragma unroll
-                    for (int be = 0; be < 3; ++be) {
-                        const int k = 3 * al + be;
-                        hh[k] = dp4a_ss(A[al], B[be], hh[k]);
-                        hx[k] = dp4a_us((int)Al[al], B[be], dp4a_su(A[al], (int)Bl[be], hx[k]));
-                        ll[k] = dp4a_uu(Al[al], Bl[be], ll[k]);
-                    }
+        for (int k = 0; k < 9; ++k) {
+            // this lane's part of the sum, |t| < 2^36, reduced exactly as two 32-bit halves
+            const long long t = 65536LL * hh[k] + 256LL * hx[k] + (long long)ll[k];
+            const long long shi = __reduce_add_sync(0xffffffffu, (int)(t >> 24));
+            const long long slo = __reduce_add_sync(0xffffffffu, (int)(t & 0xFFFFFF));
+            if (lane == slot) v[k] = (shi << 24) + slo;
+        }
+        if (lane == slot) {
+            sa = a;
+            sb = b;
+            oidx = li;
+        }
+        if (++cnt == 32) flush();
+    };
+    // mask words w0 + nwarps (32 it + j): lane j loads one word per iteration, so the scan
+    // issues 32 loads at a time yet keeps the round-robin assignment of words to warps
+    for (int64_t base = w0; base < nwords; base += 32 * nwarps) {
+        const int64_t wl = base + (int64_t)lane * nwarps;
+        uint32_t word = wl < nwords ? flags[wl] : 0u;
+        if (wl == nwords - 1 && (npairs & 31)) word &= ~0u >> (32 - (int)(npairs & 31));
+        uint32_t nz = __ballot_sync(0xffffffffu, word != 0u);
+        while (nz) {
+            const int src = __ffs(nz) - 1;
+            nz &= nz - 1;
+            const int64_t wi = base + (int64_t)src * nwarps;
+            uint32_t wd = __shfl_sync(0xffffffffu, word, src);
+            while (wd) {
+                const int bit = __ffs(wd) - 1;
+                wd &= wd - 1;
+                pair(wi * 32 + bit);
             }
-            const int slot = cnt;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                const long long shh = __reduce_add_sync(0xffffffffu, hh[k]);
-                const long long shx = __reduce_add_sync(0xffffffffu, hx[k]);
-                const long long sll = (long long)__reduce_add_sync(0xffffffffu, ll[k]);
-                if (lane == slot) v[k] = 65536LL * shh + 256LL * shx + sll;
-            }
-            if (lane == slot) {
-                sa = a;
-                sb = b;
-                oidx = li;
-            }
-            if (++cnt == 32) flush();
         }
     }
     flush();
