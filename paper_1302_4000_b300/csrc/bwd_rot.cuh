@@ -169,7 +169,9 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
     __shared__ int abort_flag;
     __shared__ float dsum[TC_MA];
 
-    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // 1024-byte aligned in the shared window; indexing smem_raw (not an integer cast) keeps the
+    // pointer in the shared address space, so accesses through it compile to shared loads/stores
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint8_t *A2 = smem;                                       // two operands of BR_A2 bytes: [hi 16 KB][lo 16 KB]
     uint8_t *XT = smem + 2 * BR_A2;                           // BR_XSTAGES chunk buffers of BR_XBUF bytes
     uint8_t *REC = XT + BR_XSTAGES * BR_XBUF;                 // 2 stages x 8 warps x 10 segments

@@ -158,7 +158,9 @@ __global__ void __launch_bounds__(BT_THREADS, 1)
     __shared__ float sB_G32[TC_MB];
     __shared__ float dsum[TC_MA];
 
-    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // 1024-byte aligned in the shared window; indexing smem_raw (not an integer cast) keeps the
+    // pointer in the shared address space, so accesses through it compile to shared loads/stores
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const uint32_t sbase0 = smem_u32(smem);
     uint8_t *XT = smem + BT_RING;            // two X^T chunk buffers of BT_XBUF bytes
     uint8_t *A2 = smem + BT_RING + BT_XT;    // [hi 32 KB][lo 32 KB]

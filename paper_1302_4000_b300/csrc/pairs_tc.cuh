@@ -275,7 +275,9 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
-    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // 1024-byte aligned in the shared window; indexing smem_raw (not an integer cast) keeps the
+    // pointer in the shared address space, so accesses through it compile to shared loads/stores
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const uint32_t sbase0 = smem_u32(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr uint32_t STAGE_BYTES = (LAYOUT == TC_TF32) ? STAGE_BYTES_TF32 : STAGE_BYTES_BF16;
