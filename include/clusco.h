@@ -97,6 +97,20 @@ int clusco_crmsd_allpairs_panel(const float *coords, int64_t N, int64_t L, int64
                                 int64_t row_end, float *out_panel, int form, void *workspace,
                                 size_t workspace_bytes, void *stream);
 
+/* Pairs within a cRMSD threshold (section "Selecting of pairs of models within a given cRMSD
+ * threshold": the pairs with cRMSD below a cutoff, there 3.2 A, instead of the whole matrix).
+ * Appends every pair a < b whose cRMSD, exactly as clusco_crmsd_allpairs computes it in the
+ * same form, is < tau (strictly; NaN never qualifies): list[k] = its condensed index
+ * idx(a, b) = a N - a (a + 1) / 2 + (b - a - 1) (int64), vals[k] = its cRMSD (FP32), for
+ * k < min(*count, cap), in no particular order. *count (device, uint64) is reset by the call
+ * and ends as the number of qualifying pairs, also when that exceeds cap: entries past cap are
+ * dropped, and the caller can call again with cap >= *count. No dense output is written.
+ * list (8-byte aligned) and vals may be NULL when cap = 0; tau may be +inf (every finite pair).
+ * Workspace: that of CLUSCO_OP_ALLPAIRS. */
+int clusco_crmsd_allpairs_below(const float *coords, int64_t N, int64_t L, float tau, int64_t *list,
+                                float *vals, int64_t cap, uint64_t *count, int form, void *workspace,
+                                size_t workspace_bytes, void *stream);
+
 /* One-versus-reference: out[a] = cRMSD(model a, ref) for a in [0, N).
  * ref: float[L][3] device; out: float[N] device. Exact-integer covariance on
  * 24-bit fixed point coordinates, FP64 epilogue. N >= 1, L >= 1. */

@@ -37,6 +37,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EOVE
           6: "ENONFINITE", 7: "EUNSUPPORTED"}
 
 EXPORTS = ("clusco_version", "clusco_workspace_bytes", "clusco_crmsd_allpairs", "clusco_crmsd_allpairs_panel",
+           "clusco_crmsd_allpairs_below",
            "clusco_crmsd_vs_ref", "clusco_crmsd_vs_ref_noalloc", "clusco_crmsd_allpairs_backward",
            "clusco_sync_status", "clusco_last_error", "clusco_profile_enable", "clusco_profile_read",
            "clusco_crmsd_allpairs_rot", "clusco_crmsd_allpairs_backward_rot")
@@ -69,6 +70,8 @@ def load(path: str = LIB_PATH):
             lib.clusco_workspace_bytes.argtypes = [ctypes.c_int, i64, i64, ctypes.c_int]
             lib.clusco_crmsd_allpairs.argtypes = [vp, i64, i64, vp, ctypes.c_int, vp, sz, vp]
             lib.clusco_crmsd_allpairs_panel.argtypes = [vp, i64, i64, i64, i64, vp, ctypes.c_int, vp, sz, vp]
+            lib.clusco_crmsd_allpairs_below.argtypes = [vp, i64, i64, ctypes.c_float, vp, vp, i64, vp,
+                                                        ctypes.c_int, vp, sz, vp]
             lib.clusco_crmsd_vs_ref.argtypes = [vp, i64, i64, vp, vp, vp, sz, vp]
             lib.clusco_crmsd_vs_ref_noalloc.argtypes = [vp, i64, i64, vp, vp, vp]
             lib.clusco_crmsd_allpairs_backward.argtypes = [vp, i64, i64, vp, vp, vp, ctypes.c_float, ctypes.c_int,
@@ -148,6 +151,42 @@ def crmsd_allpairs(coords: torch.Tensor, form: int = FORM_BF16_EXACT2, out: torc
     _check(load().clusco_crmsd_allpairs(coords.data_ptr(), N, L, out.data_ptr(), form, ws.data_ptr(), nb,
                                         _stream(stream)))
     return out
+
+
+def crmsd_pairs_below(coords: torch.Tensor, tau: float, form: int = FORM_BF16_EXACT2, capacity: int | None = None,
+                      workspace: torch.Tensor | None = None, stream=None):
+    """(idx, vals): every pair a < b with cRMSD < tau, as int64 condensed indices and their
+    float32 cRMSD (exactly the values crmsd_allpairs gives in the same form), in no particular
+    order. capacity is the first guess at their number; when more qualify, the call runs again
+    with room for all of them (the library reports the full count)."""
+    coords = _coords(coords)
+    N, L = coords.shape[0], coords.shape[1]
+    P = N * (N - 1) // 2
+    cap = max(1024, P // 64) if capacity is None else int(capacity)
+    cap = min(cap, P)
+    ws, nb = _ws(workspace, OP_ALLPAIRS, N, L, form, coords.device)
+    count = torch.zeros(1, dtype=torch.int64, device=coords.device)
+    while True:
+        idx = torch.empty(max(cap, 1), dtype=torch.int64, device=coords.device)
+        vals = torch.empty(max(cap, 1), dtype=torch.float32, device=coords.device)
+        _check(load().clusco_crmsd_allpairs_below(coords.data_ptr(), N, L, float(tau), idx.data_ptr(), vals.data_ptr(),
+                                                  cap, count.data_ptr(), form, ws.data_ptr(), nb, _stream(stream)))
+        n = int(count.item())
+        if n <= cap:
+            return idx[:n], vals[:n]
+        cap = n
+
+
+def condensed_pairs(idx: torch.Tensor, N: int):
+    """(a, b) with a < b for condensed indices idx = a N - a (a + 1) / 2 + (b - a - 1)."""
+    i = idx.to(torch.float64)
+    t = 2.0 * N - 1.0
+    a = torch.floor(0.5 * (t - torch.sqrt(torch.clamp(t * t - 8.0 * i, min=0.0)))).to(torch.int64).clamp(0, N - 2)
+    start = lambda r: r * N - r * (r + 1) // 2
+    a = torch.where(start(a) > idx, a - 1, a)
+    a = torch.where(start(a + 1) <= idx, a + 1, a)
+    b = idx - start(a) + a + 1
+    return a, b
 
 
 ROT_STRIDE = 12

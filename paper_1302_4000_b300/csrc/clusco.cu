@@ -201,13 +201,23 @@ int run_prepass(const float *coords, int64_t N, int64_t L, int form, const Pairs
     return CLUSCO_OK;
 }
 
+// Threshold mode of the all-pairs call: the pairs with c < tau as a list (see PairSink).
+struct Threshold {
+    long long *list;
+    float *vals;
+    unsigned long long *count;
+    int64_t cap;
+    float tau;
+};
+
 int allpairs_impl(const float *coords, int64_t N, int64_t L, int64_t row_begin, int64_t row_end, float *out,
-                  int form, void *ws, size_t ws_bytes, cudaStream_t st, float *rot = nullptr)
+                  int form, void *ws, size_t ws_bytes, cudaStream_t st, float *rot = nullptr,
+                  const Threshold *thr = nullptr)
 {
     int rc;
     if ((rc = check_sizes(N, L, 2))) return rc;
     if ((rc = check_ptr(coords, "coords", 4))) return rc;
-    if ((rc = check_ptr(out, "out", 4))) return rc;
+    if (!thr && (rc = check_ptr(out, "out", 4))) return rc;
     if (!valid_form(form)) return fail(CLUSCO_EINVAL, "unknown form %d", form);
     if (rot && form == CLUSCO_FORM_FP32_SIMT)
         return fail(CLUSCO_EUNSUPPORTED, "rotations are produced by the tensor-core forms only");
@@ -227,8 +237,19 @@ int allpairs_impl(const float *coords, int64_t N, int64_t L, int64_t row_begin, 
         const int64_t T = w.Npad / SIMT_TILE;
         const int64_t I0 = row_begin / SIMT_TILE, I1 = (row_end - 1) / SIMT_TILE + 1;
         const int64_t t0 = tri_row_start(I0, T), nt = tri_row_start(I1, T) - t0;
+        PairSink sink;
+        sink.out = out;
+        sink.out_base = out_base;
+        if (thr) {
+            sink.list = thr->list;
+            sink.vals = thr->vals;
+            sink.count = thr->count;
+            sink.cap = thr->cap;
+            sink.tau = thr->tau;
+            CUDA_TRY(cudaMemsetAsync(thr->count, 0, sizeof(unsigned long long), st));
+        }
         pairs_simt_kernel<<<(unsigned)nt, 256, 0, st>>>(w.Xk, w.G64, N, w.Npad, (int)w.Lp, (int)L, T, t0,
-                                                        row_begin, row_end, out, out_base);
+                                                        row_begin, row_end, sink);
         CUDA_TRY(cudaGetLastError());
     } else {
         TcArgs a;
@@ -252,6 +273,13 @@ int allpairs_impl(const float *coords, int64_t N, int64_t L, int64_t row_begin, 
         a.flags = w.flags;
         a.hplane = w.hplane;
         a.lplane = w.lplane;
+        if (thr) {
+            a.list = thr->list;
+            a.vals = thr->vals;
+            a.count = thr->count;
+            a.cap = thr->cap;
+            a.tau = thr->tau;
+        }
         std::string err;
         rc = tc_launch_allpairs(a, st, err);
         if (rc) return fail(rc, "%s", err.c_str());
@@ -309,6 +337,26 @@ int clusco_crmsd_allpairs_panel(const float *coords, int64_t N, int64_t L, int64
     g_last_error.clear();
     return allpairs_impl(coords, N, L, row_begin, row_end, out_panel, form, workspace, workspace_bytes,
                          (cudaStream_t)stream);
+}
+
+int clusco_crmsd_allpairs_below(const float *coords, int64_t N, int64_t L, float tau, int64_t *list, float *vals,
+                                int64_t cap, uint64_t *count, int form, void *workspace, size_t workspace_bytes,
+                                void *stream)
+{
+    g_last_error.clear();
+    int rc;
+    if (tau != tau) return fail(CLUSCO_EINVAL, "tau is NaN");
+    if (cap < 0) return fail(CLUSCO_EINVAL, "cap=%lld must be >= 0", (long long)cap);
+    if (cap > 0) {
+        if ((rc = check_ptr(list, "list", 8))) return rc;
+        if ((rc = check_ptr(vals, "vals", 4))) return rc;
+    }
+    if ((rc = check_ptr(count, "count", 8))) return rc;
+    static_assert(sizeof(int64_t) == sizeof(long long) && sizeof(uint64_t) == sizeof(unsigned long long), "");
+    const Threshold t{reinterpret_cast<long long *>(list), vals, reinterpret_cast<unsigned long long *>(count), cap,
+                      tau};
+    return allpairs_impl(coords, N, L, 0, N - 1, nullptr, form, workspace, workspace_bytes, (cudaStream_t)stream,
+                         nullptr, &t);
 }
 
 int clusco_crmsd_vs_ref(const float *coords, int64_t N, int64_t L, const float *ref, float *out, void *workspace,

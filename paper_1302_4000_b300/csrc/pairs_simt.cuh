@@ -25,11 +25,11 @@ __device__ __forceinline__ void tri_decode(int64_t t, int64_t T, int64_t *I, int
 
 // One CTA = one 64x64 model tile; 256 threads as 16x16, each 4 A-models x 4 B-models.
 // Xk: [Lp][Npad][3] centred FP32 (zero padded). Rows a outside [row_begin, row_end) are skipped;
-// out is indexed by condensed(a, b) - out_base.
+// each pair's value goes to the sink (dense: out[condensed(a, b) - out_base]; or the list of
+// pairs below the threshold).
 __global__ void __launch_bounds__(256, 1)
     pairs_simt_kernel(const float *__restrict__ Xk, const double *__restrict__ G64, int64_t N, int64_t Npad, int Lp,
-                      int L, int64_t T, int64_t tile0, int64_t row_begin, int64_t row_end, float *__restrict__ out,
-                      int64_t out_base)
+                      int L, int64_t T, int64_t tile0, int64_t row_begin, int64_t row_end, PairSink sink)
 {
     __shared__ __align__(16) float As[SIMT_KC][SIMT_TILE * 3];
     __shared__ __align__(16) float Bs[SIMT_KC][SIMT_TILE * 3];
@@ -82,25 +82,32 @@ __global__ void __launch_bounds__(256, 1)
     }
 
     const double invL = 1.0 / (double)L;
+    // every thread runs all 16 (i, j) steps, so that threshold mode's warp appends line up
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int64_t a = a0 + ty * 4 + i;
-        if (a < row_begin || a >= row_end || a >= N) continue;
-        const double Ga = G64[a];
+        const bool arow = a >= row_begin && a < row_end && a < N;
+        const double Ga = arow ? G64[a] : 0.0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int64_t b = b0 + tx * 4 + j;
-            if (b <= a || b >= N) continue;
-            double H[9];
+            const bool ok = arow && b > a && b < N;
+            float c = 0.f;
+            if (ok) {
+                double H[9];
 #pragma unroll
-            for (int e = 0; e < 9; ++e) H[e] = (double)acc[i][j][e];
-            const double Gb = G64[b];
-            float c;
-            if (isnan(Ga) || isnan(Gb))
-                c = __int_as_float(0x7fc00000);
-            else
-                c = crmsd_plain_fp64(H, Ga, Gb, invL);
-            out[condensed_idx(a, b, N) - out_base] = c;
+                for (int e = 0; e < 9; ++e) H[e] = (double)acc[i][j][e];
+                const double Gb = G64[b];
+                if (isnan(Ga) || isnan(Gb))
+                    c = __int_as_float(0x7fc00000);
+                else
+                    c = crmsd_plain_fp64(H, Ga, Gb, invL);
+            }
+            if (!sink.list) {
+                if (ok) sink.out[condensed_idx(a, b, N) - sink.out_base] = c;
+            } else {
+                sink_append_warp(sink, ok && c < sink.tau, ok ? condensed_idx(a, b, N) : 0, c);
+            }
         }
     }
 }

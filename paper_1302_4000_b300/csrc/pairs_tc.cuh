@@ -84,6 +84,12 @@ struct TcArgs {
     uint32_t *flags = nullptr;  // EXACT2: one bit per output pair, set where the FP32 bound fails
     int8_t *hplane = nullptr;   // EXACT2: the 16-bit fixed-point coordinates as bytes (h, l), for
     uint8_t *lplane = nullptr;  // the refinement of flagged pairs
+    // threshold mode (list != nullptr; no rotations): the pairs with c < tau instead of out
+    long long *list = nullptr;
+    float *vals = nullptr;
+    unsigned long long *count = nullptr;
+    int64_t cap = 0;
+    float tau = 0.f;
 };
 
 
@@ -97,7 +103,10 @@ constexpr uint32_t STAGE_BYTES_TF32 = 16384 + 8192;          // A, B
 constexpr int FW_EGROUPS = CLUSCO_FW_EGROUPS;
 constexpr int FW_THREADS = 64 + 256 * FW_EGROUPS;
 constexpr int FW_STAGES = FW_EGROUPS == 2 ? 2 : 3;
-constexpr size_t FW_SMEM = 1024 + FW_STAGES * STAGE_BYTES_BF16;
+// threshold mode: per epilogue warp, a staging buffer of 64 kept pairs (global index, value),
+// published 32 at a time with one atomic
+constexpr int FW_SBUF = 64;
+constexpr size_t FW_SMEM = 1024 + FW_STAGES * STAGE_BYTES_BF16 + 8 * FW_EGROUPS * FW_SBUF * 12;
 static_assert(FW_SMEM <= 227 * 1024, "shared memory per CTA");
 
 __host__ __device__ __forceinline__ int64_t tc_row_start(int64_t I, int64_t TB) { return I * TB - I * (I - 1); }
@@ -257,12 +266,12 @@ __global__ void __launch_bounds__(256) rot_fixup_kernel(const RotFix *__restrict
 // ROT: also write each pair's optimal rotation R_ab (b onto a, natural axis order, row-major)
 // to rot[(idx - out_base) * ROT_STRIDE ..], computed as dSigma/dM from the fast path's Sigma (Horn's
 // key matrix near a double root); the adjoint reads it instead of recomputing the covariance.
-template <int LAYOUT, bool ROT>
+template <int LAYOUT, bool ROT, bool SPARSE = false>
 __global__ void __launch_bounds__(FW_THREADS, 1)
     pairs_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                     const float *__restrict__ scales, const float *__restrict__ G32,
                     int64_t N, int L, int nkb, int64_t Rpad, int64_t TA, int64_t TB, int64_t tile0, int64_t ntiles,
-                    int64_t row_begin, int64_t row_end, float *__restrict__ out, int64_t out_base,
+                    int64_t row_begin, int64_t row_end, PairSink sink,
                     float *__restrict__ rot, RotFix *__restrict__ fix, unsigned long long *__restrict__ fix_count,
                     int64_t fix_cap, uint32_t *__restrict__ flags)
 {
@@ -387,6 +396,24 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
         const int sp = warp & 3, g = (ew & 7) >> 2;
         const int mloc = lane / 3, alpha = lane - 3 * (lane / 3);
         const float invL = 1.f / (float)L;
+        float *const out = sink.out;
+        const int64_t out_base = sink.out_base;
+        // threshold mode: this warp's staging buffer of kept pairs (fill is warp-uniform)
+        long long *sidx = reinterpret_cast<long long *>(smem + FW_STAGES * STAGE_BYTES_BF16) + ew * FW_SBUF;
+        float *sval = reinterpret_cast<float *>(smem + FW_STAGES * STAGE_BYTES_BF16 + 8 * 8 * FW_EGROUPS * FW_SBUF) +
+                      ew * FW_SBUF;
+        int fill = 0;
+        auto publish = [&](int n) {  // the first n staged pairs to the list, one atomic
+            __syncwarp();
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(sink.count, (unsigned long long)n);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (lane < n && base + lane < (unsigned long long)sink.cap) {
+                sink.list[base + lane] = sidx[lane];
+                sink.vals[base + lane] = sval[lane];
+            }
+            __syncwarp();
+        };
 
         const int64_t gstep = (int64_t)FW_EGROUPS * gridDim.x;
         int64_t k = gp;
@@ -507,13 +534,34 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                         }
                     }
                 }
-                if (pok[0]) {
-                    if (LAYOUT == TC_EXACT2 && !(ev <= 2.f * CLUSCO_TOL_FAST * cv)) {
-                        // the bound fails: refine_flagged_kernel writes this pair's value
-                        const int64_t li = rowbase + b;
-                        atomicOr(flags + (li >> 5), 1u << (li & 31));
-                    } else {
-                        out[rowbase + b] = (isnan(Ga) || isnan(Gb[0])) ? __int_as_float(0x7fc00000) : cv;
+                const bool flagged = LAYOUT == TC_EXACT2 && pok[0] && !(ev <= 2.f * CLUSCO_TOL_FAST * cv);
+                const float cfin = (isnan(Ga) || isnan(Gb[0])) ? __int_as_float(0x7fc00000) : cv;
+                if (flagged) {
+                    // the bound fails: refine_flagged_kernel writes (or keeps) this pair's value
+                    const int64_t li = rowbase + b;
+                    atomicOr(flags + (li >> 5), 1u << (li & 31));
+                } else if (!SPARSE && pok[0]) {
+                    out[rowbase + b] = cfin;
+                }
+                if (SPARSE) {
+                    const bool keep = pok[0] && !flagged && cfin < sink.tau;
+                    const unsigned m = __ballot_sync(0xffffffffu, keep);
+                    if (m) {
+                        if (keep) {
+                            const int my = fill + __popc(m & ((1u << lane) - 1u));
+                            sidx[my] = rowbase + b + out_base;
+                            sval[my] = cfin;
+                        }
+                        fill += __popc(m);
+                        if (fill >= 32) {
+                            publish(32);
+                            if (lane < fill - 32) {
+                                sidx[lane] = sidx[32 + lane];
+                                sval[lane] = sval[32 + lane];
+                            }
+                            __syncwarp();
+                            fill -= 32;
+                        }
                     }
                 }
 #pragma unroll
@@ -527,6 +575,7 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty_bar[buf]);
         }
+        if (SPARSE && fill > 0) publish(fill);
     }
     tc_fence_before();
     __syncthreads();
@@ -653,8 +702,7 @@ __global__ void __launch_bounds__(256, 2) refine_flagged_kernel(const int8_t *__
                                                                 const float *__restrict__ scales,
                                                                 const double *__restrict__ G64, int64_t N, int L,
                                                                 int Lp, int64_t npairs, int64_t out_base,
-                                                                const uint32_t *__restrict__ flags,
-                                                                float *__restrict__ out)
+                                                                const uint32_t *__restrict__ flags, PairSink sink)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -669,6 +717,7 @@ __global__ void __launch_bounds__(256, 2) refine_flagged_kernel(const int8_t *__
     int64_t sa = 0, sb = 0, oidx = -1;
     int cnt = 0;
     auto flush = [&]() {
+        float c = 0.f;
         if (lane < cnt) {
             float s3a[3], s3b[3];
 #pragma unroll
@@ -687,8 +736,10 @@ __global__ void __launch_bounds__(256, 2) refine_flagged_kernel(const int8_t *__
                 mf[k] = (float)v[k] * (s3a[k / 3] * s3b[k % 3]) * nrmf;
                 H[k] = (double)v[k] * ((double)s3a[k / 3] * (double)s3b[k % 3]);
             }
-            out[oidx] = crmsd_refine_newton_fp64(H, Ga, Gb, invL, sigma_hat_f32(mf));
+            c = crmsd_refine_newton_fp64(H, Ga, Gb, invL, sigma_hat_f32(mf));
+            if (!sink.list) sink.out[oidx] = c;
         }
+        if (sink.list) sink_append_warp(sink, lane < cnt && c < sink.tau, oidx + out_base, c);
         cnt = 0;
     };
     // one flagged pair: its nine exact sums reduced across the warp into lane cnt's slot
@@ -785,7 +836,16 @@ inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    auto kern = a.rot ? pairs_tc_kernel<LAYOUT, true> : pairs_tc_kernel<LAYOUT, false>;
+    auto kern = a.rot ? pairs_tc_kernel<LAYOUT, true, false>
+                      : (a.list ? pairs_tc_kernel<LAYOUT, false, true> : pairs_tc_kernel<LAYOUT, false, false>);
+    PairSink sink;
+    sink.out = a.out;
+    sink.out_base = a.out_base;
+    sink.list = a.list;
+    sink.vals = a.vals;
+    sink.count = a.count;
+    sink.cap = a.cap;
+    sink.tau = a.tau;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FW_SMEM);
     if (e != cudaSuccess) {
         err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
@@ -801,6 +861,13 @@ inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
             return CLUSCO_ECUDA;
         }
     }
+    if (a.list) {
+        e = cudaMemsetAsync(a.count, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) {
+            err = std::string("list count reset: ") + cudaGetErrorString(e);
+            return CLUSCO_ECUDA;
+        }
+    }
     prof_mark(PROF_PAIRS, st);
     if (a.rot) {
         e = cudaMemsetAsync(a.fix_count, 0, sizeof(unsigned long long), st);
@@ -810,14 +877,14 @@ inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
         }
     }
     kern<<<grid, FW_THREADS, FW_SMEM, st>>>(mA, mB, a.scales, a.G32, a.N, (int)a.L, nkb, a.Rpad, TA, TB, t0, nt,
-                                             a.row_begin, a.row_end, a.out, a.out_base, a.rot, a.fix, a.fix_count,
-                                             a.fix_cap, a.flags);
+                                             a.row_begin, a.row_end, sink, a.rot, a.fix, a.fix_count, a.fix_cap,
+                                             a.flags);
     e = cudaGetLastError();
     prof_mark(PROF_PAIRS, st);
     if (e == cudaSuccess && LAYOUT == TC_EXACT2) {
         refine_flagged_kernel<<<4 * (sms > 0 ? sms : 148), 256, 0, st>>>(a.hplane, a.lplane, a.scales, a.G64, a.N,
                                                                           (int)a.L, (int)a.Lp, npairs, a.out_base,
-                                                                          a.flags, a.out);
+                                                                          a.flags, sink);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && a.rot) {

@@ -67,3 +67,28 @@ def test_host_side_validation(lib):
                                               None, 0, None) == 1  # eps must be > 0
     # a workspace that is too small is refused before any launch
     assert lib.clusco_crmsd_allpairs(fake, 10, 10, fake, 0, fake, 16, None) == 2
+    # threshold mode: NaN tau, negative capacity, missing or unaligned list / count
+    nan = ctypes.c_float(float("nan"))
+    assert lib.clusco_crmsd_allpairs_below(fake, 10, 10, nan, fake, fake, 4, fake, 0, None, 0, None) == 1
+    assert lib.clusco_crmsd_allpairs_below(fake, 10, 10, ctypes.c_float(1.0), fake, fake, -1, fake, 0, None, 0,
+                                           None) == 1
+    assert lib.clusco_crmsd_allpairs_below(fake, 10, 10, ctypes.c_float(1.0), None, fake, 4, fake, 0, None, 0,
+                                           None) == 1
+    assert lib.clusco_crmsd_allpairs_below(fake, 10, 10, ctypes.c_float(1.0), ctypes.c_void_p(0x1004), fake, 4,
+                                           fake, 0, None, 0, None) == 1
+    assert lib.clusco_crmsd_allpairs_below(fake, 10, 10, ctypes.c_float(1.0), fake, fake, 4, None, 0, None, 0,
+                                           None) == 1
+
+
+def test_condensed_pairs_inverts_the_condensed_index():
+    """The binding's host-side inverse of idx(a, b) = a N - a (a + 1) / 2 + (b - a - 1)."""
+    import numpy as np
+    import torch
+    for N in (2, 3, 7, 50, 1001):
+        a_ref, b_ref = np.triu_indices(N, 1)
+        a, b = clusco.condensed_pairs(torch.arange(N * (N - 1) // 2), N)
+        assert np.array_equal(a.numpy(), a_ref) and np.array_equal(b.numpy(), b_ref), N
+    N = 3_000_000  # last and first pairs at a size where the float estimate needs its corrections
+    P = N * (N - 1) // 2
+    a, b = clusco.condensed_pairs(torch.tensor([0, 1, N - 2, N - 1, P - 2, P - 1]), N)
+    assert a.tolist() == [0, 0, 0, 1, N - 3, N - 2] and b.tolist() == [1, 2, N - 1, 2, N - 1, N - 1]

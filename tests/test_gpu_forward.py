@@ -200,3 +200,94 @@ def test_refinement_of_flagged_pairs_in_panels():
     pieces = [clusco.crmsd_allpairs_panel(X, r0, r1, clusco.FORM_BF16_EXACT2).cpu()
               for r0, r1 in [(0, 1), (1, 37), (37, 101), (101, 149), (149, 150)]]
     assert torch.equal(torch.cat(pieces), full.cpu())
+
+
+def _sorted_list(idx, vals):
+    order = torch.argsort(idx)
+    return idx[order], vals[order]
+
+
+def test_pairs_below_threshold_equal_the_matrix_and_the_oracle():
+    """Threshold mode returns exactly the dense matrix's entries below tau (same form, bit for
+    bit, in any order), for tau = 0, 3.2 A, the median and +inf, through the retry path of a
+    too small first capacity; against the oracle, the exact-digit list holds every pair below
+    tau - 1e-3 A and none at or above tau + 1e-3 A (the form's tolerance band)."""
+    e = E.config0()
+    N = e.N
+    X = torch.from_numpy(e.coords).cuda()
+    ia, ib = all_pairs(N)
+    ref = oracle.crmsd_pairs(e.coords, ia, ib)
+    for form in forms_available():
+        full = clusco.crmsd_allpairs(X, form)
+        for tau in (0.0, 3.2, float(np.median(ref)), float("inf")):
+            idx, vals = _sorted_list(*clusco.crmsd_pairs_below(X, tau, form, capacity=64))
+            assert clusco.sync_status() == 0
+            want = torch.nonzero(full < tau).squeeze(1)
+            assert torch.equal(idx, want), (form, tau)
+            assert torch.equal(vals, full[want]), (form, tau)
+            if form == clusco.FORM_BF16_EXACT2:
+                got = np.zeros(len(ref), dtype=bool)
+                got[idx.cpu().numpy()] = True
+                assert got[ref < tau - 1e-3].all(), tau
+                assert not got[ref >= tau + 1e-3].any(), tau
+    a, b = clusco.condensed_pairs(idx, N)
+    assert torch.all(a < b) and torch.all(b < N)
+
+
+def test_pairs_below_threshold_skip_nonfinite_models():
+    e = E.decoy_ensemble(60, 30, 1, (0.5, 6.0), 19)
+    C = e.coords.copy()
+    C[11, 4, 2] = np.nan
+    X = torch.from_numpy(C).cuda()
+    N = e.N
+    for form in forms_available():
+        idx, vals = clusco.crmsd_pairs_below(X, float("inf"), form)
+        clusco.sync_status()  # the non-finite model sets the status word; it is cleared here
+        a, b = clusco.condensed_pairs(idx, N)
+        assert idx.numel() == (N - 1) * (N - 2) // 2, form  # every pair without model 11
+        assert not torch.any((a == 11) | (b == 11)) and torch.all(torch.isfinite(vals))
+
+
+def test_pairs_below_threshold_bench_workload():
+    """The 5,000 x 300 bench ensemble at the paper's 3.2 A cutoff in the exact-digit form: the
+    list equals the dense matrix below the cutoff, bit for bit; times both calls."""
+    if clusco.FORM_BF16_EXACT2 not in forms_available():
+        pytest.skip("exact-digit form unavailable")
+    e = E.config1()
+    X = torch.from_numpy(e.coords).cuda()
+    N, L = e.N, e.L
+    P = N * (N - 1) // 2
+    full = clusco.crmsd_allpairs(X, clusco.FORM_BF16_EXACT2)
+    idx, vals = _sorted_list(*clusco.crmsd_pairs_below(X, 3.2, clusco.FORM_BF16_EXACT2, capacity=P))
+    want = torch.nonzero(full < 3.2).squeeze(1)
+    assert torch.equal(idx, want) and torch.equal(vals, full[want])
+    ws = torch.empty(clusco.workspace_bytes(clusco.OP_ALLPAIRS, N, L), dtype=torch.uint8, device="cuda")
+    lst = torch.empty(idx.numel() + 1024, dtype=torch.int64, device="cuda")
+    val = torch.empty(idx.numel() + 1024, dtype=torch.float32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    lib = clusco.load()
+    st = torch.cuda.current_stream().cuda_stream
+
+    def dense():
+        clusco.crmsd_allpairs(X, clusco.FORM_BF16_EXACT2, out=full, workspace=ws)
+
+    def below():
+        assert lib.clusco_crmsd_allpairs_below(X.data_ptr(), N, L, 3.2, lst.data_ptr(), val.data_ptr(), lst.numel(),
+                                               cnt.data_ptr(), clusco.FORM_BF16_EXACT2, ws.data_ptr(), ws.numel(),
+                                               st) == 0
+
+    t = {}
+    for name, fn in (("dense", dense), ("below", below)):
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(10):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        t[name] = a.elapsed_time(b) / 10
+    assert int(cnt.item()) == idx.numel()
+    print(f"\n3.2 A cutoff at 5000 x 300: {idx.numel()} of {P} pairs kept; dense {t['dense']:.3f} ms, "
+          f"threshold {t['below']:.3f} ms")
