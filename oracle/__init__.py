@@ -1,16 +1,20 @@
-"""FP64 CPU oracle for all-versus-all cRMSD (TEST INFRASTRUCTURE).
+"""FP64 CPU oracle for all-versus-all cRMSD and dRMSD (TEST INFRASTRUCTURE).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline /
 reference leg may import this package. It shares no code with the CUDA path:
-the C source ``crmsd_oracle.c`` is compiled on its own with gcc (OpenMP for
-timing only) and loaded through ctypes.
+the C sources ``crmsd_oracle.c`` and ``drmsd_oracle.c`` are compiled on their own
+with gcc (OpenMP for timing only) and loaded through ctypes.
 
-Every function follows ClusCo's definition of cRMSD (section "Algorithms",
+The cRMSD functions follow ClusCo's definition (section "Algorithms",
 eq. 1: RMS deviation of matched atoms after the optimal superposition, with the
 cited Kabsch method). ``crmsd_eq2_pair`` restates the paper's closed form
 (eq. 2: radii of gyration, eigenvalues of M^T M from a cubic, sign of det M)
 and serves as a pin and as a second CPU method; the oracle's answers never
 come from it.
+
+The dRMSD functions follow eq. 5 (the RMS difference of the two models'
+intra-model distance matrices over the L(L-1)/2 atom pairs), formed directly
+from the distances.
 
 Parity pins: every function here is pinned by ``tests/test_oracle_pins.py``
 (closed forms, invariances, brute-force rotation search, eq. 2, finite
@@ -27,6 +31,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "crmsd_oracle.c")
+_DSRC = os.path.join(_HERE, "drmsd_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -36,10 +41,11 @@ _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
 
 
-def build(src: str = _SRC, out: str = _LIB, extra_flags=()) -> str:
-    """Compile the oracle with gcc (-O2, FP64, OpenMP). Returns the .so path."""
+def build(src=(_SRC, _DSRC), out: str = _LIB, extra_flags=()) -> str:
+    """Compile the oracle source(s) with gcc (-O2, FP64, OpenMP). Returns the .so path."""
+    srcs = [src] if isinstance(src, str) else list(src)
     cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-fopenmp",
-           "-fno-fast-math", *extra_flags, src, "-o", out, "-lm"]
+           "-fno-fast-math", *extra_flags, *srcs, "-o", out, "-lm"]
     subprocess.run(cmd, check=True)
     return out
 
@@ -51,14 +57,25 @@ def load(path: str | None = None):
         return _bind(ctypes.CDLL(path))
     with _lock:
         if _lib is None:
-            if (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+            if (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC),
+                                                                          os.path.getmtime(_DSRC)):
                 build()
             _lib = _bind(ctypes.CDLL(_LIB))
     return _lib
 
 
 def _bind(lib):
+    """Declare the signatures of whichever entry points the library holds (a test may load a
+    library built from one of the two sources)."""
     i64 = ctypes.c_int64
+    if hasattr(lib, "oracle_drmsd_pair"):
+        lib.oracle_drmsd_pair.argtypes = [_f32p, _f32p, i64, ctypes.POINTER(ctypes.c_double)]
+        lib.oracle_drmsd_allpairs.argtypes = [_f32p, i64, i64, _f64p, ctypes.c_int]
+        lib.oracle_drmsd_pairs.argtypes = [_f32p, i64, i64, _i64p, _i64p, i64, _f64p, ctypes.c_int]
+        for f in ("oracle_drmsd_pair", "oracle_drmsd_allpairs", "oracle_drmsd_pairs"):
+            getattr(lib, f).restype = ctypes.c_int
+    if not hasattr(lib, "oracle_crmsd_pair"):
+        return lib
     lib.oracle_max_threads.restype = ctypes.c_int
     lib.oracle_crmsd_pair.argtypes = [_f32p, _f32p, i64, ctypes.POINTER(ctypes.c_double), _f64p]
     lib.oracle_crmsd_allpairs.argtypes = [_f32p, i64, i64, _f64p, ctypes.c_int]
@@ -159,3 +176,35 @@ def crmsd_eq2_pair(A, B, lib=None) -> float:
     c = ctypes.c_double()
     _check(lib.oracle_crmsd_eq2(A, B, A.shape[0], ctypes.byref(c)), "eq2")
     return c.value
+
+
+def drmsd_pair(A, B, lib=None) -> float:
+    """dRMSD (eq. 5) of one pair of models [L, 3], L >= 2, in FP64."""
+    lib = lib or load()
+    A, B = _f32(A), _f32(B)
+    assert A.shape == B.shape and A.ndim == 2 and A.shape[1] == 3
+    c = ctypes.c_double()
+    _check(lib.oracle_drmsd_pair(A, B, A.shape[0], ctypes.byref(c)), "drmsd_pair")
+    return c.value
+
+
+def drmsd_allpairs(X, nthreads: int = 0, lib=None) -> np.ndarray:
+    """Condensed N(N-1)/2 FP64 dRMSD matrix, row-major upper triangle (a < b)."""
+    lib = lib or load()
+    X = _f32(X)
+    N, L = X.shape[0], X.shape[1]
+    out = np.empty(N * (N - 1) // 2, dtype=np.float64)
+    _check(lib.oracle_drmsd_allpairs(X, N, L, out, nthreads), "drmsd_allpairs")
+    return out
+
+
+def drmsd_pairs(X, ia, ib, nthreads: int = 0, lib=None) -> np.ndarray:
+    """dRMSD for the listed pairs (ia[k], ib[k])."""
+    lib = lib or load()
+    X = _f32(X)
+    ia = np.ascontiguousarray(ia, dtype=np.int64)
+    ib = np.ascontiguousarray(ib, dtype=np.int64)
+    out = np.empty(ia.shape[0], dtype=np.float64)
+    _check(lib.oracle_drmsd_pairs(X, X.shape[0], X.shape[1], ia, ib, ia.shape[0], out, nthreads),
+           "drmsd_pairs")
+    return out
