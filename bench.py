@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--L", type=int, default=300)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-drmsd", action="store_true", help="skip the all-versus-all dRMSD measurement")
     p.add_argument("--cpu-models", type=int, default=5000, help="models in the oracle's timed sample")
     p.add_argument("--ref-models", type=int, default=800, help="models per step of the reference arm")
     return p.parse_args()
@@ -425,6 +426,60 @@ def run_ours(args):
         del bufs
 
     hbm, bf16, bf16_sus, pk_kind = peaks()
+    # All-versus-all dRMSD (eq. 5) on the same ensemble: the tensor-core form (exact Gram of the
+    # 16-bit rounded distances) against the plain FP32 form, L2 flushed before each call; the
+    # contraction is 2 K flop per pair over K = L (L - 1) / 2 distances (one multiply-add per
+    # atom pair), executed as four BF16 digit-product classes.
+    drmsd = None
+    if not args.no_drmsd and form == clusco.FORM_BF16_EXACT2 and 2 <= L <= 4096:
+        K = L * (L - 1) // 2
+        ws_d = torch.empty(clusco.workspace_bytes(clusco.OP_DRMSD, N, L, form), dtype=torch.uint8, device=dev)
+        out_d = torch.empty(P, dtype=torch.float32, device=dev)
+
+        def dfwd():
+            clusco.drmsd_allpairs(X, clusco.FORM_BF16_EXACT2, out=out_d, workspace=ws_d)
+        d_ms = statistics.mean(timed(dfwd, max(3, args.steps // 20), max(2, args.warmup), prof=True)[0])
+        tot_ms, n = clusco.profile_read(clusco.KERNEL_DRMSD)
+        dk_ms = tot_ms / n if n else None
+        ws_dp = torch.empty(clusco.workspace_bytes(clusco.OP_DRMSD, N, L, clusco.FORM_FP32_SIMT), dtype=torch.uint8,
+                            device=dev)
+        out_dp = torch.empty_like(out_d)
+
+        def dplain():
+            clusco.drmsd_allpairs(X, clusco.FORM_FP32_SIMT, out=out_dp, workspace=ws_dp)
+        dp_ms = statistics.mean(timed(dplain, 2, 1)[0])
+        if clusco.sync_status() != 0:
+            raise RuntimeError("device status set during the dRMSD calls: " + lib.clusco_last_error().decode())
+        if ws_ > 1:
+            t = torch.tensor([d_ms, dp_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            d_ms, dp_ms = float(t[0]), float(t[1])
+        d_err = None
+        if rank == 0:
+            import oracle
+            rng = np.random.default_rng(4)
+            ia = rng.integers(0, N, 4000)
+            ib = rng.integers(0, N, 4000)
+            keep = ia != ib
+            ia, ib = np.minimum(ia[keep], ib[keep]), np.maximum(ia[keep], ib[keep])
+            idx = ia * N - ia * (ia + 1) // 2 + (ib - ia - 1)
+            d_err = float(np.abs(out_d.cpu().numpy()[idx].astype(np.float64)
+                                 - oracle.drmsd_pairs(e.coords, ia, ib)).max())
+        kms = dk_ms if dk_ms else d_ms
+        ach = 2.0 * K * P / (kms * 1e-3) / 1e12
+        Npad = (N + 127) // 128 * 128
+        tiles = (Npad // 128) * (Npad // 64) - (Npad // 128) * (Npad // 128 - 1)
+        executed = 4 * 2.0 * ((K + 63) // 64 * 64) * 128 * 64 * tiles  # digit classes, padded K, whole tiles
+        drmsd = {"value": ws_ * P / (d_ms * 1e-3), "unit": UNIT, "ms": d_ms, "form": "bf16_exact2",
+                 "vs_plain_fp32": dp_ms / d_ms, "plain_fp32_ms": dp_ms, "max_err_sampled_A": d_err,
+                 "roofline": {"kernel": "drmsd_tc_kernel (Gram of the rounded distances, 2 K flop/pair)",
+                              "launch_ms": kms, "timing": "kernel launch events" if dk_ms else "API call bracket",
+                              "bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
+                              "frac": ach / bf16, "peak_kind": f"{pk_kind} bf16 burst",
+                              "executed_tflops": executed / (kms * 1e-3) / 1e12,
+                              "traffic": traffic_for("drmsd_tc")}}
+        del ws_d, out_d, ws_dp, out_dp
+
     # Rooflines of the two tensor-core kernels. Algorithmic flop per pair: the forward
     # contraction is 18 L (the 3x3 covariance over L atoms); the adjoint is 54 L (that
     # covariance once, plus R x_b and R^T x_a over L atoms for the two gradients). One launch
@@ -479,6 +534,8 @@ def run_ours(args):
             "clocks": clk, "gpu_launches": launches_per_step * args.steps}
     if e2e:
         line["e2e"] = e2e
+    if drmsd:
+        line["drmsd"] = drmsd
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(e, w, native, args.cpu_models)
     if rank == 0:

@@ -74,7 +74,8 @@ typedef enum {
     CLUSCO_OP_VS_REF = 1,
     CLUSCO_OP_BACKWARD = 2,
     CLUSCO_OP_BACKWARD_ROT = 3,
-    CLUSCO_OP_ALLPAIRS_ROT = 4
+    CLUSCO_OP_ALLPAIRS_ROT = 4,
+    CLUSCO_OP_DRMSD = 5
 } clusco_op;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -110,6 +111,23 @@ int clusco_crmsd_allpairs_panel(const float *coords, int64_t N, int64_t L, int64
 int clusco_crmsd_allpairs_below(const float *coords, int64_t N, int64_t L, float tau, int64_t *list,
                                 float *vals, int64_t cap, uint64_t *count, int form, void *workspace,
                                 size_t workspace_bytes, void *stream);
+
+/* All-versus-all dRMSD (section "Algorithms", eq. 5): out[idx(a,b)] for a < b, condensed as
+ * above, the RMS difference of the two models' intra-model distances over the L (L - 1) / 2
+ * atom pairs i < j. No superposition; a mirror image scores 0. coords: float[N][L][3] device.
+ * Forms:
+ *  CLUSCO_FORM_BF16_EXACT2 -- every distance rounded to 16-bit fixed point with one scale q
+ *    and one offset for the ensemble (q = largest distance / 65278); the Gram matrix of the
+ *    rounded distances on tcgen05 as four exact BF16 digit classes, drained to int64 every
+ *    1024 terms, so the result is the exact dRMSD of the rounded distances: |error| <= q plus
+ *    FP32 rounding of the distances (about q / 4 for near-identical models).
+ *  CLUSCO_FORM_FP32_SIMT -- FP32 distances, squared differences summed directly on CUDA cores.
+ * Other forms return CLUSCO_EUNSUPPORTED. 2 <= N <= 2^24, 2 <= L <= 4096. A model with a
+ * non-finite coordinate gives NaN for its pairs (and sets CLUSCO_ENONFINITE in the device status).
+ * Workspace: clusco_workspace_bytes(CLUSCO_OP_DRMSD, N, L, form), about 2 N L^2 bytes
+ * (the rounded or FP32 distances of every model). */
+int clusco_drmsd_allpairs(const float *coords, int64_t N, int64_t L, float *out, int form, void *workspace,
+                          size_t workspace_bytes, void *stream);
 
 /* One-versus-reference: out[a] = cRMSD(model a, ref) for a in [0, N).
  * ref: float[L][3] device; out: float[N] device. Exact-integer covariance on
@@ -149,14 +167,15 @@ int clusco_crmsd_allpairs_backward(const float *coords, int64_t N, int64_t L, co
                                    void *workspace, size_t workspace_bytes, void *stream);
 
 /* Kernel timing for benchmarks (no counterpart in the paper). While enabled, every launch
- * of the all-pairs tensor-core kernel (CLUSCO_KERNEL_PAIRS) or of the adjoint kernel
- * (CLUSCO_KERNEL_ADJOINT) is bracketed by two CUDA events recorded on the launch's own
+ * of the all-pairs tensor-core kernel (CLUSCO_KERNEL_PAIRS), of the adjoint kernel
+ * (CLUSCO_KERNEL_ADJOINT) or of the dRMSD tensor-core kernel (CLUSCO_KERNEL_DRMSD) is bracketed by two CUDA events recorded on the launch's own
  * stream. clusco_profile_enable(1) starts a fresh window (unread brackets are dropped),
  * clusco_profile_enable(0) stops recording. clusco_profile_read waits for the kernel's
  * recorded brackets, returns their summed duration (ms) and count, and frees them.
  * Host-side state shared by all threads; EINVAL for an unknown kernel id or null output. */
 #define CLUSCO_KERNEL_PAIRS 0
 #define CLUSCO_KERNEL_ADJOINT 1
+#define CLUSCO_KERNEL_DRMSD 2
 int clusco_profile_enable(int on);
 int clusco_profile_read(int kernel, double *total_ms, long long *launches);
 

@@ -19,6 +19,7 @@
 #include "backward.cuh"
 #include "bwd_tc.cuh"
 #include "bwd_rot.cuh"
+#include "drmsd.cuh"
 
 using namespace clusco;
 
@@ -287,6 +288,29 @@ int allpairs_impl(const float *coords, int64_t N, int64_t L, int64_t row_begin, 
     return CLUSCO_OK;
 }
 
+// dRMSD workspace (see drmsd.cuh); also used (base == nullptr) to size it.
+DrWs carve_drmsd(void *base, int64_t N, int64_t L, int form)
+{
+    DrWs w;
+    Carver c(base);
+    const int64_t K = L * (L - 1) / 2;
+    w.Kp = round_up(K, 64);
+    w.Npad = round_up(N, DR_MA);
+    if (form == CLUSCO_FORM_BF16_EXACT2)
+        w.planes = c.take<char>((size_t)(2 * w.Npad * w.Kp) * 2);
+    else
+        w.planes = c.take<float>((size_t)(w.Npad * w.Kp));
+    w.S = c.take<long long>((size_t)w.Npad);
+    w.fin = c.take<int>((size_t)N);
+    w.dmax = c.take<unsigned>(1);
+    w.ntiles = dr_ntiles(w.Npad / DR_MA, w.Npad / DR_MB);
+    if (form == CLUSCO_FORM_BF16_EXACT2) w.tiles = c.take<int2>((size_t)w.ntiles);
+    w.bytes = c.off;
+    return w;
+}
+
+bool drmsd_form(int form) { return form == CLUSCO_FORM_FP32_SIMT || form == CLUSCO_FORM_BF16_EXACT2; }
+
 }  // namespace
 
 extern "C" {
@@ -319,6 +343,10 @@ size_t clusco_workspace_bytes(int op, int64_t N, int64_t L, int form)
     if (op == CLUSCO_OP_BACKWARD_ROT) {
         if (N < 2 || !bwr_supported(L)) return 0;
         return carve_bt(nullptr, N, L).bytes;
+    }
+    if (op == CLUSCO_OP_DRMSD) {
+        if (!drmsd_form(form) || N < 2 || L < 2 || L > DR_MAX_L) return 0;
+        return carve_drmsd(nullptr, N, L, form).bytes;
     }
     return 0;
 }
@@ -357,6 +385,31 @@ int clusco_crmsd_allpairs_below(const float *coords, int64_t N, int64_t L, float
                       tau};
     return allpairs_impl(coords, N, L, 0, N - 1, nullptr, form, workspace, workspace_bytes, (cudaStream_t)stream,
                          nullptr, &t);
+}
+
+int clusco_drmsd_allpairs(const float *coords, int64_t N, int64_t L, float *out, int form, void *workspace,
+                          size_t workspace_bytes, void *stream)
+{
+    g_last_error.clear();
+    int rc;
+    if ((rc = check_sizes(N, L, 2))) return rc;
+    if (L < 2) return fail(CLUSCO_EINVAL, "L=%lld: dRMSD needs at least one atom pair", (long long)L);
+    if (L > DR_MAX_L) return fail(CLUSCO_EINVAL, "dRMSD supports L <= %d", DR_MAX_L);
+    if (N > (int64_t)1 << 24) return fail(CLUSCO_EINVAL, "dRMSD supports N <= 2^24 models");
+    if ((rc = check_ptr(coords, "coords", 4))) return rc;
+    if ((rc = check_ptr(out, "out", 4))) return rc;
+    if (!drmsd_form(form)) return fail(CLUSCO_EUNSUPPORTED, "dRMSD forms: FP32_SIMT and BF16_EXACT2 (got %d)", form);
+    if (form == CLUSCO_FORM_BF16_EXACT2 && (rc = tc_supported(CLUSCO_FORM_BF16X3, L)))
+        return fail(rc, "the tensor-core dRMSD form needs an sm_103 device");
+    cudaStream_t st = (cudaStream_t)stream;
+    const DrWs sized = carve_drmsd(nullptr, N, L, form);
+    Scratch s;
+    if ((rc = get_scratch(s, workspace, workspace_bytes, sized.bytes, st))) return rc;
+    const DrWs w = carve_drmsd(s.ptr, N, L, form);
+    std::string err;
+    rc = drmsd_launch(coords, N, L, out, form == CLUSCO_FORM_BF16_EXACT2, w, st, err);
+    if (rc) return fail(rc, "%s", err.c_str());
+    return CLUSCO_OK;
 }
 
 int clusco_crmsd_vs_ref(const float *coords, int64_t N, int64_t L, const float *ref, float *out, void *workspace,

@@ -92,3 +92,20 @@ def test_condensed_pairs_inverts_the_condensed_index():
     P = N * (N - 1) // 2
     a, b = clusco.condensed_pairs(torch.tensor([0, 1, N - 2, N - 1, P - 2, P - 1]), N)
     assert a.tolist() == [0, 0, 0, 1, N - 3, N - 2] and b.tolist() == [1, 2, N - 1, 2, N - 1, N - 1]
+
+
+def test_drmsd_host_side_validation(lib):
+    fake = ctypes.c_void_p(0x1000)
+    call = lib.clusco_drmsd_allpairs
+    assert call(fake, 1, 10, fake, 0, None, 0, None) == 1        # N < 2
+    assert call(fake, 10, 1, fake, 0, None, 0, None) == 1        # L < 2: no atom pair
+    assert call(fake, 10, 5000, fake, 0, None, 0, None) == 1     # above the staged-coordinates limit
+    assert call(fake, 10, 10, None, 0, None, 0, None) == 1       # null out
+    assert call(fake, 10, 10, fake, clusco.FORM_TF32, None, 0, None) == 7  # form without a dRMSD kernel
+    assert call(fake, 10, 10, fake, 0, fake, 16, None) == 2      # workspace too small
+    for form in (clusco.FORM_FP32_SIMT, clusco.FORM_BF16_EXACT2):
+        nb = clusco.workspace_bytes(clusco.OP_DRMSD, 5000, 300, form)
+        # the distances of every model dominate: 4 bytes per model and atom pair, padded
+        assert 5000 * 44850 * 4 <= nb <= 5120 * 44864 * 4 + (1 << 20)
+    assert clusco.workspace_bytes(clusco.OP_DRMSD, 5000, 300, clusco.FORM_TF32) == 0
+    assert clusco.workspace_bytes(clusco.OP_DRMSD, 10, 1, 0) == 0
