@@ -1,9 +1,10 @@
-"""FP64 CPU oracle for all-versus-all cRMSD and dRMSD (TEST INFRASTRUCTURE).
+"""FP64 CPU oracle for all-versus-all cRMSD, dRMSD and CMO (TEST INFRASTRUCTURE).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline /
 reference leg may import this package. It shares no code with the CUDA path:
-the C sources ``crmsd_oracle.c`` and ``drmsd_oracle.c`` are compiled on their own
-with gcc (OpenMP for timing only) and loaded through ctypes.
+the C sources ``crmsd_oracle.c``, ``drmsd_oracle.c`` and ``cmo_oracle.c`` are compiled
+on their own with gcc (OpenMP for timing only, no floating-point contraction) and loaded
+through ctypes.
 
 The cRMSD functions follow ClusCo's definition (section "Algorithms",
 eq. 1: RMS deviation of matched atoms after the optimal superposition, with the
@@ -14,7 +15,9 @@ come from it.
 
 The dRMSD functions follow eq. 5 (the RMS difference of the two models'
 intra-model distance matrices over the L(L-1)/2 atom pairs), formed directly
-from the distances.
+from the distances. The CMO functions follow eq. 6 and eq. 7 (contact maps over the
+atom pairs i < j, the Sorensen index of two maps); the contact test is taken in FP32,
+the precision of the CUDA kernels, and the score in FP64.
 
 Parity pins: every function here is pinned by ``tests/test_oracle_pins.py``
 (closed forms, invariances, brute-force rotation search, eq. 2, finite
@@ -32,6 +35,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "crmsd_oracle.c")
 _DSRC = os.path.join(_HERE, "drmsd_oracle.c")
+_CSRC = os.path.join(_HERE, "cmo_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -41,11 +45,11 @@ _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
 
 
-def build(src=(_SRC, _DSRC), out: str = _LIB, extra_flags=()) -> str:
+def build(src=(_SRC, _DSRC, _CSRC), out: str = _LIB, extra_flags=()) -> str:
     """Compile the oracle source(s) with gcc (-O2, FP64, OpenMP). Returns the .so path."""
     srcs = [src] if isinstance(src, str) else list(src)
     cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-fopenmp",
-           "-fno-fast-math", *extra_flags, *srcs, "-o", out, "-lm"]
+           "-fno-fast-math", "-ffp-contract=off", *extra_flags, *srcs, "-o", out, "-lm"]
     subprocess.run(cmd, check=True)
     return out
 
@@ -57,8 +61,8 @@ def load(path: str | None = None):
         return _bind(ctypes.CDLL(path))
     with _lock:
         if _lib is None:
-            if (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC),
-                                                                          os.path.getmtime(_DSRC)):
+            if (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < max(
+                    os.path.getmtime(f) for f in (_SRC, _DSRC, _CSRC)):
                 build()
             _lib = _bind(ctypes.CDLL(_LIB))
     return _lib
@@ -73,6 +77,14 @@ def _bind(lib):
         lib.oracle_drmsd_allpairs.argtypes = [_f32p, i64, i64, _f64p, ctypes.c_int]
         lib.oracle_drmsd_pairs.argtypes = [_f32p, i64, i64, _i64p, _i64p, i64, _f64p, ctypes.c_int]
         for f in ("oracle_drmsd_pair", "oracle_drmsd_allpairs", "oracle_drmsd_pairs"):
+            getattr(lib, f).restype = ctypes.c_int
+    if hasattr(lib, "oracle_cmo_pair"):
+        f32 = ctypes.c_float
+        lib.oracle_cmo_counts.argtypes = [_f32p, _f32p, i64, f32] + [ctypes.POINTER(ctypes.c_int64)] * 3
+        lib.oracle_cmo_pair.argtypes = [_f32p, _f32p, i64, f32, ctypes.POINTER(ctypes.c_double)]
+        lib.oracle_cmo_allpairs.argtypes = [_f32p, i64, i64, f32, _f64p, ctypes.c_int]
+        lib.oracle_cmo_pairs.argtypes = [_f32p, i64, i64, f32, _i64p, _i64p, i64, _f64p, ctypes.c_int]
+        for f in ("oracle_cmo_counts", "oracle_cmo_pair", "oracle_cmo_allpairs", "oracle_cmo_pairs"):
             getattr(lib, f).restype = ctypes.c_int
     if not hasattr(lib, "oracle_crmsd_pair"):
         return lib
@@ -207,4 +219,45 @@ def drmsd_pairs(X, ia, ib, nthreads: int = 0, lib=None) -> np.ndarray:
     out = np.empty(ia.shape[0], dtype=np.float64)
     _check(lib.oracle_drmsd_pairs(X, X.shape[0], X.shape[1], ia, ib, ia.shape[0], out, nthreads),
            "drmsd_pairs")
+    return out
+
+
+def cmo_counts(A, B, cutoff: float, lib=None):
+    """(n(A), n(B), n(A and B)): contact counts over atom pairs i < j (eq. 6)."""
+    lib = lib or load()
+    A, B = _f32(A), _f32(B)
+    na, nb, nab = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.oracle_cmo_counts(A, B, A.shape[0], float(cutoff), ctypes.byref(na), ctypes.byref(nb),
+                                 ctypes.byref(nab)), "cmo_counts")
+    return na.value, nb.value, nab.value
+
+
+def cmo_pair(A, B, cutoff: float, lib=None) -> float:
+    """CMO score (eq. 7, in percent) of one pair of models."""
+    lib = lib or load()
+    A, B = _f32(A), _f32(B)
+    c = ctypes.c_double()
+    _check(lib.oracle_cmo_pair(A, B, A.shape[0], float(cutoff), ctypes.byref(c)), "cmo_pair")
+    return c.value
+
+
+def cmo_allpairs(X, cutoff: float, nthreads: int = 0, lib=None) -> np.ndarray:
+    """Condensed N(N-1)/2 FP64 CMO matrix, row-major upper triangle (a < b)."""
+    lib = lib or load()
+    X = _f32(X)
+    N, L = X.shape[0], X.shape[1]
+    out = np.empty(N * (N - 1) // 2, dtype=np.float64)
+    _check(lib.oracle_cmo_allpairs(X, N, L, float(cutoff), out, nthreads), "cmo_allpairs")
+    return out
+
+
+def cmo_pairs(X, ia, ib, cutoff: float, nthreads: int = 0, lib=None) -> np.ndarray:
+    """CMO for the listed pairs (ia[k], ib[k])."""
+    lib = lib or load()
+    X = _f32(X)
+    ia = np.ascontiguousarray(ia, dtype=np.int64)
+    ib = np.ascontiguousarray(ib, dtype=np.int64)
+    out = np.empty(ia.shape[0], dtype=np.float64)
+    _check(lib.oracle_cmo_pairs(X, X.shape[0], X.shape[1], float(cutoff), ia, ib, ia.shape[0], out, nthreads),
+           "cmo_pairs")
     return out
