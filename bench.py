@@ -49,7 +49,8 @@ def parse():
     p.add_argument("--L", type=int, default=300)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--no-drmsd", action="store_true", help="skip the all-versus-all dRMSD measurement")
+    p.add_argument("--no-drmsd", action="store_true",
+                   help="skip the all-versus-all dRMSD and contact map overlap measurements")
     p.add_argument("--cpu-models", type=int, default=5000, help="models in the oracle's timed sample")
     p.add_argument("--ref-models", type=int, default=800, help="models per step of the reference arm")
     return p.parse_args()
@@ -480,6 +481,56 @@ def run_ours(args):
                               "traffic": traffic_for("drmsd_tc")}}
         del ws_d, out_d, ws_dp, out_dp
 
+    # All-versus-all contact map overlap (eq. 6, eq. 7) at an 8 A cutoff: the tensor-core form
+    # (E4M3 0/1 maps, kind::f8f6f4) against the plain bit-count form. The contraction is 2 K flop
+    # per pair (n(A and B) over K atom pairs); its peak is the FP8 rate, twice the measured BF16.
+    cmo = None
+    if not args.no_drmsd and form == clusco.FORM_BF16_EXACT2 and 2 <= L <= 4096:
+        K = L * (L - 1) // 2
+        ws_c = torch.empty(clusco.workspace_bytes(clusco.OP_CMO, N, L, clusco.FORM_FP8_EXACT), dtype=torch.uint8,
+                           device=dev)
+        out_c = torch.empty(P, dtype=torch.float32, device=dev)
+
+        def cfwd():
+            clusco.cmo_allpairs(X, 8.0, clusco.FORM_FP8_EXACT, out=out_c, workspace=ws_c)
+        c_ms = statistics.mean(timed(cfwd, max(3, args.steps // 10), max(2, args.warmup), prof=True)[0])
+        tot_ms, n = clusco.profile_read(clusco.KERNEL_CMO)
+        ck_ms = tot_ms / n if n else None
+        ws_cp = torch.empty(clusco.workspace_bytes(clusco.OP_CMO, N, L, clusco.FORM_FP32_SIMT), dtype=torch.uint8,
+                            device=dev)
+        out_cp = torch.empty_like(out_c)
+
+        def cplain():
+            clusco.cmo_allpairs(X, 8.0, clusco.FORM_FP32_SIMT, out=out_cp, workspace=ws_cp)
+        cp_ms = statistics.mean(timed(cplain, 3, 1)[0])
+        if clusco.sync_status() != 0:
+            raise RuntimeError("device status set during the contact-map calls: " + lib.clusco_last_error().decode())
+        if ws_ > 1:
+            t = torch.tensor([c_ms, cp_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            c_ms, cp_ms = float(t[0]), float(t[1])
+        c_err = None
+        if rank == 0:
+            import oracle
+            rng = np.random.default_rng(6)
+            ia = rng.integers(0, N, 4000)
+            ib = rng.integers(0, N, 4000)
+            keep = ia != ib
+            ia, ib = np.minimum(ia[keep], ib[keep]), np.maximum(ia[keep], ib[keep])
+            idx = ia * N - ia * (ia + 1) // 2 + (ib - ia - 1)
+            c_err = float(np.abs(out_c.cpu().numpy()[idx].astype(np.float64)
+                                 - oracle.cmo_pairs(e.coords, ia, ib, 8.0)).max())
+        kms = ck_ms if ck_ms else c_ms
+        ach = 2.0 * K * P / (kms * 1e-3) / 1e12
+        cmo = {"value": ws_ * P / (c_ms * 1e-3), "unit": UNIT, "ms": c_ms, "form": "fp8_exact", "cutoff_A": 8.0,
+               "vs_plain_popcount": cp_ms / c_ms, "plain_popcount_ms": cp_ms, "max_err_sampled_pct": c_err,
+               "roofline": {"kernel": "cmo_tc_kernel (Gram of the 0/1 contact maps, 2 K flop/pair)",
+                            "launch_ms": kms, "timing": "kernel launch events" if ck_ms else "API call bracket",
+                            "bound": "tensor", "achieved": ach, "peak": 2.0 * bf16, "unit": "TFLOP/s",
+                            "frac": ach / (2.0 * bf16), "peak_kind": f"{pk_kind} bf16 burst x 2 (FP8 nominal ratio)",
+                            "traffic": traffic_for("cmo_tc")}}
+        del ws_c, out_c, ws_cp, out_cp
+
     # Rooflines of the two tensor-core kernels. Algorithmic flop per pair: the forward
     # contraction is 18 L (the 3x3 covariance over L atoms); the adjoint is 54 L (that
     # covariance once, plus R x_b and R^T x_a over L atoms for the two gradients). One launch
@@ -536,6 +587,8 @@ def run_ours(args):
         line["e2e"] = e2e
     if drmsd:
         line["drmsd"] = drmsd
+    if cmo:
+        line["cmo"] = cmo
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(e, w, native, args.cpu_models)
     if rank == 0:

@@ -61,12 +61,15 @@ typedef enum {
  *  BF16_EXACT2 -- tcgen05 bf16 on 16-bit fixed point coordinates split in two
  *                 8-bit digits; all four digit products kept in separate FP32
  *                 accumulators, exact for L <= 1024; FP32 epilogue with FP64
- *                 refinement of the pairs whose FP32 error bound is too large. */
+ *                 refinement of the pairs whose FP32 error bound is too large.
+ *  FP8_EXACT   -- tcgen05 kind::f8f6f4 on 0/1 operands (exact integer counts);
+ *                 the tensor-core form of the contact map overlap only. */
 typedef enum {
     CLUSCO_FORM_FP32_SIMT = 0,
     CLUSCO_FORM_TF32 = 1,
     CLUSCO_FORM_BF16X3 = 2,
-    CLUSCO_FORM_BF16_EXACT2 = 3
+    CLUSCO_FORM_BF16_EXACT2 = 3,
+    CLUSCO_FORM_FP8_EXACT = 4
 } clusco_form;
 
 typedef enum {
@@ -75,7 +78,8 @@ typedef enum {
     CLUSCO_OP_BACKWARD = 2,
     CLUSCO_OP_BACKWARD_ROT = 3,
     CLUSCO_OP_ALLPAIRS_ROT = 4,
-    CLUSCO_OP_DRMSD = 5
+    CLUSCO_OP_DRMSD = 5,
+    CLUSCO_OP_CMO = 6
 } clusco_op;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -129,6 +133,21 @@ int clusco_crmsd_allpairs_below(const float *coords, int64_t N, int64_t L, float
 int clusco_drmsd_allpairs(const float *coords, int64_t N, int64_t L, float *out, int form, void *workspace,
                           size_t workspace_bytes, void *stream);
 
+/* All-versus-all contact map overlap (section "Algorithms", eq. 6 and eq. 7): out[idx(a,b)] for
+ * a < b, condensed as above, S = 100 * 2 n(A and B) / (n(A) + n(B)) in percent, with contact maps
+ * C_ij = [ |x_i - x_j| < cutoff ] over the atom pairs i < j (the test taken in FP32 as
+ * fma(dx, dx, fma(dy, dy, dz * dz)) < cutoff^2) and n(.) their contact counts; S = 0 where
+ * neither model has a contact, NaN for a model with a non-finite coordinate (which also sets
+ * CLUSCO_ENONFINITE in the device status). The counts are exact integers in both forms, so
+ * the score is the FP32 rounding of the exact ratio:
+ *  CLUSCO_FORM_FP8_EXACT -- maps as E4M3 0/1 bytes, n(A and B) by tcgen05 kind::f8f6f4 (needs sm_103);
+ *  CLUSCO_FORM_FP32_SIMT -- the plain CUDA-core form: maps packed to bits, AND + population count.
+ * Other forms return CLUSCO_EUNSUPPORTED. cutoff > 0 and finite (A; 8 A is the customary C-alpha
+ * value, the paper gives none). 2 <= N <= 2^24, 2 <= L <= 4096.
+ * Workspace: clusco_workspace_bytes(CLUSCO_OP_CMO, N, L, form), about N L^2 / 2 bytes. */
+int clusco_cmo_allpairs(const float *coords, int64_t N, int64_t L, float cutoff, float *out, int form,
+                        void *workspace, size_t workspace_bytes, void *stream);
+
 /* One-versus-reference: out[a] = cRMSD(model a, ref) for a in [0, N).
  * ref: float[L][3] device; out: float[N] device. Exact-integer covariance on
  * 24-bit fixed point coordinates, FP64 epilogue. N >= 1, L >= 1. */
@@ -168,7 +187,8 @@ int clusco_crmsd_allpairs_backward(const float *coords, int64_t N, int64_t L, co
 
 /* Kernel timing for benchmarks (no counterpart in the paper). While enabled, every launch
  * of the all-pairs tensor-core kernel (CLUSCO_KERNEL_PAIRS), of the adjoint kernel
- * (CLUSCO_KERNEL_ADJOINT) or of the dRMSD tensor-core kernel (CLUSCO_KERNEL_DRMSD) is bracketed by two CUDA events recorded on the launch's own
+ * (CLUSCO_KERNEL_ADJOINT), of the dRMSD tensor-core kernel (CLUSCO_KERNEL_DRMSD) or of the
+ * contact-map tensor-core kernel (CLUSCO_KERNEL_CMO) is bracketed by two CUDA events recorded on the launch's own
  * stream. clusco_profile_enable(1) starts a fresh window (unread brackets are dropped),
  * clusco_profile_enable(0) stops recording. clusco_profile_read waits for the kernel's
  * recorded brackets, returns their summed duration (ms) and count, and frees them.
@@ -176,6 +196,7 @@ int clusco_crmsd_allpairs_backward(const float *coords, int64_t N, int64_t L, co
 #define CLUSCO_KERNEL_PAIRS 0
 #define CLUSCO_KERNEL_ADJOINT 1
 #define CLUSCO_KERNEL_DRMSD 2
+#define CLUSCO_KERNEL_CMO 3
 int clusco_profile_enable(int on);
 int clusco_profile_read(int kernel, double *total_ms, long long *launches);
 

@@ -7,8 +7,9 @@ non-OK status. All arithmetic runs in the library's CUDA kernels; there is no
 CPU fallback: if ``libclusco.so`` is missing or no CUDA device is present, the
 calls raise.
 
-The operations are ClusCo's cRMSD (section "Algorithms", eq. 1 / eq. 2) and dRMSD
-(eq. 5) over the N(N-1)/2 pairs of an ensemble (section "Background").
+The operations are ClusCo's cRMSD (section "Algorithms", eq. 1 / eq. 2), dRMSD (eq. 5)
+and contact map overlap (eq. 6 / eq. 7) over the N(N-1)/2 pairs of an ensemble (section
+"Background").
 """
 from __future__ import annotations
 
@@ -25,6 +26,7 @@ FORM_FP32_SIMT = 0
 FORM_TF32 = 1
 FORM_BF16X3 = 2
 FORM_BF16_EXACT2 = 3
+FORM_FP8_EXACT = 4  # the contact map overlap's tensor-core form
 FORMS = {"fp32_simt": FORM_FP32_SIMT, "tf32": FORM_TF32, "bf16x3": FORM_BF16X3, "bf16_exact2": FORM_BF16_EXACT2}
 
 OP_ALLPAIRS = 0
@@ -33,6 +35,7 @@ OP_BACKWARD = 2
 OP_BACKWARD_ROT = 3
 OP_ALLPAIRS_ROT = 4
 OP_DRMSD = 5
+OP_CMO = 6
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EOVERFLOW",
           6: "ENONFINITE", 7: "EUNSUPPORTED"}
@@ -41,10 +44,12 @@ EXPORTS = ("clusco_version", "clusco_workspace_bytes", "clusco_crmsd_allpairs", 
            "clusco_crmsd_allpairs_below",
            "clusco_crmsd_vs_ref", "clusco_crmsd_vs_ref_noalloc", "clusco_crmsd_allpairs_backward",
            "clusco_sync_status", "clusco_last_error", "clusco_profile_enable", "clusco_profile_read",
-           "clusco_crmsd_allpairs_rot", "clusco_crmsd_allpairs_backward_rot", "clusco_drmsd_allpairs")
+           "clusco_crmsd_allpairs_rot", "clusco_crmsd_allpairs_backward_rot", "clusco_drmsd_allpairs",
+           "clusco_cmo_allpairs")
 KERNEL_PAIRS = 0
 KERNEL_ADJOINT = 1
 KERNEL_DRMSD = 2
+KERNEL_CMO = 3
 NOALLOC_MAX_L = 16384
 
 _lib = None
@@ -83,13 +88,15 @@ def load(path: str = LIB_PATH):
             lib.clusco_crmsd_allpairs_backward_rot.argtypes = [vp, i64, i64, vp, vp, vp, vp, ctypes.c_float, vp, sz,
                                                                vp]
             lib.clusco_drmsd_allpairs.argtypes = [vp, i64, i64, vp, ctypes.c_int, vp, sz, vp]
+            lib.clusco_cmo_allpairs.argtypes = [vp, i64, i64, ctypes.c_float, vp, ctypes.c_int, vp, sz, vp]
             lib.clusco_profile_enable.argtypes = [ctypes.c_int]
             lib.clusco_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(ctypes.c_longlong)]
             for f in ("clusco_crmsd_allpairs", "clusco_crmsd_allpairs_panel", "clusco_crmsd_vs_ref",
                       "clusco_crmsd_vs_ref_noalloc", "clusco_crmsd_allpairs_backward", "clusco_sync_status",
                       "clusco_profile_enable", "clusco_profile_read", "clusco_crmsd_allpairs_rot",
-                      "clusco_crmsd_allpairs_backward_rot", "clusco_crmsd_allpairs_below", "clusco_drmsd_allpairs"):
+                      "clusco_crmsd_allpairs_backward_rot", "clusco_crmsd_allpairs_below", "clusco_drmsd_allpairs",
+                      "clusco_cmo_allpairs"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -170,6 +177,23 @@ def drmsd_allpairs(coords: torch.Tensor, form: int = FORM_BF16_EXACT2, out: torc
     ws, nb = _ws(workspace, OP_DRMSD, N, L, form, coords.device)
     _check(load().clusco_drmsd_allpairs(coords.data_ptr(), N, L, out.data_ptr(), form, ws.data_ptr(), nb,
                                         _stream(stream)))
+    return out
+
+
+def cmo_allpairs(coords: torch.Tensor, cutoff: float = 8.0, form: int = FORM_FP8_EXACT,
+                 out: torch.Tensor | None = None, workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Condensed all-versus-all contact map overlap (eq. 7, percent; float32, length N(N-1)/2) with
+    contacts |x_i - x_j| < cutoff (A) over atom pairs i < j. Forms: FORM_FP8_EXACT (tensor cores)
+    and FORM_FP32_SIMT (plain: bit-packed maps, population count); both count exactly."""
+    coords = _coords(coords)
+    N, L = coords.shape[0], coords.shape[1]
+    P = N * (N - 1) // 2
+    if out is None:
+        out = torch.empty(P, dtype=torch.float32, device=coords.device)
+    assert out.is_cuda and out.dtype == torch.float32 and out.numel() >= P and out.is_contiguous()
+    ws, nb = _ws(workspace, OP_CMO, N, L, form, coords.device)
+    _check(load().clusco_cmo_allpairs(coords.data_ptr(), N, L, float(cutoff), out.data_ptr(), form, ws.data_ptr(),
+                                      nb, _stream(stream)))
     return out
 
 

@@ -20,6 +20,7 @@
 #include "bwd_tc.cuh"
 #include "bwd_rot.cuh"
 #include "drmsd.cuh"
+#include "cmo.cuh"
 
 using namespace clusco;
 
@@ -311,6 +312,29 @@ DrWs carve_drmsd(void *base, int64_t N, int64_t L, int form)
 
 bool drmsd_form(int form) { return form == CLUSCO_FORM_FP32_SIMT || form == CLUSCO_FORM_BF16_EXACT2; }
 
+// Contact-map workspace (see cmo.cuh); also used (base == nullptr) to size it. K is padded to
+// 1024 so that the bit-packed rows hold whole 32-word slabs.
+CmWs carve_cmo(void *base, int64_t N, int64_t L, int form)
+{
+    CmWs w;
+    Carver c(base);
+    const int64_t K = L * (L - 1) / 2;
+    w.Kp = round_up(K, 1024);
+    w.Npad = round_up(N, CM_MB);
+    w.map = c.take<uint8_t>((size_t)(w.Npad * w.Kp));
+    w.cnt = c.take<int>((size_t)w.Npad);
+    if (form == CLUSCO_FORM_FP8_EXACT) {
+        w.ntiles = cm_ntiles(w.Npad / CM_MA, w.Npad / CM_MB);
+        w.tiles = c.take<int2>((size_t)w.ntiles);
+    } else {
+        w.bits = c.take<uint32_t>((size_t)(w.Npad * (w.Kp / 32)));
+    }
+    w.bytes = c.off;
+    return w;
+}
+
+bool cmo_form(int form) { return form == CLUSCO_FORM_FP32_SIMT || form == CLUSCO_FORM_FP8_EXACT; }
+
 }  // namespace
 
 extern "C" {
@@ -347,6 +371,10 @@ size_t clusco_workspace_bytes(int op, int64_t N, int64_t L, int form)
     if (op == CLUSCO_OP_DRMSD) {
         if (!drmsd_form(form) || N < 2 || L < 2 || L > DR_MAX_L) return 0;
         return carve_drmsd(nullptr, N, L, form).bytes;
+    }
+    if (op == CLUSCO_OP_CMO) {
+        if (!cmo_form(form) || N < 2 || L < 2 || L > DR_MAX_L) return 0;
+        return carve_cmo(nullptr, N, L, form).bytes;
     }
     return 0;
 }
@@ -408,6 +436,33 @@ int clusco_drmsd_allpairs(const float *coords, int64_t N, int64_t L, float *out,
     const DrWs w = carve_drmsd(s.ptr, N, L, form);
     std::string err;
     rc = drmsd_launch(coords, N, L, out, form == CLUSCO_FORM_BF16_EXACT2, w, st, err);
+    if (rc) return fail(rc, "%s", err.c_str());
+    return CLUSCO_OK;
+}
+
+int clusco_cmo_allpairs(const float *coords, int64_t N, int64_t L, float cutoff, float *out, int form,
+                        void *workspace, size_t workspace_bytes, void *stream)
+{
+    g_last_error.clear();
+    int rc;
+    if ((rc = check_sizes(N, L, 2))) return rc;
+    if (L < 2) return fail(CLUSCO_EINVAL, "L=%lld: a contact map needs at least one atom pair", (long long)L);
+    if (L > DR_MAX_L) return fail(CLUSCO_EINVAL, "the contact map overlap supports L <= %d", DR_MAX_L);
+    if (N > (int64_t)1 << 24) return fail(CLUSCO_EINVAL, "the contact map overlap supports N <= 2^24 models");
+    if (!(cutoff > 0.f) || !std::isfinite(cutoff)) return fail(CLUSCO_EINVAL, "cutoff must be positive and finite");
+    if ((rc = check_ptr(coords, "coords", 4))) return rc;
+    if ((rc = check_ptr(out, "out", 4))) return rc;
+    if (!cmo_form(form))
+        return fail(CLUSCO_EUNSUPPORTED, "contact map overlap forms: FP32_SIMT and FP8_EXACT (got %d)", form);
+    if (form == CLUSCO_FORM_FP8_EXACT && (rc = tc_supported(CLUSCO_FORM_BF16X3, L)))
+        return fail(rc, "the tensor-core contact map form needs an sm_103 device");
+    cudaStream_t st = (cudaStream_t)stream;
+    const CmWs sized = carve_cmo(nullptr, N, L, form);
+    Scratch s;
+    if ((rc = get_scratch(s, workspace, workspace_bytes, sized.bytes, st))) return rc;
+    const CmWs w = carve_cmo(s.ptr, N, L, form);
+    std::string err;
+    rc = cmo_launch(coords, N, L, cutoff, out, form == CLUSCO_FORM_FP8_EXACT, w, st, err);
     if (rc) return fail(rc, "%s", err.c_str());
     return CLUSCO_OK;
 }

@@ -8,7 +8,7 @@
 // every distance is rounded to 16-bit fixed point with ONE scale q and ONE offset c0 for the
 // whole ensemble, d ~ c0 + q n with |n| <= 32639, so that the differences of the rounded
 // distances are q (n_a,k - n_b,k) exactly and only the integers n enter the contraction:
-// n = 256 h + l with digits |h| <= 127, -128 <= l <= 127 (exact in BF16), four digit-product
+// n = 256 h + l with digits |h| <= 127, |l| <= 128 (exact in BF16), four digit-product
 // classes hh, hl, lh, ll accumulated by tcgen05 in FP32. A class sum is exact while it has at
 // most 1024 terms (1024 x 128^2 = 2^24), so the accumulator is drained every 1024 terms of K
 // into an int64 sum per pair while the MMAs of the next 1024 terms run in the other half of
@@ -18,7 +18,7 @@
 //
 // Kernels: drmsd_range_kernel (largest distance of every model, hence q and c0),
 // drmsd_quant_kernel (distances again, rounded, as two BF16 digit planes; or FP32 distances
-// for the plain form), drmsd_tiles_kernel (grouped tile order), drmsd_tc_kernel (the
+// for the plain form), grouped_tiles_kernel (grouped tile order), drmsd_tc_kernel (the
 // persistent tcgen05 contraction with the int64 drains and the eq. 5 epilogue) and
 // drmsd_simt_kernel (the plain FP32 form: the squared differences summed directly on CUDA
 // cores, compensated across K slabs).
@@ -44,30 +44,39 @@ constexpr int DR_EWARPS = 16;        // epilogue warps: 4 per TMEM lane quadrant
 constexpr int DR_THREADS = 64 + 32 * DR_EWARPS;  // warp 0 TMA, warp 1 MMA, warps 2-17 epilogue
 constexpr int DR_GROUP = 8;           // tile rows per group of the schedule
 constexpr int DR_NMAX = 32639;        // |n| <= 127 * 256 + 127
-constexpr int DR_MAX_L = 4096;        // coordinates staged in shared memory (48 KB)
+constexpr int DR_MAX_L = 4096;        // coordinates staged in shared memory (64 KB as float4)
 constexpr size_t DR_SMEM = 1024 + (size_t)DR_STAGES * STAGE_BYTES_BF16;
 static_assert(DR_SMEM <= 227 * 1024, "shared memory per CTA");
 
 // ---- distance index: k = i (2L - i - 1) / 2 + (j - i - 1) for i < j ---------------------
 __host__ __device__ __forceinline__ int64_t dr_row_start(int i, int L) { return (int64_t)i * (2 * L - i - 1) / 2; }
 
-// Stage model a's coordinates in shared memory; true if all are finite (block-uniform).
-__device__ __forceinline__ bool dr_stage(const float *__restrict__ coords, int64_t a, int L, float *xs)
+// Stage model a's coordinates in shared memory as float4 (x, y, z, 0), one 16-byte load per
+// atom in the distance loops; true if all are finite (block-uniform).
+__device__ __forceinline__ bool dr_stage(const float *__restrict__ coords, int64_t a, int L, float4 *xs)
 {
     const float *x = coords + a * (int64_t)L * 3;
     bool ok = true;
-    for (int t = threadIdx.x; t < 3 * L; t += blockDim.x) {
-        const float v = __ldg(x + t);
+    for (int t = threadIdx.x; t < L; t += blockDim.x) {
+        const float4 v = make_float4(__ldg(x + 3 * t), __ldg(x + 3 * t + 1), __ldg(x + 3 * t + 2), 0.f);
         xs[t] = v;
-        ok = ok && isfinite(v);
+        ok = ok && isfinite(v.x) && isfinite(v.y) && isfinite(v.z);
     }
     return __syncthreads_and(ok) != 0;
 }
 
-// Distances are enumerated row by row: warp w of a block takes the rows i = w, w + 8, ... and
-// its lanes the columns j = i + 1 + lane, + 32, ...: no index decoding, coalesced stores along
-// a row, and the warps' shares balanced to within one row.
+__device__ __forceinline__ float dr_dist2(const float4 &p, const float4 &q)
+{
+    const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
+// Distances are enumerated by groups of DR_ROWS consecutive rows: warp w of a block takes the
+// groups g = w, w + 8, ... and its lanes the columns j = DR_ROWS g + 1 + lane, + 32, ...; each
+// staged atom j serves the group's DR_ROWS rows (one shared-memory load per DR_ROWS distances),
+// stores are coalesced along each row, and no index is decoded.
 constexpr int DR_PRE_THREADS = 256;
+constexpr int DR_ROWS = 4;
 
 // One block per model: the largest intra-model distance (the square root of the largest squared
 // distance, which is the largest rounded distance because sqrtf is monotone), folded into the
@@ -77,7 +86,7 @@ __global__ void __launch_bounds__(DR_PRE_THREADS) drmsd_range_kernel(const float
                                                                      unsigned *__restrict__ dmax_bits,
                                                                      int *__restrict__ fin)
 {
-    extern __shared__ float xs[];
+    extern __shared__ float4 xs[];
     __shared__ float red[DR_PRE_THREADS / 32];
     const int64_t a = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -90,11 +99,15 @@ __global__ void __launch_bounds__(DR_PRE_THREADS) drmsd_range_kernel(const float
         return;
     }
     float m2 = 0.f;
-    for (int i = warp; i < L - 1; i += NW) {
-        const float xi = xs[3 * i], yi = xs[3 * i + 1], zi = xs[3 * i + 2];
-        for (int j = i + 1 + lane; j < L; j += 32) {
-            const float dx = xi - xs[3 * j], dy = yi - xs[3 * j + 1], dz = zi - xs[3 * j + 2];
-            m2 = fmaxf(m2, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    for (int i0 = DR_ROWS * warp; i0 < L - 1; i0 += DR_ROWS * NW) {
+        float4 pr[DR_ROWS];
+#pragma unroll
+        for (int r = 0; r < DR_ROWS; ++r) pr[r] = xs[min(i0 + r, L - 1)];
+        for (int j = i0 + 1 + lane; j < L; j += 32) {
+            const float4 pj = xs[j];
+#pragma unroll
+            for (int r = 0; r < DR_ROWS; ++r)
+                if (j > i0 + r) m2 = fmaxf(m2, dr_dist2(pr[r], pj));
         }
     }
     m2 = warp_max_f(m2);
@@ -123,11 +136,6 @@ __device__ __forceinline__ DrScale dr_scale(unsigned dmax_bits)
     return s;
 }
 
-__device__ __forceinline__ int dr_round(float d, const DrScale &s)
-{
-    const float v = rintf((d - s.c0) * s.iq);
-    return (int)fminf(fmaxf(v, -(float)DR_NMAX), (float)DR_NMAX);
-}
 
 // One block per padded model row. EXACT: digit planes (bf16, row a of the h plane and row
 // Npad + a of the l plane, Kp wide, zero past K and for padding / non-finite models) and
@@ -140,7 +148,7 @@ __global__ void __launch_bounds__(DR_PRE_THREADS) drmsd_quant_kernel(const float
                                                                      const int *__restrict__ fin,
                                                                      void *__restrict__ out, long long *__restrict__ S)
 {
-    extern __shared__ float xs[];
+    extern __shared__ float4 xs[];
     constexpr int NW = DR_PRE_THREADS / 32;
     __shared__ long long red[NW];
     const int64_t a = blockIdx.x;
@@ -172,20 +180,42 @@ __global__ void __launch_bounds__(DR_PRE_THREADS) drmsd_quant_kernel(const float
     dr_stage(coords, a, L, xs);
     const DrScale sc = dr_scale(EXACT ? *dmax_bits : 0u);
     long long s = 0;
-    for (int i = warp; i < L - 1; i += NW) {
-        const float xi = xs[3 * i], yi = xs[3 * i + 1], zi = xs[3 * i + 2];
-        const int64_t base = dr_row_start(i, L) - i - 1;  // k = base + j
-        for (int j = i + 1 + lane; j < L; j += 32) {
-            const float dx = xi - xs[3 * j], dy = yi - xs[3 * j + 1], dz = zi - xs[3 * j + 2];
-            const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-            if (EXACT) {
-                const int n = dr_round(d, sc);
-                const int l = ((n + 128) & 255) - 128, h = (n - l) >> 8;
-                hrow[base + j] = __float2bfloat16_rn((float)h);
-                lrow[base + j] = __float2bfloat16_rn((float)l);
-                s += (long long)n * n;
-            } else {
-                frow[base + j] = d;
+    const float ofs = -sc.c0 * sc.iq;
+    for (int i0 = DR_ROWS * warp; i0 < L - 1; i0 += DR_ROWS * NW) {
+        float4 pr[DR_ROWS];
+        int64_t base[DR_ROWS];  // k = base + j in row i0 + r
+#pragma unroll
+        for (int r = 0; r < DR_ROWS; ++r) {
+            pr[r] = xs[min(i0 + r, L - 1)];
+            base[r] = dr_row_start(i0 + r, L) - (i0 + r) - 1;
+        }
+        for (int j = i0 + 1 + lane; j < L; j += 32) {
+            const float4 pj = xs[j];
+#pragma unroll
+            for (int r = 0; r < DR_ROWS; ++r) {
+                if (j <= i0 + r) continue;
+                const float d2 = dr_dist2(pr[r], pj);
+                if (EXACT) {
+                    // Conversions and the special-function unit run at a quarter of the FP32 rate,
+                    // so this path uses one sqrt.approx (within 2 ulp; the rounding below absorbs
+                    // it) and does every rounding with the 1.5 * 2^23 shift on the FP32 pipe:
+                    // n = rint(clamp((d - c0) / q)), h = rint(n / 256) (|h| <= 127),
+                    // l = n - 256 h (|l| <= 128); h and l are small integers, so their BF16
+                    // encodings are the upper halves of their FP32 encodings
+                    float d;
+                    asm("sqrt.approx.f32 %0, %1;" : "=f"(d) : "f"(d2));
+                    const float x = fminf(fmaxf(fmaf(d, sc.iq, ofs), -(float)DR_NMAX), (float)DR_NMAX);
+                    const float t = x + 12582912.f;
+                    const float v = t - 12582912.f;
+                    const float h = (v * (1.f / 256.f) + 12582912.f) - 12582912.f;
+                    const float l = fmaf(-256.f, h, v);
+                    reinterpret_cast<unsigned short *>(hrow)[base[r] + j] = (unsigned short)(__float_as_uint(h) >> 16);
+                    reinterpret_cast<unsigned short *>(lrow)[base[r] + j] = (unsigned short)(__float_as_uint(l) >> 16);
+                    const int n = __float_as_int(t) - 0x4B400000;
+                    s += (long long)(n * n);  // n^2 <= 32639^2 < 2^31
+                } else {
+                    frow[base[r] + j] = sqrtf(d2);
+                }
             }
         }
     }
@@ -209,19 +239,22 @@ __global__ void __launch_bounds__(DR_PRE_THREADS) drmsd_quant_kernel(const float
     }
 }
 
-// Tile order of the tensor-core kernel: tiles (I, J), J >= 2 I, of DR_MA x DR_MB models, in
-// groups of DR_GROUP tile rows; within a group J ascending, then I. A persistent grid's
-// concurrent tiles then share a few A row panels and a few B panels, which stay in L2 while
-// the CTAs stream K. One thread per group writes its tiles (prefix over earlier groups).
-__global__ void drmsd_tiles_kernel(int64_t TA, int64_t TB, int2 *__restrict__ tiles)
+// Tile order of the persistent tensor-core kernels: tiles (I, J) of MA x MB models with pairs
+// a < b, i.e. J >= jmin(I) = I MA / MB (MA and MB powers of two), in groups of `group` tile
+// rows; within a group J ascending, then I. The grid's concurrent tiles then share a few A
+// row panels and a few B panels, which stay in L2 while the CTAs stream K. One thread per
+// group writes its tiles after those of the earlier groups.
+__global__ void grouped_tiles_kernel(int64_t TA, int64_t TB, int MA, int MB, int group, int2 *__restrict__ tiles)
 {
-    const int64_t ng = (TA + DR_GROUP - 1) / DR_GROUP;
+    // jmin(I) = I MA / MB with MA / MB or MB / MA a power of two: shifts, no 64-bit division
+    const int up = MA >= MB ? __ffs(MA / MB) - 1 : 0, dn = MB > MA ? __ffs(MB / MA) - 1 : 0;
+    const int64_t ng = (TA + group - 1) / group;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
-        int64_t t = 0;  // tiles of the rows before this group: sum over I < g G of (TB - 2 I)
-        const int64_t I0 = g * DR_GROUP, I1 = min(TA, I0 + DR_GROUP);
-        t = I0 * TB - I0 * (I0 - 1);
-        for (int64_t J = 2 * I0; J < TB; ++J)
-            for (int64_t I = I0; I < I1 && 2 * I <= J; ++I) tiles[t++] = make_int2((int)I, (int)J);
+        const int64_t I0 = g * group, I1 = min(TA, I0 + group);
+        int64_t t = 0;
+        for (int64_t I = 0; I < I0; ++I) t += TB - ((I << up) >> dn);
+        for (int64_t J = (I0 << up) >> dn; J < TB; ++J)
+            for (int64_t I = I0; I < I1 && ((I << up) >> dn) <= J; ++I) tiles[t++] = make_int2((int)I, (int)J);
     }
 }
 
@@ -491,7 +524,18 @@ inline int drmsd_launch(const float *coords, int64_t N, int64_t L, float *out, b
                         cudaStream_t st, std::string &err)
 {
     cudaError_t e = cudaSuccess;
-    const size_t xsm = (size_t)L * 3 * sizeof(float);
+    const size_t xsm = (size_t)L * sizeof(float4);
+    if (xsm > 48 * 1024) {
+        e = cudaFuncSetAttribute(drmsd_range_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(drmsd_quant_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(drmsd_quant_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm);
+        if (e != cudaSuccess) {
+            err = std::string("dRMSD pre-pass shared memory: ") + cudaGetErrorString(e);
+            return CLUSCO_ECUDA;
+        }
+    }
     e = cudaMemsetAsync(w.dmax, 0, sizeof(unsigned), st);
     if (e == cudaSuccess) {
         drmsd_range_kernel<<<(unsigned)N, DR_PRE_THREADS, xsm, st>>>(coords, (int)L, w.dmax, w.fin);
@@ -526,7 +570,7 @@ inline int drmsd_launch(const float *coords, int64_t N, int64_t L, float *out, b
     if ((rc = make_map(&mA, w.planes, false, w.Kp, 2 * w.Npad, DR_MA, err))) return rc;
     if ((rc = make_map(&mB, w.planes, false, w.Kp, 2 * w.Npad, DR_MB, err))) return rc;
     const int64_t TA = w.Npad / DR_MA, TB = w.Npad / DR_MB;
-    drmsd_tiles_kernel<<<1, 128, 0, st>>>(TA, TB, w.tiles);
+    grouped_tiles_kernel<<<1, 128, 0, st>>>(TA, TB, DR_MA, DR_MB, DR_GROUP, w.tiles);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaFuncSetAttribute(drmsd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)DR_SMEM);

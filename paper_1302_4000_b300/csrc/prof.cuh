@@ -1,7 +1,7 @@
 // prof.cuh -- optional timing of the tensor-core kernels with CUDA events.
 //
 // When enabled (clusco_profile_enable), every launch of the all-pairs kernel, of the
-// adjoint kernel or of the dRMSD kernel is bracketed by two CUDA events recorded on the launch's own stream;
+// adjoint kernel, of the dRMSD kernel or of the contact-map kernel is bracketed by two CUDA events recorded on the launch's own stream;
 // clusco_profile_read sums the bracketed durations. Off by default; the only cost when off
 // is one atomic load per launch.
 #pragma once
@@ -13,7 +13,7 @@
 
 namespace clusco {
 
-enum ProfKind { PROF_PAIRS = 0, PROF_ADJOINT = 1, PROF_DRMSD = 2, PROF_KINDS = 3 };
+enum ProfKind { PROF_PAIRS = 0, PROF_ADJOINT = 1, PROF_DRMSD = 2, PROF_CMO = 3, PROF_KINDS = 4 };
 
 struct ProfState {
     std::atomic<bool> on{false};

@@ -201,6 +201,18 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint6
         : "memory");
 }
 
+// Same with 8-bit floating-point operands (kind::f8f6f4; E4M3 when the descriptor's formats are 0).
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                       uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Arrive on bar once every tcgen05 op issued so far by this thread has completed.
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
@@ -301,7 +313,7 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
 }
 
 // Instruction descriptor: FP32 accumulator, A/B format (0 = fp16 or 1 = bf16 for kind::f16,
-// 2 = tf32 for kind::tf32), both K-major, shape M x N.
+// 2 = tf32 for kind::tf32, 0 = e4m3 for kind::f8f6f4), both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t make_idesc(int M, int N, uint32_t ab_format)
 {
     return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(N >> 3) << 17) |

@@ -109,3 +109,23 @@ def test_drmsd_host_side_validation(lib):
         assert 5000 * 44850 * 4 <= nb <= 5120 * 44864 * 4 + (1 << 20)
     assert clusco.workspace_bytes(clusco.OP_DRMSD, 5000, 300, clusco.FORM_TF32) == 0
     assert clusco.workspace_bytes(clusco.OP_DRMSD, 10, 1, 0) == 0
+
+
+def test_cmo_host_side_validation(lib):
+    fake = ctypes.c_void_p(0x1000)
+    call = lib.clusco_cmo_allpairs
+    c8 = ctypes.c_float(8.0)
+    assert call(fake, 1, 10, c8, fake, 0, None, 0, None) == 1                      # N < 2
+    assert call(fake, 10, 1, c8, fake, 0, None, 0, None) == 1                      # L < 2
+    assert call(fake, 10, 5000, c8, fake, 0, None, 0, None) == 1                   # L above 4096
+    assert call(fake, 10, 10, ctypes.c_float(0.0), fake, 0, None, 0, None) == 1    # cutoff must be > 0
+    assert call(fake, 10, 10, ctypes.c_float(float("inf")), fake, 0, None, 0, None) == 1
+    assert call(fake, 10, 10, c8, None, 0, None, 0, None) == 1                     # null out
+    assert call(fake, 10, 10, c8, fake, clusco.FORM_BF16_EXACT2, None, 0, None) == 7  # no such CMO form
+    assert call(fake, 10, 10, c8, fake, 0, fake, 16, None) == 2                    # workspace too small
+    for form in (clusco.FORM_FP32_SIMT, clusco.FORM_FP8_EXACT):
+        nb = clusco.workspace_bytes(clusco.OP_CMO, 5000, 300, form)
+        assert 5000 * 44850 <= nb <= 5120 * 45056 * 1.2 + (1 << 20)
+    assert clusco.workspace_bytes(clusco.OP_CMO, 5000, 300, clusco.FORM_TF32) == 0
+    # the cRMSD entry points do not take the contact-map form
+    assert lib.clusco_crmsd_allpairs(fake, 10, 10, fake, clusco.FORM_FP8_EXACT, None, 0, None) == 1

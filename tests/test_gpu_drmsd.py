@@ -146,3 +146,17 @@ def test_drmsd_bench_workload_sampled():
                   + bound(clusco.FORM_FP32_SIMT, d_plain, dmax))
     print(f"\ndRMSD 5000 x 300: dmax {dmax:.2f} A, q {dmax / 65278:.2e} A; exact max |err| {err_e.max():.2e} "
           f"(p99 {np.quantile(err_e, 0.99):.2e}); plain max |err| {err_p.max():.2e}")
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_drmsd_largest_supported_chain(form):
+    """L = 4096 (the largest supported chain: K = 8,386,560 distances per model, coordinates
+    staged in 64 KB of shared memory): sampled pairs against the oracle."""
+    e = E.decoy_ensemble(129, 4096, 2, (0.5, 8.0), seed=31)
+    X = e.coords
+    got = run(X, form)
+    a, b = sample_pairs(129, 24, seed=8)
+    a = np.concatenate([a, [0, 127]])
+    b = np.concatenate([b, [128, 128]])
+    ref = oracle.drmsd_pairs(X, a, b)
+    check(X, form, got[condensed_index(a, b, 129)], a, b, ref)
