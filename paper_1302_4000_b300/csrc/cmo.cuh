@@ -61,6 +61,8 @@ __global__ void __launch_bounds__(DR_PRE_THREADS) cmo_map_kernel(const float *__
         }
         return;
     }
+    // scalar FP32 here: with one compare and one byte store per distance the packed pipe's
+    // operand moves cost more than they save (measured)
     int c = 0;
     for (int i0 = DR_ROWS * warp; i0 < L - 1; i0 += DR_ROWS * NW) {
         float4 pr[DR_ROWS];
@@ -75,7 +77,8 @@ __global__ void __launch_bounds__(DR_PRE_THREADS) cmo_map_kernel(const float *__
 #pragma unroll
             for (int r = 0; r < DR_ROWS; ++r) {
                 if (j <= i0 + r) continue;
-                const bool in = dr_dist2(pr[r], pj) < cut2;
+                const float dx = pr[r].x - pj.x, dy = pr[r].y - pj.y, dz = pr[r].z - pj.z;
+                const bool in = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < cut2;
                 row[base[r] + j] = in ? CM_ONE : (uint8_t)0;
                 c += in ? 1 : 0;
             }
@@ -388,7 +391,8 @@ inline int cmo_launch(const float *coords, int64_t N, int64_t L, float cutoff, f
     if ((rc = make_map_u8(&mA, w.map, w.Kp, w.Npad, CM_MA, err))) return rc;
     if ((rc = make_map_u8(&mB, w.map, w.Kp, w.Npad, CM_MB, err))) return rc;
     const int64_t TA = w.Npad / CM_MA, TB = w.Npad / CM_MB;
-    grouped_tiles_kernel<<<1, 128, 0, st>>>(TA, TB, CM_MA, CM_MB, CM_GROUP, w.tiles);
+    grouped_tiles_kernel<<<(unsigned)((TA + CM_GROUP - 1) / CM_GROUP), 128, 0, st>>>(TA, TB, CM_MA, CM_MB, CM_GROUP,
+                                                                                  w.tiles);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaFuncSetAttribute(cmo_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CM_SMEM);
     if (e == cudaSuccess) {

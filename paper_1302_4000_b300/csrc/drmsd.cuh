@@ -65,18 +65,50 @@ __device__ __forceinline__ bool dr_stage(const float *__restrict__ coords, int64
     return __syncthreads_and(ok) != 0;
 }
 
-__device__ __forceinline__ float dr_dist2(const float4 &p, const float4 &q)
-{
-    const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
-    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-}
-
-// Distances are enumerated by groups of DR_ROWS consecutive rows: warp w of a block takes the
-// groups g = w, w + 8, ... and its lanes the columns j = DR_ROWS g + 1 + lane, + 32, ...; each
-// staged atom j serves the group's DR_ROWS rows (one shared-memory load per DR_ROWS distances),
-// stores are coalesced along each row, and no index is decoded.
+// Distances are enumerated by groups of DR_ROWS = 4 consecutive rows: warp w of a block takes
+// the groups g = w, w + 8, ... and its lanes the columns j = 4 g + 1 + lane, + 32, ...; each
+// staged atom j serves the group's four rows (one shared-memory load per four distances), the
+// four squared distances take two passes of the packed FP32x2 pipe, stores are coalesced along
+// each row, and no index is decoded. These kernels are issue-bound, hence the packing.
 constexpr int DR_PRE_THREADS = 256;
 constexpr int DR_ROWS = 4;
+
+// The atoms of a row group by axis and row pair: x[p] = (x of row i0 + 2p, x of row i0 + 2p + 1).
+// Rows past L - 2 repeat atom L - 1 (their distances are never stored).
+struct DrRows {
+    float2 x[2], y[2], z[2];
+};
+
+__device__ __forceinline__ DrRows dr_rows(const float4 *xs, int i0, int L)
+{
+    DrRows R;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const float4 a = xs[min(i0 + 2 * p, L - 1)], b = xs[min(i0 + 2 * p + 1, L - 1)];
+        R.x[p] = make_float2(a.x, b.x);
+        R.y[p] = make_float2(a.y, b.y);
+        R.z[p] = make_float2(a.z, b.z);
+    }
+    return R;
+}
+
+// d2[r] = squared distance of atom j to row atom i0 + r in FP32, rounded as
+// fma(dx, dx, fma(dy, dy, dz * dz)) with each difference row - j rounded once (the contact test
+// of the contact map overlap depends on this exact expression).
+__device__ __forceinline__ void dr_dist2x4(const DrRows &R, const float4 &pj, float (&d2)[4])
+{
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 xj = make_float2(pj.x, pj.x), yj = make_float2(pj.y, pj.y), zj = make_float2(pj.z, pj.z);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const float2 dx = __ffma2_rn(xj, m1, R.x[p]), dy = __ffma2_rn(yj, m1, R.y[p]), dz = __ffma2_rn(zj, m1, R.z[p]);
+        float2 q = __fmul2_rn(dz, dz);
+        q = __ffma2_rn(dy, dy, q);
+        q = __ffma2_rn(dx, dx, q);
+        d2[2 * p] = q.x;
+        d2[2 * p + 1] = q.y;
+    }
+}
 
 // One block per model: the largest intra-model distance (the square root of the largest squared
 // distance, which is the largest rounded distance because sqrtf is monotone), folded into the
@@ -98,16 +130,15 @@ __global__ void __launch_bounds__(DR_PRE_THREADS) drmsd_range_kernel(const float
         }
         return;
     }
+    // every d2 below is the squared distance of some atom pair of the model (or 0), so none
+    // needs the masks that keep the quantiser to pairs i < j
     float m2 = 0.f;
     for (int i0 = DR_ROWS * warp; i0 < L - 1; i0 += DR_ROWS * NW) {
-        float4 pr[DR_ROWS];
-#pragma unroll
-        for (int r = 0; r < DR_ROWS; ++r) pr[r] = xs[min(i0 + r, L - 1)];
+        const DrRows R = dr_rows(xs, i0, L);
         for (int j = i0 + 1 + lane; j < L; j += 32) {
-            const float4 pj = xs[j];
-#pragma unroll
-            for (int r = 0; r < DR_ROWS; ++r)
-                if (j > i0 + r) m2 = fmaxf(m2, dr_dist2(pr[r], pj));
+            float d2[4];
+            dr_dist2x4(R, xs[j], d2);
+            m2 = fmaxf(m2, fmaxf(fmaxf(d2[0], d2[1]), fmaxf(d2[2], d2[3])));
         }
     }
     m2 = warp_max_f(m2);
@@ -181,41 +212,51 @@ __global__ void __launch_bounds__(DR_PRE_THREADS) drmsd_quant_kernel(const float
     const DrScale sc = dr_scale(EXACT ? *dmax_bits : 0u);
     long long s = 0;
     const float ofs = -sc.c0 * sc.iq;
+    const float2 M2 = make_float2(12582912.f, 12582912.f), nM2 = make_float2(-12582912.f, -12582912.f);
+    const float2 iq2 = make_float2(sc.iq, sc.iq), ofs2 = make_float2(ofs, ofs);
+    const float2 r256 = make_float2(1.f / 256.f, 1.f / 256.f), m256 = make_float2(-256.f, -256.f);
     for (int i0 = DR_ROWS * warp; i0 < L - 1; i0 += DR_ROWS * NW) {
-        float4 pr[DR_ROWS];
+        const DrRows R = dr_rows(xs, i0, L);
         int64_t base[DR_ROWS];  // k = base + j in row i0 + r
 #pragma unroll
-        for (int r = 0; r < DR_ROWS; ++r) {
-            pr[r] = xs[min(i0 + r, L - 1)];
-            base[r] = dr_row_start(i0 + r, L) - (i0 + r) - 1;
-        }
+        for (int r = 0; r < DR_ROWS; ++r) base[r] = dr_row_start(i0 + r, L) - (i0 + r) - 1;
         for (int j = i0 + 1 + lane; j < L; j += 32) {
-            const float4 pj = xs[j];
+            float d2[4];
+            dr_dist2x4(R, xs[j], d2);
+            if (EXACT) {
+                // Conversions and the special-function unit run at a quarter of the FP32 rate, so
+                // this path takes one sqrt.approx per distance (within 2 ulp; the rounding below
+                // absorbs it) and does every rounding with the 1.5 * 2^23 shift on the FP32x2 pipe:
+                // n = rint(clamp((d - c0) / q)), h = rint(n / 256) (|h| <= 127), l = n - 256 h
+                // (|l| <= 128); h and l are small integers, so their BF16 encodings are the upper
+                // halves of their FP32 encodings
 #pragma unroll
-            for (int r = 0; r < DR_ROWS; ++r) {
-                if (j <= i0 + r) continue;
-                const float d2 = dr_dist2(pr[r], pj);
-                if (EXACT) {
-                    // Conversions and the special-function unit run at a quarter of the FP32 rate,
-                    // so this path uses one sqrt.approx (within 2 ulp; the rounding below absorbs
-                    // it) and does every rounding with the 1.5 * 2^23 shift on the FP32 pipe:
-                    // n = rint(clamp((d - c0) / q)), h = rint(n / 256) (|h| <= 127),
-                    // l = n - 256 h (|l| <= 128); h and l are small integers, so their BF16
-                    // encodings are the upper halves of their FP32 encodings
-                    float d;
-                    asm("sqrt.approx.f32 %0, %1;" : "=f"(d) : "f"(d2));
-                    const float x = fminf(fmaxf(fmaf(d, sc.iq, ofs), -(float)DR_NMAX), (float)DR_NMAX);
-                    const float t = x + 12582912.f;
-                    const float v = t - 12582912.f;
-                    const float h = (v * (1.f / 256.f) + 12582912.f) - 12582912.f;
-                    const float l = fmaf(-256.f, h, v);
-                    reinterpret_cast<unsigned short *>(hrow)[base[r] + j] = (unsigned short)(__float_as_uint(h) >> 16);
-                    reinterpret_cast<unsigned short *>(lrow)[base[r] + j] = (unsigned short)(__float_as_uint(l) >> 16);
-                    const int n = __float_as_int(t) - 0x4B400000;
-                    s += (long long)(n * n);  // n^2 <= 32639^2 < 2^31
-                } else {
-                    frow[base[r] + j] = sqrtf(d2);
+                for (int p = 0; p < 2; ++p) {
+                    float da, db;
+                    asm("sqrt.approx.f32 %0, %1;" : "=f"(da) : "f"(d2[2 * p]));
+                    asm("sqrt.approx.f32 %0, %1;" : "=f"(db) : "f"(d2[2 * p + 1]));
+                    float2 x = __ffma2_rn(make_float2(da, db), iq2, ofs2);
+                    x.x = fminf(fmaxf(x.x, -(float)DR_NMAX), (float)DR_NMAX);
+                    x.y = fminf(fmaxf(x.y, -(float)DR_NMAX), (float)DR_NMAX);
+                    const float2 t = __fadd2_rn(x, M2);
+                    const float2 v = __fadd2_rn(t, nM2);
+                    const float2 h = __fadd2_rn(__ffma2_rn(v, r256, M2), nM2);
+                    const float2 l = __ffma2_rn(h, m256, v);
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int r = 2 * p + u;
+                        if (j <= i0 + r) continue;
+                        const float hu = u ? h.y : h.x, lu = u ? l.y : l.x, tu = u ? t.y : t.x;
+                        reinterpret_cast<unsigned short *>(hrow)[base[r] + j] = (unsigned short)(__float_as_uint(hu) >> 16);
+                        reinterpret_cast<unsigned short *>(lrow)[base[r] + j] = (unsigned short)(__float_as_uint(lu) >> 16);
+                        const int n = __float_as_int(tu) - 0x4B400000;
+                        s += (long long)(n * n);  // n^2 <= 32639^2 < 2^31
+                    }
                 }
+            } else {
+#pragma unroll
+                for (int r = 0; r < DR_ROWS; ++r)
+                    if (j > i0 + r) frow[base[r] + j] = sqrtf(d2[r]);
             }
         }
     }
@@ -242,19 +283,23 @@ __global__ void __launch_bounds__(DR_PRE_THREADS) drmsd_quant_kernel(const float
 // Tile order of the persistent tensor-core kernels: tiles (I, J) of MA x MB models with pairs
 // a < b, i.e. J >= jmin(I) = I MA / MB (MA and MB powers of two), in groups of `group` tile
 // rows; within a group J ascending, then I. The grid's concurrent tiles then share a few A
-// row panels and a few B panels, which stay in L2 while the CTAs stream K. One thread per
-// group writes its tiles after those of the earlier groups.
+// row panels and a few B panels, which stay in L2 while the CTAs stream K.
 __global__ void grouped_tiles_kernel(int64_t TA, int64_t TB, int MA, int MB, int group, int2 *__restrict__ tiles)
 {
-    // jmin(I) = I MA / MB with MA / MB or MB / MA a power of two: shifts, no 64-bit division
+    // one block per group, its threads over the columns J; jmin(I) = I MA / MB with MA / MB or
+    // MB / MA a power of two (shifts, no 64-bit division)
     const int up = MA >= MB ? __ffs(MA / MB) - 1 : 0, dn = MB > MA ? __ffs(MB / MA) - 1 : 0;
-    const int64_t ng = (TA + group - 1) / group;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t I0 = g * group, I1 = min(TA, I0 + group);
-        int64_t t = 0;
-        for (int64_t I = 0; I < I0; ++I) t += TB - ((I << up) >> dn);
-        for (int64_t J = (I0 << up) >> dn; J < TB; ++J)
-            for (int64_t I = I0; I < I1 && ((I << up) >> dn) <= J; ++I) tiles[t++] = make_int2((int)I, (int)J);
+    auto jmin = [&](int64_t I) { return (I << up) >> dn; };
+    const int64_t I0 = (int64_t)blockIdx.x * group, I1 = min(TA, I0 + group);
+    if (I0 >= TA) return;
+    int64_t t0 = 0;  // tiles of the earlier groups
+    for (int64_t I = 0; I < I0; ++I) t0 += TB - jmin(I);
+    const int64_t J0 = jmin(I0);
+    for (int64_t J = J0 + threadIdx.x; J < TB; J += blockDim.x) {
+        int64_t t = t0;
+        for (int64_t Jp = J0; Jp < J; ++Jp)
+            for (int64_t I = I0; I < I1 && jmin(I) <= Jp; ++I) ++t;
+        for (int64_t I = I0; I < I1 && jmin(I) <= J; ++I) tiles[t++] = make_int2((int)I, (int)J);
     }
 }
 
@@ -570,7 +615,8 @@ inline int drmsd_launch(const float *coords, int64_t N, int64_t L, float *out, b
     if ((rc = make_map(&mA, w.planes, false, w.Kp, 2 * w.Npad, DR_MA, err))) return rc;
     if ((rc = make_map(&mB, w.planes, false, w.Kp, 2 * w.Npad, DR_MB, err))) return rc;
     const int64_t TA = w.Npad / DR_MA, TB = w.Npad / DR_MB;
-    grouped_tiles_kernel<<<1, 128, 0, st>>>(TA, TB, DR_MA, DR_MB, DR_GROUP, w.tiles);
+    grouped_tiles_kernel<<<(unsigned)((TA + DR_GROUP - 1) / DR_GROUP), 128, 0, st>>>(TA, TB, DR_MA, DR_MB, DR_GROUP,
+                                                                                  w.tiles);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaFuncSetAttribute(drmsd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)DR_SMEM);
