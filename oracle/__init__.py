@@ -13,6 +13,10 @@ cited Kabsch method). ``crmsd_eq2_pair`` restates the paper's closed form
 and serves as a pin and as a second CPU method; the oracle's answers never
 come from it.
 
+``gdt_tm_vs_ref`` scores models against a reference with GDT_TS, TM-score and MaxSub (eq. 3,
+eq. 4) as maxima over the paper's superposition search (fragment seeds of 4, L/4, L/2 and L
+atoms, refinement on the atoms within 3.5 A), each superposition from the Kabsch path above.
+
 The dRMSD functions follow eq. 5 (the RMS difference of the two models'
 intra-model distance matrices over the L(L-1)/2 atom pairs), formed directly
 from the distances. The CMO functions follow eq. 6 and eq. 7 (contact maps over the
@@ -96,8 +100,10 @@ def _bind(lib):
     lib.oracle_crmsd_grad.argtypes = [_f32p, i64, i64, _f64p, ctypes.c_double, _f64p, ctypes.c_int]
     lib.oracle_crmsd_eq2.argtypes = [_f32p, _f32p, i64, ctypes.POINTER(ctypes.c_double)]
     lib.oracle_crmsd_grad_rows.argtypes = [_f32p, i64, i64, _f64p, ctypes.c_double, _i64p, i64, _f64p, ctypes.c_int]
+    lib.oracle_gdt_tm_vs_ref.argtypes = [_f32p, i64, i64, _f32p, _f64p, ctypes.c_int]
     for f in ("oracle_crmsd_pair", "oracle_crmsd_allpairs", "oracle_crmsd_pairs",
-              "oracle_crmsd_vs_ref", "oracle_crmsd_grad", "oracle_crmsd_eq2", "oracle_crmsd_grad_rows"):
+              "oracle_crmsd_vs_ref", "oracle_crmsd_grad", "oracle_crmsd_eq2", "oracle_crmsd_grad_rows",
+              "oracle_gdt_tm_vs_ref"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -260,4 +266,15 @@ def cmo_pairs(X, ia, ib, cutoff: float, nthreads: int = 0, lib=None) -> np.ndarr
     out = np.empty(ia.shape[0], dtype=np.float64)
     _check(lib.oracle_cmo_pairs(X, X.shape[0], X.shape[1], float(cutoff), ia, ib, ia.shape[0], out, nthreads),
            "cmo_pairs")
+    return out
+
+
+def gdt_tm_vs_ref(X, ref, nthreads: int = 0, lib=None) -> np.ndarray:
+    """[N, 3] FP64: GDT_TS (fraction), TM-score, MaxSub of every model against the reference, each
+    the maximum over the paper's superposition search (fragment seeds, 3.5 A refinement)."""
+    lib = lib or load()
+    X, ref = _f32(X), _f32(ref)
+    N, L = X.shape[0], X.shape[1]
+    out = np.empty((N, 3), dtype=np.float64)
+    _check(lib.oracle_gdt_tm_vs_ref(X, N, L, ref, out.reshape(-1), nthreads), "gdt_tm_vs_ref")
     return out

@@ -467,3 +467,140 @@ int oracle_crmsd_eq2(const float *A, const float *B, int64_t L, double *c_out)
     free(bc);
     return ORACLE_OK;
 }
+
+/* ======================= GDT_TS, TM-score, MaxSub ======================= */
+/*
+ * Scores of a model against a reference after a search over superpositions (section
+ * "Algorithms": GDT_TS eq. 3, TM-score eq. 4, MaxSub = TM-score with d0 = 3.5 A), by the
+ * search the paper describes, in this order:
+ *   1. seeds: every contiguous fragment of 4, L/4, L/2 and L atoms (lengths below 3 or above L
+ *      dropped, repeated lengths taken once);
+ *   2. for each seed, the whole model is superimposed on the reference by the optimal proper
+ *      rotation and translation of the seed's atoms (Kabsch on their centred coordinates);
+ *   3. that superposition is scored: d_i = |R b_i + t - a_i| for every atom, C_x = #{d_i < x}
+ *      for x = 1, 2, 4, 8 A, the TM sum (1/L) sum_i 1 / (1 + (d_i/d0)^2) with
+ *      d0 = max(1.24 (L - 15)^(1/3) - 1.8, 0.5) A and the same sum with d0 = 3.5 A (MaxSub);
+ *   4. the atoms with d_i < 3.5 A are selected and the model is superimposed again on them,
+ *      scored again, and so on, until the number of selected atoms repeats, fewer than 3 are
+ *      selected, or four such refinements have been made;
+ * and each score is the maximum over every superposition scored:
+ *   GDT_TS = (max C_1 + max C_2 + max C_4 + max C_8) / (4 L), TM = max TM sum, MaxSub = max.
+ */
+static double tm_d0(int64_t L)
+{
+    const double d0 = 1.24 * cbrt((double)L - 15.0) - 1.8;
+    return d0 > 0.5 ? d0 : 0.5;
+}
+
+/* R, t with R b_i + t ~ a_i from the atoms idx[0 .. n) (steps 2 and 4) */
+static int fit_subset(const double *a, const double *b, const int64_t *idx, int64_t n, double *ac, double *bc,
+                      double R[3][3], double t[3])
+{
+    double ma[3] = {0, 0, 0}, mb[3] = {0, 0, 0};
+    for (int64_t q = 0; q < n; ++q)
+        for (int k = 0; k < 3; ++k) {
+            ma[k] += a[3 * idx[q] + k];
+            mb[k] += b[3 * idx[q] + k];
+        }
+    for (int k = 0; k < 3; ++k) {
+        ma[k] /= (double)n;
+        mb[k] /= (double)n;
+    }
+    for (int64_t q = 0; q < n; ++q)
+        for (int k = 0; k < 3; ++k) {
+            ac[3 * q + k] = a[3 * idx[q] + k] - ma[k];
+            bc[3 * q + k] = b[3 * idx[q] + k] - mb[k];
+        }
+    int st = kabsch(ac, bc, n, R);
+    if (st) return st;
+    for (int r = 0; r < 3; ++r) t[r] = ma[r] - (R[r][0] * mb[0] + R[r][1] * mb[1] + R[r][2] * mb[2]);
+    return ORACLE_OK;
+}
+
+/* out[0..3) = GDT_TS, TM-score, MaxSub of model b against reference a (L atoms each). */
+static int gdt_tm_one(const double *a, const double *b, int64_t L, int64_t *idx, int64_t *sel, double *ac,
+                      double *bc, double out[3])
+{
+    const double cuts[4] = {1.0, 2.0, 4.0, 8.0};
+    const double d0 = tm_d0(L), d0m = 3.5;
+    int64_t best_c[4] = {0, 0, 0, 0};
+    double best_tm = 0.0, best_ms = 0.0;
+    int64_t lens[4] = {4, L / 4, L / 2, L};
+    for (int li = 0; li < 4; ++li) {
+        const int64_t len = lens[li];
+        if (len < 3 || len > L) continue;
+        int dup = 0;
+        for (int lj = 0; lj < li; ++lj)
+            if (lens[lj] == len) dup = 1;
+        if (dup) continue;
+        for (int64_t s0 = 0; s0 + len <= L; ++s0) {
+            int64_t n = len, prev = -1;
+            for (int64_t q = 0; q < n; ++q) idx[q] = s0 + q;
+            for (int it = 0; it <= 4; ++it) {
+                double R[3][3], t[3];
+                int st = fit_subset(a, b, idx, n, ac, bc, R, t);
+                if (st) return st;
+                int64_t c[4] = {0, 0, 0, 0}, ns = 0;
+                double tm = 0.0, ms = 0.0;
+                for (int64_t i = 0; i < L; ++i) {
+                    double d2 = 0.0;
+                    for (int r = 0; r < 3; ++r) {
+                        const double x = R[r][0] * b[3 * i] + R[r][1] * b[3 * i + 1] + R[r][2] * b[3 * i + 2] + t[r];
+                        const double e = x - a[3 * i + r];
+                        d2 += e * e;
+                    }
+                    const double d = sqrt(d2);
+                    for (int k = 0; k < 4; ++k) c[k] += d < cuts[k];
+                    tm += 1.0 / (1.0 + (d / d0) * (d / d0));
+                    ms += 1.0 / (1.0 + (d / d0m) * (d / d0m));
+                    if (d < 3.5) sel[ns++] = i;
+                }
+                for (int k = 0; k < 4; ++k)
+                    if (c[k] > best_c[k]) best_c[k] = c[k];
+                if (tm / (double)L > best_tm) best_tm = tm / (double)L;
+                if (ms / (double)L > best_ms) best_ms = ms / (double)L;
+                if (it == 4 || ns < 3 || ns == prev) break;
+                prev = ns;
+                n = ns;
+                for (int64_t q = 0; q < n; ++q) idx[q] = sel[q];
+            }
+        }
+    }
+    out[0] = (double)(best_c[0] + best_c[1] + best_c[2] + best_c[3]) / (4.0 * (double)L);
+    out[1] = best_tm;
+    out[2] = best_ms;
+    return ORACLE_OK;
+}
+
+/* GDT_TS, TM-score and MaxSub of every model against the reference: out[3 a + {0,1,2}]. */
+int oracle_gdt_tm_vs_ref(const float *X, int64_t N, int64_t L, const float *ref, double *out, int nthreads)
+{
+    if (!X || !ref || !out || N < 1 || L < 3) return ORACLE_EINVAL;
+    double *a = (double *)malloc(sizeof(double) * 3 * L);
+    if (!a) return ORACLE_EINVAL;
+    for (int64_t t = 0; t < 3 * L; ++t) a[t] = (double)ref[t];
+    int bad = 0;
+    set_threads(nthreads);
+#pragma omp parallel reduction(| : bad)
+    {
+        double *b = (double *)malloc(sizeof(double) * 3 * L);
+        double *ac = (double *)malloc(sizeof(double) * 3 * L);
+        double *bc = (double *)malloc(sizeof(double) * 3 * L);
+        int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * L);
+        int64_t *sel = (int64_t *)malloc(sizeof(int64_t) * L);
+        if (!b || !ac || !bc || !idx || !sel) bad = 1;
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t m = 0; m < N; ++m) {
+            if (bad) continue;
+            for (int64_t t = 0; t < 3 * L; ++t) b[t] = (double)X[3 * L * m + t];
+            bad |= gdt_tm_one(a, b, L, idx, sel, ac, bc, out + 3 * m);
+        }
+        free(b);
+        free(ac);
+        free(bc);
+        free(idx);
+        free(sel);
+    }
+    free(a);
+    return bad ? ORACLE_ENOCONV : ORACLE_OK;
+}
