@@ -148,6 +148,20 @@ int clusco_drmsd_allpairs(const float *coords, int64_t N, int64_t L, float *out,
 int clusco_cmo_allpairs(const float *coords, int64_t N, int64_t L, float cutoff, float *out, int form,
                         void *workspace, size_t workspace_bytes, void *stream);
 
+/* GDT_TS, TM-score and MaxSub of every model against a reference (section "Algorithms", eq. 3
+ * and eq. 4; MaxSub is the TM-score with d0 = 3.5 A): out[3 a + 0] = GDT_TS as a fraction
+ * (max C_1 + max C_2 + max C_4 + max C_8) / (4 L), C_x = number of atoms with d < x A;
+ * out[3 a + 1] = TM-score with d0 = max(1.24 (L - 15)^(1/3) - 1.8, 0.5) A; out[3 a + 2] = MaxSub.
+ * Each is the maximum over the superpositions of one search: seeds are the contiguous fragments
+ * of 4, L/4, L/2 and L atoms (lengths below 3 dropped, repeats once); the model is superimposed on
+ * the reference by the optimal proper rotation and translation of the seed's atoms, scored, then
+ * superimposed again on the atoms within 3.5 A until their number repeats, fewer than 3 remain,
+ * or four refinements were made. Distances and the integer decisions in FP64; TM terms summed in
+ * FP32. coords float[N][L][3], ref float[L][3], out float[N][3], all device. 3 <= L <= 1024,
+ * N >= 1. A model (or reference) with a non-finite coordinate gives NaN scores and sets
+ * CLUSCO_ENONFINITE in the device status. No workspace. */
+int clusco_gdt_tm_vs_ref(const float *coords, int64_t N, int64_t L, const float *ref, float *out, void *stream);
+
 /* One-versus-reference: out[a] = cRMSD(model a, ref) for a in [0, N).
  * ref: float[L][3] device; out: float[N] device. Exact-integer covariance on
  * 24-bit fixed point coordinates, FP64 epilogue. N >= 1, L >= 1. */

@@ -18,7 +18,8 @@
  *      difference);
  *   2. H = sum_i a_i b_i^T over the centred coordinates (3x3);
  *   3. one-sided Jacobi SVD H = U diag(s) V^T, swept until every column pair
- *      is orthogonal to 4 ulp (at most 64 sweeps, failure reported);
+ *      is orthogonal to 4 ulp or one of the two is numerically zero (at most
+ *      64 sweeps, failure reported);
  *   4. the optimal proper rotation R = U diag(1, 1, d) V^T with
  *      d = sign(det(U V^T)) (Kabsch);
  *   5. the RMS of the residuals a_i - R b_i, computed directly from the
@@ -87,6 +88,13 @@ static int svd3(const double H[3][3], double U[3][3], double s[3], double V[3][3
         for (int c = 0; c < 3; ++c) V[r][c] = (r == c) ? 1.0 : 0.0;
 
     const double tol = 4.0 * 2.220446049250313e-16;
+    /* a column whose squared norm is below (tol |H|)^2 is numerically zero: its singular value
+     * is 0 and its direction is completed below, so it takes no rotation (without this floor a
+     * rank-deficient H, e.g. three reference atoms in one coordinate plane, can cycle forever) */
+    double hn2 = 0.0;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) hn2 += H[r][c] * H[r][c];
+    const double zero_col = tol * tol * hn2;
     int converged = 0;
     for (int sweep = 0; sweep < 64 && !converged; ++sweep) {
         converged = 1;
@@ -98,7 +106,8 @@ static int svd3(const double H[3][3], double U[3][3], double s[3], double V[3][3
                     beta += W[i][q] * W[i][q];
                     gamma += W[i][p] * W[i][q];
                 }
-                if (gamma == 0.0 || fabs(gamma) <= tol * sqrt(alpha * beta)) continue;
+                if (gamma == 0.0 || fabs(gamma) <= tol * sqrt(alpha * beta) || alpha <= zero_col || beta <= zero_col)
+                    continue;
                 converged = 0;
                 double zeta = (beta - alpha) / (2.0 * gamma);
                 double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));

@@ -9,7 +9,7 @@ calls raise.
 
 The operations are ClusCo's cRMSD (section "Algorithms", eq. 1 / eq. 2), dRMSD (eq. 5)
 and contact map overlap (eq. 6 / eq. 7) over the N(N-1)/2 pairs of an ensemble (section
-"Background").
+"Background"), and GDT_TS / TM-score / MaxSub (eq. 3 / eq. 4) against a reference.
 """
 from __future__ import annotations
 
@@ -45,7 +45,7 @@ EXPORTS = ("clusco_version", "clusco_workspace_bytes", "clusco_crmsd_allpairs", 
            "clusco_crmsd_vs_ref", "clusco_crmsd_vs_ref_noalloc", "clusco_crmsd_allpairs_backward",
            "clusco_sync_status", "clusco_last_error", "clusco_profile_enable", "clusco_profile_read",
            "clusco_crmsd_allpairs_rot", "clusco_crmsd_allpairs_backward_rot", "clusco_drmsd_allpairs",
-           "clusco_cmo_allpairs")
+           "clusco_cmo_allpairs", "clusco_gdt_tm_vs_ref")
 KERNEL_PAIRS = 0
 KERNEL_ADJOINT = 1
 KERNEL_DRMSD = 2
@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH):
                                                                vp]
             lib.clusco_drmsd_allpairs.argtypes = [vp, i64, i64, vp, ctypes.c_int, vp, sz, vp]
             lib.clusco_cmo_allpairs.argtypes = [vp, i64, i64, ctypes.c_float, vp, ctypes.c_int, vp, sz, vp]
+            lib.clusco_gdt_tm_vs_ref.argtypes = [vp, i64, i64, vp, vp, vp]
             lib.clusco_profile_enable.argtypes = [ctypes.c_int]
             lib.clusco_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(ctypes.c_longlong)]
@@ -96,7 +97,7 @@ def load(path: str = LIB_PATH):
                       "clusco_crmsd_vs_ref_noalloc", "clusco_crmsd_allpairs_backward", "clusco_sync_status",
                       "clusco_profile_enable", "clusco_profile_read", "clusco_crmsd_allpairs_rot",
                       "clusco_crmsd_allpairs_backward_rot", "clusco_crmsd_allpairs_below", "clusco_drmsd_allpairs",
-                      "clusco_cmo_allpairs"):
+                      "clusco_cmo_allpairs", "clusco_gdt_tm_vs_ref"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -194,6 +195,21 @@ def cmo_allpairs(coords: torch.Tensor, cutoff: float = 8.0, form: int = FORM_FP8
     ws, nb = _ws(workspace, OP_CMO, N, L, form, coords.device)
     _check(load().clusco_cmo_allpairs(coords.data_ptr(), N, L, float(cutoff), out.data_ptr(), form, ws.data_ptr(),
                                       nb, _stream(stream)))
+    return out
+
+
+def gdt_tm_vs_ref(coords: torch.Tensor, ref: torch.Tensor, out: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """[N, 3] float32: GDT_TS (fraction), TM-score and MaxSub of every model against the reference
+    (eq. 3, eq. 4), each the maximum over the paper's superposition search."""
+    coords = _coords(coords)
+    N, L = coords.shape[0], coords.shape[1]
+    ref = ref.contiguous()
+    assert ref.is_cuda and ref.dtype == torch.float32 and tuple(ref.shape) == (L, 3)
+    if out is None:
+        out = torch.empty((N, 3), dtype=torch.float32, device=coords.device)
+    assert out.is_cuda and out.dtype == torch.float32 and out.numel() >= 3 * N and out.is_contiguous()
+    _check(load().clusco_gdt_tm_vs_ref(coords.data_ptr(), N, L, ref.data_ptr(), out.data_ptr(), _stream(stream)))
     return out
 
 

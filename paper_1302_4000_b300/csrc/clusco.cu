@@ -21,6 +21,7 @@
 #include "bwd_rot.cuh"
 #include "drmsd.cuh"
 #include "cmo.cuh"
+#include "gdt.cuh"
 
 using namespace clusco;
 
@@ -463,6 +464,22 @@ int clusco_cmo_allpairs(const float *coords, int64_t N, int64_t L, float cutoff,
     const CmWs w = carve_cmo(s.ptr, N, L, form);
     std::string err;
     rc = cmo_launch(coords, N, L, cutoff, out, form == CLUSCO_FORM_FP8_EXACT, w, st, err);
+    if (rc) return fail(rc, "%s", err.c_str());
+    return CLUSCO_OK;
+}
+
+int clusco_gdt_tm_vs_ref(const float *coords, int64_t N, int64_t L, const float *ref, float *out, void *stream)
+{
+    g_last_error.clear();
+    int rc;
+    if ((rc = check_sizes(N, L, 1))) return rc;
+    if (L < 3 || L > GT_MAX_L) return fail(CLUSCO_EINVAL, "GDT_TS / TM-score need 3 <= L <= %d", GT_MAX_L);
+    if (N > ((int64_t)1 << 31) - 1) return fail(CLUSCO_EINVAL, "N=%lld above one block per model", (long long)N);
+    if ((rc = check_ptr(coords, "coords", 4))) return rc;
+    if ((rc = check_ptr(ref, "ref", 4))) return rc;
+    if ((rc = check_ptr(out, "out", 4))) return rc;
+    std::string err;
+    rc = gdt_tm_launch(coords, N, L, ref, out, (cudaStream_t)stream, err);
     if (rc) return fail(rc, "%s", err.c_str());
     return CLUSCO_OK;
 }

@@ -362,7 +362,7 @@ inline int cmo_launch(const float *coords, int64_t N, int64_t L, float cutoff, f
 {
     cudaError_t e = cudaSuccess;
     const size_t xsm = (size_t)L * sizeof(float4);
-    if (xsm > 48 * 1024) e = cudaFuncSetAttribute(cmo_map_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm);
+    if (xsm > 40 * 1024) e = cudaFuncSetAttribute(cmo_map_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm);
     if (e == cudaSuccess) {
         cmo_map_kernel<<<(unsigned)w.Npad, DR_PRE_THREADS, xsm, st>>>(coords, N, (int)L, w.Kp, cutoff * cutoff, w.map,
                                                                       w.cnt);

@@ -570,7 +570,7 @@ inline int drmsd_launch(const float *coords, int64_t N, int64_t L, float *out, b
 {
     cudaError_t e = cudaSuccess;
     const size_t xsm = (size_t)L * sizeof(float4);
-    if (xsm > 48 * 1024) {
+    if (xsm > 40 * 1024) {  // the static shared arrays count against the default 48 KB too
         e = cudaFuncSetAttribute(drmsd_range_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(drmsd_quant_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm);
