@@ -129,3 +129,13 @@ def test_cmo_host_side_validation(lib):
     assert clusco.workspace_bytes(clusco.OP_CMO, 5000, 300, clusco.FORM_TF32) == 0
     # the cRMSD entry points do not take the contact-map form
     assert lib.clusco_crmsd_allpairs(fake, 10, 10, fake, clusco.FORM_FP8_EXACT, None, 0, None) == 1
+
+
+def test_gdt_tm_host_side_validation(lib):
+    fake = ctypes.c_void_p(0x1000)
+    call = lib.clusco_gdt_tm_vs_ref
+    assert call(fake, 0, 10, fake, fake, None) == 1        # N < 1
+    assert call(fake, 10, 2, fake, fake, None) == 1        # L < 3
+    assert call(fake, 10, 1025, fake, fake, None) == 1     # L above 1024
+    assert call(fake, 10, 10, None, fake, None) == 1       # null reference
+    assert call(fake, 10, 10, fake, None, None) == 1       # null out
