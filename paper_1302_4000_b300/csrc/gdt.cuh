@@ -5,14 +5,22 @@
 // superimposed again on the atoms that came within 3.5 A, until that number repeats, fewer
 // than 3 atoms qualify, or four refinements were made.
 //
-// Layout: one block per model, the model and the reference staged in shared memory in FP64;
-// each warp runs 32 seeds side by side, one per lane, so that the 4x4 eigenproblem of every
-// superposition (Horn's quaternion form, cyclic Jacobi sweeps) runs once per lane instead of
-// redundantly across a warp. Every lane walks all L atoms in the same order (broadcast reads).
-// The decisions that make the scores integers -- d < 1, 2, 4, 8 A and the 3.5 A selection --
-// are taken in FP64 like the oracle's, so they agree with it except at exact ties; the TM and
-// MaxSub terms 1 / (1 + (d / d0)^2) are summed in FP32. One pass over the atoms scores a
+// Layout: one block per model, the model and the reference staged in shared memory (as given,
+// and centred); each warp runs 32 seeds side by side, one per lane, so that the eigenproblem of
+// every superposition runs once per lane instead of redundantly across a warp, and every lane
+// walks all L atoms in the same order (broadcast reads). One pass over the atoms scores a
 // superposition and accumulates the moments of the atoms it selects, which give the next fit.
+//
+// Precision (B300's FP64 rate is 1/64 of FP32, so FP64 is kept off the per-atom path): the
+// moments (sums of a, b, a b^T over the selected atoms) are accumulated from the given FP32
+// coordinates as double-float pairs (exact products by FMA, compensated sums), good to about
+// 2^-48; the superposition is solved in FP64 from them (the largest root of the key matrix's
+// quartic by Newton from an upper bound, the rotation from the adjugate of K - lambda I, cyclic
+// Jacobi sweeps where that root is nearly repeated); each atom's squared distance is then taken
+// in FP32 in the centred frame, and where it falls within its error bound of a cutoff
+// (1, 2, 3.5, 4, 8 A) it is recomputed in FP64 from the given coordinates. So every integer
+// decision is the one FP64 arithmetic takes, as in the oracle; the TM and MaxSub terms
+// 1 / (1 + (d / d0)^2) are summed in FP32.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -47,68 +55,147 @@ __device__ __forceinline__ int gt_lengths(int L, int (&lens)[4])
     return n;
 }
 
-// Moments of a set of atom pairs (a_i reference, b_i model): sums of a, b and a b^T, and the count.
+// Double-float accumulator: hi + lo, with the rounding error of every addition carried in lo
+// (Knuth's two-sum) and products split exactly by FMA. The _rn intrinsics keep the compiler from
+// contracting the error terms away.
+struct GtDF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void df_add(GtDF &s, float v)
+{
+    const float t = __fadd_rn(s.hi, v);
+    const float bp = __fsub_rn(t, s.hi);
+    const float err = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+    s.hi = t;
+    s.lo = __fadd_rn(s.lo, err);
+}
+
+__device__ __forceinline__ void df_add_prod(GtDF &s, float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    const float e = fmaf(a, b, -p);  // a b - p exactly
+    df_add(s, p);
+    s.lo = __fadd_rn(s.lo, e);
+}
+
+__device__ __forceinline__ double df_value(const GtDF &s) { return (double)s.hi + (double)s.lo; }
+
+// Moments of a set of atom pairs (a_i reference, b_i model, as given): sums of a, b and a b^T.
 struct GtMoments {
-    double sa[3], sb[3], sab[9];
+    GtDF sa[3], sb[3], sab[9];
     int n;
 };
 
 __device__ __forceinline__ void gt_zero(GtMoments &m)
 {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) m.sa[k] = m.sb[k] = 0.0;
+    for (int k = 0; k < 3; ++k) m.sa[k] = m.sb[k] = GtDF{0.f, 0.f};
 #pragma unroll
-    for (int k = 0; k < 9; ++k) m.sab[k] = 0.0;
+    for (int k = 0; k < 9; ++k) m.sab[k] = GtDF{0.f, 0.f};
     m.n = 0;
 }
 
-__device__ __forceinline__ void gt_add(GtMoments &m, const double *a, const double *b)
+__device__ __forceinline__ void gt_add(GtMoments &m, const float4 &a, const float4 &b)
 {
+    const float av[3] = {a.x, a.y, a.z}, bv[3] = {b.x, b.y, b.z};
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        m.sa[r] += a[r];
-        m.sb[r] += b[r];
+        df_add(m.sa[r], av[r]);
+        df_add(m.sb[r], bv[r]);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) m.sab[3 * r + c] = fma(a[r], b[c], m.sab[3 * r + c]);
+        for (int c = 0; c < 3; ++c) df_add_prod(m.sab[3 * r + c], av[r], bv[c]);
     }
     ++m.n;
 }
 
-// The superposition R b + t ~ a of the moments' atoms: H = sum (a - abar)(b - bbar)^T, R from
-// Horn's key matrix by Jacobi sweeps, t = abar - R bbar.
+// The optimal rotation for H = sum (a - abar)(b - bbar)^T in FP64. Its quality is the largest
+// eigenvalue lambda of Horn's key matrix K(H), the largest root of
+//   P(x) = x^4 - 2 I1 x^2 - 8 det(H) x + (I1^2 - 4 I2)
+// (I1 = |H|_F^2, I2 = sum of the squared 2x2 minors), found by Newton from the upper bound
+// sqrt(3 I1), where P is increasing and convex; the rotation comes from the adjugate of
+// K - lambda I, or from Jacobi sweeps where lambda is nearly repeated.
+__device__ __forceinline__ void gt_rotation(const double H[9], double R[9])
+{
+    double I1 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) I1 = fma(H[k], H[k], I1);
+    const double det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                       H[2] * (H[3] * H[7] - H[4] * H[6]);
+    double I2 = 0.0;
+#pragma unroll
+    for (int r0 = 0; r0 < 2; ++r0)
+#pragma unroll
+        for (int r1 = r0 + 1; r1 < 3; ++r1)
+#pragma unroll
+            for (int c0 = 0; c0 < 2; ++c0)
+#pragma unroll
+                for (int c1 = c0 + 1; c1 < 3; ++c1) {
+                    const double mn = H[3 * r0 + c0] * H[3 * r1 + c1] - H[3 * r0 + c1] * H[3 * r1 + c0];
+                    I2 = fma(mn, mn, I2);
+                }
+    const double c0 = I1 * I1 - 4.0 * I2;
+    double x = sqrt(3.0 * I1);
+    for (int k = 0; k < 60; ++k) {
+        const double x2 = x * x;
+        const double p = fma(x2, x2 - 2.0 * I1, fma(-8.0 * det, x, c0));
+        const double dp = 4.0 * x * (x2 - I1) - 8.0 * det;
+        if (!(dp > 0.0)) break;
+        const double step = p / dp;
+        x -= step;
+        if (!(fabs(step) > 1e-15 * x)) break;
+    }
+    if (!(I1 > 0.0) || !horn_rotation<double>(H, x, 1e-6, R)) rotation_jacobi4<double, 10>(H, R);
+}
+
+// The superposition R b + t ~ a of the moments' atoms.
 __device__ __forceinline__ void gt_fit(const GtMoments &m, double R[9], double t[3])
 {
     const double inv = 1.0 / (double)m.n;
-    double ma[3], mb[3], H[9];
+    double sa[3], mb[3], H[9];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        ma[k] = m.sa[k] * inv;
-        mb[k] = m.sb[k] * inv;
+        sa[k] = df_value(m.sa[k]);
+        mb[k] = df_value(m.sb[k]) * inv;
     }
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) H[3 * r + c] = m.sab[3 * r + c] - m.sa[r] * mb[c];
-    rotation_jacobi4<double, 10>(H, R);
+        for (int c = 0; c < 3; ++c) H[3 * r + c] = df_value(m.sab[3 * r + c]) - sa[r] * mb[c];
+    gt_rotation(H, R);
 #pragma unroll
-    for (int r = 0; r < 3; ++r) t[r] = ma[r] - (R[3 * r] * mb[0] + R[3 * r + 1] * mb[1] + R[3 * r + 2] * mb[2]);
+    for (int r = 0; r < 3; ++r)
+        t[r] = sa[r] * inv - (R[3 * r] * mb[0] + R[3 * r + 1] * mb[1] + R[3 * r + 2] * mb[2]);
 }
 
 __global__ void __launch_bounds__(GT_THREADS) gdt_tm_kernel(const float *__restrict__ coords, int64_t N, int L,
                                                             const float *__restrict__ ref, float *__restrict__ out)
 {
-    extern __shared__ double gs[];  // reference a[L][3], then model b[L][3]
+    // reference and model as given (fa, fb) and centred on their centroids in FP32 (ca, cb)
+    extern __shared__ float4 gsm[];
+    float4 *fa = gsm, *fb = gsm + L, *ca = gsm + 2 * L, *cb = gsm + 3 * L;
     __shared__ int wbest_c[GT_WARPS][4];
     __shared__ float wbest_f[GT_WARPS][2];
-    double *sa = gs, *sb = gs + 3 * L;
+    __shared__ float s_cen[6];
+    __shared__ float s_red[GT_WARPS][7];
     const int64_t m = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     bool ok = true;
-    for (int t = threadIdx.x; t < 3 * L; t += blockDim.x) {
-        const float va = __ldg(ref + t), vb = __ldg(coords + m * (int64_t)L * 3 + t);
-        ok = ok && isfinite(va) && isfinite(vb);
-        sa[t] = (double)va;
-        sb[t] = (double)vb;
+    float part[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const float *pa = ref + 3 * i, *pb = coords + (m * (int64_t)L + i) * 3;
+        const float4 va = make_float4(__ldg(pa), __ldg(pa + 1), __ldg(pa + 2), 0.f);
+        const float4 vb = make_float4(__ldg(pb), __ldg(pb + 1), __ldg(pb + 2), 0.f);
+        ok = ok && isfinite(va.x) && isfinite(va.y) && isfinite(va.z) && isfinite(vb.x) && isfinite(vb.y) &&
+             isfinite(vb.z);
+        fa[i] = va;
+        fb[i] = vb;
+        part[0] += va.x;
+        part[1] += va.y;
+        part[2] += va.z;
+        part[3] += vb.x;
+        part[4] += vb.y;
+        part[5] += vb.z;
     }
     if (!__syncthreads_and(ok)) {
         if (threadIdx.x == 0) {
@@ -117,12 +204,42 @@ __global__ void __launch_bounds__(GT_THREADS) gdt_tm_kernel(const float *__restr
         }
         return;
     }
+    // centroids (any FP32 values serve: the centred copies are only the fast path's frame)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) part[k] = warp_sum_f(part[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s_red[warp][k] = part[k];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        float v = 0.f;
+        for (int w = 0; w < GT_WARPS; ++w) v += s_red[w][threadIdx.x];
+        s_cen[threadIdx.x] = v / (float)L;
+    }
+    __syncthreads();
+    const float cax = s_cen[0], cay = s_cen[1], caz = s_cen[2], cbx = s_cen[3], cby = s_cen[4], cbz = s_cen[5];
+    float mc = 0.f;  // largest centred coordinate
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const float4 va = fa[i], vb = fb[i];
+        const float4 a2 = make_float4(va.x - cax, va.y - cay, va.z - caz, 0.f);
+        const float4 b2 = make_float4(vb.x - cbx, vb.y - cby, vb.z - cbz, 0.f);
+        ca[i] = a2;
+        cb[i] = b2;
+        mc = fmaxf(mc, fmaxf(fmaxf(fabsf(a2.x), fabsf(a2.y)), fmaxf(fabsf(a2.z), fmaxf(fabsf(b2.x), fmaxf(fabsf(b2.y), fabsf(b2.z))))));
+    }
+    mc = warp_max_f(mc);
+    if (lane == 0) s_red[warp][6] = mc;
+    __syncthreads();
+    mc = 0.f;
+    for (int w = 0; w < GT_WARPS; ++w) mc = fmaxf(mc, s_red[w][6]);
+
     int lens[4];
     const int nl = gt_lengths(L, lens);
     int S = 0;
     for (int c = 0; c < nl; ++c) S += L - lens[c] + 1;
     const double d0 = gt_d0(L);
     const float k_tm = (float)(1.0 / (d0 * d0)), k_ms = 1.f / 12.25f;
+    const float cut[5] = {1.f, 4.f, 12.25f, 16.f, 64.f};
 
     int best_c[4] = {0, 0, 0, 0};
     float best_tm = 0.f, best_ms = 0.f;
@@ -145,32 +262,68 @@ __global__ void __launch_bounds__(GT_THREADS) gdt_tm_kernel(const float *__restr
         GtMoments mom;
         gt_zero(mom);
         if (active)
-            for (int i = s0; i < s0 + len; ++i) gt_add(mom, sa + 3 * i, sb + 3 * i);
+            for (int i = s0; i < s0 + len; ++i) gt_add(mom, fa[i], fb[i]);
         int prev = -1;
         for (int it = 0; it <= 4 && __any_sync(0xffffffffu, active); ++it) {
             double R[9], t[3];
-            if (active) gt_fit(mom, R, t);
+            float R32[9], tc[3], marg[5];
+            if (active) {
+                gt_fit(mom, R, t);
+                // the fast path's frame: x = R cb + tc - ca with tc = R c_b + t - c_a
+                float tmax = 0.f;
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) R32[3 * r + c] = (float)R[3 * r + c];
+                    tc[r] = (float)(R[3 * r] * cbx + R[3 * r + 1] * cby + R[3 * r + 2] * cbz + t[r] -
+                                    (double)(r == 0 ? cax : (r == 1 ? cay : caz)));
+                    tmax = fmaxf(tmax, fabsf(tc[r]));
+                }
+                // error bound of a component of x in FP32 (the rounded R and tc, the centring, the
+                // fused steps: about 2^-24 (15 mc + 5 |tc|), taken 4x), then of d^2 near each cutoff
+                // (2 sqrt(3) |x| dx + 3 dx^2 + the rounding of the sum of squares)
+                const float dx = 32.f * 5.9604645e-8f * (2.f * mc + tmax);
+#pragma unroll
+                for (int k = 0; k < 5; ++k) marg[k] = 3.5f * sqrtf(cut[k]) * dx + 3.f * dx * dx + 4.8e-7f * cut[k];
+            }
             GtMoments next;
             gt_zero(next);
             int c[4] = {0, 0, 0, 0};
             float tm = 0.f, ms = 0.f;
             if (active) {
                 for (int i = 0; i < L; ++i) {
-                    const double *ai = sa + 3 * i, *bi = sb + 3 * i;
-                    double d2 = 0.0;
+                    const float4 pa = ca[i], pb = cb[i];
+                    const float x0 = fmaf(R32[0], pb.x, fmaf(R32[1], pb.y, fmaf(R32[2], pb.z, tc[0]))) - pa.x;
+                    const float x1 = fmaf(R32[3], pb.x, fmaf(R32[4], pb.y, fmaf(R32[5], pb.z, tc[1]))) - pa.y;
+                    const float x2 = fmaf(R32[6], pb.x, fmaf(R32[7], pb.y, fmaf(R32[8], pb.z, tc[2]))) - pa.z;
+                    float d2 = fmaf(x0, x0, fmaf(x1, x1, x2 * x2));
+                    bool near = false;
 #pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        const double e = fma(R[3 * r], bi[0], fma(R[3 * r + 1], bi[1], fma(R[3 * r + 2], bi[2], t[r]))) - ai[r];
-                        d2 = fma(e, e, d2);
+                    for (int k = 0; k < 5; ++k) near = near || fabsf(d2 - cut[k]) < marg[k];
+                    bool in1 = d2 < 1.f, in2 = d2 < 4.f, in4 = d2 < 16.f, in8 = d2 < 64.f, sel = d2 < 12.25f;
+                    if (near) {  // rare: the decision in FP64 from the given coordinates
+                        const float4 ga = fa[i], gb = fb[i];
+                        const double bv[3] = {gb.x, gb.y, gb.z}, av[3] = {ga.x, ga.y, ga.z};
+                        double e2 = 0.0;
+#pragma unroll
+                        for (int r = 0; r < 3; ++r) {
+                            const double e = fma(R[3 * r], bv[0], fma(R[3 * r + 1], bv[1], fma(R[3 * r + 2], bv[2], t[r]))) - av[r];
+                            e2 = fma(e, e, e2);
+                        }
+                        in1 = e2 < 1.0;
+                        in2 = e2 < 4.0;
+                        in4 = e2 < 16.0;
+                        in8 = e2 < 64.0;
+                        sel = e2 < 12.25;
+                        d2 = (float)e2;
                     }
-                    c[0] += d2 < 1.0;
-                    c[1] += d2 < 4.0;
-                    c[2] += d2 < 16.0;
-                    c[3] += d2 < 64.0;
-                    const float df = (float)d2;
-                    tm += __frcp_rn(fmaf(df, k_tm, 1.f));
-                    ms += __frcp_rn(fmaf(df, k_ms, 1.f));
-                    if (d2 < 12.25) gt_add(next, ai, bi);
+                    c[0] += in1;
+                    c[1] += in2;
+                    c[2] += in4;
+                    c[3] += in8;
+                    tm += __frcp_rn(fmaf(d2, k_tm, 1.f));
+                    ms += __frcp_rn(fmaf(d2, k_ms, 1.f));
+                    if (sel) gt_add(next, fa[i], fb[i]);
                 }
 #pragma unroll
                 for (int k = 0; k < 4; ++k) best_c[k] = max(best_c[k], c[k]);
@@ -218,7 +371,7 @@ __global__ void __launch_bounds__(GT_THREADS) gdt_tm_kernel(const float *__restr
 inline int gdt_tm_launch(const float *coords, int64_t N, int64_t L, const float *ref, float *out, cudaStream_t st,
                          std::string &err)
 {
-    const size_t smem = (size_t)L * 6 * sizeof(double);
+    const size_t smem = (size_t)L * 4 * sizeof(float4);
     cudaError_t e = cudaSuccess;
     // the static shared arrays count against the default 48 KB too, so the dynamic limit is raised
     // whenever the staged coordinates come near it
