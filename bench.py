@@ -38,7 +38,7 @@ METRIC = "all-vs-all cRMSD pairs/s (fwd+bwd step) at max err <= 1e-3 A"
 UNIT = "pairs/s"
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=200)
@@ -53,7 +53,7 @@ def parse():
                    help="skip the dRMSD, contact map overlap and GDT / TM-score measurements")
     p.add_argument("--cpu-models", type=int, default=5000, help="models in the oracle's timed sample")
     p.add_argument("--ref-models", type=int, default=800, help="models per step of the reference arm")
-    return p.parse_args()
+    return p.parse_args(argv)
 
 
 def dist_env():
@@ -61,6 +61,23 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(vals, device, world):
+    """Element-wise maximum of vals over the ranks (each time is the slowest rank's); the values
+    themselves at world size 1. The only collective of the replicas: no data crosses ranks."""
+    if world <= 1:
+        return [float(v) for v in vals]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def whole_job_rate(units_per_rank, ms, world):
+    """Units processed by all ranks per second, timed by the slowest rank."""
+    return world * units_per_rank / (ms * 1e-3)
 
 
 def workload(N, L):
@@ -327,10 +344,7 @@ def run_ours(args):
     ms = statistics.mean(step_ms)
     fms = statistics.mean(fwd_list)
     bms = statistics.mean(bwd_list)
-    if ws_ > 1:
-        t = torch.tensor([ms, fms, bms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, fms, bms = float(t[0]), float(t[1]), float(t[2])
+    ms, fms, bms = max_over_ranks([ms, fms, bms], dev, ws_)
 
     # plain-form forward for the "vs plain FP32" ratio (same GPU, same inputs)
     plain_fwd = None
@@ -414,13 +428,10 @@ def run_ours(args):
         if ws_ > 1:
             dist.barrier()
         e_ms = e2e_run(args.steps) / args.steps
-        if ws_ > 1:
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t[0])
+        e_ms = max_over_ranks([e_ms], dev, ws_)[0]
         h2d = Xh.numel() * 4 + Wh.numel() * 4 + Rh.numel() * 4
         d2h = out_h.numel() * 4 + vs_h.numel() * 4 + g_h.numel() * 4
-        e2e = {"value": ws_ * P / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+        e2e = {"value": whole_job_rate(P, e_ms, ws_), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": e_ms,
                "pipelined": "three buffer sets; uploads of step k+1 and downloads of step k-1 overlap step k",
                "l2": "working set larger than L2, no flush"}
@@ -451,10 +462,7 @@ def run_ours(args):
         dp_ms = statistics.mean(timed(dplain, 2, 1)[0])
         if clusco.sync_status() != 0:
             raise RuntimeError("device status set during the dRMSD calls: " + lib.clusco_last_error().decode())
-        if ws_ > 1:
-            t = torch.tensor([d_ms, dp_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            d_ms, dp_ms = float(t[0]), float(t[1])
+        d_ms, dp_ms = max_over_ranks([d_ms, dp_ms], dev, ws_)
         d_err = None
         if rank == 0:
             import oracle
@@ -471,7 +479,7 @@ def run_ours(args):
         Npad = (N + 127) // 128 * 128
         tiles = (Npad // 128) * (Npad // 64) - (Npad // 128) * (Npad // 128 - 1)
         executed = 4 * 2.0 * ((K + 63) // 64 * 64) * 128 * 64 * tiles  # digit classes, padded K, whole tiles
-        drmsd = {"value": ws_ * P / (d_ms * 1e-3), "unit": UNIT, "ms": d_ms, "form": "bf16_exact2",
+        drmsd = {"value": whole_job_rate(P, d_ms, ws_), "unit": UNIT, "ms": d_ms, "form": "bf16_exact2",
                  "vs_plain_fp32": dp_ms / d_ms, "plain_fp32_ms": dp_ms, "max_err_sampled_A": d_err,
                  "roofline": {"kernel": "drmsd_tc_kernel (Gram of the rounded distances, 2 K flop/pair)",
                               "launch_ms": kms, "timing": "kernel launch events" if dk_ms else "API call bracket",
@@ -505,10 +513,7 @@ def run_ours(args):
         cp_ms = statistics.mean(timed(cplain, 3, 1)[0])
         if clusco.sync_status() != 0:
             raise RuntimeError("device status set during the contact-map calls: " + lib.clusco_last_error().decode())
-        if ws_ > 1:
-            t = torch.tensor([c_ms, cp_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            c_ms, cp_ms = float(t[0]), float(t[1])
+        c_ms, cp_ms = max_over_ranks([c_ms, cp_ms], dev, ws_)
         c_err = None
         if rank == 0:
             import oracle
@@ -522,7 +527,7 @@ def run_ours(args):
                                  - oracle.cmo_pairs(e.coords, ia, ib, 8.0)).max())
         kms = ck_ms if ck_ms else c_ms
         ach = 2.0 * K * P / (kms * 1e-3) / 1e12
-        cmo = {"value": ws_ * P / (c_ms * 1e-3), "unit": UNIT, "ms": c_ms, "form": "fp8_exact", "cutoff_A": 8.0,
+        cmo = {"value": whole_job_rate(P, c_ms, ws_), "unit": UNIT, "ms": c_ms, "form": "fp8_exact", "cutoff_A": 8.0,
                "vs_plain_popcount": cp_ms / c_ms, "plain_popcount_ms": cp_ms, "max_err_sampled_pct": c_err,
                "roofline": {"kernel": "cmo_tc_kernel (Gram of the 0/1 contact maps, 2 K flop/pair)",
                             "launch_ms": kms, "timing": "kernel launch events" if ck_ms else "API call bracket",
@@ -544,10 +549,7 @@ def run_ours(args):
         g_ms = statistics.mean(timed(gfwd, 3, 1)[0])
         if clusco.sync_status() != 0:
             raise RuntimeError("device status set during the GDT / TM-score calls: " + lib.clusco_last_error().decode())
-        if ws_ > 1:
-            t = torch.tensor([g_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            g_ms = float(t[0])
+        g_ms = max_over_ranks([g_ms], dev, ws_)[0]
         g_err, g_cpu = None, None
         if rank == 0:
             import oracle
@@ -558,7 +560,7 @@ def run_ours(args):
             g_err = float(np.abs(out_g.cpu().numpy()[idx].astype(np.float64) - want).max())
             g_cpu = {"value": len(idx) / dt, "unit": "models/s", "cores": oracle.max_threads(), "kind": "oracle",
                      "sample": f"{len(idx)} sampled models against the native, {dt:.1f} s"}
-        gdt = {"value": ws_ * N / (g_ms * 1e-3), "unit": "models/s", "ms": g_ms,
+        gdt = {"value": whole_job_rate(N, g_ms, ws_), "unit": "models/s", "ms": g_ms,
                "scores": "GDT_TS, TM-score, MaxSub", "reference": "first native",
                "max_abs_diff_sampled": g_err, "cpu_baseline": g_cpu,
                "bound": "fp64 (superpositions and cutoff decisions in FP64)"}
@@ -600,7 +602,7 @@ def run_ours(args):
     else:
         r_bwd = rf(54.0 * L * P, ka, bms, "bwd_tc_kernel (adjoint, 54 L flop/pair)", "bwd_tc")
     dominant, other = (r_bwd, r_fwd) if r_bwd["launch_ms"] >= r_fwd["launch_ms"] else (r_fwd, r_bwd)
-    line = {"metric": METRIC, "value": ws_ * P / (ms * 1e-3), "unit": UNIT, "n_gpus": ws_, "steps": args.steps,
+    line = {"metric": METRIC, "value": whole_job_rate(P, ms, ws_), "unit": UNIT, "n_gpus": ws_, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp32_simt": "f32+f64", "tf32": "tf32+f32",
                                            "bf16x3": "bf16+f32", "bf16_exact2": "bf16(exact int)+f32/f64"}[form_name],
@@ -609,7 +611,7 @@ def run_ours(args):
                        "pairs": P, "step": "prepass + all-pairs fwd + vs-native + backward",
                        "adjoint": "from stored rotations" if use_rot else "recomputed covariances",
                        "l2": "flushed (512 MiB write) before each timed step", "parallelism": f"replicas x{ws_}"},
-            "fwd": {"value": ws_ * P / (fms * 1e-3), "unit": UNIT, "ms": fms},
+            "fwd": {"value": whole_job_rate(P, fms, ws_), "unit": UNIT, "ms": fms},
             "bwd_ms": bms,
             "vs_plain_fp32_fwd": (plain_fwd / fms) if plain_fwd else 1.0,
             "plain_fp32_fwd_ms": plain_fwd,
