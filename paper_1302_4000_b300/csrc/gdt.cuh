@@ -5,8 +5,9 @@
 // superimposed again on the atoms that came within 3.5 A, until that number repeats, fewer
 // than 3 atoms qualify, or four refinements were made.
 //
-// Layout: one block per model, the model and the reference staged in shared memory (as given,
-// and centred); each warp runs 32 seeds side by side, one per lane, so that the eigenproblem of
+// Layout: one block of four warps per model (six blocks per SM: the search is latency-bound, so
+// occupancy beats the few registers it spills), the model and the reference staged in shared
+// memory (as given, and centred); each warp runs 32 seeds side by side, one per lane, so that the eigenproblem of
 // every superposition runs once per lane instead of redundantly across a warp, and every lane
 // walks all L atoms in the same order (broadcast reads). One pass over the atoms scores a
 // superposition and accumulates the moments of the atoms it selects, which give the next fit.
@@ -29,7 +30,7 @@
 
 namespace clusco {
 
-constexpr int GT_WARPS = 8;
+constexpr int GT_WARPS = 4;
 constexpr int GT_THREADS = 32 * GT_WARPS;
 constexpr int GT_MAX_L = 1024;
 
@@ -168,7 +169,7 @@ __device__ __forceinline__ void gt_fit(const GtMoments &m, double R[9], double t
         t[r] = sa[r] * inv - (R[3 * r] * mb[0] + R[3 * r + 1] * mb[1] + R[3 * r + 2] * mb[2]);
 }
 
-__global__ void __launch_bounds__(GT_THREADS) gdt_tm_kernel(const float *__restrict__ coords, int64_t N, int L,
+__global__ void __launch_bounds__(GT_THREADS, 6) gdt_tm_kernel(const float *__restrict__ coords, int64_t N, int L,
                                                             const float *__restrict__ ref, float *__restrict__ out)
 {
     // reference and model as given (fa, fb) and centred on their centroids in FP32 (ca, cb)
