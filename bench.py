@@ -563,7 +563,8 @@ def run_ours(args):
         gdt = {"value": whole_job_rate(N, g_ms, ws_), "unit": "models/s", "ms": g_ms,
                "scores": "GDT_TS, TM-score, MaxSub", "reference": "first native",
                "max_abs_diff_sampled": g_err, "cpu_baseline": g_cpu,
-               "bound": "fp64 (superpositions and cutoff decisions in FP64)"}
+               "bound": "issue latency (per-atom distances in FP32; FP64 for each superposition's solve and "
+                        "for the distances near a cutoff)"}
         del out_g
 
     # Rooflines of the two tensor-core kernels. Algorithmic flop per pair: the forward
