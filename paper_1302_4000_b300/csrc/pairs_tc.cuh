@@ -40,7 +40,7 @@
 #include "rotation.cuh"
 
 #ifndef CLUSCO_TOL_FAST
-#define CLUSCO_TOL_FAST 2.5e-4f  // A: largest FP32 fast-path error accepted for the exact form
+#define CLUSCO_TOL_FAST 5e-4f  // A: largest FP32 fast-path error accepted for the exact form
 #endif
 
 namespace clusco {

@@ -70,9 +70,9 @@ def test_rotations_every_pair_config0():
         if form == clusco.FORM_BF16_EXACT2:
             # the rotation variant is a separate compiled kernel: the same arithmetic up to the
             # compiler's contraction choices, so the two agree within twice the FP32 fast
-            # path's accepted error (2.5e-4 A; larger errors are refined in FP64 by both)
+            # path's accepted error (5e-4 A; larger errors are refined in FP64 by both)
             d = (out - plain).abs().max().item()
-            assert d <= 5e-4, d
+            assert d <= 1e-3, d
             assert np.abs(out.double().cpu().numpy() - c_ref).max() <= 1e-3
         assert torch.all(rot[:, 9:] == 0)
         R = clusco.rotations_view(rot).double().cpu().numpy()
