@@ -882,7 +882,9 @@ inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
     e = cudaGetLastError();
     prof_mark(PROF_PAIRS, st);
     if (e == cudaSuccess && LAYOUT == TC_EXACT2) {
-        refine_flagged_kernel<<<4 * (sms > 0 ? sms : 148), 256, 0, st>>>(a.hplane, a.lplane, a.scales, a.G64, a.N,
+        // one wave (two CTAs per SM by the launch bound): with the few flagged pairs spread over
+        // many warps, a second wave only added its latency
+        refine_flagged_kernel<<<2 * (sms > 0 ? sms : 148), 256, 0, st>>>(a.hplane, a.lplane, a.scales, a.G64, a.N,
                                                                           (int)a.L, (int)a.Lp, npairs, a.out_base,
                                                                           a.flags, sink);
         e = cudaGetLastError();
