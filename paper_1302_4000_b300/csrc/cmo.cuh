@@ -391,8 +391,8 @@ inline int cmo_launch(const float *coords, int64_t N, int64_t L, float cutoff, f
     if ((rc = make_map_u8(&mA, w.map, w.Kp, w.Npad, CM_MA, err))) return rc;
     if ((rc = make_map_u8(&mB, w.map, w.Kp, w.Npad, CM_MB, err))) return rc;
     const int64_t TA = w.Npad / CM_MA, TB = w.Npad / CM_MB;
-    grouped_tiles_kernel<<<(unsigned)((TA + CM_GROUP - 1) / CM_GROUP), 128, 0, st>>>(TA, TB, CM_MA, CM_MB, CM_GROUP,
-                                                                                  w.tiles);
+    grouped_tiles_kernel<<<(unsigned)((TA + CM_GROUP - 1) / CM_GROUP), TILE_ORDER_THREADS, 0, st>>>(TA, TB, CM_MA, CM_MB,
+                                                                                      CM_GROUP, w.tiles);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaFuncSetAttribute(cmo_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CM_SMEM);
     if (e == cudaSuccess) {

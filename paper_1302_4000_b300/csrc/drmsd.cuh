@@ -284,22 +284,48 @@ __global__ void __launch_bounds__(DR_PRE_THREADS) drmsd_quant_kernel(const float
 // a < b, i.e. J >= jmin(I) = I MA / MB (MA and MB powers of two), in groups of `group` tile
 // rows; within a group J ascending, then I. The grid's concurrent tiles then share a few A
 // row panels and a few B panels, which stay in L2 while the CTAs stream K.
-__global__ void grouped_tiles_kernel(int64_t TA, int64_t TB, int MA, int MB, int group, int2 *__restrict__ tiles)
+constexpr int TILE_ORDER_THREADS = 256;
+
+__global__ void __launch_bounds__(TILE_ORDER_THREADS) grouped_tiles_kernel(int64_t TA, int64_t TB, int MA, int MB,
+                                                                        int group, int2 *__restrict__ tiles)
 {
-    // one block per group, its threads over the columns J; jmin(I) = I MA / MB with MA / MB or
+    // one block per group, its threads over the columns J (a block-wide exclusive scan of the
+    // columns' tile counts gives each column's first slot); jmin(I) = I MA / MB with MA / MB or
     // MB / MA a power of two (shifts, no 64-bit division)
+    __shared__ int64_t s_off[TILE_ORDER_THREADS];
+    __shared__ int64_t s_base;
     const int up = MA >= MB ? __ffs(MA / MB) - 1 : 0, dn = MB > MA ? __ffs(MB / MA) - 1 : 0;
     auto jmin = [&](int64_t I) { return (I << up) >> dn; };
     const int64_t I0 = (int64_t)blockIdx.x * group, I1 = min(TA, I0 + group);
     if (I0 >= TA) return;
-    int64_t t0 = 0;  // tiles of the earlier groups
-    for (int64_t I = 0; I < I0; ++I) t0 += TB - jmin(I);
+    if (threadIdx.x == 0) {
+        int64_t t0 = 0;  // tiles of the earlier groups
+        for (int64_t I = 0; I < I0; ++I) t0 += TB - jmin(I);
+        s_base = t0;
+    }
     const int64_t J0 = jmin(I0);
-    for (int64_t J = J0 + threadIdx.x; J < TB; J += blockDim.x) {
-        int64_t t = t0;
-        for (int64_t Jp = J0; Jp < J; ++Jp)
-            for (int64_t I = I0; I < I1 && jmin(I) <= Jp; ++I) ++t;
-        for (int64_t I = I0; I < I1 && jmin(I) <= J; ++I) tiles[t++] = make_int2((int)I, (int)J);
+    for (int64_t Jc = J0; Jc < TB; Jc += TILE_ORDER_THREADS) {
+        const int64_t J = Jc + threadIdx.x;
+        int64_t cnt = 0;
+        if (J < TB)
+            for (int64_t I = I0; I < I1 && jmin(I) <= J; ++I) ++cnt;
+        s_off[threadIdx.x] = cnt;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t run = s_base;
+            for (int k = 0; k < TILE_ORDER_THREADS; ++k) {
+                const int64_t v = s_off[k];
+                s_off[k] = run;
+                run += v;
+            }
+            s_base = run;
+        }
+        __syncthreads();
+        if (J < TB) {
+            int64_t t = s_off[threadIdx.x];
+            for (int64_t I = I0; I < I1 && jmin(I) <= J; ++I) tiles[t++] = make_int2((int)I, (int)J);
+        }
+        __syncthreads();
     }
 }
 
@@ -615,8 +641,8 @@ inline int drmsd_launch(const float *coords, int64_t N, int64_t L, float *out, b
     if ((rc = make_map(&mA, w.planes, false, w.Kp, 2 * w.Npad, DR_MA, err))) return rc;
     if ((rc = make_map(&mB, w.planes, false, w.Kp, 2 * w.Npad, DR_MB, err))) return rc;
     const int64_t TA = w.Npad / DR_MA, TB = w.Npad / DR_MB;
-    grouped_tiles_kernel<<<(unsigned)((TA + DR_GROUP - 1) / DR_GROUP), 128, 0, st>>>(TA, TB, DR_MA, DR_MB, DR_GROUP,
-                                                                                  w.tiles);
+    grouped_tiles_kernel<<<(unsigned)((TA + DR_GROUP - 1) / DR_GROUP), TILE_ORDER_THREADS, 0, st>>>(TA, TB, DR_MA, DR_MB,
+                                                                                      DR_GROUP, w.tiles);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaFuncSetAttribute(drmsd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)DR_SMEM);
