@@ -5,8 +5,8 @@
 // superimposed again on the atoms that came within 3.5 A, until that number repeats, fewer
 // than 3 atoms qualify, or four refinements were made.
 //
-// Layout: one block of four warps per model (six blocks per SM: the search is latency-bound, so
-// occupancy beats the few registers it spills), the model and the reference staged in shared
+// Layout: one block of four warps per model (seven blocks per SM: the search is latency-bound, so
+// occupancy beats the registers it spills), the model and the reference staged in shared
 // memory (as given, and centred); each warp runs 32 seeds side by side, one per lane, so that the eigenproblem of
 // every superposition runs once per lane instead of redundantly across a warp, and every lane
 // walks all L atoms in the same order (broadcast reads). One pass over the atoms scores a
@@ -169,7 +169,7 @@ __device__ __forceinline__ void gt_fit(const GtMoments &m, double R[9], double t
         t[r] = sa[r] * inv - (R[3 * r] * mb[0] + R[3 * r + 1] * mb[1] + R[3 * r + 2] * mb[2]);
 }
 
-__global__ void __launch_bounds__(GT_THREADS, 6) gdt_tm_kernel(const float *__restrict__ coords, int64_t N, int L,
+__global__ void __launch_bounds__(GT_THREADS, 7) gdt_tm_kernel(const float *__restrict__ coords, int64_t N, int L,
                                                             const float *__restrict__ ref, float *__restrict__ out)
 {
     // reference and model as given (fa, fb) and centred on their centroids in FP32 (ca, cb)
@@ -322,8 +322,12 @@ __global__ void __launch_bounds__(GT_THREADS, 6) gdt_tm_kernel(const float *__re
                     c[1] += in2;
                     c[2] += in4;
                     c[3] += in8;
-                    tm += __frcp_rn(fmaf(d2, k_tm, 1.f));
-                    ms += __frcp_rn(fmaf(d2, k_ms, 1.f));
+                    // both terms from one approximate reciprocal, 1/qa = qb/(qa qb) and 1/qb = qa/(qa qb)
+                    // (a few ulp each, far inside the FP32 sum's own rounding)
+                    const float qa = fmaf(d2, k_tm, 1.f), qb = fmaf(d2, k_ms, 1.f);
+                    const float rq = __fdividef(1.f, qa * qb);
+                    tm = fmaf(qb, rq, tm);
+                    ms = fmaf(qa, rq, ms);
                     if (sel) gt_add(next, fa[i], fb[i]);
                 }
 #pragma unroll
