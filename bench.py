@@ -445,10 +445,35 @@ def run_ours(args):
         e_ms = max_over_ranks([e_ms], dev, ws_)[0]
         h2d = Xh.numel() * 4 + Wh.numel() * 4 + Rh.numel() * 4
         d2h = out_h.numel() * 4 + vs_h.numel() * 4 + g_h.numel() * 4
+        # The host link's own rates with the same pinned buffers (the weights up, the matrix
+        # down): one direction at a time, then both at once, as the pipelined steps run them.
+        # With both directions busy the step cannot take less than its larger byte count at
+        # the concurrent rate.
+        b0 = bufs[0]
+        up = lambda: b0["W"].copy_(Wh, non_blocking=True)
+        down = lambda: out_h.copy_(b0["out"], non_blocking=True)
+
+        def link_gbs(pairs, nrep=5):
+            for st, fn in pairs:
+                with torch.cuda.stream(st):
+                    fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(nrep):
+                for st, fn in pairs:
+                    with torch.cuda.stream(st):
+                        fn()
+            torch.cuda.synchronize()
+            return nrep * Wh.numel() * 4 / (time.perf_counter() - t0) / 1e9
+        l_up = link_gbs([(s_in, up)])
+        l_down = link_gbs([(s_out, down)])
+        l_both = link_gbs([(s_in, up), (s_out, down)])
         e2e = {"value": whole_job_rate(P, e_ms, ws_), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": e_ms,
                "pipelined": "three buffer sets; uploads of step k+1 and downloads of step k-1 overlap step k",
-               "l2": "working set larger than L2, no flush"}
+               "l2": "working set larger than L2, no flush",
+               "link_GBs": {"h2d": l_up, "d2h": l_down, "each_way_when_both": l_both,
+                            "floor_ms_per_step": max(h2d, d2h) / (l_both * 1e6)}}
         del bufs
 
     hbm, bf16, bf16_sus, pk_kind = peaks()

@@ -266,51 +266,74 @@ __device__ __forceinline__ float sigma_hat_f32(const float m[9])
 // takes Sigma (of m) as computed; both return false, leaving R unset, where P' falls below
 // 1e-2 of 8 Sigma^3 (near a double root, where this quotient loses accuracy); the caller then
 // takes the eigenvector route of rotation.cuh.
-// The rotation from m, its minors mn (minors3), det, I1 and Sigma s.
+__device__ __forceinline__ float2 f2b(float x) { return make_float2(x, x); }
+
+// The rotation from m, its minors mn (minors3), det, I1 and Sigma s. Columns 0 and 1 of every
+// 3 x 3 product go through the paired FP32 instructions (__ffma2_rn: two IEEE FMAs per
+// instruction), column 2 through scalar FMAs.
 __device__ __forceinline__ bool rotation_core_f32(const float m[9], const float mn[9], float det, float I1, float s,
                                                   float R[9])
 {
     const float s2 = s * s;
     const float dP = fmaf(fmaf(4.f, s2, -4.f * I1), s, -8.f * det);
     if (!(dP > 8e-2f * s2 * s)) return false;
-    // cofactor matrix (signed minors), row-major
-    const float cf[9] = {mn[2], -mn[1], mn[0], -mn[5], mn[4], -mn[3], mn[8], -mn[7], mn[6]};
-    // g = m^T m (symmetric)
-    const float g00 = m[0] * m[0] + m[3] * m[3] + m[6] * m[6];
-    const float g01 = m[0] * m[1] + m[3] * m[4] + m[6] * m[7];
-    const float g02 = m[0] * m[2] + m[3] * m[5] + m[6] * m[8];
-    const float g11 = m[1] * m[1] + m[4] * m[4] + m[7] * m[7];
-    const float g12 = m[1] * m[2] + m[4] * m[5] + m[7] * m[8];
-    const float g22 = m[2] * m[2] + m[5] * m[5] + m[8] * m[8];
+    // cofactor matrix (signed minors), row-major: columns 0, 1 as pairs, column 2 alone
+    const float2 cf01[3] = {make_float2(mn[2], -mn[1]), make_float2(-mn[5], mn[4]), make_float2(mn[8], -mn[7])};
+    const float cf2[3] = {mn[0], -mn[3], mn[6]};
+    float2 v[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[i] = make_float2(m[3 * i], m[3 * i + 1]);
+    // g = m^T m (symmetric): (g00, g11), (g02, g12) as pairs
+    float2 gd = __fmul2_rn(v[0], v[0]);
+    gd = __ffma2_rn(v[1], v[1], gd);
+    gd = __ffma2_rn(v[2], v[2], gd);
+    float2 gc = __fmul2_rn(v[0], f2b(m[2]));
+    gc = __ffma2_rn(v[1], f2b(m[5]), gc);
+    gc = __ffma2_rn(v[2], f2b(m[8]), gc);
+    const float g01 = fmaf(m[6], m[7], fmaf(m[3], m[4], m[0] * m[1]));
+    const float g22 = fmaf(m[8], m[8], fmaf(m[5], m[5], m[2] * m[2]));
+    const float2 gA = make_float2(gd.x, g01), gB = make_float2(g01, gd.y);
     const float inv = __fdividef(1.f, dP);
     const float al = 4.f * (I1 + s2) * inv, be = 8.f * s * inv, ga = -8.f * inv;
+    float2 R01[3];
+    float R2[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const float r0 = m[3 * i], r1 = m[3 * i + 1], r2 = m[3 * i + 2];
-        const float mg0 = r0 * g00 + r1 * g01 + r2 * g02;
-        const float mg1 = r0 * g01 + r1 * g11 + r2 * g12;
-        const float mg2 = r0 * g02 + r1 * g12 + r2 * g22;
-        R[3 * i + 0] = fmaf(al, r0, fmaf(ga, mg0, be * cf[3 * i + 0]));
-        R[3 * i + 1] = fmaf(al, r1, fmaf(ga, mg1, be * cf[3 * i + 1]));
-        R[3 * i + 2] = fmaf(al, r2, fmaf(ga, mg2, be * cf[3 * i + 2]));
+        float2 mg = __fmul2_rn(f2b(r0), gA);
+        mg = __ffma2_rn(f2b(r1), gB, mg);
+        mg = __ffma2_rn(f2b(r2), gc, mg);
+        const float mg2 = fmaf(r2, g22, fmaf(r1, gc.y, r0 * gc.x));
+        float2 t = __fmul2_rn(f2b(be), cf01[i]);
+        t = __ffma2_rn(f2b(ga), mg, t);
+        R01[i] = __ffma2_rn(f2b(al), v[i], t);
+        R2[i] = fmaf(al, r2, fmaf(ga, mg2, be * cf2[i]));
     }
     // The quotient inherits Sigma's FP32 error amplified by about Q/P', mostly as a departure
     // from orthogonality; one Newton-Schulz step R <- R (3 I - R^T R) / 2 removes that to
-    // second order (the polar factor of R is the nearest rotation).
-    const float q00 = R[0] * R[0] + R[3] * R[3] + R[6] * R[6];
-    const float q01 = R[0] * R[1] + R[3] * R[4] + R[6] * R[7];
-    const float q02 = R[0] * R[2] + R[3] * R[5] + R[6] * R[8];
-    const float q11 = R[1] * R[1] + R[4] * R[4] + R[7] * R[7];
-    const float q12 = R[1] * R[2] + R[4] * R[5] + R[7] * R[8];
-    const float q22 = R[2] * R[2] + R[5] * R[5] + R[8] * R[8];
-    const float t00 = 1.5f - 0.5f * q00, t11 = 1.5f - 0.5f * q11, t22 = 1.5f - 0.5f * q22;
-    const float t01 = -0.5f * q01, t02 = -0.5f * q02, t12 = -0.5f * q12;
+    // second order (the polar factor of R is the nearest rotation). q = R^T R with (q00, q11),
+    // (q02, q12) as pairs.
+    float2 qd = __fmul2_rn(R01[0], R01[0]);
+    qd = __ffma2_rn(R01[1], R01[1], qd);
+    qd = __ffma2_rn(R01[2], R01[2], qd);
+    float2 qc = __fmul2_rn(R01[0], f2b(R2[0]));
+    qc = __ffma2_rn(R01[1], f2b(R2[1]), qc);
+    qc = __ffma2_rn(R01[2], f2b(R2[2]), qc);
+    const float q01 = fmaf(R01[2].x, R01[2].y, fmaf(R01[1].x, R01[1].y, R01[0].x * R01[0].y));
+    const float q22 = fmaf(R2[2], R2[2], fmaf(R2[1], R2[1], R2[0] * R2[0]));
+    const float2 td = __ffma2_rn(f2b(-0.5f), qd, f2b(1.5f));  // (t00, t11)
+    const float2 tc = __fmul2_rn(f2b(-0.5f), qc);             // (t02, t12)
+    const float t01 = -0.5f * q01, t22 = fmaf(-0.5f, q22, 1.5f);
+    const float2 tA = make_float2(td.x, t01), tB = make_float2(t01, td.y);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const float r0 = R[3 * i], r1 = R[3 * i + 1], r2 = R[3 * i + 2];
-        R[3 * i + 0] = r0 * t00 + r1 * t01 + r2 * t02;
-        R[3 * i + 1] = r0 * t01 + r1 * t11 + r2 * t12;
-        R[3 * i + 2] = r0 * t02 + r1 * t12 + r2 * t22;
+        const float r0 = R01[i].x, r1 = R01[i].y, r2 = R2[i];
+        float2 o = __fmul2_rn(f2b(r0), tA);
+        o = __ffma2_rn(f2b(r1), tB, o);
+        o = __ffma2_rn(f2b(r2), tc, o);
+        R[3 * i + 0] = o.x;
+        R[3 * i + 1] = o.y;
+        R[3 * i + 2] = fmaf(r2, t22, fmaf(r1, tc.y, r0 * tc.x));
     }
     return true;
 }
