@@ -5,7 +5,7 @@
 // superimposed again on the atoms that came within 3.5 A, until that number repeats, fewer
 // than 3 atoms qualify, or four refinements were made.
 //
-// Layout: one block of four warps per model (seven blocks per SM: the search is latency-bound, so
+// Layout: one block of four warps per model (six blocks per SM: the search is latency-bound, so
 // occupancy beats the registers it spills), the model and the reference staged in shared
 // memory (as given, and centred); each warp runs 32 seeds side by side, one per lane, so that the eigenproblem of
 // every superposition runs once per lane instead of redundantly across a warp, and every lane
@@ -169,7 +169,7 @@ __device__ __forceinline__ void gt_fit(const GtMoments &m, double R[9], double t
         t[r] = sa[r] * inv - (R[3 * r] * mb[0] + R[3 * r + 1] * mb[1] + R[3 * r + 2] * mb[2]);
 }
 
-__global__ void __launch_bounds__(GT_THREADS, 7) gdt_tm_kernel(const float *__restrict__ coords, int64_t N, int L,
+__global__ void __launch_bounds__(GT_THREADS, 6) gdt_tm_kernel(const float *__restrict__ coords, int64_t N, int L,
                                                             const float *__restrict__ ref, float *__restrict__ out)
 {
     // reference and model as given (fa, fb) and centred on their centroids in FP32 (ca, cb)
@@ -179,6 +179,9 @@ __global__ void __launch_bounds__(GT_THREADS, 7) gdt_tm_kernel(const float *__re
     __shared__ float wbest_f[GT_WARPS][2];
     __shared__ float s_cen[6];
     __shared__ float s_red[GT_WARPS][7];
+    // each lane's current superposition in FP64 (R row-major, then t), read only by the rare
+    // re-check near a cutoff, so that the atom loop does not hold it in registers
+    __shared__ double s_rt[GT_WARPS][12][32];
     const int64_t m = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     bool ok = true;
@@ -266,10 +269,14 @@ __global__ void __launch_bounds__(GT_THREADS, 7) gdt_tm_kernel(const float *__re
             for (int i = s0; i < s0 + len; ++i) gt_add(mom, fa[i], fb[i]);
         int prev = -1;
         for (int it = 0; it <= 4 && __any_sync(0xffffffffu, active); ++it) {
-            double R[9], t[3];
             float R32[9], tc[3], marg[5];
             if (active) {
+                double R[9], t[3];
                 gt_fit(mom, R, t);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) s_rt[warp][k][lane] = R[k];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) s_rt[warp][9 + k][lane] = t[k];
                 // the fast path's frame: x = R cb + tc - ca with tc = R c_b + t - c_a
                 float tmax = 0.f;
 #pragma unroll
@@ -308,7 +315,10 @@ __global__ void __launch_bounds__(GT_THREADS, 7) gdt_tm_kernel(const float *__re
                         double e2 = 0.0;
 #pragma unroll
                         for (int r = 0; r < 3; ++r) {
-                            const double e = fma(R[3 * r], bv[0], fma(R[3 * r + 1], bv[1], fma(R[3 * r + 2], bv[2], t[r]))) - av[r];
+                            const double e = fma(s_rt[warp][3 * r][lane], bv[0],
+                                                 fma(s_rt[warp][3 * r + 1][lane], bv[1],
+                                                     fma(s_rt[warp][3 * r + 2][lane], bv[2], s_rt[warp][9 + r][lane]))) -
+                                             av[r];
                             e2 = fma(e, e, e2);
                         }
                         in1 = e2 < 1.0;
@@ -378,9 +388,9 @@ inline int gdt_tm_launch(const float *coords, int64_t N, int64_t L, const float 
 {
     const size_t smem = (size_t)L * 4 * sizeof(float4);
     cudaError_t e = cudaSuccess;
-    // the static shared arrays count against the default 48 KB too, so the dynamic limit is raised
-    // whenever the staged coordinates come near it
-    if (smem > 40 * 1024) e = cudaFuncSetAttribute(gdt_tm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the static shared arrays (12.5 KB) count against the default 48 KB too, so the dynamic limit
+    // is raised whenever the staged coordinates come near it
+    if (smem > 32 * 1024) e = cudaFuncSetAttribute(gdt_tm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
         gdt_tm_kernel<<<(unsigned)N, GT_THREADS, smem, st>>>(coords, N, (int)L, ref, out);
         e = cudaGetLastError();

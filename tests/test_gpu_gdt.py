@@ -35,10 +35,12 @@ def check(got, ref):
     assert np.all(np.abs(got[:, 1:] - ref[:, 1:]) <= 1e-5), np.abs(got[:, 1:] - ref[:, 1:]).max()
 
 
-@pytest.mark.parametrize("N,L", [(200, 100), (64, 3), (64, 4), (64, 5), (64, 15), (64, 16), (64, 33), (48, 300)])
+@pytest.mark.parametrize("N,L", [(200, 100), (64, 3), (64, 4), (64, 5), (64, 15), (64, 16), (64, 33), (48, 300),
+                                 (8, 600)])
 def test_scores_match_oracle(N, L):
     """L from the smallest chain (3 atoms: only the whole-chain seed) through lengths where
-    4 = L/4 repeats or L/4 < 3 drops, to 300 atoms."""
+    4 = L/4 repeats or L/4 < 3 drops, to 300 atoms, and 600 atoms (the staged chain alone below
+    the default 48 KB of shared memory, with the kernel's static arrays above it)."""
     e = E.decoy_ensemble(N, L, 2, (0.3, 6.0), seed=13024700 + L)
     ref = e.coords[0]
     got = run(e.coords, ref)
