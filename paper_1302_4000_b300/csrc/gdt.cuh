@@ -5,8 +5,8 @@
 // superimposed again on the atoms that came within 3.5 A, until that number repeats, fewer
 // than 3 atoms qualify, or four refinements were made.
 //
-// Layout: one block of four warps per model (six blocks per SM: the search is latency-bound, so
-// occupancy beats the registers it spills), the model and the reference staged in shared
+// Layout: one block of four warps per model (five blocks per SM, where the latency-bound search
+// balances occupancy against the registers it spills), the model and the reference staged in shared
 // memory (as given, and centred); each warp runs 32 seeds side by side, one per lane, so that the eigenproblem of
 // every superposition runs once per lane instead of redundantly across a warp, and every lane
 // walks all L atoms in the same order (broadcast reads). One pass over the atoms scores a
@@ -14,8 +14,8 @@
 //
 // Precision (B300's FP64 rate is 1/64 of FP32, so FP64 is kept off the per-atom path): the
 // moments (sums of a, b, a b^T over the selected atoms) are accumulated from the given FP32
-// coordinates as double-float pairs (exact products by FMA, compensated sums), good to about
-// 2^-48; the superposition is solved in FP64 from them (the largest root of the key matrix's
+// coordinates as double-float values (exact products by FMA, compensated sums; two accumulators
+// per paired FP32 instruction), good to about 2^-48; the superposition is solved in FP64 from them (the largest root of the key matrix's
 // quartic by Newton from an upper bound, the rotation from the adjugate of K - lambda I, cyclic
 // Jacobi sweeps where that root is nearly repeated); each atom's squared distance is then taken
 // in FP32 in the centred frame, and where it falls within its error bound of a cutoff
@@ -56,57 +56,60 @@ __device__ __forceinline__ int gt_lengths(int L, int (&lens)[4])
     return n;
 }
 
-// Double-float accumulator: hi + lo, with the rounding error of every addition carried in lo
-// (Knuth's two-sum) and products split exactly by FMA. The _rn intrinsics keep the compiler from
-// contracting the error terms away.
-struct GtDF {
-    float hi, lo;
-};
+// Double-float accumulators: hi + lo, with the rounding error of every addition carried in lo
+// (Knuth's two-sum) and products split exactly by FMA, kept in pairs so that two accumulators
+// advance per paired FP32 instruction (__fadd2_rn, __ffma2_rn: each half an IEEE operation,
+// the same sequence per accumulator as one at a time). The _rn intrinsics keep the compiler
+// from contracting the error terms away.
+__device__ __forceinline__ float2 gt_neg2(float2 v) { return make_float2(-v.x, -v.y); }
 
-__device__ __forceinline__ void df_add(GtDF &s, float v)
+__device__ __forceinline__ void df2_add(float2 &hi, float2 &lo, float2 v)
 {
-    const float t = __fadd_rn(s.hi, v);
-    const float bp = __fsub_rn(t, s.hi);
-    const float err = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bp)), __fsub_rn(v, bp));
-    s.hi = t;
-    s.lo = __fadd_rn(s.lo, err);
+    const float2 t = __fadd2_rn(hi, v);
+    const float2 bp = __fadd2_rn(t, gt_neg2(hi));
+    const float2 err = __fadd2_rn(__fadd2_rn(hi, gt_neg2(__fadd2_rn(t, gt_neg2(bp)))), __fadd2_rn(v, gt_neg2(bp)));
+    hi = t;
+    lo = __fadd2_rn(lo, err);
 }
 
-__device__ __forceinline__ void df_add_prod(GtDF &s, float a, float b)
+__device__ __forceinline__ void df2_add_prod(float2 &hi, float2 &lo, float2 a, float2 b)
 {
-    const float p = __fmul_rn(a, b);
-    const float e = fmaf(a, b, -p);  // a b - p exactly
-    df_add(s, p);
-    s.lo = __fadd_rn(s.lo, e);
+    const float2 p = __fmul2_rn(a, b);
+    const float2 e = __ffma2_rn(a, b, gt_neg2(p));  // a b - p exactly, per half
+    df2_add(hi, lo, p);
+    lo = __fadd2_rn(lo, e);
 }
 
-__device__ __forceinline__ double df_value(const GtDF &s) { return (double)s.hi + (double)s.lo; }
-
-// Moments of a set of atom pairs (a_i reference, b_i model, as given): sums of a, b and a b^T.
+// Moments of a set of atom pairs (a_i reference, b_i model, as given): sums of a (slots 0..2),
+// b (3..5) and a b^T (6..14, row-major); slot k is half k % 2 of pair k / 2 (slot 15 unused).
 struct GtMoments {
-    GtDF sa[3], sb[3], sab[9];
+    float2 hi[8], lo[8];
     int n;
 };
+
+__device__ __forceinline__ double gt_slot(const GtMoments &m, int k)
+{
+    const float2 h = m.hi[k >> 1], l = m.lo[k >> 1];
+    return (k & 1) ? (double)h.y + (double)l.y : (double)h.x + (double)l.x;
+}
 
 __device__ __forceinline__ void gt_zero(GtMoments &m)
 {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) m.sa[k] = m.sb[k] = GtDF{0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < 9; ++k) m.sab[k] = GtDF{0.f, 0.f};
+    for (int k = 0; k < 8; ++k) m.hi[k] = m.lo[k] = make_float2(0.f, 0.f);
     m.n = 0;
 }
 
 __device__ __forceinline__ void gt_add(GtMoments &m, const float4 &a, const float4 &b)
 {
-    const float av[3] = {a.x, a.y, a.z}, bv[3] = {b.x, b.y, b.z};
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        df_add(m.sa[r], av[r]);
-        df_add(m.sb[r], bv[r]);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) df_add_prod(m.sab[3 * r + c], av[r], bv[c]);
-    }
+    df2_add(m.hi[0], m.lo[0], make_float2(a.x, a.y));
+    df2_add(m.hi[1], m.lo[1], make_float2(a.z, b.x));
+    df2_add(m.hi[2], m.lo[2], make_float2(b.y, b.z));
+    df2_add_prod(m.hi[3], m.lo[3], make_float2(a.x, a.x), make_float2(b.x, b.y));
+    df2_add_prod(m.hi[4], m.lo[4], make_float2(a.x, a.y), make_float2(b.z, b.x));
+    df2_add_prod(m.hi[5], m.lo[5], make_float2(a.y, a.y), make_float2(b.y, b.z));
+    df2_add_prod(m.hi[6], m.lo[6], make_float2(a.z, a.z), make_float2(b.x, b.y));
+    df2_add_prod(m.hi[7], m.lo[7], make_float2(a.z, 0.f), make_float2(b.z, 0.f));
     ++m.n;
 }
 
@@ -156,20 +159,20 @@ __device__ __forceinline__ void gt_fit(const GtMoments &m, double R[9], double t
     double sa[3], mb[3], H[9];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        sa[k] = df_value(m.sa[k]);
-        mb[k] = df_value(m.sb[k]) * inv;
+        sa[k] = gt_slot(m, k);
+        mb[k] = gt_slot(m, 3 + k) * inv;
     }
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) H[3 * r + c] = df_value(m.sab[3 * r + c]) - sa[r] * mb[c];
+        for (int c = 0; c < 3; ++c) H[3 * r + c] = gt_slot(m, 6 + 3 * r + c) - sa[r] * mb[c];
     gt_rotation(H, R);
 #pragma unroll
     for (int r = 0; r < 3; ++r)
         t[r] = sa[r] * inv - (R[3 * r] * mb[0] + R[3 * r + 1] * mb[1] + R[3 * r + 2] * mb[2]);
 }
 
-__global__ void __launch_bounds__(GT_THREADS, 6) gdt_tm_kernel(const float *__restrict__ coords, int64_t N, int L,
+__global__ void __launch_bounds__(GT_THREADS, 5) gdt_tm_kernel(const float *__restrict__ coords, int64_t N, int L,
                                                             const float *__restrict__ ref, float *__restrict__ out)
 {
     // reference and model as given (fa, fb) and centred on their centroids in FP32 (ca, cb)
