@@ -150,16 +150,18 @@ def csrc_hash():
     return h.hexdigest()
 
 
-def traffic_for(key):
-    """DRAM bytes per launch of a kernel from its committed ncu summary, or None once any
-    library source has changed since the counters were taken (csrc_hash recorded beside them)."""
+def traffic_for(key, N, L):
+    """DRAM bytes per launch of a kernel from its committed ncu summary, or None for another
+    workload than the one captured (N models of L atoms) or once any library source has changed
+    since the counters were taken (csrc_hash recorded beside them)."""
     try:
         h = csrc_hash()
         for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
             parts = line.split()
-            if len(parts) == 4 and parts[0] == key and parts[1] == h:
-                return float(parts[2])
-    except OSError:
+            if (len(parts) == 6 and parts[0] == key and parts[1] == h and int(parts[2]) == N
+                    and int(parts[3]) == L):
+                return float(parts[4])
+    except (OSError, ValueError):
         pass
     return None
 
@@ -525,7 +527,7 @@ def run_ours(args):
                               "bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
                               "frac": ach / bf16, "peak_kind": f"{pk_kind} bf16 burst",
                               "executed_tflops": executed / (kms * 1e-3) / 1e12,
-                              "traffic": traffic_for("drmsd_tc")}}
+                              "traffic": traffic_for("drmsd_tc", N, L)}}
         del ws_d, out_d, ws_dp, out_dp
 
     # All-versus-all contact map overlap (eq. 6, eq. 7) at an 8 A cutoff: the tensor-core form
@@ -572,7 +574,7 @@ def run_ours(args):
                             "launch_ms": kms, "timing": "kernel launch events" if ck_ms else "API call bracket",
                             "bound": "tensor", "achieved": ach, "peak": 2.0 * bf16, "unit": "TFLOP/s",
                             "frac": ach / (2.0 * bf16), "peak_kind": f"{pk_kind} bf16 burst x 2 (FP8 nominal ratio)",
-                            "traffic": traffic_for("cmo_tc")}}
+                            "traffic": traffic_for("cmo_tc", N, L)}}
         del ws_c, out_c, ws_cp, out_cp
 
     # GDT_TS / TM-score / MaxSub of every model against its first native (eq. 3, eq. 4; the
@@ -615,7 +617,7 @@ def run_ours(args):
     def rf(flop, kms, call_ms, kernel, hash_key, hbm_bytes=None):
         msec = kms if kms else call_ms
         r = {"kernel": kernel, "launch_ms": msec, "timing": "kernel launch events" if kms else "API call bracket",
-             "traffic": traffic_for(hash_key)}
+             "traffic": traffic_for(hash_key, N, L)}
         if hbm_bytes is None:
             ach = flop / (msec * 1e-3) / 1e12
             r.update({"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
