@@ -280,6 +280,14 @@ def run_ours(args):
             clusco.crmsd_allpairs_backward_rot(Xd, Wd, o, rot, 1e-6, grad_coords=gr, workspace=ws_bw, stream=st)
         else:
             clusco.crmsd_allpairs_backward(Xd, Wd, o, 1e-6, form, grad_coords=gr, workspace=ws_bw, stream=st)
+    # the fused step (forward, then the adjoint from its rotations, in one call: the adjoint's
+    # pre-pass runs beside the forward on the library's own stream)
+    ws_st = (torch.empty(clusco.workspace_bytes(clusco.OP_STEP_ROT, N, L, form), dtype=torch.uint8, device=dev)
+             if use_rot else None)
+
+    def fused(Xd, Wd, o=None, gr=None, st=None):
+        clusco.crmsd_allpairs_step_rot(Xd, Wd, form, 1e-6, out=out if o is None else o, rot=rot,
+                                       grad_coords=grad if gr is None else gr, workspace=ws_st, stream=st)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -290,7 +298,8 @@ def run_ours(args):
     side = torch.cuda.Stream()
     fork, join = torch.cuda.Event(), torch.cuda.Event()
 
-    def step(evs=None):
+    def step_split(evs=None):
+        # the two calls in turn, with events between them: the forward / adjoint breakdown
         if evs:
             evs[0].record(stream)
         fork.record(stream)
@@ -305,6 +314,17 @@ def run_ours(args):
         stream.wait_event(join)
         if evs:
             evs[3].record(stream)
+
+    def step():
+        # the timed step: the fused call where rotations are stored, else the two calls
+        if not use_rot:
+            return step_split()
+        fork.record(stream)
+        side.wait_event(fork)
+        clusco.crmsd_vs_ref(X, ref, out=vs, workspace=ws_vs, stream=side)
+        join.record(side)
+        fused(X, W)
+        stream.wait_event(join)
 
     # our kernels per step: forward (pre-pass + pairs, + the refinement of flagged pairs in the
     # exact-digit form, + the deferred-rotation kernel when storing rotations); ref pre-pass + vs-ref; adjoint from stored rotations (pre-pass, FP16
@@ -344,7 +364,7 @@ def run_ours(args):
 
     clocks = Clocks(local if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
     clocks.start()
-    step_ms, fwd_list, bwd_list = timed(step, args.steps, args.warmup, split=True, prof=True)
+    step_ms = timed(step, args.steps, args.warmup, prof=True)[0]
     clk = clocks.stop()
     # per-launch device time of the two tensor-core kernels inside the timed steps
     kern = {}
@@ -353,6 +373,7 @@ def run_ours(args):
         kern[name] = (tot_ms / n, n) if n else (None, 0)
     if clusco.sync_status() != 0:
         raise RuntimeError("device status set during the timed steps: " + lib.clusco_last_error().decode())
+    _, fwd_list, bwd_list = timed(step_split, max(3, args.steps // 4), 2, split=True)
     ms = statistics.mean(step_ms)
     fms = statistics.mean(fwd_list)
     bms = statistics.mean(bwd_list)
@@ -426,6 +447,8 @@ def run_ours(args):
                 s_vs.wait_event(b["in_ready"])
                 clusco.crmsd_vs_ref(b["X"], b["R"], out=b["vs"], workspace=ws_vs, stream=s_vs)
                 b["vs_done"].record(s_vs)
+                # the two calls in turn: with the host link the bound here, the fused call's side
+                # stream measured 1.2 % slower per step (1.911 against 1.888 ms) in this pipeline
                 forward(b["X"], o=b["out"], st=s_cmp)
                 backward(b["X"], b["W"], o=b["out"], gr=b["g"], st=s_cmp)
                 s_cmp.wait_event(b["vs_done"])
@@ -473,6 +496,7 @@ def run_ours(args):
         e2e = {"value": whole_job_rate(P, e_ms, ws_), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": e_ms,
                "pipelined": "three buffer sets; uploads of step k+1 and downloads of step k-1 overlap step k",
+               "calls": "forward and backward in turn (the faster of the two public paths here)",
                "l2": "working set larger than L2, no flush",
                "link_GBs": {"h2d": l_up, "d2h": l_down, "each_way_when_both": l_both,
                             "floor_ms_per_step": max(h2d, d2h) / (l_both * 1e6)}}
@@ -650,7 +674,10 @@ def run_ours(args):
                                            "bf16x3": "bf16+f32", "bf16_exact2": "bf16(exact int)+f32/f64"}[form_name],
             "data": "synthetic",
             "config": {"workload": f"decoy ensemble N={N} L={L}, 5 natives, sigma~U(0.5,10) A", "form": form_name,
-                       "pairs": P, "step": "prepass + all-pairs fwd + vs-native + backward",
+                       "pairs": P,
+                       "step": ("prepass + all-pairs fwd + vs-native + backward"
+                                + (" (fwd and backward in one call, the backward's pre-pass beside the fwd; fwd and"
+                                   " bwd_ms from the two calls in turn)" if use_rot else "")),
                        "adjoint": "from stored rotations" if use_rot else "recomputed covariances",
                        "l2": "flushed (512 MiB write) before each timed step", "parallelism": f"replicas x{ws_}"},
             "fwd": {"value": whole_job_rate(P, fms, ws_), "unit": UNIT, "ms": fms},

@@ -79,7 +79,8 @@ typedef enum {
     CLUSCO_OP_BACKWARD_ROT = 3,
     CLUSCO_OP_ALLPAIRS_ROT = 4,
     CLUSCO_OP_DRMSD = 5,
-    CLUSCO_OP_CMO = 6
+    CLUSCO_OP_CMO = 6,
+    CLUSCO_OP_STEP_ROT = 7
 } clusco_op;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -237,6 +238,22 @@ int clusco_crmsd_allpairs_rot(const float *coords, int64_t N, int64_t L, float *
 int clusco_crmsd_allpairs_backward_rot(const float *coords, int64_t N, int64_t L, const float *grad_out,
                                        const float *crmsd, const float *rot, float *grad_coords, float eps,
                                        void *workspace, size_t workspace_bytes, void *stream);
+
+/* One training step of the all-pairs matrix in one call: clusco_crmsd_allpairs_rot (out, rot)
+ * followed by clusco_crmsd_allpairs_backward_rot of the weights grad_out (grad_coords), with the
+ * same arguments, results and limits as those two calls made in turn. The adjoint's pre-pass
+ * reads only coords and grad_out, so the call runs it on a stream of the library's own (one per
+ * device, created on first use and kept until the process exits), forked from and joined back
+ * into stream by events, beside the forward. grad_out must therefore be final when the call is
+ * made (its values may not depend on this call's out). Every kernel is ordered after the work
+ * already enqueued on stream, and every later work on stream after the call's. Calls that run at
+ * the same time from several host threads share that stream, which stays correct (each call
+ * waits for its own events) but serialises their pre-passes; a graph captured from stream takes
+ * in the fork and the join. Workspace: CLUSCO_OP_STEP_ROT bytes (the two calls' workspaces,
+ * each 256-byte aligned). No counterpart in the paper, which gives no gradient. */
+int clusco_crmsd_allpairs_step_rot(const float *coords, int64_t N, int64_t L, const float *grad_out, float *out,
+                                   float *rot, float *grad_coords, int form, float eps, void *workspace,
+                                   size_t workspace_bytes, void *stream);
 
 /* Synchronise stream, return the device status word (CLUSCO_OK if clean) and clear it. */
 int clusco_sync_status(void *stream);

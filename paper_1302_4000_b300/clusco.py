@@ -36,6 +36,7 @@ OP_BACKWARD_ROT = 3
 OP_ALLPAIRS_ROT = 4
 OP_DRMSD = 5
 OP_CMO = 6
+OP_STEP_ROT = 7
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EOVERFLOW",
           6: "ENONFINITE", 7: "EUNSUPPORTED"}
@@ -87,6 +88,8 @@ def load(path: str = LIB_PATH):
             lib.clusco_crmsd_allpairs_rot.argtypes = [vp, i64, i64, vp, vp, ctypes.c_int, vp, sz, vp]
             lib.clusco_crmsd_allpairs_backward_rot.argtypes = [vp, i64, i64, vp, vp, vp, vp, ctypes.c_float, vp, sz,
                                                                vp]
+            lib.clusco_crmsd_allpairs_step_rot.argtypes = [vp, i64, i64, vp, vp, vp, vp, ctypes.c_int, ctypes.c_float,
+                                                           vp, sz, vp]
             lib.clusco_drmsd_allpairs.argtypes = [vp, i64, i64, vp, ctypes.c_int, vp, sz, vp]
             lib.clusco_cmo_allpairs.argtypes = [vp, i64, i64, ctypes.c_float, vp, ctypes.c_int, vp, sz, vp]
             lib.clusco_gdt_tm_vs_ref.argtypes = [vp, i64, i64, vp, vp, vp]
@@ -364,6 +367,33 @@ def crmsd_allpairs_backward_rot(coords: torch.Tensor, grad_out: torch.Tensor, cr
                                                      rot.data_ptr(), grad_coords.data_ptr(), float(eps),
                                                      ws.data_ptr(), nb, _stream(stream)))
     return grad_coords
+
+
+def crmsd_allpairs_step_rot(coords: torch.Tensor, grad_out: torch.Tensor, form: int = FORM_BF16_EXACT2,
+                            eps: float = 1e-6, out: torch.Tensor | None = None, rot: torch.Tensor | None = None,
+                            grad_coords: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                            stream=None):
+    """One training step in one call: the matrix and the rotations (crmsd_allpairs_rot), then the
+    adjoint of the weights grad_out from them (crmsd_allpairs_backward_rot), with the adjoint's
+    pre-pass beside the forward. Returns (out, rot, grad_coords)."""
+    coords = _coords(coords)
+    N, L = coords.shape[0], coords.shape[1]
+    P = N * (N - 1) // 2
+    grad_out = grad_out.contiguous().to(torch.float32)
+    assert grad_out.numel() == P and grad_out.is_cuda
+    if out is None:
+        out = torch.empty(P, dtype=torch.float32, device=coords.device)
+    if rot is None:
+        rot = torch.empty((P, ROT_STRIDE), dtype=torch.float32, device=coords.device)
+    if grad_coords is None:
+        grad_coords = torch.empty_like(coords)
+    assert out.is_contiguous() and rot.is_contiguous() and grad_coords.is_contiguous()
+    assert out.numel() == P and rot.numel() == ROT_STRIDE * P and grad_coords.shape == coords.shape
+    ws, nb = _ws(workspace, OP_STEP_ROT, N, L, form, coords.device)
+    _check(load().clusco_crmsd_allpairs_step_rot(coords.data_ptr(), N, L, grad_out.data_ptr(), out.data_ptr(),
+                                                 rot.data_ptr(), grad_coords.data_ptr(), int(form), float(eps),
+                                                 ws.data_ptr(), nb, _stream(stream)))
+    return out, rot, grad_coords
 
 
 def sync_status(stream=None) -> int:

@@ -512,11 +512,13 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
 
 inline bool bwr_supported(int64_t L) { return (L + 63) / 64 * 64 <= BR_MAXLP; }
 
-// Host side: pre-pass (centred FP32 rows, transposed FP16 parts, the two scales), the
-// contraction sweep from stored rotations, the reduction, and the FP64 near-duplicate kernel.
-// Workspace: carve_bt's layout (its TF32 transpose buffer holds the FP16 parts here).
-inline int bwr_launch(const float *coords, int64_t N, int64_t L, const float *grad_out, const float *crmsd,
-                      const float *rot, float *grad, float eps, void *ws, cudaStream_t st, std::string &err)
+// Host side, in two parts. bwr_prepare: the pre-pass (centred FP32 rows, transposed FP16
+// parts, the two scales), which reads only the coordinates and the weights, so that it may run
+// beside the forward. bwr_sweep: the contraction sweep from stored rotations, the reduction and
+// the FP64 near-duplicate kernel, after the forward and the pre-pass. Workspace: carve_bt's
+// layout (its TF32 transpose buffer holds the FP16 parts here).
+inline int bwr_prepare(const float *coords, int64_t N, int64_t L, const float *grad_out, void *ws, cudaStream_t st,
+                       std::string &err)
 {
     const BtWs w = carve_bt(ws, N, L);
     const int64_t P = N * (N - 1) / 2;
@@ -541,6 +543,15 @@ inline int bwr_launch(const float *coords, int64_t N, int64_t L, const float *gr
         err = std::string("backward pre-pass: ") + cudaGetErrorString(e);
         return CLUSCO_ECUDA;
     }
+    return CLUSCO_OK;
+}
+
+inline int bwr_sweep(const float *coords, int64_t N, int64_t L, const float *grad_out, const float *crmsd,
+                     const float *rot, float *grad, float eps, void *ws, cudaStream_t st, std::string &err)
+{
+    const BtWs w = carve_bt(ws, N, L);
+    __half *xT = reinterpret_cast<__half *>(w.xT);
+    cudaError_t e = cudaSuccess;
     CUtensorMap mXh, mXl;
     for (int part = 0; part < 2; ++part) {
         // X^T hi / lo parts: FP16 [Lp][Rpad] each; boxes of the tile's 64 operand rows (128
@@ -585,6 +596,13 @@ inline int bwr_launch(const float *coords, int64_t N, int64_t L, const float *gr
         return CLUSCO_ECUDA;
     }
     return CLUSCO_OK;
+}
+
+inline int bwr_launch(const float *coords, int64_t N, int64_t L, const float *grad_out, const float *crmsd,
+                      const float *rot, float *grad, float eps, void *ws, cudaStream_t st, std::string &err)
+{
+    const int rc = bwr_prepare(coords, N, L, grad_out, ws, st, err);
+    return rc ? rc : bwr_sweep(coords, N, L, grad_out, crmsd, rot, grad, eps, ws, st, err);
 }
 
 }  // namespace clusco

@@ -199,3 +199,53 @@ def test_backward_rot_full_size_rows(which):
     print(f"\n{which}: per-model rel err {rel.max():.3e}, coords ok {coord.mean():.6f}")
     assert rel.max() <= 1e-3
     assert coord.all()
+
+
+@pytest.mark.parametrize("N,L,form", [(2, 1, clusco.FORM_BF16_EXACT2), (129, 255, clusco.FORM_BF16_EXACT2),
+                                      (300, 100, clusco.FORM_TF32), (5000, 300, clusco.FORM_BF16_EXACT2)])
+def test_fused_step_equals_the_two_calls(N, L, form):
+    """clusco_crmsd_allpairs_step_rot runs the same kernels on the same inputs as the forward and
+    adjoint calls made in turn (only the adjoint's pre-pass moves to a side stream): the matrix
+    and the rotations are bitwise the same; the gradient is the same up to the order of its
+    atomically accumulated FP32 terms (the near-duplicate pairs' direct terms and the per-model
+    coefficient sums), which varies from run to run, so it is compared per model to 1e-5 of its
+    norm (the accuracy bar against the oracle is 1e-3); the small shapes also go against the
+    oracle's gradient."""
+    e = E.config1(N=N, L=L) if N == 5000 else E.decoy_ensemble(N, L, 2, (0.5, 6.0), 2000 + N + L)
+    w = torch.from_numpy(E.weights(N * (N - 1) // 2, 29 + N)).cuda()
+    X = torch.from_numpy(e.coords).cuda()
+    out, rot = clusco.crmsd_allpairs_rot(X, form)
+    g = clusco.crmsd_allpairs_backward_rot(X, w, out, rot, 1e-6)
+    out2, rot2, g2 = clusco.crmsd_allpairs_step_rot(X, w, form, 1e-6)
+    assert clusco.sync_status() == 0
+
+    def same_grad(ga, gb):
+        d = torch.linalg.vector_norm((ga - gb).double().reshape(N, -1), dim=1)
+        nrm = torch.linalg.vector_norm(ga.double().reshape(N, -1), dim=1)
+        return bool((d <= 1e-5 * nrm.clamp_min(1e-30)).all())
+    assert torch.equal(out, out2) and torch.equal(rot, rot2) and same_grad(g, g2)
+    # on another stream, with a caller's workspace and output buffers
+    s = torch.cuda.Stream()
+    ws = torch.empty(clusco.workspace_bytes(clusco.OP_STEP_ROT, N, L, form), dtype=torch.uint8, device="cuda")
+    o3, r3, g3 = torch.full_like(out, -1.0), torch.full_like(rot, -1.0), torch.full_like(g, -1.0)
+    s.wait_stream(torch.cuda.current_stream())
+    clusco.crmsd_allpairs_step_rot(X, w, form, 1e-6, out=o3, rot=r3, grad_coords=g3, workspace=ws, stream=s)
+    assert clusco.sync_status(s) == 0
+    assert torch.equal(out, o3) and torch.equal(rot, r3) and same_grad(g, g3)
+    if N <= 300:
+        gref = oracle.crmsd_grad(e.coords, w.double().cpu().numpy(), 1e-6)
+        gg = g2.double().cpu().numpy()
+        rel = (np.linalg.norm((gg - gref).reshape(N, -1), axis=1)
+               / np.maximum(np.linalg.norm(gref.reshape(N, -1), axis=1), 1e-300))
+        assert rel.max() <= 1e-3
+
+
+def test_fused_step_argument_errors():
+    X = torch.zeros((4, 600, 3), device="cuda")
+    w = torch.ones(6, device="cuda")
+    with pytest.raises(clusco.ClusCoError):  # the plain form produces no rotations
+        clusco.crmsd_allpairs_step_rot(X[:, :300].contiguous(), w, clusco.FORM_FP32_SIMT)
+    with pytest.raises(clusco.ClusCoError):  # above the 512 atoms of the stored-rotation adjoint
+        clusco.crmsd_allpairs_step_rot(X, w, clusco.FORM_BF16_EXACT2)
+    assert clusco.workspace_bytes(clusco.OP_STEP_ROT, 4, 600, clusco.FORM_BF16_EXACT2) == 0
+    assert clusco.workspace_bytes(clusco.OP_STEP_ROT, 4, 300, clusco.FORM_FP32_SIMT) == 0
