@@ -139,3 +139,28 @@ def test_gdt_tm_host_side_validation(lib):
     assert call(fake, 10, 1025, fake, fake, None) == 1     # L above 1024
     assert call(fake, 10, 10, None, fake, None) == 1       # null reference
     assert call(fake, 10, 10, fake, None, None) == 1       # null out
+
+
+def test_step_rot_host_side_validation(lib):
+    """The fused step's workspace is the two calls' workspaces, the forward's rounded up to 256
+    bytes; its argument errors return before anything is enqueued."""
+    r256 = lambda x: (x + 255) // 256 * 256
+    for N, L, form in ((5000, 300, clusco.FORM_BF16_EXACT2), (129, 255, clusco.FORM_TF32),
+                       (2, 1, clusco.FORM_BF16X3)):
+        fwd = clusco.workspace_bytes(clusco.OP_ALLPAIRS_ROT, N, L, form)
+        bwd = clusco.workspace_bytes(clusco.OP_BACKWARD_ROT, N, L, form)
+        assert fwd > 0 and bwd > 0
+        assert clusco.workspace_bytes(clusco.OP_STEP_ROT, N, L, form) == r256(fwd) + bwd
+    assert clusco.workspace_bytes(clusco.OP_STEP_ROT, 5000, 300, clusco.FORM_FP32_SIMT) == 0  # no rotations
+    assert clusco.workspace_bytes(clusco.OP_STEP_ROT, 100, 600, clusco.FORM_BF16_EXACT2) == 0  # L > 512
+    assert clusco.workspace_bytes(clusco.OP_STEP_ROT, 1, 300, clusco.FORM_BF16_EXACT2) == 0
+    fake, eps = ctypes.c_void_p(0x1000), ctypes.c_float(1e-6)
+    step = lib.clusco_crmsd_allpairs_step_rot
+    ex = clusco.FORM_BF16_EXACT2
+    assert step(fake, 10, 10, None, fake, fake, fake, ex, eps, None, 0, None) == 1  # null weights
+    assert step(fake, 10, 10, fake, fake, ctypes.c_void_p(0x1004), fake, ex, eps, None, 0, None) == 1  # rot 16 B
+    assert step(fake, 10, 10, fake, fake, fake, fake, 42, eps, None, 0, None) == 1  # unknown form
+    assert step(fake, 10, 10, fake, fake, fake, fake, ex, ctypes.c_float(0.0), None, 0, None) == 1  # eps
+    assert step(fake, 1, 10, fake, fake, fake, fake, ex, eps, None, 0, None) == 1  # N < 2
+    assert step(fake, 10, 10, fake, fake, fake, fake, clusco.FORM_FP32_SIMT, eps, None, 0, None) == 7
+    assert step(fake, 10, 600, fake, fake, fake, fake, ex, eps, None, 0, None) == 7  # L > 512
