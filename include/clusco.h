@@ -80,7 +80,8 @@ typedef enum {
     CLUSCO_OP_ALLPAIRS_ROT = 4,
     CLUSCO_OP_DRMSD = 5,
     CLUSCO_OP_CMO = 6,
-    CLUSCO_OP_STEP_ROT = 7
+    CLUSCO_OP_STEP_ROT = 7,
+    CLUSCO_OP_STEP = 8
 } clusco_op;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -194,7 +195,15 @@ int clusco_crmsd_vs_ref_noalloc(const float *coords, int64_t N, int64_t L, const
  * with R_ab the optimal rotation of centred b onto centred a (recomputed, never
  * stored) and c_ab = crmsd[idx] (the forward output, reused). grad_coords is
  * float[N][L][3], overwritten. eps > 0 guards cRMSD -> 0. Pairs with
- * c_ab below the near-duplicate threshold use a direct FP64 residual path.
+ * c_ab below the near-duplicate threshold (0.5 A) use a direct FP64 residual path, whose two
+ * contributions per pair are added with float atomics: their order, and so the last bits of
+ * the gradients of models in such pairs, can differ between runs.
+ * On an sm_103 device with L <= 1024 the covariances (three FP16 passes) and the contraction
+ * with the rotations (three FP16 passes) run on the tensor cores, in thread-block clusters that
+ * compute each rotation once; the form argument is then not used. Otherwise (other devices,
+ * larger L) an FP32 CUDA-core path runs. Setting the environment variable
+ * CLUSCO_BACKWARD_CLUSTERS=0 makes the tensor-core path run without clusters (each CTA of a
+ * row tile recomputes the rotations; same results), for comparison.
  * No counterpart in the paper, which gives no gradient. */
 int clusco_crmsd_allpairs_backward(const float *coords, int64_t N, int64_t L, const float *grad_out,
                                    const float *crmsd, float *grad_coords, float eps, int form,
@@ -246,14 +255,28 @@ int clusco_crmsd_allpairs_backward_rot(const float *coords, int64_t N, int64_t L
  * device, created on first use and kept until the process exits), forked from and joined back
  * into stream by events, beside the forward. grad_out must therefore be final when the call is
  * made (its values may not depend on this call's out). Every kernel is ordered after the work
- * already enqueued on stream, and every later work on stream after the call's. Calls that run at
- * the same time from several host threads share that stream, which stays correct (each call
- * waits for its own events) but serialises their pre-passes; a graph captured from stream takes
- * in the fork and the join. Workspace: CLUSCO_OP_STEP_ROT bytes (the two calls' workspaces,
+ * already enqueued on stream, and every later work on stream after the call's. Each host thread
+ * has its own side stream per device, so that calls from several threads never share one.
+ * Workspace: CLUSCO_OP_STEP_ROT bytes (the two calls' workspaces,
  * each 256-byte aligned). No counterpart in the paper, which gives no gradient. */
 int clusco_crmsd_allpairs_step_rot(const float *coords, int64_t N, int64_t L, const float *grad_out, float *out,
                                    float *rot, float *grad_coords, int form, float eps, void *workspace,
                                    size_t workspace_bytes, void *stream);
+
+/* One training step in one call, nothing stored between its halves: clusco_crmsd_allpairs (out)
+ * followed by clusco_crmsd_allpairs_backward of the weights grad_out (grad_coords), with the same
+ * arguments, results and limits as those two calls made in turn; tensor-core forms only,
+ * L <= 1024 (else CLUSCO_EUNSUPPORTED). The adjoint's pre-pass reads only coords and grad_out, so
+ * the call runs it on a stream of the library's own, one per host thread and device (created on
+ * the thread's first fused call, kept until the process exits), forked from and joined back into
+ * stream by events, beside the forward. grad_out must therefore be final when the call is made (its
+ * values may not depend on this call's out). Every kernel is ordered after the work already
+ * enqueued on stream, and every later work on stream after the call's. Workspace: CLUSCO_OP_STEP
+ * bytes (the two calls' workspaces, each 256-byte aligned). No counterpart in the paper, which
+ * gives no gradient. */
+int clusco_crmsd_allpairs_step(const float *coords, int64_t N, int64_t L, const float *grad_out, float *out,
+                               float *grad_coords, int form, float eps, void *workspace, size_t workspace_bytes,
+                               void *stream);
 
 /* Synchronise stream, return the device status word (CLUSCO_OK if clean) and clear it. */
 int clusco_sync_status(void *stream);

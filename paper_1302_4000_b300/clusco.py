@@ -37,6 +37,7 @@ OP_ALLPAIRS_ROT = 4
 OP_DRMSD = 5
 OP_CMO = 6
 OP_STEP_ROT = 7
+OP_STEP = 8
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EOVERFLOW",
           6: "ENONFINITE", 7: "EUNSUPPORTED"}
@@ -46,7 +47,8 @@ EXPORTS = ("clusco_version", "clusco_workspace_bytes", "clusco_crmsd_allpairs", 
            "clusco_crmsd_vs_ref", "clusco_crmsd_vs_ref_noalloc", "clusco_crmsd_allpairs_backward",
            "clusco_sync_status", "clusco_last_error", "clusco_profile_enable", "clusco_profile_read",
            "clusco_crmsd_allpairs_rot", "clusco_crmsd_allpairs_backward_rot", "clusco_drmsd_allpairs",
-           "clusco_cmo_allpairs", "clusco_gdt_tm_vs_ref")
+           "clusco_cmo_allpairs", "clusco_gdt_tm_vs_ref", "clusco_crmsd_allpairs_step_rot",
+           "clusco_crmsd_allpairs_step")
 KERNEL_PAIRS = 0
 KERNEL_ADJOINT = 1
 KERNEL_DRMSD = 2
@@ -90,6 +92,8 @@ def load(path: str = LIB_PATH):
                                                                vp]
             lib.clusco_crmsd_allpairs_step_rot.argtypes = [vp, i64, i64, vp, vp, vp, vp, ctypes.c_int, ctypes.c_float,
                                                            vp, sz, vp]
+            lib.clusco_crmsd_allpairs_step.argtypes = [vp, i64, i64, vp, vp, vp, ctypes.c_int, ctypes.c_float, vp,
+                                                       sz, vp]
             lib.clusco_drmsd_allpairs.argtypes = [vp, i64, i64, vp, ctypes.c_int, vp, sz, vp]
             lib.clusco_cmo_allpairs.argtypes = [vp, i64, i64, ctypes.c_float, vp, ctypes.c_int, vp, sz, vp]
             lib.clusco_gdt_tm_vs_ref.argtypes = [vp, i64, i64, vp, vp, vp]
@@ -100,7 +104,8 @@ def load(path: str = LIB_PATH):
                       "clusco_crmsd_vs_ref_noalloc", "clusco_crmsd_allpairs_backward", "clusco_sync_status",
                       "clusco_profile_enable", "clusco_profile_read", "clusco_crmsd_allpairs_rot",
                       "clusco_crmsd_allpairs_backward_rot", "clusco_crmsd_allpairs_below", "clusco_drmsd_allpairs",
-                      "clusco_cmo_allpairs", "clusco_gdt_tm_vs_ref"):
+                      "clusco_cmo_allpairs", "clusco_gdt_tm_vs_ref", "clusco_crmsd_allpairs_step_rot",
+                      "clusco_crmsd_allpairs_step"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -396,6 +401,31 @@ def crmsd_allpairs_step_rot(coords: torch.Tensor, grad_out: torch.Tensor, form: 
     return out, rot, grad_coords
 
 
+def crmsd_allpairs_step(coords: torch.Tensor, grad_out: torch.Tensor, form: int = FORM_BF16_EXACT2,
+                        eps: float = 1e-6, out: torch.Tensor | None = None, grad_coords: torch.Tensor | None = None,
+                        workspace: torch.Tensor | None = None, stream=None):
+    """One training step in one call, nothing stored between its halves: the matrix
+    (crmsd_allpairs), then the adjoint of the weights grad_out with every rotation recomputed
+    (crmsd_allpairs_backward), with the adjoint's pre-pass beside the forward. Returns
+    (out, grad_coords)."""
+    coords = _coords(coords)
+    N, L = coords.shape[0], coords.shape[1]
+    P = N * (N - 1) // 2
+    grad_out = grad_out.contiguous().to(torch.float32)
+    assert grad_out.numel() == P and grad_out.is_cuda
+    if out is None:
+        out = torch.empty(P, dtype=torch.float32, device=coords.device)
+    if grad_coords is None:
+        grad_coords = torch.empty_like(coords)
+    assert out.is_contiguous() and grad_coords.is_contiguous()
+    assert out.numel() == P and grad_coords.shape == coords.shape
+    ws, nb = _ws(workspace, OP_STEP, N, L, form, coords.device)
+    _check(load().clusco_crmsd_allpairs_step(coords.data_ptr(), N, L, grad_out.data_ptr(), out.data_ptr(),
+                                             grad_coords.data_ptr(), int(form), float(eps), ws.data_ptr(), nb,
+                                             _stream(stream)))
+    return out, grad_coords
+
+
 def sync_status(stream=None) -> int:
     """Synchronise the stream and return the device status word (0 = clean); clears it."""
     rc = load().clusco_sync_status(_stream(stream))
@@ -403,14 +433,16 @@ def sync_status(stream=None) -> int:
 
 
 class CRMSDAllPairs(torch.autograd.Function):
-    """Condensed all-pairs cRMSD with the library's hand-written adjoint."""
+    """Condensed all-pairs cRMSD with the library's hand-written adjoint.
 
-    # With a tensor-core form and L <= 512 the forward also stores each pair's rotation
-    # (36 bytes per pair) and the backward contracts from it; otherwise the backward
-    # recomputes the covariances.
+    By default nothing but the matrix is kept for the backward, which recomputes every pair's
+    rotation. With store_rotations (a tensor-core form and L <= 512) the forward also stores each
+    pair's rotation (48 bytes per pair) and the backward contracts from it instead."""
+
     @staticmethod
-    def forward(ctx, coords, form: int, eps: float):
-        store = ctx.needs_input_grad[0] and form != FORM_FP32_SIMT and coords.shape[1] <= 512
+    def forward(ctx, coords, form: int, eps: float, store_rotations: bool = False):
+        store = (store_rotations and ctx.needs_input_grad[0] and form != FORM_FP32_SIMT
+                 and coords.shape[1] <= 512)
         if store:
             out, rot = crmsd_allpairs_rot(coords, form)
             ctx.save_for_backward(coords, out, rot)
@@ -428,12 +460,14 @@ class CRMSDAllPairs(torch.autograd.Function):
         else:
             coords, out = ctx.saved_tensors
             g = crmsd_allpairs_backward(coords, grad_out, out, ctx.eps, ctx.form)
-        return g, None, None
+        return g, None, None, None
 
 
-def crmsd_matrix(coords: torch.Tensor, form: int = FORM_BF16_EXACT2, eps: float = 1e-6) -> torch.Tensor:
-    """Differentiable condensed cRMSD matrix."""
-    return CRMSDAllPairs.apply(coords, form, eps)
+def crmsd_matrix(coords: torch.Tensor, form: int = FORM_BF16_EXACT2, eps: float = 1e-6,
+                 store_rotations: bool = False) -> torch.Tensor:
+    """Differentiable condensed cRMSD matrix (the backward recomputes the rotations unless
+    store_rotations)."""
+    return CRMSDAllPairs.apply(coords, form, eps, store_rotations)
 
 
 def crmsd_allpairs_host(coords_host: torch.Tensor, form: int = FORM_BF16_EXACT2, out_host: torch.Tensor | None = None,

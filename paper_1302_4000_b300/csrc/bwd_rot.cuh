@@ -4,8 +4,8 @@
 //
 // The forward can store each pair's optimal rotation R_ab (pairs_tc_kernel with ROT); then the
 // adjoint needs no covariance and no rotation arithmetic: per tile it only gathers R_ab (or
-// R_ba^T for the lower triangle), c_ab and w_ab, scales, and contracts. Same tiling as
-// bwd_tc_kernel: a CTA owns one A tile I (40 models = 128 operand rows) and a contiguous range
+// R_ba^T for the lower triangle), c_ab and w_ab, scales, and contracts. Same tiling as the
+// recomputing adjoint (bwd_rc.cuh): a CTA owns one A tile I (40 models = 128 operand rows) and a contiguous range
 // of B tiles J over the full square (every b != a in both orders, so no atomics on the
 // gradient). Roles:
 //   warp 0 (TMA): X_J^T hi / lo FP16 chunks (128 atoms x the tile's 64 operand rows) into a

@@ -19,6 +19,7 @@
 #include "backward.cuh"
 #include "bwd_tc.cuh"
 #include "bwd_rot.cuh"
+#include "bwd_rc.cuh"
 #include "drmsd.cuh"
 #include "cmo.cuh"
 #include "gdt.cuh"
@@ -377,6 +378,10 @@ size_t clusco_workspace_bytes(int op, int64_t N, int64_t L, int form)
         if (!cmo_form(form) || N < 2 || L < 2 || L > DR_MAX_L) return 0;
         return carve_cmo(nullptr, N, L, form).bytes;
     }
+    if (op == CLUSCO_OP_STEP) {
+        if (!valid_form(form) || form == CLUSCO_FORM_FP32_SIMT || N < 2 || !rc_supported(L)) return 0;
+        return align256(carve_pairs(nullptr, N, L, form).bytes) + carve_rc(nullptr, N, L).bytes;
+    }
     if (op == CLUSCO_OP_STEP_ROT) {
         if (!valid_form(form) || form == CLUSCO_FORM_FP32_SIMT || N < 2 || !bwr_supported(L)) return 0;
         return align256(carve_pairs(nullptr, N, L, form, true).bytes) + carve_bt(nullptr, N, L).bytes;
@@ -694,22 +699,23 @@ int clusco_sync_status(void *stream)
 }  // extern "C"
 
 // ---- one training step in one call ------------------------------------------------------
-// The adjoint's pre-pass reads only the coordinates and the weights, so the fused step runs it on
+// The adjoint's pre-pass reads only the coordinates and the weights, so the fused steps run it on
 // a stream of the library's own, forked from and joined back into the caller's stream by events
-// of this call, while the forward runs on the caller's stream.
+// of the call, while the forward runs on the caller's stream. Every host thread has its own side
+// stream per device (created on the thread's first fused call on that device, kept until the
+// process exits), so that calls from different threads, captured into a graph or not, never
+// share one.
 namespace {
 constexpr int SIDE_MAX_DEVICES = 64;
-std::mutex g_side_mu;
-cudaStream_t g_side[SIDE_MAX_DEVICES] = {};
+thread_local cudaStream_t t_side[SIDE_MAX_DEVICES] = {};
 
 int side_stream(cudaStream_t *out)
 {
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= SIDE_MAX_DEVICES) return fail(CLUSCO_EUNSUPPORTED, "device %d beyond the side-stream table", dev);
-    std::lock_guard<std::mutex> lock(g_side_mu);
-    if (!g_side[dev]) CUDA_TRY(cudaStreamCreateWithFlags(&g_side[dev], cudaStreamNonBlocking));
-    *out = g_side[dev];
+    if (!t_side[dev]) CUDA_TRY(cudaStreamCreateWithFlags(&t_side[dev], cudaStreamNonBlocking));
+    *out = t_side[dev];
     return CLUSCO_OK;
 }
 
@@ -723,6 +729,48 @@ struct EventPair {
         if (join) cudaEventDestroy(join);
     }
 };
+
+// The fused step: prepare(side) beside forward(stream), then the join, then sweep(stream). The join
+// is recorded whatever happened, so that stream never waits on an unrecorded event, and stream
+// waits on it before anything that follows (the sweep, and on every return the stream-ordered free
+// of a workspace the call allocated). Should recording the join itself fail, stream cannot be
+// ordered after the side stream: outside a capture the call then synchronises the side stream;
+// inside one it returns the error (the capture is invalid anyway).
+template <typename Prep, typename Fwd, typename Sweep>
+int fused_step(cudaStream_t st, Prep prepare, Fwd forward, Sweep sweep)
+{
+    cudaStream_t side = nullptr;
+    int rc;
+    if ((rc = side_stream(&side))) return rc;
+    EventPair ev;
+    CUDA_TRY(cudaEventCreateWithFlags(&ev.fork, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&ev.join, cudaEventDisableTiming));
+    // fork: the pre-pass after everything already on stream (its inputs, the workspace)
+    CUDA_TRY(cudaEventRecord(ev.fork, st));
+    CUDA_TRY(cudaStreamWaitEvent(side, ev.fork, 0));
+    std::string err;
+    rc = prepare(side, err);
+    const cudaError_t ej = cudaEventRecord(ev.join, side);
+    if (rc == CLUSCO_OK && ej == cudaSuccess)
+        rc = forward();
+    else if (rc)
+        rc = fail(rc, "%s", err.c_str());
+    else
+        rc = fail(CLUSCO_ECUDA, "cudaEventRecord (join): %s", cudaGetErrorString(ej));
+    cudaError_t ew;
+    if (ej == cudaSuccess) {
+        ew = cudaStreamWaitEvent(st, ev.join, 0);
+    } else {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        ew = cudaStreamIsCapturing(side, &cs);
+        if (ew == cudaSuccess && cs == cudaStreamCaptureStatusNone) ew = cudaStreamSynchronize(side);
+    }
+    if (rc) return rc;
+    if (ew != cudaSuccess) return fail(CLUSCO_ECUDA, "join of the side stream: %s", cudaGetErrorString(ew));
+    rc = sweep(err);
+    if (rc) return fail(rc, "%s", err.c_str());
+    return CLUSCO_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -746,37 +794,47 @@ int clusco_crmsd_allpairs_step_rot(const float *coords, int64_t N, int64_t L, co
     if (!bwr_supported(L)) return fail(CLUSCO_EUNSUPPORTED, "L=%lld above the 512 atoms of this path", (long long)L);
     if ((rc = tc_supported(CLUSCO_FORM_BF16_EXACT2, L))) return fail(rc, "tensor-core path unavailable on this device");
     if ((rc = tc_supported(form, L))) return fail(rc, "tensor-core path unavailable for form %d", form);
-    cudaStream_t st = (cudaStream_t)stream, side = nullptr;
-    if ((rc = side_stream(&side))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
     const size_t fwd_bytes = align256(carve_pairs(nullptr, N, L, form, true).bytes);
     const size_t need = fwd_bytes + carve_bt(nullptr, N, L).bytes;
     Scratch s;
     if ((rc = get_scratch(s, workspace, workspace_bytes, need, st))) return rc;
     void *ws_bwd = static_cast<unsigned char *>(s.ptr) + fwd_bytes;
-    EventPair ev;
-    CUDA_TRY(cudaEventCreateWithFlags(&ev.fork, cudaEventDisableTiming));
-    CUDA_TRY(cudaEventCreateWithFlags(&ev.join, cudaEventDisableTiming));
-    // fork: the pre-pass after everything already on stream (its inputs, the workspace)
-    CUDA_TRY(cudaEventRecord(ev.fork, st));
-    CUDA_TRY(cudaStreamWaitEvent(side, ev.fork, 0));
-    std::string err;
-    rc = bwr_prepare(coords, N, L, grad_out, ws_bwd, side, err);
-    // the join is recorded whatever happened, so that stream never waits on an unrecorded event,
-    // and stream waits on it before anything that follows: the sweep, and on every return the
-    // stream-ordered free of a workspace this call allocated
-    const cudaError_t ej = cudaEventRecord(ev.join, side);
-    if (rc == CLUSCO_OK && ej == cudaSuccess)
-        rc = allpairs_impl(coords, N, L, 0, N - 1, out, form, s.ptr, fwd_bytes, st, rot);
-    else if (rc)
-        rc = fail(rc, "%s", err.c_str());
-    else
-        rc = fail(CLUSCO_ECUDA, "cudaEventRecord (join): %s", cudaGetErrorString(ej));
-    const cudaError_t ew = ej == cudaSuccess ? cudaStreamWaitEvent(st, ev.join, 0) : cudaStreamSynchronize(side);
-    if (rc) return rc;
-    if (ew != cudaSuccess) return fail(CLUSCO_ECUDA, "join of the side stream: %s", cudaGetErrorString(ew));
-    rc = bwr_sweep(coords, N, L, grad_out, out, rot, grad_coords, eps, ws_bwd, st, err);
-    if (rc) return fail(rc, "%s", err.c_str());
-    return CLUSCO_OK;
+    return fused_step(
+        st, [&](cudaStream_t side, std::string &err) { return bwr_prepare(coords, N, L, grad_out, ws_bwd, side, err); },
+        [&]() { return allpairs_impl(coords, N, L, 0, N - 1, out, form, s.ptr, fwd_bytes, st, rot); },
+        [&](std::string &err) {
+            return bwr_sweep(coords, N, L, grad_out, out, rot, grad_coords, eps, ws_bwd, st, err);
+        });
+}
+
+int clusco_crmsd_allpairs_step(const float *coords, int64_t N, int64_t L, const float *grad_out, float *out,
+                               float *grad_coords, int form, float eps, void *workspace, size_t workspace_bytes,
+                               void *stream)
+{
+    g_last_error.clear();
+    int rc;
+    if ((rc = check_sizes(N, L, 2))) return rc;
+    if ((rc = check_ptr(coords, "coords", 4))) return rc;
+    if ((rc = check_ptr(grad_out, "grad_out", 4))) return rc;
+    if ((rc = check_ptr(out, "out", 4))) return rc;
+    if ((rc = check_ptr(grad_coords, "grad_coords", 4))) return rc;
+    if (!valid_form(form)) return fail(CLUSCO_EINVAL, "unknown form %d", form);
+    if (form == CLUSCO_FORM_FP32_SIMT) return fail(CLUSCO_EUNSUPPORTED, "the fused step needs a tensor-core form");
+    if (!(eps > 0.f) || !std::isfinite(eps)) return fail(CLUSCO_EINVAL, "eps=%g must be finite and > 0", (double)eps);
+    if (!rc_supported(L)) return fail(CLUSCO_EUNSUPPORTED, "L=%lld above the 1024 atoms of this path", (long long)L);
+    if ((rc = tc_supported(CLUSCO_FORM_BF16_EXACT2, L))) return fail(rc, "tensor-core path unavailable on this device");
+    if ((rc = tc_supported(form, L))) return fail(rc, "tensor-core path unavailable for form %d", form);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t fwd_bytes = align256(carve_pairs(nullptr, N, L, form).bytes);
+    const size_t need = fwd_bytes + carve_rc(nullptr, N, L).bytes;
+    Scratch s;
+    if ((rc = get_scratch(s, workspace, workspace_bytes, need, st))) return rc;
+    void *ws_bwd = static_cast<unsigned char *>(s.ptr) + fwd_bytes;
+    return fused_step(
+        st, [&](cudaStream_t side, std::string &err) { return rc_prepare(coords, N, L, grad_out, ws_bwd, side, err); },
+        [&]() { return allpairs_impl(coords, N, L, 0, N - 1, out, form, s.ptr, fwd_bytes, st); },
+        [&](std::string &err) { return rc_sweep(coords, N, L, grad_out, out, grad_coords, eps, ws_bwd, st, err); });
 }
 
 }  // extern "C"

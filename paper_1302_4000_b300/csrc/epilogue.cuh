@@ -354,6 +354,20 @@ __device__ __forceinline__ bool sigma_rotation_f32(const float m[9], float R[9])
     return rotation_from_sigma_f32(m, sigma_hat_f32(m), R);
 }
 
+// Sigma and the rotation from one set of minors (I1, I2 and det for the cubic and the Newton
+// steps, the cofactors for the rotation): the recomputing adjoint's per-pair work. False, R
+// unset, where the closed form is ill-conditioned (see rotation_core_f32).
+__device__ __forceinline__ bool sigma_rotation_once_f32(const float m[9], float R[9])
+{
+    float mn[9];
+    minors3(m, mn);
+    float I1, det, I2, dP;
+    invariants_from_minors(m, mn, I1, det, I2);
+    bool deg;
+    const float s = quartic_newton_f(sigma_cubic_f(I1, det, I2), I1, det, I2, 2, &deg, &dP);
+    return rotation_core_f32(m, mn, det, I1, s, R);
+}
+
 // FP32 fast path on a rounded covariance: cubic start + two Newton steps, all FP32.
 // Returns cRMSD and, through err_c2, a bound on the absolute error of cRMSD^2 from FP32
 // rounding. The bound follows the root's conditioning: the quartic is evaluated with an

@@ -153,7 +153,7 @@ def test_autograd_uses_stored_rotations():
     N = 300
     X = torch.from_numpy(e.coords[:N]).cuda().requires_grad_(True)
     wt = torch.from_numpy(w[: N * (N - 1) // 2]).cuda()
-    loss = (wt * clusco.crmsd_matrix(X, clusco.FORM_BF16_EXACT2, 1e-6)).sum()
+    loss = (wt * clusco.crmsd_matrix(X, clusco.FORM_BF16_EXACT2, 1e-6, store_rotations=True)).sum()
     loss.backward()
     out, rot = clusco.crmsd_allpairs_rot(X.detach(), clusco.FORM_BF16_EXACT2)
     g = clusco.crmsd_allpairs_backward_rot(X.detach(), wt, out, rot, 1e-6)
