@@ -70,12 +70,12 @@ struct RcWs {
     __half *x16 = nullptr;    // [2][Rpad][Lp] FP16 hi / lo parts of xf 2^kx, atoms contiguous
     __half *xT = nullptr;     // [2][Lp][Rpad] the same parts transposed
     float *G32 = nullptr;     // [Npad] sum of squares of the centred coordinates
-    float *Gp = nullptr;      // [S][Rpad][Lp] partial gradients (one slice per column range)
-    float *dp = nullptr;      // [S C][Npad] partial row sums of w~
+    float *Gp = nullptr;      // [Smax][Rpad][Lp] partial gradients (one slice per column range)
+    float *dp = nullptr;      // [Smax C][Npad] partial row sums of w~
     long long *nd_list = nullptr;
     unsigned long long *nd_count = nullptr;
     unsigned *scl = nullptr;  // max |centred x|, max |w| (float bits)
-    int64_t Lp = 0, Npad = 0, Rpad = 0, S = 1, C = 1, q = 1, nblk = 1, nd_cap = 0;
+    int64_t Lp = 0, Npad = 0, Rpad = 0, Smax = 1, C = 1, q = 1, nblk = 1, nd_cap = 0;
     size_t bytes = 0;
 };
 
@@ -87,12 +87,39 @@ inline void rc_chunks(int64_t Lp, int64_t &nblk, int64_t &C, int64_t &q)
     q = (nblk + C - 1) / C;
 }
 
-// Column ranges per A tile: enough CTAs for about four waves of 148 SMs.
+// Column ranges per A tile: about four waves of 148 SMs, and at most twice that plus two (the
+// workspace's partial slices); the launch picks the count within that bound that fills whole waves
+// of the clusters the device can hold at once (rc_pick_splits).
 inline int64_t rc_splits(int64_t TA, int64_t TB, int64_t C)
 {
     int64_t S = (4 * 148 + TA * C - 1) / (TA * C);
     if (S > TB) S = TB;
     return S < 1 ? 1 : S;
+}
+
+inline int64_t rc_max_splits(int64_t TA, int64_t TB, int64_t C)
+{
+    const int64_t S = 2 * rc_splits(TA, TB, C) + 2;
+    return S > TB ? TB : S;
+}
+
+// The count of column ranges that minimises waves x tiles per range for `resident` work groups
+// (clusters, or CTAs without clusters) at a time, each group taking one (A tile, range); a 1 %
+// charge per range stands for the reduction of the partial slices.
+inline int64_t rc_pick_splits(int64_t TA, int64_t TB, int64_t Smax, int64_t resident)
+{
+    if (resident < 1) resident = 1;
+    int64_t best = 1;
+    double best_cost = 1e300;
+    for (int64_t S = 1; S <= Smax; ++S) {
+        const double waves = (double)((TA * S + resident - 1) / resident);
+        const double cost = waves * (double)((TB + S - 1) / S) * (1.0 + 0.01 * (double)S);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = S;
+        }
+    }
+    return best;
 }
 
 inline RcWs carve_rc(void *base, int64_t N, int64_t L)
@@ -109,13 +136,13 @@ inline RcWs carve_rc(void *base, int64_t N, int64_t L)
     w.Npad = (N + TC_MA - 1) / TC_MA * TC_MA;
     w.Rpad = w.Npad / 10 * 32;
     rc_chunks(w.Lp, w.nblk, w.C, w.q);
-    w.S = rc_splits(w.Npad / TC_MA, w.Npad / TC_MB, w.C);
+    w.Smax = rc_max_splits(w.Npad / TC_MA, w.Npad / TC_MB, w.C);
     w.xf = (float *)take(sizeof(float) * w.Rpad * w.Lp);
     w.x16 = (__half *)take(sizeof(__half) * 2 * w.Rpad * w.Lp);
     w.xT = (__half *)take(sizeof(__half) * 2 * w.Lp * w.Rpad);
     w.G32 = (float *)take(sizeof(float) * w.Npad);
-    w.Gp = (float *)take(sizeof(float) * w.S * w.Rpad * w.Lp);
-    w.dp = (float *)take(sizeof(float) * w.S * w.C * w.Npad);
+    w.Gp = (float *)take(sizeof(float) * w.Smax * w.Rpad * w.Lp);
+    w.dp = (float *)take(sizeof(float) * w.Smax * w.C * w.Npad);
     const int64_t P = N * (N - 1) / 2;
     w.nd_cap = P < (int64_t)(1 << 22) ? P : (int64_t)(1 << 22);
     w.nd_list = (long long *)take(sizeof(long long) * 2 * w.nd_cap);
@@ -553,7 +580,8 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
                 vc[r] = val[r];
             }
             float V[32];
-            bool fail = !mbar_wait_sleep(&done1_bar, (uint32_t)(ko & 1));
+            // warp-uniform: tcgen05.ld below is a warp-wide instruction
+            bool fail = __any_sync(0xffffffffu, !mbar_wait_sleep(&done1_bar, (uint32_t)(ko & 1)));
             ++ko;
             if (!fail) {
                 tc_fence_after();
@@ -608,11 +636,14 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
 #pragma unroll
                 for (int e = 0; e < 9; ++e) send[e] = 0.f;
                 if (coef != 0.f && !fail) {
-                    const float nrm = __fdividef(2.f, Ga + gb) * ixs * ixs;
+                    const float igs = __fdividef(1.f, Ga + gb);
+                    const float nrm = 2.f * igs * ixs * ixs;
                     float m[9], R[9];
 #pragma unroll
                     for (int e = 0; e < 9; ++e) m[e] = blk[e] * nrm;
-                    if (!sigma_rotation_once_f32(m, R)) rotation_robust(m, R);
+                    // Sigma_hat from the forward's cRMSD: L c^2 = (G_A + G_B)(1 - Sigma_hat)
+                    const float s0 = fmaf(-fL * c * c, igs, 1.f);
+                    if (!sigma_rotation_from_f32(m, s0, R)) rotation_robust(m, R);
                     const float cs = coef * sP;
 #pragma unroll
                     for (int e = 0; e < 9; ++e) send[e] = cs * R[e];
@@ -795,16 +826,14 @@ inline int rc_sweep(const float *coords, int64_t N, int64_t L, const float *grad
         return CLUSCO_ECUDA;
     }
     const int64_t TA = w.Npad / TC_MA, TB = w.Npad / TC_MB;
-    const int64_t JC = (TB + w.S - 1) / w.S;
     const int nkb = (int)(w.Lp / 64);
-    const unsigned grid = (unsigned)(TA * w.S * w.C);
     e = cudaFuncSetAttribute(bwd_rc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC_SMEM);
     if (e != cudaSuccess) {
         err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
         return CLUSCO_ECUDA;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
+    cfg.gridDim = dim3((unsigned)(TA * w.C));  // the grid's x is set below, with the column ranges
     cfg.blockDim = dim3(RC_THREADS);
     cfg.dynamicSmemBytes = RC_SMEM;
     cfg.stream = st;
@@ -814,31 +843,46 @@ inline int rc_sweep(const float *coords, int64_t N, int64_t L, const float *grad
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     int CS = 1;
+    int64_t resident = 0;  // work groups the device runs at once
     if (w.C > 1 && allow_cluster) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, bwd_rc_kernel, &cfg) == cudaSuccess && nclusters > 0)
+        if (cudaOccupancyMaxActiveClusters(&nclusters, bwd_rc_kernel, &cfg) == cudaSuccess && nclusters > 0) {
             CS = (int)w.C;
-        else
+            resident = nclusters;
+        } else {
             (void)cudaGetLastError();  // clear: fall back to independent chunk CTAs
+        }
     }
     if (CS == 1) {
         cfg.attrs = nullptr;
         cfg.numAttrs = 0;
+        int dev = 0, sms = 148, per_sm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd_rc_kernel, RC_THREADS, RC_SMEM) != cudaSuccess ||
+            per_sm < 1) {
+            (void)cudaGetLastError();
+            per_sm = 1;
+        }
+        resident = (int64_t)sms * per_sm / w.C;  // a group is C chunk CTAs
     }
+    const int64_t S = rc_pick_splits(TA, TB, w.Smax, resident);
+    const int64_t JC = (TB + S - 1) / S;
+    cfg.gridDim = dim3((unsigned)(TA * S * w.C));
     prof_mark(PROF_ADJOINT, st);
     e = cudaLaunchKernelEx(&cfg, bwd_rc_kernel, mXA, mXB, mTh, mTl, (const float *)w.G32, N, (int)L, (int)w.Lp, nkb,
-                           w.Rpad, TB, w.S, JC, (int)w.C, (int)w.q, (int)w.nblk, CS, crmsd, grad_out, eps,
+                           w.Rpad, TB, S, JC, (int)w.C, (int)w.q, (int)w.nblk, CS, crmsd, grad_out, eps,
                            (const unsigned *)w.scl, w.Gp, w.dp, w.nd_list, w.nd_count, w.nd_cap);
     prof_mark(PROF_ADJOINT, st);
     if (e == cudaSuccess) {
         if (w.Lp <= 128 * BRED_MAXQ)
             bwd_reduce_kernel<BRED_MAXQ><<<(unsigned)N, BRED_THREADS, (size_t)(3 * L * sizeof(float)), st>>>(
-                w.Gp, w.dp, w.xf, N, (int)L, (int)w.Lp, w.Rpad, w.S, w.S * w.C, grad);
+                w.Gp, w.dp, w.xf, N, (int)L, (int)w.Lp, w.Rpad, S, S * w.C, grad);
         else
             bwd_reduce_kernel<8><<<(unsigned)N, BRED_THREADS, (size_t)(3 * L * sizeof(float)), st>>>(
-                w.Gp, w.dp, w.xf, N, (int)L, (int)w.Lp, w.Rpad, w.S, w.S * w.C, grad);
+                w.Gp, w.dp, w.xf, N, (int)L, (int)w.Lp, w.Rpad, S, S * w.C, grad);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {

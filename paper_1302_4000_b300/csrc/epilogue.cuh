@@ -354,6 +354,23 @@ __device__ __forceinline__ bool sigma_rotation_f32(const float m[9], float R[9])
     return rotation_from_sigma_f32(m, sigma_hat_f32(m), R);
 }
 
+// Sigma and the rotation from one set of minors, starting the Newton steps from a known
+// estimate s0 of Sigma_hat instead of the cubic: the recomputing adjoint has the forward's
+// cRMSD c of the pair, and L c^2 = (G_A + G_B)(1 - Sigma_hat), so s0 = 1 - L c^2 / (G_A + G_B)
+// is within the forward's error of the root; one Newton step on this covariance's own quartic
+// (quadratic convergence) takes it to the root of the matrix at hand. False, R unset, where the
+// closed form is ill-conditioned (see rotation_core_f32).
+__device__ __forceinline__ bool sigma_rotation_from_f32(const float m[9], float s0, float R[9])
+{
+    float mn[9];
+    minors3(m, mn);
+    float I1, det, I2, dP;
+    invariants_from_minors(m, mn, I1, det, I2);
+    bool deg;
+    const float s = quartic_newton_f(s0, I1, det, I2, 1, &deg, &dP);
+    return rotation_core_f32(m, mn, det, I1, s, R);
+}
+
 // Sigma and the rotation from one set of minors (I1, I2 and det for the cubic and the Newton
 // steps, the cofactors for the rotation): the recomputing adjoint's per-pair work. False, R
 // unset, where the closed form is ill-conditioned (see rotation_core_f32).
