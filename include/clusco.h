@@ -157,8 +157,10 @@ int clusco_cmo_allpairs(const float *coords, int64_t N, int64_t L, float cutoff,
  * Each is the maximum over the superpositions of one search: seeds are the contiguous fragments
  * of 4, L/4, L/2 and L atoms (lengths below 3 dropped, repeats once); the model is superimposed on
  * the reference by the optimal proper rotation and translation of the seed's atoms, scored, then
- * superimposed again on the atoms within 3.5 A until their number repeats, fewer than 3 remain,
- * or four refinements were made. Distances and the integer decisions in FP64; TM terms summed in
+ * superimposed again on the atoms within 3.5 A until their number has not changed in four
+ * iterations (four refinements in a row select as many atoms as the one before), fewer than 3
+ * remain, or 20 refinements were made (a refinement that selects exactly the atoms it was fitted
+ * on ends the search too: every later one is the same). Distances and the integer decisions in FP64; TM terms summed in
  * FP32. coords float[N][L][3], ref float[L][3], out float[N][3], all device. 3 <= L <= 1024,
  * N >= 1. A model (or reference) with a non-finite coordinate gives NaN scores and sets
  * CLUSCO_ENONFINITE in the device status. No workspace. */

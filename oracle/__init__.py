@@ -101,9 +101,11 @@ def _bind(lib):
     lib.oracle_crmsd_eq2.argtypes = [_f32p, _f32p, i64, ctypes.POINTER(ctypes.c_double)]
     lib.oracle_crmsd_grad_rows.argtypes = [_f32p, i64, i64, _f64p, ctypes.c_double, _i64p, i64, _f64p, ctypes.c_int]
     lib.oracle_gdt_tm_vs_ref.argtypes = [_f32p, i64, i64, _f32p, _f64p, ctypes.c_int]
+    lib.oracle_gdt_tm_vs_ref_rule.argtypes = [_f32p, i64, i64, _f32p, _f64p, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int]
     for f in ("oracle_crmsd_pair", "oracle_crmsd_allpairs", "oracle_crmsd_pairs",
               "oracle_crmsd_vs_ref", "oracle_crmsd_grad", "oracle_crmsd_eq2", "oracle_crmsd_grad_rows",
-              "oracle_gdt_tm_vs_ref"):
+              "oracle_gdt_tm_vs_ref", "oracle_gdt_tm_vs_ref_rule"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -277,4 +279,17 @@ def gdt_tm_vs_ref(X, ref, nthreads: int = 0, lib=None) -> np.ndarray:
     N, L = X.shape[0], X.shape[1]
     out = np.empty((N, 3), dtype=np.float64)
     _check(lib.oracle_gdt_tm_vs_ref(X, N, L, ref, out.reshape(-1), nthreads), "gdt_tm_vs_ref")
+    return out
+
+
+def gdt_tm_vs_ref_rule(X, ref, stable: int, max_refine: int, nthreads: int = 0, lib=None) -> np.ndarray:
+    """gdt_tm_vs_ref with the search's stop rule given: stop after `stable` refinements in a row
+    that select as many atoms as the superposition before them, or after `max_refine`
+    refinements. gdt_tm_vs_ref is (4, 20); (1, 4) is the shorter reading."""
+    lib = lib or load()
+    X, ref = _f32(X), _f32(ref)
+    N, L = X.shape[0], X.shape[1]
+    out = np.empty((N, 3), dtype=np.float64)
+    _check(lib.oracle_gdt_tm_vs_ref_rule(X, N, L, ref, out.reshape(-1), nthreads, stable, max_refine),
+           "gdt_tm_vs_ref_rule")
     return out

@@ -10,11 +10,11 @@
  *   score        S(A, B) = 100 * 2 n(A and B) / (n(A) + n(B)),
  * with n(.) the number of contacts (of a map, or of both maps at once).
  * Steps, in this order:
- *   1. each model's contact map. The contact test is an integer decision taken in
- *      floating point, so it is taken in the precision of the CUDA kernels: FP32
- *      coordinate differences, the squared distance as fma(dx, dx, fma(dy, dy, dz*dz))
- *      in FP32 and a strict comparison with cutoff^2 rounded to FP32 (compiled with
- *      contraction off, so the expression is evaluated exactly as written);
+ *   1. each model's contact map, the test |x_i - x_j| < cutoff taken in FP64 from the given
+ *      FP32 coordinates: the differences and their squares are exact in FP64, so the squared
+ *      distance carries one rounding of its sum (2^-53 relative) and the strict comparison
+ *      with cutoff^2 (exact) decides the definition's inequality except for distances within
+ *      that rounding of the cutoff (compiled with contraction off, as written);
  *   2. the counts n(A), n(B) and n(A and B), exact integers;
  *   3. the score in FP64. Where n(A) + n(B) = 0 (neither model has a contact) the
  *      score is taken as 0.
@@ -40,14 +40,14 @@ static int finite_model(const float *x, int64_t L)
 /* step 1: the contact map of one model, c[k] for i < j in row-major order */
 static void contact_map(const float *x, int64_t L, float cutoff, unsigned char *c)
 {
-    const float cut2 = cutoff * cutoff;
+    const double cut2 = (double)cutoff * (double)cutoff;
     int64_t k = 0;
     for (int64_t i = 0; i < L; ++i)
         for (int64_t j = i + 1; j < L; ++j) {
-            const float dx = x[3 * i] - x[3 * j];
-            const float dy = x[3 * i + 1] - x[3 * j + 1];
-            const float dz = x[3 * i + 2] - x[3 * j + 2];
-            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const double dx = (double)x[3 * i] - (double)x[3 * j];
+            const double dy = (double)x[3 * i + 1] - (double)x[3 * j + 1];
+            const double dz = (double)x[3 * i + 2] - (double)x[3 * j + 2];
+            const double d2 = dx * dx + dy * dy + dz * dz;
             c[k++] = d2 < cut2 ? 1 : 0;
         }
 }

@@ -490,8 +490,12 @@ int oracle_crmsd_eq2(const float *A, const float *B, int64_t L, double *c_out)
  *      for x = 1, 2, 4, 8 A, the TM sum (1/L) sum_i 1 / (1 + (d_i/d0)^2) with
  *      d0 = max(1.24 (L - 15)^(1/3) - 1.8, 0.5) A and the same sum with d0 = 3.5 A (MaxSub);
  *   4. the atoms with d_i < 3.5 A are selected and the model is superimposed again on them,
- *      scored again, and so on, until the number of selected atoms repeats, fewer than 3 are
- *      selected, or four such refinements have been made;
+ *      scored again, and so on, "until the number of selected atoms does not change in four
+ *      iterations": the refinements stop once four refinements in a row have selected as many
+ *      atoms as the superposition before them, when fewer than 3 atoms are selected, or after
+ *      a bound of 20 refinements (the text gives none) where the count keeps changing. Where a
+ *      refinement selects exactly the atoms it was fitted on, every later superposition is the
+ *      same one, so the search stops there too (it cannot change any maximum);
  * and each score is the maximum over every superposition scored:
  *   GDT_TS = (max C_1 + max C_2 + max C_4 + max C_8) / (4 L), TM = max TM sum, MaxSub = max.
  */
@@ -526,9 +530,13 @@ static int fit_subset(const double *a, const double *b, const int64_t *idx, int6
     return ORACLE_OK;
 }
 
-/* out[0..3) = GDT_TS, TM-score, MaxSub of model b against reference a (L atoms each). */
+#define GDT_STABLE 4       /* iterations without a change of the selected count that end a search */
+#define GDT_MAX_REFINE 20  /* refinements at most */
+
+/* out[0..3) = GDT_TS, TM-score, MaxSub of model b against reference a (L atoms each); the search
+ * stops after `stable` refinements in a row without a change of the count, or `max_refine`. */
 static int gdt_tm_one(const double *a, const double *b, int64_t L, int64_t *idx, int64_t *sel, double *ac,
-                      double *bc, double out[3])
+                      double *bc, int stable, int max_refine, double out[3])
 {
     const double cuts[4] = {1.0, 2.0, 4.0, 8.0};
     const double d0 = tm_d0(L), d0m = 3.5;
@@ -544,8 +552,9 @@ static int gdt_tm_one(const double *a, const double *b, int64_t L, int64_t *idx,
         if (dup) continue;
         for (int64_t s0 = 0; s0 + len <= L; ++s0) {
             int64_t n = len, prev = -1;
+            int same = 0;
             for (int64_t q = 0; q < n; ++q) idx[q] = s0 + q;
-            for (int it = 0; it <= 4; ++it) {
+            for (int it = 0; it <= max_refine; ++it) {
                 double R[3][3], t[3];
                 int st = fit_subset(a, b, idx, n, ac, bc, R, t);
                 if (st) return st;
@@ -568,7 +577,14 @@ static int gdt_tm_one(const double *a, const double *b, int64_t L, int64_t *idx,
                     if (c[k] > best_c[k]) best_c[k] = c[k];
                 if (tm / (double)L > best_tm) best_tm = tm / (double)L;
                 if (ms / (double)L > best_ms) best_ms = ms / (double)L;
-                if (it == 4 || ns < 3 || ns == prev) break;
+                if (it == max_refine || ns < 3) break;
+                same = (ns == prev) ? same + 1 : 0;
+                if (same >= stable) break;
+                if (ns == n) {  /* the atoms it was fitted on: the same superposition from here on */
+                    int64_t q = 0;
+                    while (q < n && idx[q] == sel[q]) ++q;
+                    if (q == n) break;
+                }
                 prev = ns;
                 n = ns;
                 for (int64_t q = 0; q < n; ++q) idx[q] = sel[q];
@@ -581,10 +597,14 @@ static int gdt_tm_one(const double *a, const double *b, int64_t L, int64_t *idx,
     return ORACLE_OK;
 }
 
-/* GDT_TS, TM-score and MaxSub of every model against the reference: out[3 a + {0,1,2}]. */
-int oracle_gdt_tm_vs_ref(const float *X, int64_t N, int64_t L, const float *ref, double *out, int nthreads)
+/* GDT_TS, TM-score and MaxSub of every model against the reference, out[3 a + {0,1,2}], with the
+ * search's stop rule as parameters: stable = 4, max_refine = 20 is the reading above; stable = 1,
+ * max_refine = 4 stops at the first repeated count or after four refinements (a shorter reading of
+ * the same sentence, kept for the tests that tell the two apart). */
+int oracle_gdt_tm_vs_ref_rule(const float *X, int64_t N, int64_t L, const float *ref, double *out, int nthreads,
+                              int stable, int max_refine)
 {
-    if (!X || !ref || !out || N < 1 || L < 3) return ORACLE_EINVAL;
+    if (!X || !ref || !out || N < 1 || L < 3 || stable < 1 || max_refine < 0) return ORACLE_EINVAL;
     double *a = (double *)malloc(sizeof(double) * 3 * L);
     if (!a) return ORACLE_EINVAL;
     for (int64_t t = 0; t < 3 * L; ++t) a[t] = (double)ref[t];
@@ -602,7 +622,7 @@ int oracle_gdt_tm_vs_ref(const float *X, int64_t N, int64_t L, const float *ref,
         for (int64_t m = 0; m < N; ++m) {
             if (bad) continue;
             for (int64_t t = 0; t < 3 * L; ++t) b[t] = (double)X[3 * L * m + t];
-            bad |= gdt_tm_one(a, b, L, idx, sel, ac, bc, out + 3 * m);
+            bad |= gdt_tm_one(a, b, L, idx, sel, ac, bc, stable, max_refine, out + 3 * m);
         }
         free(b);
         free(ac);
@@ -612,4 +632,10 @@ int oracle_gdt_tm_vs_ref(const float *X, int64_t N, int64_t L, const float *ref,
     }
     free(a);
     return bad ? ORACLE_ENOCONV : ORACLE_OK;
+}
+
+/* GDT_TS, TM-score and MaxSub with the stop rule of the search described above. */
+int oracle_gdt_tm_vs_ref(const float *X, int64_t N, int64_t L, const float *ref, double *out, int nthreads)
+{
+    return oracle_gdt_tm_vs_ref_rule(X, N, L, ref, out, nthreads, GDT_STABLE, GDT_MAX_REFINE);
 }

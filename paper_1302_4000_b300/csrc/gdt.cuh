@@ -2,8 +2,11 @@
 // "Algorithms", eq. 3 and eq. 4), each the maximum over the paper's superposition search:
 // seeds are the contiguous fragments of 4, L/4, L/2 and L atoms; the model is superimposed on
 // the reference by the optimal rotation and translation of a seed's atoms, scored, and then
-// superimposed again on the atoms that came within 3.5 A, until that number repeats, fewer
-// than 3 atoms qualify, or four refinements were made.
+// superimposed again on the atoms that came within 3.5 A, until the number of selected atoms has
+// not changed in four iterations (four refinements in a row select as many atoms as the one
+// before), fewer than 3 atoms qualify, or 20 refinements were made; a refinement that selects
+// exactly the atoms it was fitted on (equal moments) repeats itself from then on, so the search
+// stops there as well, with the same maxima.
 //
 // Layout: one block of four warps per model (five blocks per SM, where the latency-bound search
 // balances occupancy against the registers it spills), the model and the reference staged in shared
@@ -91,6 +94,22 @@ __device__ __forceinline__ double gt_slot(const GtMoments &m, int k)
 {
     const float2 h = m.hi[k >> 1], l = m.lo[k >> 1];
     return (k & 1) ? (double)h.y + (double)l.y : (double)h.x + (double)l.x;
+}
+
+constexpr int GT_STABLE = 4;       // iterations without a change of the selected count that end a search
+constexpr int GT_MAX_REFINE = 20;  // refinements at most
+
+// Bitwise equal moments (the same atoms summed in the same order): the same fit follows.
+__device__ __forceinline__ bool gt_equal(const GtMoments &x, const GtMoments &y)
+{
+    bool eq = x.n == y.n;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        eq = eq && __float_as_uint(x.hi[k].x) == __float_as_uint(y.hi[k].x) &&
+             __float_as_uint(x.hi[k].y) == __float_as_uint(y.hi[k].y) &&
+             __float_as_uint(x.lo[k].x) == __float_as_uint(y.lo[k].x) &&
+             __float_as_uint(x.lo[k].y) == __float_as_uint(y.lo[k].y);
+    return eq;
 }
 
 __device__ __forceinline__ void gt_zero(GtMoments &m)
@@ -270,8 +289,8 @@ __global__ void __launch_bounds__(GT_THREADS, 5) gdt_tm_kernel(const float *__re
         gt_zero(mom);
         if (active)
             for (int i = s0; i < s0 + len; ++i) gt_add(mom, fa[i], fb[i]);
-        int prev = -1;
-        for (int it = 0; it <= 4 && __any_sync(0xffffffffu, active); ++it) {
+        int prev = -1, same = 0;
+        for (int it = 0; it <= GT_MAX_REFINE && __any_sync(0xffffffffu, active); ++it) {
             float R32[9], tc[3], marg[5];
             if (active) {
                 double R[9], t[3];
@@ -348,7 +367,8 @@ __global__ void __launch_bounds__(GT_THREADS, 5) gdt_tm_kernel(const float *__re
                 best_tm = fmaxf(best_tm, tm);
                 best_ms = fmaxf(best_ms, ms);
                 const int ns = next.n;
-                if (it == 4 || ns < 3 || ns == prev) {
+                same = (ns == prev) ? same + 1 : 0;
+                if (it == GT_MAX_REFINE || ns < 3 || same >= GT_STABLE || gt_equal(next, mom)) {
                     active = false;
                 } else {
                     prev = ns;

@@ -35,3 +35,28 @@ def c_error_bound(c_ref, Ga, Gb, L, rel_c2, floor=0.0):
     d2 = rel_c2 * (Ga + Gb) / L
     c = np.asarray(c_ref, dtype=np.float64)
     return np.minimum(d2 / np.maximum(c, 1e-300), np.sqrt(d2)) + floor
+
+
+def contact_band(X, cutoff, rel=2.0 ** -20):
+    """Per model, the number of atom pairs i < j whose FP64 squared distance lies within
+    rel * cutoff^2 of cutoff^2: the pairs where a contact test evaluated in FP32 (about 5 ulp of
+    rounding in the differences, their squares and the sum) may decide otherwise than FP64."""
+    X = np.asarray(X, dtype=np.float64)
+    L = X.shape[1]
+    i, j = np.triu_indices(L, 1)
+    c2 = float(np.float32(cutoff)) ** 2
+    out = np.empty(X.shape[0], dtype=np.int64)
+    for m in range(X.shape[0]):
+        d2 = ((X[m, i] - X[m, j]) ** 2).sum(axis=1)
+        out[m] = int((np.abs(d2 - c2) <= rel * c2).sum())
+    return out
+
+
+def cmo_bounds(na, nb, nab, ka, kb):
+    """Interval of 200 n'(A and B) / (n'(A) + n'(B)) when up to ka contacts of A and kb of B may be
+    decided the other way (each changes n(A) or n(B) by one and n(A and B) by at most one)."""
+    k = ka + kb
+    lo_den = max(na + nb - k, 1)
+    lo = 200.0 * max(nab - k, 0) / (na + nb + k) if na + nb + k > 0 else 0.0
+    hi = min(100.0, 200.0 * (nab + k) / lo_den)
+    return lo, hi

@@ -78,3 +78,24 @@ def test_bench_ensemble_against_a_native():
     got = run(e.coords, native)
     idx = np.random.default_rng(4).choice(e.coords.shape[0], 300, replace=False)
     check(got[idx], oracle.gdt_tm_vs_ref(e.coords[idx], native))
+
+
+def test_stop_rule_on_drifting_helices():
+    """The refinement runs until the selected count has not changed in four iterations: on the
+    helices whose second part drifts away (see the oracle's pins), the kernel finds the atom that
+    a search stopping at the first repeated count, or after four refinements, misses."""
+    t = np.arange(32)
+    A = np.stack([2.3 * np.cos(1.75 * t), 2.3 * np.sin(1.75 * t), 1.5 * t], axis=1)
+    models = []
+    for c in (0.33, 0.42):
+        B = A.copy()
+        B[:, 0] += c * np.maximum(0, t - 32 // 3) ** 1.5
+        models.append(B)
+    X = np.stack(models).astype(np.float32)
+    A = A.astype(np.float32)
+    got = run(X, A)
+    want = oracle.gdt_tm_vs_ref(X, A)
+    check(got, want)
+    # drift 0.33 against a stop at the first repeated count, 0.42 against four refinements at most
+    short = np.array([oracle.gdt_tm_vs_ref_rule(X[:1], A, 1, 20)[0, 0], oracle.gdt_tm_vs_ref_rule(X[1:], A, 4, 4)[0, 0]])
+    assert np.array_equal(np.round(got[:, 0] * 4 * 32), np.round(short * 4 * 32) + 1)

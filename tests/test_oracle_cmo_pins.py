@@ -2,9 +2,9 @@
 and by counting.
 
 No expected value comes from the oracle itself: hand-counted cases
-(tests/golden/cmo_closed_forms.txt), a brute-force count with numpy in FP64 on models whose
-distances keep clear of the cutoff (where FP32 and FP64 take the same contact decisions), and
-the invariances and bounds of the score.
+(tests/golden/cmo_closed_forms.txt), a brute-force count with numpy in FP64 (the oracle takes the
+contact test in FP64 too; the models are kept clear of the cutoff so that numpy's square root
+cannot tip a decision), and the invariances and bounds of the score.
 """
 import itertools
 import os
@@ -108,8 +108,8 @@ CMO_MUTANTS = [
     ("contact test not strict", "c[k++] = d2 < cut2 ? 1 : 0;", "c[k++] = d2 <= cut2 ? 1 : 0;"),
     ("score without the factor 2", "return 100.0 * 2.0 * (double)nab / (double)(na + nb);",
      "return 100.0 * (double)nab / (double)(na + nb);"),
-    ("self pairs counted", "for (int64_t j = i + 1; j < L; ++j) {\n            const float dx",
-     "for (int64_t j = i; j < L && k < L * (L - 1) / 2; ++j) {\n            const float dx"),
+    ("self pairs counted", "for (int64_t j = i + 1; j < L; ++j) {\n            const double dx",
+     "for (int64_t j = i; j < L && k < L * (L - 1) / 2; ++j) {\n            const double dx"),
     ("union in the denominator", "return 100.0 * 2.0 * (double)nab / (double)(na + nb);",
      "return 100.0 * 2.0 * (double)nab / (double)(na + nb - nab);"),
 ]

@@ -91,7 +91,7 @@ def test_model_and_reference_swap():
 GDT_MUTANTS = [
     ("d0 constant", "const double d0 = 1.24 * cbrt((double)L - 15.0) - 1.8;",
      "const double d0 = 1.42 * cbrt((double)L - 15.0) - 1.8;"),
-    ("no refinement", "if (it == 4 || ns < 3 || ns == prev) break;", "if (1) break;"),
+    ("no refinement", "if (it == max_refine || ns < 3) break;", "if (1) break;"),
     ("GDT counts not normalised by L", "out[0] = (double)(best_c[0] + best_c[1] + best_c[2] + best_c[3]) / (4.0 * (double)L);",
      "out[0] = (double)(best_c[0] + best_c[1] + best_c[2] + best_c[3]) / 4.0;"),
     ("TM sum over the selected atoms", "if (tm / (double)L > best_tm) best_tm = tm / (double)L;",
@@ -115,4 +115,65 @@ def test_planted_gdt_mistakes_are_caught(mut):
             B = displaced(A, atoms, 20.0, seed=0 if L == 40 else 1)
             got = oracle.gdt_tm_vs_ref(B[None], A, lib=lib)[0]
             caught |= not np.allclose(got, expected(A, B), rtol=0, atol=1e-9)
+        assert caught, f"planted mistake '{desc}' was not caught"
+
+
+def drifting_helix(L, c, p):
+    """A regular helix (radius 2.3 A, 1.75 rad and 1.5 A rise per atom) as the reference and, as
+    the model, the same helix whose atoms past the first third drift along x by c (i - L/3)^p A."""
+    t = np.arange(L)
+    A = np.stack([2.3 * np.cos(1.75 * t), 2.3 * np.sin(1.75 * t), 1.5 * t], axis=1)
+    B = A.copy()
+    B[:, 0] += c * np.maximum(0, t - L // 3) ** p
+    return A.astype(np.float32), B.astype(np.float32)
+
+
+def test_stop_rule_four_unchanged_iterations():
+    """The refinement stops once the number of selected atoms "does not change in four
+    iterations" (four refinements in a row select as many atoms as the one before; at most 20).
+    On a helix whose second part drifts away from the reference, the refinements keep moving the
+    superposition after the count first repeats or after four refinements, which a search that
+    stops there (the shorter reading of the sentence) misses: its GDT_TS is lower. Every
+    superposition the shorter search scores is also scored by the longer one, so its scores are
+    never higher on any model."""
+    for c, short in ((0.33, (1, 20)), (0.42, (4, 4))):
+        # drift 0.33: the count repeats once while the atoms still change (a stop at the first
+        # repeat misses the last atom); drift 0.42: the count keeps changing past four refinements
+        A, B = drifting_helix(32, c, 1.5)
+        new = oracle.gdt_tm_vs_ref(B[None], A)[0]
+        assert np.array_equal(new, oracle.gdt_tm_vs_ref_rule(B[None], A, 4, 20)[0])
+        old = oracle.gdt_tm_vs_ref_rule(B[None], A, 1, 4)[0]
+        part = oracle.gdt_tm_vs_ref_rule(B[None], A, *short)[0]
+        L = A.shape[0]
+        assert round(new[0] * 4 * L) == round(old[0] * 4 * L) + 1  # one more atom within a cutoff
+        assert round(new[0] * 4 * L) == round(part[0] * 4 * L) + 1
+        assert new[0] > old[0] and new[1] >= old[1] and new[2] >= old[2]
+    e = E.config1(N=120)
+    Xn = oracle.gdt_tm_vs_ref(e.coords, e.natives[0])
+    Xo = oracle.gdt_tm_vs_ref_rule(e.coords, e.natives[0], 1, 4)
+    assert np.all(Xn >= Xo - 1e-15)
+    # the bound on the refinements counts: with one refinement at most, fewer superpositions
+    X1 = oracle.gdt_tm_vs_ref_rule(e.coords, e.natives[0], 4, 1)
+    assert np.all(Xn >= X1 - 1e-15)
+
+
+@pytest.mark.parametrize("mut", [("stop at the first repeated count", "#define GDT_STABLE 4 ", "#define GDT_STABLE 1 "),
+                                 ("at most four refinements", "#define GDT_MAX_REFINE 20 ", "#define GDT_MAX_REFINE 4 ")],
+                         ids=lambda m: m[0])
+def test_planted_stop_rule_mistakes_are_caught(mut):
+    """The shorter stop rules, planted in the oracle's default, miss the drifting helix's extra atom."""
+    desc, old, new = mut
+    src = open(oracle._SRC).read()
+    assert src.count(old) == 1, desc
+    with tempfile.TemporaryDirectory() as d:
+        p = os.path.join(d, "mut.c")
+        open(p, "w").write(src.replace(old, new))
+        lib = oracle.load(oracle.build(p, os.path.join(d, "libmut.so")))
+        caught = False
+        for c in (0.33, 0.42):
+            A, B = drifting_helix(32, c, 1.5)
+            L = A.shape[0]
+            # the rule's count on this helix: one atom more than the shorter search finds
+            want = round(oracle.gdt_tm_vs_ref_rule(B[None], A, 1, 4)[0][0] * 4 * L) + 1
+            caught |= round(oracle.gdt_tm_vs_ref(B[None], A, lib=lib)[0][0] * 4 * L) != want
         assert caught, f"planted mistake '{desc}' was not caught"

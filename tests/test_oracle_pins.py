@@ -200,6 +200,25 @@ def _loss_rows(X, w, a):
     return float((w[idx] * c).sum())
 
 
+def test_allpairs_layout_against_single_pairs():
+    """Every entry of the condensed all-versus-all matrix is the single-pair value of the pair its
+    index names, idx(a, b) = a N - a (a + 1) / 2 + (b - a - 1) for a < b (the matrix's loop
+    bounds and index arithmetic, checked pair by pair on a small ensemble)."""
+    e = E.decoy_ensemble(7, 23, 2, (0.5, 6.0), 71)
+    X = e.coords
+    full = oracle.crmsd_allpairs(X)
+    N = X.shape[0]
+    assert full.shape == (N * (N - 1) // 2,)
+    seen = np.zeros(full.shape, dtype=bool)
+    for a in range(N):
+        for b in range(a + 1, N):
+            k = a * N - a * (a + 1) // 2 + (b - a - 1)
+            seen[k] = True
+            c, _ = oracle.crmsd_pair(X[a], X[b])
+            assert full[k] == c
+    assert seen.all()
+
+
 def test_gradient_matches_finite_differences():
     """Analytic envelope-theorem gradient vs FP64 central differences (exact FP32 steps)."""
     e = E.decoy_ensemble(8, 24, 2, (0.5, 6.0), 77)
