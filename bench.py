@@ -15,7 +15,8 @@ step, outside the events. ``e2e`` repeats the step through the public API with h
 the step's inputs go host->device from pinned memory and the matrix, the vs-native scores and
 the gradient come back device->host inside the timed region.
 
-Extra keys: the forward alone and its plain-form ratio, sampled errors of the matrix and of the
+Extra keys: the forward alone and its ratios to the plain FP32 form and to the exact-integer
+CUDA-core form (the accuracy-matched denominator), sampled errors of the matrix and of the
 gradient against the FP64 oracle, the rooflines of the two tensor-core kernels, the 50,000 x
 1,000 forward, the per-form errors on the precision ensemble, the stored-rotation step and the
 5,000 x 300 step (both labelled as departing from the default), and the widened scores (dRMSD,
@@ -106,29 +107,101 @@ def workload_name(N, L):
             f"{N * (N - 1) // 2} pairs")
 
 
+class _CtypesNvml:
+    """The few NVML calls the clock sampler needs, through ctypes on the driver's libnvidia-ml
+    (for hosts where the pynvml module is not importable). Reason bits as in the public nvml.h."""
+
+    NVML_CLOCK_SM = 1
+    nvmlClocksEventReasonSwPowerCap = 0x4
+    nvmlClocksEventReasonHwSlowdown = 0x8
+    nvmlClocksEventReasonSwThermalSlowdown = 0x20
+    nvmlClocksEventReasonHwThermalSlowdown = 0x40
+
+    def __init__(self):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        self._ok(self.lib.nvmlInit_v2(), "nvmlInit_v2")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    @staticmethod
+    def _ok(rc, what):
+        if rc != 0:
+            raise RuntimeError(f"{what} returned {rc}")
+
+    def handle(self, uuid, index):
+        h = self.ct.c_void_p()
+        if uuid and self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), self.ct.byref(h)) == 0:
+            return h
+        self._ok(self.lib.nvmlDeviceGetHandleByIndex_v2(self.ct.c_uint(index), self.ct.byref(h)),
+                 "nvmlDeviceGetHandleByIndex_v2")
+        return h
+
+    def nvmlDeviceGetClockInfo(self, h, kind):
+        v = self.ct.c_uint()
+        self._ok(self.lib.nvmlDeviceGetClockInfo(h, self.ct.c_int(kind), self.ct.byref(v)), "nvmlDeviceGetClockInfo")
+        return v.value
+
+    def nvmlDeviceGetMaxClockInfo(self, h, kind):
+        v = self.ct.c_uint()
+        self._ok(self.lib.nvmlDeviceGetMaxClockInfo(h, self.ct.c_int(kind), self.ct.byref(v)),
+                 "nvmlDeviceGetMaxClockInfo")
+        return v.value
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, h):
+        v = self.ct.c_ulonglong()
+        self._ok(self.reasons_fn(h, self.ct.byref(v)), "clock event reasons")
+        return v.value
+
+
 class Clocks:
     """SM clock and clock-event reasons sampled through NVML every ~10 ms in a thread, so that a
     timed region of a fraction of a second still carries samples; window() keeps those taken
-    between two perf_counter() stamps."""
+    between two perf_counter() stamps. NVML through the pynvml module, else through ctypes on
+    the driver's library. Reading only: no setting of the GPU is changed."""
 
     NAMES = (("hw_slowdown", "nvmlClocksEventReasonHwSlowdown"),
              ("hw_thermal_slowdown", "nvmlClocksEventReasonHwThermalSlowdown"),
              ("sw_thermal_slowdown", "nvmlClocksEventReasonSwThermalSlowdown"),
              ("sw_power_cap", "nvmlClocksEventReasonSwPowerCap"))
 
-    def __init__(self, gpu_index, period=0.01):
+    def __init__(self, gpu_index, uuid=None, period=0.01):
         self.samples = []
+        self.smax, self.source = None, None
         self.period = period
         self.stop_ev = threading.Event()
         self.err = None
+        self.nv = None
+        errs = []
         try:
             import pynvml
             pynvml.nvmlInit()
-            self.nv = pynvml
-            self.h = pynvml.nvmlDeviceGetHandleByIndex(gpu_index)
+            h = None
+            if uuid:
+                try:
+                    h = pynvml.nvmlDeviceGetHandleByUUID(uuid)
+                except Exception:
+                    h = None
+            self.h = h if h is not None else pynvml.nvmlDeviceGetHandleByIndex(gpu_index)
             self.smax = float(pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM))
-        except Exception as ex:  # no NVML: the line says so
-            self.nv, self.err = None, f"NVML unavailable: {ex}"
+            self.nv, self.source = pynvml, "NVML (pynvml)"
+        except Exception as ex:
+            errs.append(f"pynvml: {ex}")
+        if self.nv is None:
+            try:
+                nv = _CtypesNvml()
+                self.h = nv.handle(uuid, gpu_index)
+                self.smax = float(nv.nvmlDeviceGetMaxClockInfo(self.h, nv.NVML_CLOCK_SM))
+                self.nv, self.source = nv, "NVML (ctypes on libnvidia-ml.so.1)"
+            except Exception as ex:
+                errs.append(f"ctypes NVML: {ex}")
+        self.smi = None
+        if self.nv is None:  # no NVML: nvidia-smi's own sampling loop, else the line says so
+            self.err = "NVML unavailable: " + "; ".join(errs)
+            import shutil
+            if shutil.which("nvidia-smi"):
+                self.smi_index = gpu_index if uuid is None else uuid
         self.th = threading.Thread(target=self._run, daemon=True)
 
     def _run(self):
@@ -144,16 +217,63 @@ class Clocks:
                 return
             time.sleep(self.period)
 
+    SMI_FIELDS = ("timestamp,clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+                  "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                  "clocks_event_reasons.sw_power_cap")
+
     def start(self):
         if self.nv is not None:
             self.th.start()
+        elif hasattr(self, "smi_index"):
+            import subprocess
+            import tempfile
+            self.smi_file = tempfile.TemporaryFile(mode="w+")
+            self.wall_minus_perf = time.time() - time.perf_counter()
+            self.smi = subprocess.Popen(["nvidia-smi", "-i", str(self.smi_index), "--query-gpu=" + self.SMI_FIELDS,
+                                         "--format=csv,noheader,nounits", "-lms", "100"],
+                                        stdout=self.smi_file, stderr=subprocess.DEVNULL)
+
+    def _smi_collect(self):
+        """Ends this sampler's own nvidia-smi child and converts its rows (wall-clock stamps) into
+        perf_counter samples."""
+        import datetime
+        if self.smi is not None:
+            self.smi.terminate()
+            try:
+                self.smi.wait(timeout=5)
+            except Exception:
+                self.smi.kill()
+            self.smi = None
+            self.smi_file.seek(0)
+            bits = (8, 64, 32, 4)  # the NVML reason bits of the four fields, in NAMES order below
+            for row in self.smi_file.read().splitlines():
+                f = [x.strip() for x in row.split(",")]
+                if len(f) != 7:
+                    continue
+                try:
+                    wall = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    sm, smax = float(f[1]), float(f[2])
+                except ValueError:
+                    continue
+                r = 0
+                for b, v in zip(bits, f[3:]):
+                    if v.lower() == "active":
+                        r |= b
+                self.samples.append((wall - self.wall_minus_perf, sm, r))
+                self.smax = smax
+            self.smi_file.close()
+            self.source = "nvidia-smi -lms 100 (NVML not importable)"
 
     def stop(self):
         self.stop_ev.set()
         if self.th.is_alive():
             self.th.join(timeout=2)
+        self._smi_collect()
 
     def window(self, t0, t1):
+        if self.nv is None and self.smi is not None:
+            self._smi_collect()
+            self.nv = _CtypesNvml  # reason bit constants only
         if self.nv is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [self.err], "samples": 0}
         sel = [s for s in self.samples if t0 <= s[0] <= t1]
@@ -163,7 +283,8 @@ class Clocks:
                 if r & getattr(self.nv, const):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(s[1] for s in sel) if sel else None, "sm_max_mhz": self.smax,
-                "reasons": sorted(reasons), "samples": len(sel), "source": "NVML, every ~10 ms, timed region only"}
+                "reasons": sorted(reasons), "samples": len(sel),
+                "source": f"{self.source}, every ~10 ms, timed region only"}
 
 
 def csrc_hash():
@@ -358,7 +479,12 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", torch.cuda.current_device())
     lib = clusco.load()
-    clocks = Clocks(local if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        uuid = None
+    clocks = Clocks(local if "CUDA_VISIBLE_DEVICES" not in os.environ else 0, uuid)
     clocks.start()
     form = clusco.FORM_BF16_EXACT2
 
@@ -429,6 +555,16 @@ def run_ours(args):
     plain_fwd = statistics.mean(timer(lambda: clusco.crmsd_allpairs(X, clusco.FORM_FP32_SIMT, out=out_p,
                                                                      workspace=ws_p), 3, 1)["ms"])
     plain_fwd = max_over_ranks([plain_fwd], dev, ws_)[0]
+    del ws_p
+    # the accuracy-matched CUDA-core denominator: the exact-integer form (24-bit fixed point,
+    # int64 sums, FP64 refinement below its FP32 bound), same inputs
+    ws_p = torch.empty(clusco.workspace_bytes(clusco.OP_ALLPAIRS, N, L, clusco.FORM_INT_SIMT), dtype=torch.uint8,
+                       device=dev)
+    int_fwd = statistics.mean(timer(lambda: clusco.crmsd_allpairs(X, clusco.FORM_INT_SIMT, out=out_p,
+                                                                   workspace=ws_p), 3, 1)["ms"])
+    int_fwd = max_over_ranks([int_fwd], dev, ws_)[0]
+    if clusco.sync_status() != 0:
+        raise RuntimeError("device status set during the exact-integer forward: " + lib.clusco_last_error().decode())
     del ws_p, out_p
 
     # accuracy of this run's outputs against the oracle (outside timing): sampled pairs of the
@@ -570,6 +706,7 @@ def run_ours(args):
             "fwd": {"value": whole_job_rate(P, fms, ws_), "unit": UNIT, "ms": fms},
             "bwd": {"value": whole_job_rate(P, bms, ws_), "unit": UNIT, "ms": bms},
             "vs_plain_fp32_fwd": plain_fwd / fms, "plain_fp32_fwd_ms": plain_fwd,
+            "vs_plain_exact_int": int_fwd / fms, "plain_exact_int_fwd_ms": int_fwd,
             "accuracy": acc,
             "roofline": dominant, "roofline_other": other,
             "clocks": clk, "gpu_launches": launches_per_step * args.steps}
@@ -656,7 +793,8 @@ def extra(args, line, torch, clusco, lib, dev, timer, ws_, rank, dist):
                           f"c from {ref_nd.min():.3f} to {ref_nd.max():.2f} A, and {len(ra)} random pairs"}
         out2 = torch.empty(N2 * (N2 - 1) // 2, dtype=torch.float32, device=dev)
         for name, f in (("bf16_exact2", clusco.FORM_BF16_EXACT2), ("bf16x3", clusco.FORM_BF16X3),
-                        ("tf32", clusco.FORM_TF32), ("fp32_simt", clusco.FORM_FP32_SIMT)):
+                        ("tf32", clusco.FORM_TF32), ("fp32_simt", clusco.FORM_FP32_SIMT),
+                        ("int_simt", clusco.FORM_INT_SIMT)):
             ws2 = torch.empty(clusco.workspace_bytes(clusco.OP_ALLPAIRS, N2, e2.L, f), dtype=torch.uint8, device=dev)
             t = timer(lambda: clusco.crmsd_allpairs(X2, f, out=out2, workspace=ws2), 2, 1)
             status(f"the precision forward ({name})")
@@ -665,7 +803,8 @@ def extra(args, line, torch, clusco, lib, dev, timer, ws_, rank, dist):
             pf[name] = {"near_dup_max": float(d_nd.max()), "near_dup_p99": float(np.quantile(d_nd, 0.99)),
                         "random_max": float(d_rd.max()), "random_p99": float(np.quantile(d_rd, 0.99)),
                         "fwd_ms": statistics.mean(t["ms"]),
-                        "meets_1e-3_A": bool(max(d_nd.max(), d_rd.max()) <= 1e-3)}
+                        "meets_1e-3_A": bool(max(d_nd.max(), d_rd.max()) <= 1e-3),
+                        "meets_1e-4_A": bool(max(d_nd.max(), d_rd.max()) <= 1e-4)}
             del ws2
         line["per_form_error"] = pf
         del X2, out2

@@ -63,13 +63,20 @@ typedef enum {
  *                 accumulators, exact for L <= 1024; FP32 epilogue with FP64
  *                 refinement of the pairs whose FP32 error bound is too large.
  *  FP8_EXACT   -- tcgen05 kind::f8f6f4 on 0/1 operands (exact integer counts);
- *                 the tensor-core form of the contact map overlap only. */
+ *                 the tensor-core form of the contact map overlap only.
+ *  INT_SIMT    -- exact-integer CUDA-core form: 24-bit fixed point per model and
+ *                 axis (step max|x| / (2^23 - 1)), every product a 32 x 32 -> 64-bit
+ *                 integer multiply-add into int64 (exact for L <= 2^17); FP32 epilogue
+ *                 with FP64 refinement of every pair whose FP32 error bound exceeds
+ *                 2e-5 A. All-pairs calls (dense, panel, threshold) only; no rotations,
+ *                 no fused step, no dRMSD / CMO (CLUSCO_EUNSUPPORTED). */
 typedef enum {
     CLUSCO_FORM_FP32_SIMT = 0,
     CLUSCO_FORM_TF32 = 1,
     CLUSCO_FORM_BF16X3 = 2,
     CLUSCO_FORM_BF16_EXACT2 = 3,
-    CLUSCO_FORM_FP8_EXACT = 4
+    CLUSCO_FORM_FP8_EXACT = 4,
+    CLUSCO_FORM_INT_SIMT = 5
 } clusco_form;
 
 typedef enum {

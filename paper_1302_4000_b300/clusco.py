@@ -27,7 +27,9 @@ FORM_TF32 = 1
 FORM_BF16X3 = 2
 FORM_BF16_EXACT2 = 3
 FORM_FP8_EXACT = 4  # the contact map overlap's tensor-core form
-FORMS = {"fp32_simt": FORM_FP32_SIMT, "tf32": FORM_TF32, "bf16x3": FORM_BF16X3, "bf16_exact2": FORM_BF16_EXACT2}
+FORM_INT_SIMT = 5  # exact-integer CUDA-core form (all-pairs cRMSD only)
+FORMS = {"fp32_simt": FORM_FP32_SIMT, "tf32": FORM_TF32, "bf16x3": FORM_BF16X3, "bf16_exact2": FORM_BF16_EXACT2,
+         "int_simt": FORM_INT_SIMT}
 
 OP_ALLPAIRS = 0
 OP_VS_REF = 1

@@ -67,13 +67,17 @@ struct Carver {
 bool valid_form(int form)
 {
     return form == CLUSCO_FORM_FP32_SIMT || form == CLUSCO_FORM_TF32 || form == CLUSCO_FORM_BF16X3 ||
-           form == CLUSCO_FORM_BF16_EXACT2;
+           form == CLUSCO_FORM_BF16_EXACT2 || form == CLUSCO_FORM_INT_SIMT;
 }
+
+// The CUDA-core forms (no tcgen05, no rotations).
+bool simt_form(int form) { return form == CLUSCO_FORM_FP32_SIMT || form == CLUSCO_FORM_INT_SIMT; }
 
 // Layout of the all-pairs workspace; also used (with base == nullptr) to size it.
 struct PairsWs {
-    // SIMT
+    // SIMT (Xn: the exact-integer form's fixed-point coordinates, same layout as Xk)
     float *Xk = nullptr;
+    int *Xn = nullptr;
     double *G64 = nullptr;
     // tcgen05
     void *planes = nullptr;
@@ -107,6 +111,12 @@ PairsWs carve_pairs(void *base, int64_t N, int64_t L, int form, bool with_rot = 
         w.Lp = round_up(L, SIMT_KC);
         w.Npad = round_up(N, SIMT_TILE);
         w.Xk = c.take<float>((size_t)(w.Lp * w.Npad * 3));
+        w.G64 = c.take<double>((size_t)w.Npad);
+    } else if (form == CLUSCO_FORM_INT_SIMT) {
+        w.Lp = round_up(L, SIMT_KC);
+        w.Npad = round_up(N, SIMT_TILE);
+        w.Xn = c.take<int>((size_t)(w.Lp * w.Npad * 3));
+        w.scales = c.take<float>((size_t)w.Npad * 3);
         w.G64 = c.take<double>((size_t)w.Npad);
     } else {
         const int64_t kalign = (form == CLUSCO_FORM_TF32) ? 32 : 64;  // 128-byte rows
@@ -190,6 +200,8 @@ int run_prepass(const float *coords, int64_t N, int64_t L, int form, const Pairs
     const unsigned blocks = (unsigned)((w.Npad + 7) / 8);
     if (form == CLUSCO_FORM_FP32_SIMT) {
         prepass_simt_kernel<<<blocks, 256, 0, st>>>(coords, N, (int)L, (int)w.Lp, w.Npad, w.Xk, w.G64);
+    } else if (form == CLUSCO_FORM_INT_SIMT) {
+        prepass_int_kernel<<<blocks, 256, 0, st>>>(coords, N, (int)L, (int)w.Lp, w.Npad, w.Xn, w.scales, w.G64);
     } else if (form == CLUSCO_FORM_BF16_EXACT2) {
         prepass_tc_kernel<TC_EXACT2><<<blocks, 256, 0, st>>>(coords, N, (int)L, (int)w.Lp, w.Npad, w.Rpad,
                                                                 w.planes, w.scales, w.G64, w.G32, nullptr, w.hplane,
@@ -223,12 +235,14 @@ int allpairs_impl(const float *coords, int64_t N, int64_t L, int64_t row_begin, 
     if ((rc = check_ptr(coords, "coords", 4))) return rc;
     if (!thr && (rc = check_ptr(out, "out", 4))) return rc;
     if (!valid_form(form)) return fail(CLUSCO_EINVAL, "unknown form %d", form);
-    if (rot && form == CLUSCO_FORM_FP32_SIMT)
+    if (rot && simt_form(form))
         return fail(CLUSCO_EUNSUPPORTED, "rotations are produced by the tensor-core forms only");
+    if (form == CLUSCO_FORM_INT_SIMT && L > INT_MAX_L)
+        return fail(CLUSCO_EUNSUPPORTED, "L=%lld above the 2^17 atoms of the exact-integer form", (long long)L);
     if (row_begin < 0 || row_end > N - 1 || row_begin >= row_end)
         return fail(CLUSCO_EINVAL, "row range [%lld, %lld) outside [0, N-1=%lld)", (long long)row_begin,
                     (long long)row_end, (long long)(N - 1));
-    if (form != CLUSCO_FORM_FP32_SIMT) {
+    if (!simt_form(form)) {
         if ((rc = tc_supported(form, L))) return rc;
     }
     const PairsWs sized = carve_pairs(nullptr, N, L, form, rot != nullptr);
@@ -237,7 +251,7 @@ int allpairs_impl(const float *coords, int64_t N, int64_t L, int64_t row_begin, 
     const PairsWs w = carve_pairs(s.ptr, N, L, form, rot != nullptr);
     if ((rc = run_prepass(coords, N, L, form, w, st))) return rc;
     const int64_t out_base = condensed_idx(row_begin, row_begin + 1, N);
-    if (form == CLUSCO_FORM_FP32_SIMT) {
+    if (simt_form(form)) {
         const int64_t T = w.Npad / SIMT_TILE;
         const int64_t I0 = row_begin / SIMT_TILE, I1 = (row_end - 1) / SIMT_TILE + 1;
         const int64_t t0 = tri_row_start(I0, T), nt = tri_row_start(I1, T) - t0;
@@ -252,8 +266,12 @@ int allpairs_impl(const float *coords, int64_t N, int64_t L, int64_t row_begin, 
             sink.tau = thr->tau;
             CUDA_TRY(cudaMemsetAsync(thr->count, 0, sizeof(unsigned long long), st));
         }
-        pairs_simt_kernel<<<(unsigned)nt, 256, 0, st>>>(w.Xk, w.G64, N, w.Npad, (int)w.Lp, (int)L, T, t0,
-                                                        row_begin, row_end, sink);
+        if (form == CLUSCO_FORM_INT_SIMT)
+            pairs_int_kernel<<<(unsigned)(2 * nt), 256, 0, st>>>(w.Xn, w.scales, w.G64, N, w.Npad, (int)w.Lp,
+                                                                 (int)L, T, t0, row_begin, row_end, sink);
+        else
+            pairs_simt_kernel<<<(unsigned)nt, 256, 0, st>>>(w.Xk, w.G64, N, w.Npad, (int)w.Lp, (int)L, T, t0,
+                                                            row_begin, row_end, sink);
         CUDA_TRY(cudaGetLastError());
     } else {
         TcArgs a;
@@ -363,7 +381,7 @@ size_t clusco_workspace_bytes(int op, int64_t N, int64_t L, int form)
         return backward_ws_bytes(N, L, form);
     }
     if (op == CLUSCO_OP_ALLPAIRS_ROT) {
-        if (!valid_form(form) || form == CLUSCO_FORM_FP32_SIMT || N < 2) return 0;
+        if (!valid_form(form) || simt_form(form) || N < 2) return 0;
         return carve_pairs(nullptr, N, L, form, true).bytes;
     }
     if (op == CLUSCO_OP_BACKWARD_ROT) {
@@ -379,11 +397,11 @@ size_t clusco_workspace_bytes(int op, int64_t N, int64_t L, int form)
         return carve_cmo(nullptr, N, L, form).bytes;
     }
     if (op == CLUSCO_OP_STEP) {
-        if (!valid_form(form) || form == CLUSCO_FORM_FP32_SIMT || N < 2 || !rc_supported(L)) return 0;
+        if (!valid_form(form) || simt_form(form) || N < 2 || !rc_supported(L)) return 0;
         return align256(carve_pairs(nullptr, N, L, form).bytes) + carve_rc(nullptr, N, L).bytes;
     }
     if (op == CLUSCO_OP_STEP_ROT) {
-        if (!valid_form(form) || form == CLUSCO_FORM_FP32_SIMT || N < 2 || !bwr_supported(L)) return 0;
+        if (!valid_form(form) || simt_form(form) || N < 2 || !bwr_supported(L)) return 0;
         return align256(carve_pairs(nullptr, N, L, form, true).bytes) + carve_bt(nullptr, N, L).bytes;
     }
     return 0;
@@ -788,7 +806,7 @@ int clusco_crmsd_allpairs_step_rot(const float *coords, int64_t N, int64_t L, co
     if ((rc = check_ptr(rot, "rot", 16))) return rc;
     if ((rc = check_ptr(grad_coords, "grad_coords", 4))) return rc;
     if (!valid_form(form)) return fail(CLUSCO_EINVAL, "unknown form %d", form);
-    if (form == CLUSCO_FORM_FP32_SIMT)
+    if (simt_form(form))
         return fail(CLUSCO_EUNSUPPORTED, "rotations are produced by the tensor-core forms only");
     if (!(eps > 0.f) || !std::isfinite(eps)) return fail(CLUSCO_EINVAL, "eps=%g must be finite and > 0", (double)eps);
     if (!bwr_supported(L)) return fail(CLUSCO_EUNSUPPORTED, "L=%lld above the 512 atoms of this path", (long long)L);
@@ -820,7 +838,7 @@ int clusco_crmsd_allpairs_step(const float *coords, int64_t N, int64_t L, const 
     if ((rc = check_ptr(out, "out", 4))) return rc;
     if ((rc = check_ptr(grad_coords, "grad_coords", 4))) return rc;
     if (!valid_form(form)) return fail(CLUSCO_EINVAL, "unknown form %d", form);
-    if (form == CLUSCO_FORM_FP32_SIMT) return fail(CLUSCO_EUNSUPPORTED, "the fused step needs a tensor-core form");
+    if (simt_form(form)) return fail(CLUSCO_EUNSUPPORTED, "the fused step needs a tensor-core form");
     if (!(eps > 0.f) || !std::isfinite(eps)) return fail(CLUSCO_EINVAL, "eps=%g must be finite and > 0", (double)eps);
     if (!rc_supported(L)) return fail(CLUSCO_EUNSUPPORTED, "L=%lld above the 1024 atoms of this path", (long long)L);
     if ((rc = tc_supported(CLUSCO_FORM_BF16_EXACT2, L))) return fail(rc, "tensor-core path unavailable on this device");

@@ -17,6 +17,9 @@
 //    BF16X3: plane 0 = bf16(x), plane 1 = bf16(x - bf16(x)); G from hi + lo.
 //    TF32: one FP32 plane holding tf32-rounded x; G from those values.
 //    Optionally (xf != nullptr) the centred FP32 coordinates in the same row layout.
+//  * exact-integer SIMT form: Xn[k][a][axis] (the FP32-SIMT layout) holding the 24-bit fixed
+//    point value n = round(x / s_axis), s_axis = max|x_axis| / (2^23 - 1) per model and axis;
+//    G from the same n (exact in int64).
 //  The centroid is summed in FP32 per lane and combined in FP64 across lanes;
 //  its own rounding error only shifts the model by ~1e-6 A, which changes
 //  cRMSD at second order.
@@ -30,6 +33,7 @@ namespace clusco {
 constexpr int SIMT_TILE = 64;  // models per SIMT tile side
 constexpr int SIMT_KC = 16;    // atoms per SIMT K chunk
 constexpr int TC_MA = 40;      // models per tcgen05 A tile (128 rows)
+constexpr float Q24 = 8388607.f;  // 2^23 - 1: the 24-bit fixed-point range
 constexpr int TC_MB = 20;      // models per tcgen05 B tile (64 rows)
 
 __host__ __device__ __forceinline__ int64_t tc_row(int64_t a, int axis)
@@ -117,6 +121,56 @@ __global__ void __launch_bounds__(256) prepass_simt_kernel(const float *__restri
         }
     }
     g = warp_sum_d(g);
+    if (lane == 0) {
+        G64[a] = finite ? g : __longlong_as_double(0x7ff8000000000000ll);
+        if (!finite) set_status(CLUSCO_ST_NONFINITE);
+    }
+}
+
+// Exact-integer SIMT layout (see the header). Grid: ceil(Npad/8) blocks of 256 threads.
+__global__ void __launch_bounds__(256) prepass_int_kernel(const float *__restrict__ coords, int64_t N, int L, int Lp,
+                                                          int64_t Npad, int *__restrict__ Xn,
+                                                          float *__restrict__ scales, double *__restrict__ G64)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t a = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (a >= Npad) return;
+    if (a >= N) {
+        for (int i = lane; i < Lp; i += 32)
+            for (int ax = 0; ax < 3; ++ax) Xn[((int64_t)i * Npad + a) * 3 + ax] = 0;
+        if (lane < 3) scales[a * 3 + lane] = 1.f;
+        if (lane == 0) G64[a] = 0.0;
+        return;
+    }
+    const float *x = coords + a * (int64_t)L * 3;
+    float mu[3], mx[3];
+    bool finite;
+    model_centroid_absmax(x, L, lane, mu, mx, &finite);
+    float sc[3], inv[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const bool pos = mx[ax] > 0.f && isfinite(mx[ax]);
+        sc[ax] = pos ? mx[ax] / Q24 : 1.f;
+        inv[ax] = pos ? Q24 / mx[ax] : 1.f;
+    }
+    long long gi[3] = {0, 0, 0};
+    for (int i = lane; i < Lp; i += 32) {
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            int ni = 0;
+            if (i < L) {
+                float n = rintf((x[3 * i + ax] - mu[ax]) * inv[ax]);
+                n = isfinite(n) ? fminf(fmaxf(n, -Q24), Q24) : 0.f;
+                ni = (int)n;
+            }
+            Xn[((int64_t)i * Npad + a) * 3 + ax] = ni;
+            gi[ax] += (long long)ni * ni;
+        }
+    }
+    double g = 0.0;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) g += (double)sc[ax] * (double)sc[ax] * (double)warp_sum_ll(gi[ax]);
+    if (lane < 3) scales[a * 3 + lane] = sc[lane];
     if (lane == 0) {
         G64[a] = finite ? g : __longlong_as_double(0x7ff8000000000000ll);
         if (!finite) set_status(CLUSCO_ST_NONFINITE);

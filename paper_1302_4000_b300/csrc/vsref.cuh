@@ -12,8 +12,6 @@
 
 namespace clusco {
 
-constexpr float Q24 = 8388607.f;  // 2^23 - 1
-
 struct RefInfo {
     float scale[3];
     float mu[3];

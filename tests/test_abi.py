@@ -163,4 +163,19 @@ def test_step_rot_host_side_validation(lib):
     assert step(fake, 10, 10, fake, fake, fake, fake, ex, ctypes.c_float(0.0), None, 0, None) == 1  # eps
     assert step(fake, 1, 10, fake, fake, fake, fake, ex, eps, None, 0, None) == 1  # N < 2
     assert step(fake, 10, 10, fake, fake, fake, fake, clusco.FORM_FP32_SIMT, eps, None, 0, None) == 7
+    assert step(fake, 10, 10, fake, fake, fake, fake, clusco.FORM_INT_SIMT, eps, None, 0, None) == 7
     assert step(fake, 10, 600, fake, fake, fake, fake, ex, eps, None, 0, None) == 7  # L > 512
+
+
+def test_exact_integer_form_host_side(lib):
+    """The exact-integer CUDA-core form serves the all-pairs calls only: no rotations, no fused
+    step, no dRMSD / contact map overlap; L is capped where its int64 sums could overflow."""
+    ix = clusco.FORM_INT_SIMT
+    assert clusco.workspace_bytes(clusco.OP_ALLPAIRS, 5000, 300, ix) > 0
+    for op in (clusco.OP_ALLPAIRS_ROT, clusco.OP_STEP, clusco.OP_STEP_ROT, clusco.OP_DRMSD, clusco.OP_CMO):
+        assert clusco.workspace_bytes(op, 5000, 300, ix) == 0, op
+    fake, eps = ctypes.c_void_p(0x1000), ctypes.c_float(1e-6)
+    assert lib.clusco_crmsd_allpairs_rot(fake, 10, 10, fake, fake, ix, None, 0, None) == 7
+    assert lib.clusco_crmsd_allpairs_step(fake, 10, 10, fake, fake, fake, ix, eps, None, 0, None) == 7
+    assert lib.clusco_drmsd_allpairs(fake, 10, 10, fake, ix, None, 0, None) == 7
+    assert lib.clusco_crmsd_allpairs(fake, 10, (1 << 17) + 1, fake, ix, None, 0, None) == 7

@@ -3,7 +3,8 @@
 * Precision ensemble (20,000 x 150, half of it near-duplicate clusters, sigma 0.02-0.5 A):
   every form; all 95,000 intra-cluster pairs plus 20,000 random pairs against the FP64
   oracle; max and p99 |d| printed per form and pair class. Exact-digit BF16 must stay within
-  1e-3 A on every sampled pair; the other forms within their accumulation bounds.
+  1e-3 A on every sampled pair, the exact-integer CUDA-core form within 1e-4 A; the other
+  forms within their accumulation bounds.
 * Large ensemble (50,000 x 1,000, 1.25e9 pairs, 5 GB condensed output kept on the device):
   exact-digit BF16 on 20,000 sampled pairs; a row panel equals the same slice of the full
   matrix; the plain form on one panel.
@@ -41,6 +42,8 @@ def gather(out, ia, ib, N):
 def bound(form, ref, Ga, Gb, L):
     if form == clusco.FORM_BF16_EXACT2:
         return np.full_like(ref, 1e-3)
+    if form == clusco.FORM_INT_SIMT:
+        return np.full_like(ref, 1e-4)
     u = {clusco.FORM_FP32_SIMT: EPS32, clusco.FORM_TF32: 2.0 ** -11, clusco.FORM_BF16X3: 2.0 ** -17}[form]
     return np.maximum(c_error_bound(ref, Ga, Gb, L, 8.0 * np.sqrt(L) * u), 1e-4)
 
@@ -69,7 +72,8 @@ def test_precision_ensemble_every_form():
     nd = len(da)
     print(f"\nprecision ensemble N={N} L={L}: {nd} intra-cluster pairs (c {ref[:nd].min():.3f}-{ref[:nd].max():.3f} A), "
           f"{len(ra)} random pairs")
-    for form in (clusco.FORM_BF16_EXACT2, clusco.FORM_BF16X3, clusco.FORM_TF32, clusco.FORM_FP32_SIMT):
+    for form in (clusco.FORM_BF16_EXACT2, clusco.FORM_BF16X3, clusco.FORM_TF32, clusco.FORM_FP32_SIMT,
+                 clusco.FORM_INT_SIMT):
         out = clusco.crmsd_allpairs(X, form)
         assert clusco.sync_status() == 0
         got = gather(out, ia, ib, N)

@@ -11,6 +11,8 @@ Every call goes through the C-ABI (the ctypes binding). Tolerances:
   pushed through the cancellation in D = R_A^2 + R_B^2 - 2 Sigma.
 * TF32 and BF16X3: their input rounding (2^-11 and 2^-17 relative) is not benign on
   near-duplicates; bounds as FP32 with their own unit roundoff.
+* INT_SIMT (exact-integer CUDA-core form: 24-bit fixed point, int64 sums, FP64 refinement
+  wherever the FP32 bound exceeds 2e-5 A): 1e-4 A absolute on every pair.
 * one-vs-reference (24-bit exact integers, FP64 epilogue): 1e-4 A.
 """
 import numpy as np
@@ -41,7 +43,7 @@ def tc_forms():
 
 
 def forms_available():
-    out = [clusco.FORM_FP32_SIMT]
+    out = [clusco.FORM_FP32_SIMT, clusco.FORM_INT_SIMT]
     X = torch.zeros((4, 8, 3), device="cuda")
     X[:, :, 0] = torch.arange(8, device="cuda")
     for f in tc_forms():
@@ -58,6 +60,8 @@ def forms_available():
 def bound_for(form, c_ref, Ga, Gb, L):
     if form == clusco.FORM_BF16_EXACT2:
         return np.full_like(np.asarray(c_ref, dtype=np.float64), 1e-3)
+    if form == clusco.FORM_INT_SIMT:
+        return np.full_like(np.asarray(c_ref, dtype=np.float64), 1e-4)
     u = {clusco.FORM_FP32_SIMT: EPS32, clusco.FORM_TF32: 2.0 ** -11, clusco.FORM_BF16X3: 2.0 ** -17}[form]
     rel = 8.0 * np.sqrt(L) * u
     return np.maximum(c_error_bound(c_ref, Ga, Gb, L, rel), 1e-4)
@@ -85,7 +89,7 @@ def check(form, X, got, ia, ib, ref):
     return err
 
 
-@pytest.mark.parametrize("form", [0, 1, 2, 3])
+@pytest.mark.parametrize("form", [0, 1, 2, 3, 5])
 def test_config0_all_pairs(form):
     if form not in forms_available():
         pytest.skip("form not built")
@@ -94,8 +98,8 @@ def test_config0_all_pairs(form):
     got = run_allpairs(e.coords, form)
     ia, ib = all_pairs(e.N)
     err = check(form, e.coords, got, ia, ib, ref)
-    if form in (clusco.FORM_FP32_SIMT, clusco.FORM_BF16_EXACT2):
-        assert err.max() <= (1e-4 if form == clusco.FORM_FP32_SIMT else 1e-3)
+    if form in (clusco.FORM_FP32_SIMT, clusco.FORM_BF16_EXACT2, clusco.FORM_INT_SIMT):
+        assert err.max() <= (1e-3 if form == clusco.FORM_BF16_EXACT2 else 1e-4)
 
 
 @pytest.mark.parametrize("N", [2, 3, 5, 33, 129])
