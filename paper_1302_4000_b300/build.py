@@ -15,12 +15,15 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc", "clusco.cu")
 LIB = os.path.join(HERE, "libclusco.so")
+# the test-hook build (include/clusco_debug.h): same sources, hooks compiled in, 0.2 s device waits
+DEBUG_LIB = os.path.join(HERE, "libclusco_debug.so")
+DEBUG_FLAGS = ("-DCLUSCO_DEBUG_HOOKS", "-DCLUSCO_WAIT_NS=200000000ull")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
 def sources():
-    return [SRC] + sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh"))) + [
-        os.path.join(os.path.dirname(HERE), "include", "clusco.h")]
+    return [SRC] + sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh"))) + sorted(
+        glob.glob(os.path.join(os.path.dirname(HERE), "include", "*.h")))
 
 
 def stale(out: str = LIB) -> bool:
@@ -31,7 +34,7 @@ def stale(out: str = LIB) -> bool:
 
 
 def build(out: str = LIB, extra=(), verbose: bool = False, force: bool = False) -> str:
-    if not force and not stale(out) and not extra:
+    if not force and not stale(out) and (not extra or out == DEBUG_LIB):
         return out
     nvcc = os.environ.get("NVCC", "nvcc")
     cmd = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
@@ -45,6 +48,11 @@ def build(out: str = LIB, extra=(), verbose: bool = False, force: bool = False) 
     if verbose:
         sys.stderr.write(r.stderr)
     return out
+
+
+def build_debug(force: bool = False) -> str:
+    """The test-hook library (never loaded by the package itself)."""
+    return build(DEBUG_LIB, extra=DEBUG_FLAGS, force=force)
 
 
 if __name__ == "__main__":

@@ -62,7 +62,7 @@ inline BwWs carve_bw(void *base, int64_t N, int64_t L)
     w.G64 = (double *)take(sizeof(double) * w.Npad);
     w.Gacc = (float *)take(sizeof(float) * w.Npad * w.Lp * 3);
     const int64_t P = N * (N - 1) / 2;
-    w.nd_cap = P < (int64_t)(1 << 22) ? P : (int64_t)(1 << 22);
+    w.nd_cap = nd_cap_for(P);
     w.nd_list = (long long *)take(sizeof(long long) * 2 * w.nd_cap);
     w.nd_count = (unsigned long long *)take(sizeof(unsigned long long));
     w.bytes = off;

@@ -144,7 +144,7 @@ inline RcWs carve_rc(void *base, int64_t N, int64_t L)
     w.Gp = (float *)take(sizeof(float) * w.Smax * w.Rpad * w.Lp);
     w.dp = (float *)take(sizeof(float) * w.Smax * w.C * w.Npad);
     const int64_t P = N * (N - 1) / 2;
-    w.nd_cap = P < (int64_t)(1 << 22) ? P : (int64_t)(1 << 22);
+    w.nd_cap = nd_cap_for(P);
     w.nd_list = (long long *)take(sizeof(long long) * 2 * w.nd_cap);
     w.nd_count = (unsigned long long *)take(sizeof(unsigned long long));
     w.scl = (unsigned *)take(2 * sizeof(unsigned));
@@ -360,6 +360,7 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
     const int64_t nJ = J1 - J0;
     volatile int *abort_v = &abort_flag;
     auto owned = [&](int64_t j) { return CS == 1 || (int)(j % CS) == crank; };
+    int64_t q1 = 0, cx = 0;  // covariance and X^T stages the producer (warp 0, lane 0) has armed
 
     if (warp == 0) {
         // ================= TMA producer =================
@@ -368,7 +369,6 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
             tma_prefetch_desc(&mapXB);
             tma_prefetch_desc(&mapTh);
             tma_prefetch_desc(&mapTl);
-            int64_t q1 = 0, cx = 0;
             bool ok = true;
             auto g1_loads = [&](int64_t J) {
                 for (int kb = 0; kb < nkb && ok; ++kb, ++q1) {
@@ -410,13 +410,6 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
                 x_loads(J0 + j);
             }
             if (!ok) atomicExch(&abort_flag, 1);
-            if (*abort_v) {
-                // loads still in flight must land before the CTA leaves (bounded waits)
-                for (int64_t r = (q1 > RC_STAGES ? q1 - RC_STAGES : 0); r < q1; ++r)
-                    mbar_wait(&full_bar[r % RC_STAGES], (uint32_t)((r / RC_STAGES) & 1));
-                for (int64_t r = (cx > RC_XSTAGES ? cx - RC_XSTAGES : 0); r < cx; ++r)
-                    mbar_wait(&xfull_bar[r % RC_XSTAGES], (uint32_t)((r / RC_XSTAGES) & 1));
-            }
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -732,6 +725,14 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
+    if (tid == 0 && *abort_v) {
+        // a stopped CTA: the TMA copies of the last armed stages may still be in flight (the MMA
+        // issuer stopped waiting for them); they land before the CTA leaves (bounded waits)
+        for (int64_t r = (q1 > RC_STAGES ? q1 - RC_STAGES : 0); r < q1; ++r)
+            mbar_wait(&full_bar[r % RC_STAGES], (uint32_t)((r / RC_STAGES) & 1));
+        for (int64_t r = (cx > RC_XSTAGES ? cx - RC_XSTAGES : 0); r < cx; ++r)
+            mbar_wait(&xfull_bar[r % RC_XSTAGES], (uint32_t)((r / RC_XSTAGES) & 1));
+    }
     if (CS > 1) {
         // every CTA has issued all its copies; on a stopped sweep, operands a peer may still be
         // copying into this CTA (at most the two tiles after the last one whose GEMM2 this CTA
@@ -758,7 +759,10 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
         __syncthreads();
         cluster_sync_all();
     }
-    if (warp == 0) tmem_dealloc(tmem, 512);
+    if (warp == 0) {
+        __syncwarp();
+        tmem_dealloc(tmem, 512);
+    }
 }
 
 inline bool rc_supported(int64_t L) { return (L + 63) / 64 * 64 <= RC_MAXLP; }

@@ -220,11 +220,12 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
     const int64_t nJ = J1 - J0;
     const int nblk = (Lp + BR_ABLK - 1) / BR_ABLK;  // X^T chunks (atom blocks) per tile
     volatile int *abort_v = &abort_flag;
+    int64_t xq = 0;  // X^T stages the producer (warp 0, lane 0) has armed
 
     if (warp == 0) {
         // ================= TMA producer: X^T chunks =================
         if (lane == 0) {
-            int64_t c = 0;
+            int64_t &c = xq;
             bool ok = true;
             for (int64_t j = 0; j < nJ && ok && !*abort_v; ++j) {
                 const int64_t J = J0 + j;
@@ -243,11 +244,6 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
                 }
             }
             if (!ok) atomicExch(&abort_flag, 1);
-            if (*abort_v) {
-                // loads still in flight must land before the CTA leaves (bounded waits)
-                for (int64_t r = (c > BR_XSTAGES ? c - BR_XSTAGES : 0); r < c; ++r)
-                    mbar_wait(&xfull_bar[r % BR_XSTAGES], (uint32_t)((r / BR_XSTAGES) & 1));
-            }
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -507,7 +503,16 @@ __global__ void __launch_bounds__(BR_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, tmem_cols);
+    if (warp == 0) {
+        if (lane == 0 && *abort_v) {
+            // a stopped CTA: the copies of the last armed stages may still be in flight (the MMA
+            // issuer stopped waiting for them); they land before the CTA leaves (bounded waits)
+            for (int64_t r = (xq > BR_XSTAGES ? xq - BR_XSTAGES : 0); r < xq; ++r)
+                mbar_wait(&xfull_bar[r % BR_XSTAGES], (uint32_t)((r / BR_XSTAGES) & 1));
+        }
+        __syncwarp();
+        tmem_dealloc(tmem, tmem_cols);
+    }
 }
 
 inline bool bwr_supported(int64_t L) { return (L + 63) / 64 * 64 <= BR_MAXLP; }

@@ -52,7 +52,7 @@ inline BtWs carve_bt(void *base, int64_t N, int64_t L)
     w.Gp = (float *)take(sizeof(float) * w.S * w.Rpad * w.Lp);
     w.dp = (float *)take(sizeof(float) * w.S * w.Npad);
     const int64_t P = N * (N - 1) / 2;
-    w.nd_cap = P < (int64_t)(1 << 22) ? P : (int64_t)(1 << 22);
+    w.nd_cap = nd_cap_for(P);
     w.nd_list = (long long *)take(sizeof(long long) * 2 * w.nd_cap);
     w.nd_count = (unsigned long long *)take(sizeof(unsigned long long));
     w.scl = (unsigned *)take(2 * sizeof(unsigned));

@@ -701,6 +701,18 @@ int clusco_profile_read(int kernel, double *total_ms, long long *launches)
     return rc;
 }
 
+#ifdef CLUSCO_DEBUG_HOOKS
+int clusco_debug_hooks(int skip_arrive, int64_t nd_cap)
+{
+    g_last_error.clear();
+    if (nd_cap < 0) return fail(CLUSCO_EINVAL, "nd_cap=%lld must be >= 0", (long long)nd_cap);
+    const int v = skip_arrive ? 1 : 0;
+    CUDA_TRY(cudaMemcpyToSymbol(g_debug_skip_arrive, &v, sizeof v));
+    debug_nd_cap() = nd_cap;
+    return CLUSCO_OK;
+}
+#endif
+
 int clusco_sync_status(void *stream)
 {
     g_last_error.clear();

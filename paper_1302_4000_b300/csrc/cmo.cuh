@@ -162,13 +162,13 @@ __global__ void __launch_bounds__(CM_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     volatile int *abort_v = &abort_flag;
+    int64_t q = 0;  // stages the producer (warp 0, lane 0) has armed
 
     if (warp == 0) {
         // ================= TMA producer =================
         if (lane == 0) {
             tma_prefetch_desc(&mapA);
             tma_prefetch_desc(&mapB);
-            int64_t q = 0;
             for (int64_t t = blockIdx.x; t < ntiles && !*abort_v; t += gridDim.x) {
                 const int2 tj = tiles[t];
                 for (int kb = 0; kb < nkb; ++kb, ++q) {
@@ -184,10 +184,6 @@ __global__ void __launch_bounds__(CM_THREADS, 1)
                     tma_load_2d(st, &mapA, &full_bar[s], x, CM_MA * tj.x);
                     tma_load_2d(st + CM_MA * CM_KB, &mapB, &full_bar[s], x, CM_MB * tj.y);
                 }
-            }
-            if (*abort_v) {
-                for (int64_t r = (q > CM_STAGES ? q - CM_STAGES : 0); r < q; ++r)
-                    mbar_wait(&full_bar[r % CM_STAGES], (uint32_t)((r / CM_STAGES) & 1));
             }
         }
         __syncwarp();
@@ -272,7 +268,16 @@ __global__ void __launch_bounds__(CM_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 512);
+    if (warp == 0) {
+        if (lane == 0 && *abort_v) {
+            // a stopped CTA: the copies of the last armed stages may still be in flight (the MMA
+            // issuer stopped waiting for them); they land before the CTA leaves (bounded waits)
+            for (int64_t r = (q > CM_STAGES ? q - CM_STAGES : 0); r < q; ++r)
+                mbar_wait(&full_bar[r % CM_STAGES], (uint32_t)((r / CM_STAGES) & 1));
+        }
+        __syncwarp();
+        tmem_dealloc(tmem, 512);
+    }
 }
 
 // ---- plain form: bit-packed maps, AND + population count on CUDA cores ----

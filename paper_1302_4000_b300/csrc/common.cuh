@@ -14,6 +14,30 @@ __device__ unsigned int g_clusco_status;
 
 __device__ __forceinline__ void set_status(unsigned int bit) { atomicOr(&g_clusco_status, bit); }
 
+#ifdef CLUSCO_DEBUG_HOOKS
+// Test hooks, compiled into the separate debug library only (the production library has none):
+// g_debug_skip_arrive makes the forward's TMA producer of CTA 0 skip its first stage (no arrive,
+// no copy), so that the bounded waits give up and the status word reports the timeout;
+// debug_nd_cap() shrinks the adjoints' near-duplicate queues so that an overflow can be provoked.
+__device__ int g_debug_skip_arrive;
+inline int64_t &debug_nd_cap()
+{
+    static int64_t v = 0;
+    return v;
+}
+#endif
+
+// Capacity of an adjoint's near-duplicate queue for P pairs (pairs past it are counted, not
+// stored, and the overflow is reported through the status word).
+inline int64_t nd_cap_for(int64_t P)
+{
+    int64_t cap = (int64_t)1 << 22;
+#ifdef CLUSCO_DEBUG_HOOKS
+    if (debug_nd_cap() > 0) cap = debug_nd_cap();
+#endif
+    return P < cap ? P : cap;
+}
+
 // Row-major upper-triangle (a < b) index of the condensed matrix (int64).
 __host__ __device__ __forceinline__ int64_t condensed_idx(int64_t a, int64_t b, int64_t N)
 {

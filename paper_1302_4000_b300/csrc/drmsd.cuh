@@ -373,13 +373,13 @@ __global__ void __launch_bounds__(DR_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     volatile int *abort_v = &abort_flag;
+    int64_t q = 0;  // stages the producer (warp 0, lane 0) has armed
 
     if (warp == 0) {
         // ================= TMA producer =================
         if (lane == 0) {
             tma_prefetch_desc(&mapA);
             tma_prefetch_desc(&mapB);
-            int64_t q = 0;
             for (int64_t t = blockIdx.x; t < ntiles && !*abort_v; t += gridDim.x) {
                 const int2 tj = tiles[t];
                 for (int kb = 0; kb < nkb; ++kb, ++q) {
@@ -397,10 +397,6 @@ __global__ void __launch_bounds__(DR_THREADS, 1)
                     tma_load_2d(st + 32768, &mapB, &full_bar[s], x, DR_MB * tj.y);
                     tma_load_2d(st + 40960, &mapB, &full_bar[s], x, (int)(Npad + DR_MB * tj.y));
                 }
-            }
-            if (*abort_v) {
-                for (int64_t r = (q > DR_STAGES ? q - DR_STAGES : 0); r < q; ++r)
-                    mbar_wait(&full_bar[r % DR_STAGES], (uint32_t)((r / DR_STAGES) & 1));
             }
         }
         __syncwarp();
@@ -503,7 +499,16 @@ __global__ void __launch_bounds__(DR_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 512);
+    if (warp == 0) {
+        if (lane == 0 && *abort_v) {
+            // a stopped CTA: the copies of the last armed stages may still be in flight (the MMA
+            // issuer stopped waiting for them); they land before the CTA leaves (bounded waits)
+            for (int64_t r = (q > DR_STAGES ? q - DR_STAGES : 0); r < q; ++r)
+                mbar_wait(&full_bar[r % DR_STAGES], (uint32_t)((r / DR_STAGES) & 1));
+        }
+        __syncwarp();
+        tmem_dealloc(tmem, 512);
+    }
 }
 
 // Plain FP32 form: per 64 x 64 tile of model pairs, the squared differences of the FP32

@@ -315,13 +315,13 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     volatile int *abort_v = &abort_flag;
+    int64_t q = 0;  // stages the producer (warp 0, lane 0) has armed
 
     if (warp == 0) {
         // ================= TMA producer =================
         if (lane == 0) {
             tma_prefetch_desc(&mapA);
             tma_prefetch_desc(&mapB);
-            int64_t q = 0;
             int64_t I, J;
             tc_decode(tile0 + blockIdx.x, TB, TA, &I, &J);
             for (int64_t t = blockIdx.x; t < ntiles && !*abort_v; t += gridDim.x, tc_advance(I, J, gridDim.x, TB, TA)) {
@@ -332,6 +332,9 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                         atomicExch(&abort_flag, 1);
                         break;
                     }
+#ifdef CLUSCO_DEBUG_HOOKS
+                    if (g_debug_skip_arrive && blockIdx.x == 0 && q == 0) continue;  // stage 0 never lands
+#endif
                     uint8_t *st = smem + s * STAGE_BYTES_BF16;
                     mbar_arrive_expect_tx(&full_bar[s], STAGE_BYTES);
                     const int x = kb * KB_ELEMS;
@@ -345,11 +348,6 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                         tma_load_2d(st + 40960, &mapB, &full_bar[s], x, (int)(Rpad + 64 * J));
                     }
                 }
-            }
-            if (*abort_v) {
-                // loads still in flight must land before the CTA leaves (bounded waits)
-                for (int64_t r = (q > FW_STAGES ? q - FW_STAGES : 0); r < q; ++r)
-                    mbar_wait(&full_bar[r % FW_STAGES], (uint32_t)((r / FW_STAGES) & 1));
             }
         }
         __syncwarp();
@@ -579,7 +577,16 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 512);
+    if (warp == 0) {
+        if (lane == 0 && *abort_v) {
+            // a stopped CTA: the copies of the last FW_STAGES armed stages may still be in flight
+            // (the MMA issuer stopped waiting for them); they land before the CTA leaves (bounded)
+            for (int64_t r = (q > FW_STAGES ? q - FW_STAGES : 0); r < q; ++r)
+                mbar_wait(&full_bar[r % FW_STAGES], (uint32_t)((r / FW_STAGES) & 1));
+        }
+        __syncwarp();
+        tmem_dealloc(tmem, 512);
+    }
 }
 
 // ---- host side ----------------------------------------------------------

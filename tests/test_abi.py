@@ -19,10 +19,13 @@ def lib():
     return clusco.load()
 
 
-def declared_symbols():
+DEBUG_HEADER = "clusco_debug.h"  # the test-hook library's extra entry points
+
+
+def declared_symbols(headers=None):
     names = set()
     for h in os.listdir(os.path.join(ROOT, "include")):
-        if h.endswith(".h"):
+        if h.endswith(".h") and (h in headers if headers else h != DEBUG_HEADER):
             txt = open(os.path.join(ROOT, "include", h)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
             names |= set(re.findall(r"\b(clusco_\w+)\s*\(", txt))
@@ -35,6 +38,14 @@ def test_every_declared_symbol_is_exported(lib):
     for s in syms:
         assert hasattr(lib, s), s
     assert set(clusco.EXPORTS) <= set(syms)
+    # the test hooks exist only in the debug library, which exports everything else too
+    dbg = declared_symbols([DEBUG_HEADER])
+    assert dbg == ["clusco_debug_hooks"]
+    assert not hasattr(lib, "clusco_debug_hooks")
+    if os.path.exists(build.DEBUG_LIB) and not build.stale(build.DEBUG_LIB):
+        dlib = ctypes.CDLL(build.DEBUG_LIB)
+        for s in syms + dbg:
+            assert hasattr(dlib, s), s
 
 
 def test_version_and_workspace(lib):
