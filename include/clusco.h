@@ -190,8 +190,10 @@ int clusco_crmsd_vs_ref(const float *coords, int64_t N, int64_t L, const float *
  * the workspace: the quantised reference lives in a fixed static device array of about
  * 192 KB (references of up to CLUSCO_NOALLOC_MAX_L atoms) that every GPU loading the
  * library keeps until the process exits. L above that maximum returns CLUSCO_EINVAL.
- * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current, so make that first call before any stream capture.
+ * Every call looks up the array's device address in the current context
+ * (cudaGetSymbolAddress, host-side once the module is loaded, so the address is right
+ * after a cudaDeviceReset too); the first call on a device loads the module, so make it
+ * before any stream capture.
  * Every call shares the one array and overwrites all of it that it reads, so nothing
  * needs clearing between calls, but two calls whose kernels can overlap on the GPU
  * (unordered streams) race on it and may return wrong scores.

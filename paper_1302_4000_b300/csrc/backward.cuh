@@ -312,6 +312,11 @@ __global__ void __launch_bounds__(256) bwd_neardup_kernel(const float *__restric
         const double w = (double)wvec[condensed_idx(a, b, N)];
         const double coef = w / ((double)L * fmax(c, (double)eps));
         // a side: coef (a_i - R b_i); b side: coef (b_i - R^T a_i). Both sum to zero over atoms.
+        // Added into the gradient with FP32 atomics (several queued pairs share a model): the
+        // order of the additions, hence the last bits of the gradient rows of models with
+        // near-duplicates, varies from run to run; each term is FP64-accurate before rounding,
+        // so the run-to-run spread is a few FP32 ulps of the row, far below the 1e-3 relative
+        // tolerance of the adjoint.
         for (int i = lane; i < L; i += 32) {
             double u[3], v[3];
             for (int k = 0; k < 3; ++k) {

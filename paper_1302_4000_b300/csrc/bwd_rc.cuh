@@ -52,7 +52,10 @@
 
 namespace clusco {
 
-constexpr int RC_THREADS = 320;                       // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+// warp 0 covariance TMA, warp 1 covariance MMA (GEMM1), warps 2-9 epilogue, warp 10 X^T TMA and
+// contraction MMA (GEMM2)
+constexpr int RC_THREADS = 352;
+constexpr int RC_G2WARP = 10;
 constexpr int RC_STAGES = 2;                          // GEMM1 ring
 constexpr uint32_t RC_STAGE = 2 * 16384 + 2 * 8192;   // A_hi, A_lo (128 rows), B_hi, B_lo (64 rows) x 64 FP16
 constexpr uint32_t RC_P = 2 * 16384;                  // operand P: hi, lo parts of 128 rows x 64 FP16
@@ -283,7 +286,8 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
     __shared__ __align__(8) uint64_t pfree_bar[2];           // every CTA finished GEMM2 of the slot (CS arrivals)
     __shared__ __align__(8) uint64_t xfull_bar[RC_XSTAGES];  // an X^T block landed
     __shared__ __align__(8) uint64_t xempty_bar[RC_XSTAGES]; // GEMM2 has finished reading it
-    __shared__ __align__(8) uint64_t d2_bar;                 // every MMA of this CTA has completed
+    __shared__ __align__(8) uint64_t d2_bar;                 // every GEMM2 MMA of this CTA has completed
+    __shared__ __align__(8) uint64_t g1end_bar;              // every GEMM1 MMA of this CTA has completed
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     __shared__ int64_t g2_done, g2_seen;                     // GEMM2 tiles committed / operands waited for
@@ -342,6 +346,7 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
         mbar_init(&done1_bar, 1);
         mbar_init(&tfree_bar, 8);
         mbar_init(&d2_bar, 1);
+        mbar_init(&g1end_bar, 1);
         abort_flag = 0;
         g2_done = g2_seen = 0;
         fence_barrier_init();
@@ -360,15 +365,15 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
     const int64_t nJ = J1 - J0;
     volatile int *abort_v = &abort_flag;
     auto owned = [&](int64_t j) { return CS == 1 || (int)(j % CS) == crank; };
-    int64_t q1 = 0, cx = 0;  // covariance and X^T stages the producer (warp 0, lane 0) has armed
+    // stages armed by the covariance producer (warp 0, lane 0) and by the contraction thread's X^T
+    // loads (warp 10, lane 0)
+    int64_t q1 = 0, cx = 0;
 
     if (warp == 0) {
-        // ================= TMA producer =================
+        // ================= TMA producer: covariance operands of the owned tiles =================
         if (lane == 0) {
             tma_prefetch_desc(&mapXA);
             tma_prefetch_desc(&mapXB);
-            tma_prefetch_desc(&mapTh);
-            tma_prefetch_desc(&mapTl);
             bool ok = true;
             auto g1_loads = [&](int64_t J) {
                 for (int kb = 0; kb < nkb && ok; ++kb, ++q1) {
@@ -387,35 +392,24 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
                     tma_load_2d(st + 40960, &mapXB, &full_bar[s], x, (int)(Rpad + 64 * J));
                 }
             };
-            auto x_loads = [&](int64_t J) {
-                for (int bl = 0; bl < nb && ok; ++bl, ++cx) {
-                    const int st = (int)(cx % RC_XSTAGES);
-                    const int64_t use = cx / RC_XSTAGES;
-                    if (cx >= RC_XSTAGES && !mbar_wait_sleep(&xempty_bar[st], (uint32_t)((use - 1) & 1))) {
-                        ok = false;
-                        break;
-                    }
-                    // the tile's 64 operand rows x 128 atoms; atoms past Lp read as zeros
-                    const int x = (int)(64 * J), y = (blk0 + bl) * RC_BLK;
-                    mbar_arrive_expect_tx(&xfull_bar[st], RC_XBUF);
-                    tma_load_2d(XT + st * RC_XBUF, &mapTh, &xfull_bar[st], x, y);
-                    tma_load_2d(XT + st * RC_XBUF + RC_XBUF / 2, &mapTl, &xfull_bar[st], x, y);
-                }
-            };
-            // the order of the MMA thread's consumption: the first owned tile's covariance operands,
-            // then per tile j the next owned tile's (j + CS, when j is owned) and tile j's X^T blocks
-            if (crank < nJ) g1_loads(J0 + crank);
-            for (int64_t j = 0; j < nJ && ok && !*abort_v; ++j) {
-                if (owned(j) && j + CS < nJ) g1_loads(J0 + j + CS);
-                x_loads(J0 + j);
-            }
+            // in the order of the GEMM1 thread's consumption
+            for (int64_t j = crank; j < nJ && ok && !*abort_v; j += CS) g1_loads(J0 + j);
             if (!ok) atomicExch(&abort_flag, 1);
         }
         __syncwarp();
-    } else if (warp == 1) {
-        // ================= MMA issuer =================
+    } else if (warp == 1 || warp == RC_G2WARP) {
+        // ================= MMA issuers: covariance GEMM1 (warp 1), contraction GEMM2 (warp 10) =================
+        // Two threads, so that GEMM1 of the next owned tile goes out as soon as the epilogue has read
+        // the current covariance, whatever operand GEMM2 is waiting for; each thread's commits track
+        // its own MMAs, and they touch disjoint tensor memory and shared memory. The GEMM2 thread
+        // also loads the X^T blocks, one block ahead of its consumption (a ring of RC_XSTAGES).
         if (lane == 0) {
-            int64_t q1 = 0, cx = 0, ko = 0, gd = 0, seen = 0;
+            if (warp == RC_G2WARP) {
+                tma_prefetch_desc(&mapTh);
+                tma_prefetch_desc(&mapTl);
+            }
+            int64_t q1 = 0, xc = 0, ko = 0, gd = 0, seen = 0;
+            const int64_t nxb = nJ * nb;  // X^T blocks of the sweep, tile-major
             int po0 = 0, po1 = 0;  // own operands written into slot 0 / 1
             int rx0 = 0, rx1 = 0;  // peer operands received into slot 0 / 1
             bool ok = true;
@@ -442,6 +436,21 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
                 }
                 mma_commit(&done1_bar);
             };
+            // arm X^T block t (tile t / nb, block t mod nb of this CTA's chunk) into stage t mod
+            // RC_XSTAGES, once GEMM2 has finished reading the stage's previous block
+            auto x_arm = [&](int64_t t) {
+                const int st = (int)(t % RC_XSTAGES);
+                if (t >= RC_XSTAGES && !mbar_wait_sleep(&xempty_bar[st], (uint32_t)(((t / RC_XSTAGES) - 1) & 1))) {
+                    ok = false;
+                    return;
+                }
+                // the tile's 64 operand rows x 128 atoms; atoms past Lp read as zeros
+                const int x = (int)(64 * (J0 + t / nb)), y = (blk0 + (int)(t % nb)) * RC_BLK;
+                mbar_arrive_expect_tx(&xfull_bar[st], RC_XBUF);
+                tma_load_2d(XT + st * RC_XBUF, &mapTh, &xfull_bar[st], x, y);
+                tma_load_2d(XT + st * RC_XBUF + RC_XBUF / 2, &mapTl, &xfull_bar[st], x, y);
+                cx = t + 1;
+            };
             auto g2 = [&](int64_t jj) {
                 const int s = (int)(jj & 1);
                 bool got;
@@ -465,9 +474,9 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
                 }
                 tc_fence_after();
                 const uint32_t pb = pbase + s * RC_P;
-                for (int bl = 0; bl < nb && ok; ++bl, ++cx) {
-                    const int st = (int)(cx % RC_XSTAGES);
-                    if (!mbar_wait(&xfull_bar[st], (uint32_t)((cx / RC_XSTAGES) & 1))) {
+                for (int bl = 0; bl < nb && ok; ++bl, ++xc) {
+                    const int st = (int)(xc % RC_XSTAGES);
+                    if (!mbar_wait(&xfull_bar[st], (uint32_t)((xc / RC_XSTAGES) & 1))) {
                         ok = false;
                         break;
                     }
@@ -484,6 +493,8 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
                         mma_f16(d, xlo, phi, id128, 1u);
                     }
                     mma_commit(&xempty_bar[st]);
+                    // refill the stage the previous block used (its GEMM2 was committed a block ago)
+                    if (xc >= 1 && xc - 1 + RC_XSTAGES < nxb) x_arm(xc - 1 + RC_XSTAGES);
                 }
                 if (!ok) return;
                 if (CS > 1)
@@ -492,29 +503,30 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
                     mma_commit(&pfree_bar[s]);
                 gd = jj + 1;
             };
-            // GEMM1 of the next owned tile goes out as soon as the epilogue has read the current
-            // one's covariance, so that it runs under the epilogue's rotations; GEMM2 of every tile
-            // follows in order
-            if (crank < nJ) {
-                g1();
-                ++ko;
-            }
-            for (int64_t j = 0; j < nJ && ok && !*abort_v; ++j) {
-                if (owned(j) && j + CS < nJ) {
-                    if (!mbar_wait_sleep(&tfree_bar, (uint32_t)((ko - 1) & 1))) {
+            if (warp == 1) {
+                // GEMM1 of the next owned tile as soon as the epilogue has read the current covariance,
+                // so that it runs under the epilogue's rotations
+                for (int64_t j = crank; j < nJ && ok && !*abort_v; j += CS) {
+                    if (ko > 0 && !mbar_wait_sleep(&tfree_bar, (uint32_t)((ko - 1) & 1))) {
                         ok = false;
                         break;
                     }
                     g1();
                     ++ko;
                 }
-                if (ok) g2(j);
+            } else {
+                for (int64_t t = 0; t < RC_XSTAGES && t < nxb && ok; ++t) x_arm(t);
+                for (int64_t j = 0; j < nJ && ok && !*abort_v; ++j) g2(j);
             }
-            mma_commit(&d2_bar);  // also on abort: fires once everything issued has completed
-            if (!mbar_wait(&d2_bar, 0)) ok = false;
+            // also on abort: fires once everything this thread issued has completed
+            uint64_t *endb = (warp == 1) ? &g1end_bar : &d2_bar;
+            mma_commit(endb);
+            if (!mbar_wait(endb, 0)) ok = false;
             if (!ok) atomicExch(&abort_flag, 1);
-            g2_done = gd;
-            g2_seen = seen;
+            if (warp == RC_G2WARP) {
+                g2_done = gd;
+                g2_seen = seen;
+            }
         }
         __syncwarp();
     } else {
@@ -725,13 +737,15 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (tid == 0 && *abort_v) {
+    if (lane == 0 && *abort_v) {
         // a stopped CTA: the TMA copies of the last armed stages may still be in flight (the MMA
-        // issuer stopped waiting for them); they land before the CTA leaves (bounded waits)
-        for (int64_t r = (q1 > RC_STAGES ? q1 - RC_STAGES : 0); r < q1; ++r)
-            mbar_wait(&full_bar[r % RC_STAGES], (uint32_t)((r / RC_STAGES) & 1));
-        for (int64_t r = (cx > RC_XSTAGES ? cx - RC_XSTAGES : 0); r < cx; ++r)
-            mbar_wait(&xfull_bar[r % RC_XSTAGES], (uint32_t)((r / RC_XSTAGES) & 1));
+        // issuers stopped waiting for them); they land before the CTA leaves (bounded waits)
+        if (warp == 0)
+            for (int64_t r = (q1 > RC_STAGES ? q1 - RC_STAGES : 0); r < q1; ++r)
+                mbar_wait(&full_bar[r % RC_STAGES], (uint32_t)((r / RC_STAGES) & 1));
+        if (warp == RC_G2WARP)
+            for (int64_t r = (cx > RC_XSTAGES ? cx - RC_XSTAGES : 0); r < cx; ++r)
+                mbar_wait(&xfull_bar[r % RC_XSTAGES], (uint32_t)((r / RC_XSTAGES) & 1));
     }
     if (CS > 1) {
         // every CTA has issued all its copies; on a stopped sweep, operands a peer may still be

@@ -600,32 +600,24 @@ int clusco_crmsd_allpairs_backward_rot(const float *coords, int64_t N, int64_t L
 // ---- one-versus-reference without device allocation --------------------------
 // The scratch of clusco_crmsd_vs_ref_noalloc: the quantised reference (3 int32 per atom)
 // followed by its RefInfo. In host code g_vsref_scratch only names the symbol; its device
-// address is looked up per device with cudaGetSymbolAddress and passed to the kernels.
+// address is looked up on every call with cudaGetSymbolAddress (a host-side lookup once the
+// module is loaded), so that it is never stale: after a cudaDeviceReset the module is loaded
+// again and the symbol may move.
 namespace {
 constexpr size_t NOALLOC_REF_BYTES = ((size_t)CLUSCO_NOALLOC_MAX_L * 3 * sizeof(int) + 255) & ~(size_t)255;
-constexpr int NOALLOC_MAX_DEVICES = 64;
-std::mutex g_noalloc_mu;
-void *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
 }  // namespace
 
 static __device__ __align__(256) unsigned char g_vsref_scratch[NOALLOC_REF_BYTES + 256];
 
 namespace {
-// Device address of g_vsref_scratch on the current device; looked up on the first call per device.
+// Device address of g_vsref_scratch in the current context.
 int noalloc_scratch(void **out)
 {
-    int dev = -1;
-    CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(CLUSCO_EUNSUPPORTED, "device %d beyond %d", dev, NOALLOC_MAX_DEVICES);
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_vsref_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(CLUSCO_ECUDA, "cudaGetSymbolAddress(g_vsref_scratch): %s", cudaGetErrorString(e));
-        g_noalloc_addr[dev] = p;
-    }
-    *out = g_noalloc_addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_vsref_scratch);
+    if (e != cudaSuccess || !p)
+        return fail(CLUSCO_ECUDA, "cudaGetSymbolAddress(g_vsref_scratch): %s", cudaGetErrorString(e));
+    *out = p;
     return CLUSCO_OK;
 }
 }  // namespace

@@ -42,6 +42,32 @@ def test_noalloc_matches_regular_on_two_calls(lib):
         assert np.isfinite(err) and err <= 1e-4, err
 
 
+def test_noalloc_at_the_largest_reference_allocates_nothing(lib):
+    """L = NOALLOC_MAX_L (N = 64): the whole static array in use. After a first call (which may
+    load the module), a second call changes neither torch's allocator nor the device's free
+    memory."""
+    e = E.decoy_ensemble(64, clusco.NOALLOC_MAX_L, 2, (0.1, 6.0), 9090)
+    X = torch.from_numpy(e.coords).cuda()
+    ref = torch.from_numpy(e.natives[1].astype(np.float32)).cuda()
+    want = clusco.crmsd_vs_ref(X, ref)
+    got = torch.full((e.N,), float("nan"), device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    assert lib.clusco_crmsd_vs_ref_noalloc(X.data_ptr(), e.N, e.L, ref.data_ptr(), got.data_ptr(), stream) == 0
+    assert clusco.sync_status() == 0
+    got.fill_(float("nan"))
+    torch.cuda.synchronize()
+    alloc0, free0 = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]
+    rc = lib.clusco_crmsd_vs_ref_noalloc(X.data_ptr(), e.N, e.L, ref.data_ptr(), got.data_ptr(), stream)
+    assert rc == 0, lib.clusco_last_error()
+    torch.cuda.synchronize()
+    alloc1, free1 = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]
+    assert clusco.sync_status() == 0
+    assert alloc1 == alloc0
+    assert free1 == free0, (free0, free1)
+    err = (got - want).abs().max().item()
+    assert np.isfinite(err) and err <= 1e-4, err
+
+
 def test_noalloc_rejects_oversized_reference(lib):
     fake = ctypes.c_void_p(0x1000)
     rc = lib.clusco_crmsd_vs_ref_noalloc(fake, 4, clusco.NOALLOC_MAX_L + 1, fake, fake, None)
