@@ -26,8 +26,9 @@
 //     N = 128 rows of the A tile, K = the tile's 64 rows, three FP16 passes);
 //   warps 2-9 (epilogue): for owned tiles, read the covariance out of tensor memory (then hand
 //     it back to GEMM1), assemble each pair's 3 x 3 block (rows cyclic, as in the forward),
-//     take Sigma and the rotation R = dSigma/dM from one set of minors (Horn's key matrix, or
-//     Jacobi sweeps, only near a double root), scale by w~, move the rows to the lanes that
+//     take Sigma (one Newton step from the forward's cRMSD) and the rotation R = dSigma/dM as the
+//     top eigenvector of Horn's key matrix (Jacobi sweeps only at a numerically double root),
+//     scale by w~, move the rows to the lanes that
 //     own them with shuffles, and store the 128 x 64 operand P = w~ R as FP16 hi / lo parts
 //     (K-major, 128-byte swizzle) into one of two slots, and send it to the other CTAs of the
 //     cluster (one bulk copy into each peer's slot, shared memory to shared memory); the other
@@ -36,9 +37,15 @@
 // Synchronisation between the CTAs of a cluster, per slot s (tile j uses slot j mod 2):
 //   pfull[s] (local, 8 arrivals): this CTA has written its own tile's operand;
 //   prx[s]   (1 arrival by the owner, plus the copy's bytes): a peer's operand has landed;
-//   pfree[s] (C arrivals, a multicast tcgen05.commit from every CTA's MMA thread): every CTA
-//            has finished GEMM2 of the tile in slot s, so that the owner of tile j + 2 may
-//            rewrite its slot and copy into every peer's.
+//   pfree[s][k mod 2] (C arrivals, a multicast tcgen05.commit from every CTA's MMA thread): every
+//            CTA has finished GEMM2 of the slot's k-th tile (tile 2 k + s), so that the owner of
+//            tile j + 2 may rewrite the slot and copy into every peer's. A parity wait is exact
+//            only while the barrier is at most one phase away from the awaited one. With one
+//            barrier per slot, the owner of tile j (which knows only that tiles up to j - C - 2
+//            are done, from its wait before its previous tile j - C) could see tile j - 4's phase
+//            still open for C = 3 and pass at once. With the slot's tiles split over two
+//            barriers, the waited barrier's previous tile is j - 6, done for C <= 4, and its
+//            next tile j + 2 cannot finish before tile j is written.
 // Every wait is bounded. The CTAs of a cluster meet at cluster barriers after initialisation
 // and, twice, before exit: after every MMA (and so every multicast commit) has completed and
 // every copy has been issued, then after each CTA has waited for any copy still landing in it
@@ -67,6 +74,7 @@ constexpr int RC_MAXLP = 1024;
 constexpr uint32_t RC_G2COL = 128;                    // first TMEM column of the transposed sum
 constexpr size_t RC_SMEM = 1024 + RC_STAGES * RC_STAGE + 2 * RC_P + RC_XSTAGES * RC_XBUF;
 static_assert(RC_SMEM + 1024 <= 227 * 1024, "shared memory per CTA");
+static_assert((RC_MAXLP / RC_BLK + RC_MAXQ - 1) / RC_MAXQ <= 4, "the operand slots' barriers assume clusters of <= 4");
 
 struct RcWs {
     float *xf = nullptr;      // [Rpad][Lp] centred FP32 (zero for padding and non-finite models)
@@ -233,6 +241,137 @@ __global__ void __launch_bounds__(256) rc_split_kernel(const float *__restrict__
     }
 }
 
+// The pair's rotation from its normalised covariance m: Sigma_hat by one Newton step on m's
+// quartic from s0 (the forward's cRMSD gives it: L c^2 = (G_A + G_B)(1 - Sigma_hat)), then the top
+// eigenvector of Horn's key matrix at that Sigma_hat (the symmetric adjugate of K - Sigma_hat I,
+// its column of largest diagonal entry, as a unit quaternion). The closed form dSigma/dM loses
+// accuracy already where P'(Sigma) < 0.08 Sigma^3 (about 1 % of the pairs of a decoy ensemble,
+// and every warp round that holds one would run the slow path); the adjugate holds down to
+// P' ~ 1e-4 Sigma^3, below which no pair of these ensembles falls, and needs no orthogonality
+// polish (a unit quaternion gives an orthogonal matrix to rounding). Below that the caller takes
+// Jacobi sweeps (rotation_robust).
+//
+// Two pairs at once, one in each half of a float2, on the paired FP32 instructions (two IEEE
+// operations per instruction): the same steps as rc_rotation, so that each lane carries two
+// independent chains and half the instructions per pair. Selections, reciprocals and the
+// validity tests stay per pair.
+__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<const unsigned long long *>(&a)), "l"(*reinterpret_cast<const unsigned long long *>(&b)));
+    return *reinterpret_cast<const float2 *>(&d);
+}
+// a b - c d
+__device__ __forceinline__ float2 dif2(float2 a, float2 b, float2 c, float2 d) { return sub2(mul2(a, b), mul2(c, d)); }
+
+// Horn's adjugate column for one of the two pairs (h = 0: .x, 1: .y): the column of the
+// largest diagonal entry, and whether that entry clears tol * lam^3.
+__device__ __forceinline__ bool horn_pick(const float (&d)[10], float lam, float tol, float q[4])
+{
+    // d: d00 d01 d02 d03 d11 d12 d13 d22 d23 d33
+    float best = fabsf(d[0]);
+    q[0] = d[0], q[1] = d[1], q[2] = d[2], q[3] = d[3];
+    if (fabsf(d[4]) > best) {
+        best = fabsf(d[4]);
+        q[0] = d[1], q[1] = d[4], q[2] = d[5], q[3] = d[6];
+    }
+    if (fabsf(d[7]) > best) {
+        best = fabsf(d[7]);
+        q[0] = d[2], q[1] = d[5], q[2] = d[7], q[3] = d[8];
+    }
+    if (fabsf(d[9]) > best) {
+        best = fabsf(d[9]);
+        q[0] = d[3], q[1] = d[6], q[2] = d[8], q[3] = d[9];
+    }
+    return best > tol * fabsf(lam) * lam * lam && isfinite(best);
+}
+
+__device__ __forceinline__ void rc_rotation2(const float2 m[9], float2 s0, float2 R[9], bool &okx, bool &oky)
+{
+    // minors3 and the invariants I1, det, I2
+    float2 mn[9];
+    mn[0] = dif2(m[3], m[7], m[4], m[6]);
+    mn[1] = dif2(m[3], m[8], m[5], m[6]);
+    mn[2] = dif2(m[4], m[8], m[5], m[7]);
+    mn[3] = dif2(m[0], m[7], m[1], m[6]);
+    mn[4] = dif2(m[0], m[8], m[2], m[6]);
+    mn[5] = dif2(m[1], m[8], m[2], m[7]);
+    mn[6] = dif2(m[0], m[4], m[1], m[3]);
+    mn[7] = dif2(m[0], m[5], m[2], m[3]);
+    mn[8] = dif2(m[1], m[5], m[2], m[4]);
+    const float2 det = fma2(m[2], mn[0], sub2(mul2(m[0], mn[2]), mul2(m[1], mn[1])));
+    float2 I2 = mul2(mn[0], mn[0]), I1 = mul2(m[0], m[0]);
+#pragma unroll
+    for (int k = 1; k < 9; ++k) {
+        I2 = fma2(mn[k], mn[k], I2);
+        I1 = fma2(m[k], m[k], I1);
+    }
+    // one Newton step on x^4 - 2 I1 x^2 - 8 det x + (I1^2 - 4 I2), skipped near a double root
+    const float2 c2 = mul2(bc2(-2.f), I1), c1 = mul2(bc2(-8.f), det);
+    const float2 c0 = fma2(I1, I1, mul2(bc2(-4.f), I2));
+    const float2 sq = mul2(s0, s0);
+    const float2 P = fma2(add2(sq, c2), sq, fma2(c1, s0, c0));
+    const float2 dP = fma2(fma2(bc2(4.f), sq, mul2(bc2(2.f), c2)), s0, c1);
+    const float2 lim = mul2(bc2(8e-3f), mul2(sq, s0));
+    float2 s = s0;
+    if (dP.x > lim.x) s.x -= __fdividef(P.x, dP.x);
+    if (dP.y > lim.y) s.y -= __fdividef(P.y, dP.y);
+    // Horn's key matrix K(m) - s I and its symmetric adjugate
+    const float2 tr = add2(add2(m[0], m[4]), m[8]);
+    const float2 a00 = sub2(tr, s);
+    const float2 a11 = sub2(sub2(mul2(bc2(2.f), m[0]), tr), s);
+    const float2 a22 = sub2(sub2(mul2(bc2(2.f), m[4]), tr), s);
+    const float2 a33 = sub2(sub2(mul2(bc2(2.f), m[8]), tr), s);
+    const float2 a01 = sub2(m[7], m[5]), a02 = sub2(m[2], m[6]), a03 = sub2(m[3], m[1]);
+    const float2 a12 = add2(m[1], m[3]), a13 = add2(m[2], m[6]), a23 = add2(m[5], m[7]);
+    const float2 t0 = dif2(a00, a11, a01, a01), t1 = dif2(a00, a12, a01, a02), t2 = dif2(a00, a13, a01, a03);
+    const float2 t3 = dif2(a01, a12, a11, a02), t4 = dif2(a01, a13, a11, a03), t5 = dif2(a02, a13, a12, a03);
+    const float2 u1 = dif2(a02, a23, a03, a22), u2 = dif2(a02, a33, a03, a23), u3 = dif2(a12, a23, a13, a22);
+    const float2 u4 = dif2(a12, a33, a13, a23), u5 = dif2(a22, a33, a23, a23);
+    float2 dd[10];
+    dd[0] = fma2(a13, u3, dif2(a11, u5, a12, u4));   // d00
+    dd[1] = sub2(mul2(a02, u4), fma2(a01, u5, mul2(a03, u3)));  // d01
+    dd[2] = fma2(a33, t3, dif2(a13, t5, a23, t4));   // d02
+    dd[3] = sub2(mul2(a22, t4), fma2(a12, t5, mul2(a23, t3)));  // d03
+    dd[4] = fma2(a03, u1, dif2(a00, u5, a02, u2));   // d11
+    dd[5] = sub2(mul2(a23, t2), fma2(a03, t5, mul2(a33, t1)));  // d12
+    dd[6] = fma2(a23, t1, dif2(a02, t5, a22, t2));   // d13
+    dd[7] = fma2(a33, t0, dif2(a03, t4, a13, t2));   // d22
+    dd[8] = sub2(mul2(a12, t2), fma2(a02, t4, mul2(a23, t0)));  // d23
+    dd[9] = fma2(a22, t0, dif2(a02, t3, a12, t1));   // d33
+    float dx[10], dy[10], qx[4], qy[4];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+        dx[k] = dd[k].x;
+        dy[k] = dd[k].y;
+    }
+    okx = horn_pick(dx, s.x, 1e-4f, qx);
+    oky = horn_pick(dy, s.y, 1e-4f, qy);
+    float2 q[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = make_float2(qx[k], qy[k]);
+    const float2 n2 = fma2(q[3], q[3], fma2(q[2], q[2], fma2(q[1], q[1], mul2(q[0], q[0]))));
+    const float2 inv = make_float2(rsqrtf(n2.x), rsqrtf(n2.y));
+    const float2 w = mul2(q[0], inv), x = mul2(q[1], inv), y = mul2(q[2], inv), z = mul2(q[3], inv);
+    const float2 ww = mul2(w, w), xx = mul2(x, x), yy = mul2(y, y), zz = mul2(z, z);
+    const float2 two = bc2(2.f);
+    R[0] = sub2(add2(ww, xx), add2(yy, zz));
+    R[1] = mul2(two, dif2(x, y, w, z));
+    R[2] = mul2(two, fma2(x, z, mul2(w, y)));
+    R[3] = mul2(two, fma2(x, y, mul2(w, z)));
+    R[4] = sub2(add2(ww, yy), add2(xx, zz));
+    R[5] = mul2(two, dif2(y, z, w, x));
+    R[6] = mul2(two, dif2(x, z, w, y));
+    R[7] = mul2(two, fma2(y, z, mul2(w, x)));
+    R[8] = sub2(add2(ww, zz), add2(xx, yy));
+}
+
 // Cyclic assembly of round r's block from a lane's 32 covariance columns (see assemble_block),
 // with a compile-time round so that every index into V is static.
 template <int r>
@@ -283,7 +422,7 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
     __shared__ __align__(8) uint64_t tfree_bar;              // the epilogue has read it (8 arrivals)
     __shared__ __align__(8) uint64_t pfull_bar[2];           // an owned tile's operand is written (8 arrivals)
     __shared__ __align__(8) uint64_t prx_bar[2];             // a peer's operand has landed (1 arrival + bytes)
-    __shared__ __align__(8) uint64_t pfree_bar[2];           // every CTA finished GEMM2 of the slot (CS arrivals)
+    __shared__ __align__(8) uint64_t pfree_bar[2][2];        // every CTA finished GEMM2 of a tile (CS arrivals)
     __shared__ __align__(8) uint64_t xfull_bar[RC_XSTAGES];  // an X^T block landed
     __shared__ __align__(8) uint64_t xempty_bar[RC_XSTAGES]; // GEMM2 has finished reading it
     __shared__ __align__(8) uint64_t d2_bar;                 // every GEMM2 MMA of this CTA has completed
@@ -341,7 +480,8 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
         for (int s = 0; s < 2; ++s) {
             mbar_init(&pfull_bar[s], 8);
             mbar_init(&prx_bar[s], 1);
-            mbar_init(&pfree_bar[s], (uint32_t)CS);
+            mbar_init(&pfree_bar[s][0], (uint32_t)CS);
+            mbar_init(&pfree_bar[s][1], (uint32_t)CS);
         }
         mbar_init(&done1_bar, 1);
         mbar_init(&tfree_bar, 8);
@@ -497,10 +637,11 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
                     if (xc >= 1 && xc - 1 + RC_XSTAGES < nxb) x_arm(xc - 1 + RC_XSTAGES);
                 }
                 if (!ok) return;
+                uint64_t *pf = &pfree_bar[s][(jj >> 1) & 1];
                 if (CS > 1)
-                    mma_commit_multicast(&pfree_bar[s], mask);
+                    mma_commit_multicast(pf, mask);
                 else
-                    mma_commit(&pfree_bar[s]);
+                    mma_commit(pf);
                 gd = jj + 1;
             };
             if (warp == 1) {
@@ -605,63 +746,97 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tfree_bar);  // TMEM columns 0..127 may be overwritten now
-            fetch(j + jstep);
             float v[32];
             v[30] = v[31] = 0.f;
-            // one round at a time: the rotation's code once, the round's static indices in a switch
+            // two rounds at a time (rounds 2 d and 2 d + 1 in the two halves of the paired
+            // instructions): the rotation's code once, each half's static indices in a branch
 #pragma unroll 1
-            for (int r = 0; r < 4; ++r) {
-                float blk[9];
-                switch (r) {
-                    case 0: rc_assemble<0>(V, alpha, mloc, blk); break;
-                    case 1: rc_assemble<1>(V, alpha, mloc, blk); break;
-                    case 2: rc_assemble<2>(V, alpha, mloc, blk); break;
-                    default: rc_assemble<3>(V, alpha, mloc, blk); break;
+            for (int d = 0; d < 2; ++d) {
+                float bx[9], by[9];
+                if (d == 0) {
+                    rc_assemble<0>(V, alpha, mloc, bx);
+                    rc_assemble<1>(V, alpha, mloc, by);
+                } else {
+                    rc_assemble<2>(V, alpha, mloc, bx);
+                    rc_assemble<3>(V, alpha, mloc, by);
                 }
-                float c = 0.f, w = 0.f, gb = 0.f;
-                bool vr = false;
-                switch (r) {  // registers, not local memory
-                    case 0: c = cc[0], w = wc[0], gb = gc[0], vr = vc[0]; break;
-                    case 1: c = cc[1], w = wc[1], gb = gc[1], vr = vc[1]; break;
-                    case 2: c = cc[2], w = wc[2], gb = gc[2], vr = vc[2]; break;
-                    default: c = cc[3], w = wc[3], gb = gc[3], vr = vc[3]; break;
-                }
-                const bool far = c >= CLUSCO_NEARDUP;
-                const int64_t b = b0 + 3 * r + alpha;
-                if (lead && vr && !far && w != 0.f && a < b) {
-                    const unsigned long long slot_nd = atomicAdd(nd_count, 1ull);
-                    if ((int64_t)slot_nd < nd_cap) {
-                        nd_list[2 * slot_nd] = a;
-                        nd_list[2 * slot_nd + 1] = b;
+                // registers, not local memory: selects on d
+                const float cx = d ? cc[2] : cc[0], cy = d ? cc[3] : cc[1];
+                const float wx = d ? wc[2] : wc[0], wy = d ? wc[3] : wc[1];
+                const float gx = d ? gc[2] : gc[0], gy = d ? gc[3] : gc[1];
+                const bool vx = d ? vc[2] : vc[0], vy = d ? vc[3] : vc[1];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float c = h ? cy : cx, w = h ? wy : wx;
+                    const bool vr = h ? vy : vx;
+                    const int64_t b = b0 + 3 * (2 * d + h) + alpha;
+                    if (lead && vr && !(c >= CLUSCO_NEARDUP) && w != 0.f && a < b) {
+                        const unsigned long long slot_nd = atomicAdd(nd_count, 1ull);
+                        if ((int64_t)slot_nd < nd_cap) {
+                            nd_list[2 * slot_nd] = a;
+                            nd_list[2 * slot_nd + 1] = b;
+                        }
                     }
                 }
-                const float coef = (vr && far && w != 0.f) ? __fdividef(w, fL * fmaxf(c, eps)) : 0.f;
-                csum += coef;
-                float send[9];
+                const float coefx = (vx && cx >= CLUSCO_NEARDUP && wx != 0.f) ? __fdividef(wx, fL * fmaxf(cx, eps)) : 0.f;
+                const float coefy = (vy && cy >= CLUSCO_NEARDUP && wy != 0.f) ? __fdividef(wy, fL * fmaxf(cy, eps)) : 0.f;
+                csum += coefx + coefy;
+                float sx[9], sy[9];
 #pragma unroll
-                for (int e = 0; e < 9; ++e) send[e] = 0.f;
-                if (coef != 0.f && !fail) {
-                    const float igs = __fdividef(1.f, Ga + gb);
-                    const float nrm = 2.f * igs * ixs * ixs;
-                    float m[9], R[9];
+                for (int e = 0; e < 9; ++e) sx[e] = sy[e] = 0.f;
+                if ((coefx != 0.f || coefy != 0.f) && !fail) {
+                    const float igx = __fdividef(1.f, Ga + gx), igy = __fdividef(1.f, Ga + gy);
+                    const float2 nrm = make_float2(2.f * igx * ixs * ixs, 2.f * igy * ixs * ixs);
+                    float2 m[9], R[9];
 #pragma unroll
-                    for (int e = 0; e < 9; ++e) m[e] = blk[e] * nrm;
+                    for (int e = 0; e < 9; ++e) m[e] = mul2(make_float2(bx[e], by[e]), nrm);
                     // Sigma_hat from the forward's cRMSD: L c^2 = (G_A + G_B)(1 - Sigma_hat)
-                    const float s0 = fmaf(-fL * c * c, igs, 1.f);
-                    if (!sigma_rotation_from_f32(m, s0, R)) rotation_robust(m, R);
-                    const float cs = coef * sP;
+                    const float2 s0 = make_float2(fmaf(-fL * cx * cx, igx, 1.f), fmaf(-fL * cy * cy, igy, 1.f));
+                    bool okx, oky;
+                    rc_rotation2(m, s0, R, okx, oky);
+                    const float csx = coefx * sP, csy = coefy * sP;
+                    // a pair without a coefficient (near-duplicate, padding) has no rotation: the
+                    // half it occupied may hold anything, so select, do not multiply by zero
 #pragma unroll
-                    for (int e = 0; e < 9; ++e) send[e] = cs * R[e];
+                    for (int e = 0; e < 9; ++e) {
+                        sx[e] = coefx != 0.f ? csx * R[e].x : 0.f;
+                        sy[e] = coefy != 0.f ? csy * R[e].y : 0.f;
+                    }
+                    if ((!okx && coefx != 0.f) || (!oky && coefy != 0.f)) {  // a numerically double root
+                        float mh[9], Rh[9];
+                        if (!okx && coefx != 0.f) {
+#pragma unroll
+                            for (int e = 0; e < 9; ++e) mh[e] = m[e].x;
+                            rotation_robust(mh, Rh);
+#pragma unroll
+                            for (int e = 0; e < 9; ++e) sx[e] = csx * Rh[e];
+                        }
+                        if (!oky && coefy != 0.f) {
+#pragma unroll
+                            for (int e = 0; e < 9; ++e) mh[e] = m[e].y;
+                            rotation_robust(mh, Rh);
+#pragma unroll
+                            for (int e = 0; e < 9; ++e) sy[e] = csy * Rh[e];
+                        }
+                    }
                 }
-                switch (r) {
-                    case 0: rc_scatter<0>(send, alpha, mloc, v); break;
-                    case 1: rc_scatter<1>(send, alpha, mloc, v); break;
-                    case 2: rc_scatter<2>(send, alpha, mloc, v); break;
-                    default: rc_scatter<3>(send, alpha, mloc, v); break;
+                if (d == 0) {
+                    rc_scatter<0>(sx, alpha, mloc, v);
+                    rc_scatter<1>(sy, alpha, mloc, v);
+                } else {
+                    rc_scatter<2>(sx, alpha, mloc, v);
+                    rc_scatter<3>(sy, alpha, mloc, v);
                 }
             }
+            // the next owned tile's forward outputs and weights: their latency hides behind this
+            // tile's operand store and the wait for the next covariance (issued after the rounds,
+            // so that they hold no registers there)
+            fetch(j + jstep);
             // the slot's previous tile (j - 2) must be done in every CTA's GEMM2
-            if (!fail && j >= 2) fail = !mbar_wait_sleep(&pfree_bar[s], (uint32_t)(((j >> 1) - 1) & 1));
+            if (!fail && j >= 2) {
+                const int64_t k = (j >> 1) - 1;  // tile j - 2 is the slot's k-th tile
+                fail = !mbar_wait_sleep(&pfree_bar[s][k & 1], (uint32_t)((k >> 1) & 1));
+            }
             if (!fail && lane < 30) {
                 // row 32 sp + lane of the operand, half g of its 128 bytes: four 16-byte chunks at
                 // (chunk ^ (row mod 8)), FP16 hi / lo parts
