@@ -691,6 +691,8 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
         // loaded one owned tile ahead so that their latency hides behind the current tile
         float cpre[4], wpre[4], gpre[4];
         bool val[4];
+        // condensed index of (a, b): above the diagonal rowA + b, below it b (2N - b - 1) / 2 - b - 1 + a
+        const int64_t rowA = a * (2 * N - a - 1) / 2 - a - 1;
         auto fetch = [&](int64_t jt) {
             const int64_t b0 = (J0 + jt) * TC_MB + 10 * g;
 #pragma unroll
@@ -702,8 +704,7 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
                 wpre[r] = 0.f;
                 gpre[r] = 0.f;
                 if (val[r]) {
-                    const int64_t lo = a < b ? a : b, hi = a < b ? b : a;
-                    const int64_t idx = condensed_idx(lo, hi, N);
+                    const int64_t idx = a < b ? rowA + b : b * (2 * N - b - 1) / 2 - b - 1 + a;
                     cpre[r] = __ldg(crmsd + idx);
                     wpre[r] = __ldg(wvec + idx);
                     gpre[r] = __ldg(G32 + b);
@@ -738,7 +739,12 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
                 tmem_pin32(u0);
                 tmem_pin32(u1);
 #pragma unroll
-                for (int jj = 0; jj < 32; ++jj) V[jj] = __uint_as_float(u0[jj]) + __uint_as_float(u1[jj]);
+                for (int jj = 0; jj < 32; jj += 2) {
+                    const float2 t = add2(make_float2(__uint_as_float(u0[jj]), __uint_as_float(u0[jj + 1])),
+                                          make_float2(__uint_as_float(u1[jj]), __uint_as_float(u1[jj + 1])));
+                    V[jj] = t.x;
+                    V[jj + 1] = t.y;
+                }
             } else {
 #pragma unroll
                 for (int jj = 0; jj < 32; ++jj) V[jj] = 0.f;
