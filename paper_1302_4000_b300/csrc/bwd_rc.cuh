@@ -14,18 +14,20 @@
 // shared memory (distributed shared memory), so each covariance and each rotation is computed
 // once per ordered pair, however many chunks L needs.
 //
-// Per CTA (320 threads; tensor memory: columns [0, 128) the covariance, [128, 128 + 128 q) the
+// Per CTA (608 threads; tensor memory: columns [0, 128) the covariance, [128, 128 + 128 q) the
 // CTA's q atom blocks of the transposed sum):
 //   warp 0 (TMA): for owned tiles the covariance operands (64-atom K blocks of X_I and X_J as
-//     FP16 hi / lo parts, 2-stage ring, 128-byte swizzle); one tile behind, the transposed
-//     parts X_J^T of the CTA's atom blocks (128 atoms x the tile's 64 rows, 2-stage ring);
+//     FP16 hi / lo parts, 2-stage ring, 128-byte swizzle);
 //   warp 1 (MMA): GEMM1 of an owned tile: H = X_I X_J^T in three FP16 passes (hi.hi into
 //     columns 0..63, hi.lo + lo.hi into 64..127 of one 128-column accumulator: A_hi against
 //     the stacked [X_J,hi; X_J,lo] is one N = 128 MMA, A_lo against X_J,hi one N = 64 MMA);
-//     then GEMM2 of the previous tile: sum^T += X_J^T P^T per atom block (M = 128 atoms,
-//     N = 128 rows of the A tile, K = the tile's 64 rows, three FP16 passes);
-//   warps 2-9 (epilogue): for owned tiles, read the covariance out of tensor memory (then hand
-//     it back to GEMM1), assemble each pair's 3 x 3 block (rows cyclic, as in the forward),
+//   warp 18 (TMA and MMA): the transposed parts X_J^T of the CTA's atom blocks (128 atoms x the
+//     tile's 64 rows, 2-stage ring) and GEMM2 of every tile: sum^T += X_J^T P^T per atom block
+//     (M = 128 atoms, N = 128 rows of the A tile, K = the tile's 64 rows, three FP16 passes);
+//   warps 2-17 (epilogue; four per TMEM lane quadrant, each the quadrant's 10 A models against 5
+//     of the tile's 20 B models, two pairs per lane on the paired FP32 instructions): for owned
+//     tiles, read the covariance out of tensor memory (then hand it back to GEMM1), assemble each
+//     pair's 3 x 3 block (rows cyclic, as in the forward),
 //     take Sigma (one Newton step from the forward's cRMSD) and the rotation R = dSigma/dM as the
 //     top eigenvector of Horn's key matrix (Jacobi sweeps only at a numerically double root),
 //     scale by w~, move the rows to the lanes that
@@ -35,7 +37,7 @@
 //     tiles' operands arrive the same way without any work of this CTA's threads. Pairs below
 //     the near-duplicate threshold go to the FP64 direct kernel.
 // Synchronisation between the CTAs of a cluster, per slot s (tile j uses slot j mod 2):
-//   pfull[s] (local, 8 arrivals): this CTA has written its own tile's operand;
+//   pfull[s] (local, 16 arrivals): this CTA has written its own tile's operand;
 //   prx[s]   (1 arrival by the owner, plus the copy's bytes): a peer's operand has landed;
 //   pfree[s][k mod 2] (C arrivals, a multicast tcgen05.commit from every CTA's MMA thread): every
 //            CTA has finished GEMM2 of the slot's k-th tile (tile 2 k + s), so that the owner of
@@ -59,10 +61,11 @@
 
 namespace clusco {
 
-// warp 0 covariance TMA, warp 1 covariance MMA (GEMM1), warps 2-9 epilogue, warp 10 X^T TMA and
+// warp 0 covariance TMA, warp 1 covariance MMA (GEMM1), warps 2-17 epilogue, warp 18 X^T TMA and
 // contraction MMA (GEMM2)
-constexpr int RC_THREADS = 352;
-constexpr int RC_G2WARP = 10;
+constexpr int RC_THREADS = 608;
+constexpr int RC_G2WARP = 18;
+constexpr int RC_EPI = 16;  // epilogue warps: 4 per TMEM lane quadrant, 5 B models of a tile each
 constexpr int RC_STAGES = 2;                          // GEMM1 ring
 constexpr uint32_t RC_STAGE = 2 * 16384 + 2 * 8192;   // A_hi, A_lo (128 rows), B_hi, B_lo (64 rows) x 64 FP16
 constexpr uint32_t RC_P = 2 * 16384;                  // operand P: hi, lo parts of 128 rows x 64 FP16
@@ -372,21 +375,31 @@ __device__ __forceinline__ void rc_rotation2(const float2 m[9], float2 s0, float
     R[8] = sub2(add2(ww, zz), add2(xx, yy));
 }
 
-// Cyclic assembly of round r's block from a lane's 32 covariance columns (see assemble_block),
-// with a compile-time round so that every index into V is static.
+// Cyclic assembly (see assemble_block) of round r's block on the window of one epilogue warp: the
+// 15 covariance columns of 5 B models (rounds 0 and 1 hold B models t and 3 + t of the window; a
+// lane whose model falls past the window gets a zero block and has no pair). The round is a
+// compile-time constant so that every index into V is static.
 template <int r>
-__device__ __forceinline__ void rc_assemble(const float (&V)[32], int alpha, int mloc, float blk[9])
+__device__ __forceinline__ void rc_assemble5(const float (&V)[15], int alpha, int mloc, float blk[9])
 {
-    assemble_block(V, r, alpha, mloc, blk);
+    float cand[3][3];
+#pragma unroll
+    for (int al = 0; al < 3; ++al)
+#pragma unroll
+        for (int be = 0; be < 3; ++be) {
+            const int j = 9 * r + 3 * al + be;
+            cand[al][be] = (j < 15) ? V[j] : 0.f;
+        }
+    assemble_from_cand(cand, alpha, mloc, blk);
 }
 
-// Round r's rotation rows to the lanes that own them. Lane (mloc, t) computed the pair of B
-// model 3 r + t; its rotation rows arrive cyclically (row k of send is axis (t + k) mod 3 of
-// the A model), already scaled. Lane (mloc, alpha) needs row alpha of the three pairs: from
-// lane t it takes that lane's row (alpha - t) mod 3, so in shuffle k every lane sends row k
-// and receives from lane (alpha - k) mod 3. The rows land in v at columns 3 (3 r + t) + beta.
+// Round r's rotation rows to the lanes that own them, on a 5-model window. Lane (mloc, t) computed
+// the pair of window model 3 r + t; its rotation rows arrive cyclically (row k of send is axis
+// (t + k) mod 3 of the A model), already scaled. Lane (mloc, alpha) needs row alpha of the three
+// pairs: from lane t it takes that lane's row (alpha - t) mod 3, so in shuffle k every lane sends
+// row k and receives from lane (alpha - k) mod 3. The rows land in v at columns 3 (3 r + t) + beta.
 template <int r>
-__device__ __forceinline__ void rc_scatter(const float (&send)[9], int alpha, int mloc, float (&v)[32])
+__device__ __forceinline__ void rc_scatter5(const float (&send)[9], int alpha, int mloc, float (&v)[17])
 {
     float rcv[3][3];
 #pragma unroll
@@ -399,11 +412,23 @@ __device__ __forceinline__ void rc_scatter(const float (&send)[9], int alpha, in
     }
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
-        if (3 * r + t >= 10) continue;  // past the ten B models of this half
+        if (3 * r + t >= 5) continue;  // past the five B models of this window
         const int k = (alpha + 3 - t) % 3;
 #pragma unroll
         for (int be = 0; be < 3; ++be) v[3 * (3 * r + t) + be] = sel3(k, rcv[0][be], rcv[1][be], rcv[2][be]);
     }
+}
+
+__device__ __forceinline__ void tmem_pin1(uint32_t &r) { asm volatile("" : "+r"(r)); }
+
+// FP16 hi / lo parts of two floats, as the bits of two half2
+__device__ __forceinline__ void split_h2(float x0, float x1, uint32_t &hb, uint32_t &lb)
+{
+    const __half2 hh = __floats2half2_rn(x0, x1);
+    const float2 hf = __half22float2(hh);
+    const __half2 ll = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+    hb = *reinterpret_cast<const uint32_t *>(&hh);
+    lb = *reinterpret_cast<const uint32_t *>(&ll);
 }
 
 __global__ void __launch_bounds__(RC_THREADS, 1)
@@ -430,7 +455,7 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     __shared__ int64_t g2_done, g2_seen;                     // GEMM2 tiles committed / operands waited for
-    __shared__ float dsum[TC_MA];
+    __shared__ float dpart[4][TC_MA];  // row sums of w~ per A model, one slot per column quarter
 
     // 1024-byte aligned in the shared window; indexing smem_raw keeps the pointer in the shared
     // address space
@@ -478,13 +503,13 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
             mbar_init(&xempty_bar[s], 1);
         }
         for (int s = 0; s < 2; ++s) {
-            mbar_init(&pfull_bar[s], 8);
+            mbar_init(&pfull_bar[s], RC_EPI);
             mbar_init(&prx_bar[s], 1);
             mbar_init(&pfree_bar[s][0], (uint32_t)CS);
             mbar_init(&pfree_bar[s][1], (uint32_t)CS);
         }
         mbar_init(&done1_bar, 1);
-        mbar_init(&tfree_bar, 8);
+        mbar_init(&tfree_bar, RC_EPI);
         mbar_init(&d2_bar, 1);
         mbar_init(&g1end_bar, 1);
         abort_flag = 0;
@@ -495,7 +520,6 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
     // the operand slots' pad rows (lanes 30, 31 of each quadrant) stay zero for the whole sweep
     for (int e = tid; e < (int)(2 * RC_P / 16); e += RC_THREADS)
         reinterpret_cast<float4 *>(PS)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (tid < TC_MA) dsum[tid] = 0.f;
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
@@ -671,9 +695,12 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
         }
         __syncwarp();
     } else {
-        // ================= epilogue warps 2..9 =================
+        // ================= epilogue warps 2..17 =================
+        // Warp (sp, g, hw): TMEM lane quadrant sp (= warp mod 4, the quadrant its tcgen05.ld
+        // reaches), i.e. the 10 A models of that quadrant, against the five B models
+        // 10 g + 5 hw .. + 4 of every owned tile (covariance columns 32 g + 15 hw .. + 14).
         const int etid = tid - 64, ew = warp - 2;
-        const int sp = warp & 3, g = ew >> 2;
+        const int sp = warp & 3, g = (ew >> 2) & 1, hw = ew >> 3;
         const int mloc = lane / 3, alpha = lane - 3 * (lane / 3);
         const int la = 10 * sp + mloc;
         const int64_t a = a_base + la;
@@ -683,23 +710,23 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
         const int kx = fp16_scale_exp(__uint_as_float(scl[0]));
         const int kp = fp16_scale_exp(__uint_as_float(scl[1]) / (fL * fmaxf(CLUSCO_NEARDUP, eps)));
         const float sP = exp2i(kp), ixs = exp2i(-kx);
-        const uint32_t trow = tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)(32 * g);
+        const uint32_t tcol = tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)(32 * g);
         float csum = 0.f;
         int64_t ko = 0;
         bool alive = true;
-        // forward outputs, weights and sums of squares of this lane's four pairs of an owned tile,
-        // loaded one owned tile ahead so that their latency hides behind the current tile
-        float cpre[4], wpre[4], gpre[4];
-        bool val[4];
+        // forward outputs, weights and sums of squares of this lane's two pairs of an owned tile
+        // (B models alpha and 3 + alpha of the window)
+        float cpre[2], wpre[2], gpre[2];
+        bool val[2];
         // condensed index of (a, b): above the diagonal rowA + b, below it b (2N - b - 1) / 2 - b - 1 + a
         const int64_t rowA = a * (2 * N - a - 1) / 2 - a - 1;
         auto fetch = [&](int64_t jt) {
-            const int64_t b0 = (J0 + jt) * TC_MB + 10 * g;
+            const int64_t b0 = (J0 + jt) * TC_MB + 10 * g + 5 * hw;
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
+            for (int r = 0; r < 2; ++r) {
                 const int bq = 3 * r + alpha;
                 const int64_t b = b0 + bq;
-                val[r] = jt < nJ && lane_ok && bq < 10 && b < N && b != a;
+                val[r] = jt < nJ && lane_ok && bq < 5 && b < N && b != a;
                 cpre[r] = 0.f;
                 wpre[r] = 0.f;
                 gpre[r] = 0.f;
@@ -716,127 +743,123 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
         for (int64_t j = crank; j < nJ; j += jstep) {
             const int s = (int)(j & 1);
             uint8_t *slot = PS + s * RC_P;
-            const int64_t b0 = (J0 + j) * TC_MB + 10 * g;
-            float cc[4], wc[4], gc[4];
-            bool vc[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                cc[r] = cpre[r];
-                wc[r] = wpre[r];
-                gc[r] = gpre[r];
-                vc[r] = val[r];
-            }
-            float V[32];
+            const int64_t b0 = (J0 + j) * TC_MB + 10 * g + 5 * hw;
+            const float cx = cpre[0], cy = cpre[1], wx = wpre[0], wy = wpre[1], gx = gpre[0], gy = gpre[1];
+            const bool vx = val[0], vy = val[1];
+            float V[15];
             // warp-uniform: tcgen05.ld below is a warp-wide instruction
             bool fail = __any_sync(0xffffffffu, !mbar_wait_sleep(&done1_bar, (uint32_t)(ko & 1)));
             ++ko;
             if (!fail) {
                 tc_fence_after();
-                uint32_t u0[32], u1[32];
-                tmem_ld32_issue(trow, u0);
-                tmem_ld32_issue(trow + 64, u1);
-                tmem_wait_ld();
-                tmem_pin32(u0);
-                tmem_pin32(u1);
+                // the window's 15 columns of hh | hl (columns 0..63) and of hl + lh (64..127); window 1
+                // starts at column 15, so it takes one column and the 16 from column 16
+                uint32_t u0[16], u1[16];
+                if (hw == 0) {
+                    tmem_ld16_issue(tcol, u0);
+                    tmem_ld16_issue(tcol + 64, u1);
+                    tmem_wait_ld();
+                    tmem_pin16(u0);
+                    tmem_pin16(u1);
 #pragma unroll
-                for (int jj = 0; jj < 32; jj += 2) {
-                    const float2 t = add2(make_float2(__uint_as_float(u0[jj]), __uint_as_float(u0[jj + 1])),
-                                          make_float2(__uint_as_float(u1[jj]), __uint_as_float(u1[jj + 1])));
-                    V[jj] = t.x;
-                    V[jj + 1] = t.y;
+                    for (int jj = 0; jj < 14; jj += 2) {
+                        const float2 t = add2(make_float2(__uint_as_float(u0[jj]), __uint_as_float(u0[jj + 1])),
+                                              make_float2(__uint_as_float(u1[jj]), __uint_as_float(u1[jj + 1])));
+                        V[jj] = t.x;
+                        V[jj + 1] = t.y;
+                    }
+                    V[14] = __uint_as_float(u0[14]) + __uint_as_float(u1[14]);
+                } else {
+                    uint32_t e0 = tmem_ld1_issue(tcol + 15), e1 = tmem_ld1_issue(tcol + 79);
+                    tmem_ld16_issue(tcol + 16, u0);
+                    tmem_ld16_issue(tcol + 80, u1);
+                    tmem_wait_ld();
+                    tmem_pin1(e0);
+                    tmem_pin1(e1);
+                    tmem_pin16(u0);
+                    tmem_pin16(u1);
+                    V[0] = __uint_as_float(e0) + __uint_as_float(e1);
+#pragma unroll
+                    for (int jj = 0; jj < 14; jj += 2) {
+                        const float2 t = add2(make_float2(__uint_as_float(u0[jj]), __uint_as_float(u0[jj + 1])),
+                                              make_float2(__uint_as_float(u1[jj]), __uint_as_float(u1[jj + 1])));
+                        V[jj + 1] = t.x;
+                        V[jj + 2] = t.y;
+                    }
                 }
             } else {
 #pragma unroll
-                for (int jj = 0; jj < 32; ++jj) V[jj] = 0.f;
+                for (int jj = 0; jj < 15; ++jj) V[jj] = 0.f;
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tfree_bar);  // TMEM columns 0..127 may be overwritten now
-            float v[32];
-            v[30] = v[31] = 0.f;
-            // two rounds at a time (rounds 2 d and 2 d + 1 in the two halves of the paired
-            // instructions): the rotation's code once, each half's static indices in a branch
-#pragma unroll 1
-            for (int d = 0; d < 2; ++d) {
-                float bx[9], by[9];
-                if (d == 0) {
-                    rc_assemble<0>(V, alpha, mloc, bx);
-                    rc_assemble<1>(V, alpha, mloc, by);
-                } else {
-                    rc_assemble<2>(V, alpha, mloc, bx);
-                    rc_assemble<3>(V, alpha, mloc, by);
-                }
-                // registers, not local memory: selects on d
-                const float cx = d ? cc[2] : cc[0], cy = d ? cc[3] : cc[1];
-                const float wx = d ? wc[2] : wc[0], wy = d ? wc[3] : wc[1];
-                const float gx = d ? gc[2] : gc[0], gy = d ? gc[3] : gc[1];
-                const bool vx = d ? vc[2] : vc[0], vy = d ? vc[3] : vc[1];
+            // the lane's two pairs (rounds 0 and 1 of the window) in the two halves of the paired
+            // instructions
+            float bx[9], by[9];
+            rc_assemble5<0>(V, alpha, mloc, bx);
+            rc_assemble5<1>(V, alpha, mloc, by);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float c = h ? cy : cx, w = h ? wy : wx;
-                    const bool vr = h ? vy : vx;
-                    const int64_t b = b0 + 3 * (2 * d + h) + alpha;
-                    if (lead && vr && !(c >= CLUSCO_NEARDUP) && w != 0.f && a < b) {
-                        const unsigned long long slot_nd = atomicAdd(nd_count, 1ull);
-                        if ((int64_t)slot_nd < nd_cap) {
-                            nd_list[2 * slot_nd] = a;
-                            nd_list[2 * slot_nd + 1] = b;
-                        }
+            for (int h = 0; h < 2; ++h) {
+                const float c = h ? cy : cx, w = h ? wy : wx;
+                const bool vr = h ? vy : vx;
+                const int64_t b = b0 + 3 * h + alpha;
+                if (lead && vr && !(c >= CLUSCO_NEARDUP) && w != 0.f && a < b) {
+                    const unsigned long long slot_nd = atomicAdd(nd_count, 1ull);
+                    if ((int64_t)slot_nd < nd_cap) {
+                        nd_list[2 * slot_nd] = a;
+                        nd_list[2 * slot_nd + 1] = b;
                     }
-                }
-                const float coefx = (vx && cx >= CLUSCO_NEARDUP && wx != 0.f) ? __fdividef(wx, fL * fmaxf(cx, eps)) : 0.f;
-                const float coefy = (vy && cy >= CLUSCO_NEARDUP && wy != 0.f) ? __fdividef(wy, fL * fmaxf(cy, eps)) : 0.f;
-                csum += coefx + coefy;
-                float sx[9], sy[9];
-#pragma unroll
-                for (int e = 0; e < 9; ++e) sx[e] = sy[e] = 0.f;
-                if ((coefx != 0.f || coefy != 0.f) && !fail) {
-                    const float igx = __fdividef(1.f, Ga + gx), igy = __fdividef(1.f, Ga + gy);
-                    const float2 nrm = make_float2(2.f * igx * ixs * ixs, 2.f * igy * ixs * ixs);
-                    float2 m[9], R[9];
-#pragma unroll
-                    for (int e = 0; e < 9; ++e) m[e] = mul2(make_float2(bx[e], by[e]), nrm);
-                    // Sigma_hat from the forward's cRMSD: L c^2 = (G_A + G_B)(1 - Sigma_hat)
-                    const float2 s0 = make_float2(fmaf(-fL * cx * cx, igx, 1.f), fmaf(-fL * cy * cy, igy, 1.f));
-                    bool okx, oky;
-                    rc_rotation2(m, s0, R, okx, oky);
-                    const float csx = coefx * sP, csy = coefy * sP;
-                    // a pair without a coefficient (near-duplicate, padding) has no rotation: the
-                    // half it occupied may hold anything, so select, do not multiply by zero
-#pragma unroll
-                    for (int e = 0; e < 9; ++e) {
-                        sx[e] = coefx != 0.f ? csx * R[e].x : 0.f;
-                        sy[e] = coefy != 0.f ? csy * R[e].y : 0.f;
-                    }
-                    if ((!okx && coefx != 0.f) || (!oky && coefy != 0.f)) {  // a numerically double root
-                        float mh[9], Rh[9];
-                        if (!okx && coefx != 0.f) {
-#pragma unroll
-                            for (int e = 0; e < 9; ++e) mh[e] = m[e].x;
-                            rotation_robust(mh, Rh);
-#pragma unroll
-                            for (int e = 0; e < 9; ++e) sx[e] = csx * Rh[e];
-                        }
-                        if (!oky && coefy != 0.f) {
-#pragma unroll
-                            for (int e = 0; e < 9; ++e) mh[e] = m[e].y;
-                            rotation_robust(mh, Rh);
-#pragma unroll
-                            for (int e = 0; e < 9; ++e) sy[e] = csy * Rh[e];
-                        }
-                    }
-                }
-                if (d == 0) {
-                    rc_scatter<0>(sx, alpha, mloc, v);
-                    rc_scatter<1>(sy, alpha, mloc, v);
-                } else {
-                    rc_scatter<2>(sx, alpha, mloc, v);
-                    rc_scatter<3>(sy, alpha, mloc, v);
                 }
             }
+            const float coefx = (vx && cx >= CLUSCO_NEARDUP && wx != 0.f) ? __fdividef(wx, fL * fmaxf(cx, eps)) : 0.f;
+            const float coefy = (vy && cy >= CLUSCO_NEARDUP && wy != 0.f) ? __fdividef(wy, fL * fmaxf(cy, eps)) : 0.f;
+            csum += coefx + coefy;
+            float sx[9], sy[9];
+#pragma unroll
+            for (int e = 0; e < 9; ++e) sx[e] = sy[e] = 0.f;
+            if ((coefx != 0.f || coefy != 0.f) && !fail) {
+                const float igx = __fdividef(1.f, Ga + gx), igy = __fdividef(1.f, Ga + gy);
+                const float2 nrm = make_float2(2.f * igx * ixs * ixs, 2.f * igy * ixs * ixs);
+                float2 m[9], R[9];
+#pragma unroll
+                for (int e = 0; e < 9; ++e) m[e] = mul2(make_float2(bx[e], by[e]), nrm);
+                // Sigma_hat from the forward's cRMSD: L c^2 = (G_A + G_B)(1 - Sigma_hat)
+                const float2 s0 = make_float2(fmaf(-fL * cx * cx, igx, 1.f), fmaf(-fL * cy * cy, igy, 1.f));
+                bool okx, oky;
+                rc_rotation2(m, s0, R, okx, oky);
+                const float csx = coefx * sP, csy = coefy * sP;
+                // a pair without a coefficient (near-duplicate, padding) has no rotation: the half it
+                // occupied may hold anything, so select, do not multiply by zero
+#pragma unroll
+                for (int e = 0; e < 9; ++e) {
+                    sx[e] = coefx != 0.f ? csx * R[e].x : 0.f;
+                    sy[e] = coefy != 0.f ? csy * R[e].y : 0.f;
+                }
+                if ((!okx && coefx != 0.f) || (!oky && coefy != 0.f)) {  // a numerically double root
+                    float mh[9], Rh[9];
+                    if (!okx && coefx != 0.f) {
+#pragma unroll
+                        for (int e = 0; e < 9; ++e) mh[e] = m[e].x;
+                        rotation_robust(mh, Rh);
+#pragma unroll
+                        for (int e = 0; e < 9; ++e) sx[e] = csx * Rh[e];
+                    }
+                    if (!oky && coefy != 0.f) {
+#pragma unroll
+                        for (int e = 0; e < 9; ++e) mh[e] = m[e].y;
+                        rotation_robust(mh, Rh);
+#pragma unroll
+                        for (int e = 0; e < 9; ++e) sy[e] = csy * Rh[e];
+                    }
+                }
+            }
+            float v[17];
+            v[15] = v[16] = 0.f;  // window 1's columns 30, 31: the group's two zero rows
+            rc_scatter5<0>(sx, alpha, mloc, v);
+            rc_scatter5<1>(sy, alpha, mloc, v);
             // the next owned tile's forward outputs and weights: their latency hides behind this
-            // tile's operand store and the wait for the next covariance (issued after the rounds,
-            // so that they hold no registers there)
+            // tile's operand store and the wait for the next covariance
             fetch(j + jstep);
             // the slot's previous tile (j - 2) must be done in every CTA's GEMM2
             if (!fail && j >= 2) {
@@ -844,32 +867,49 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
                 fail = !mbar_wait_sleep(&pfree_bar[s][k & 1], (uint32_t)((k >> 1) & 1));
             }
             if (!fail && lane < 30) {
-                // row 32 sp + lane of the operand, half g of its 128 bytes: four 16-byte chunks at
-                // (chunk ^ (row mod 8)), FP16 hi / lo parts
+                // row 32 sp + lane of the operand, columns 32 g + 15 hw .. of its 64: 16-byte chunks at
+                // (chunk ^ (row mod 8)), FP16 hi / lo parts. Window 0 fills chunk 4 g and the first
+                // seven columns of chunk 4 g + 1, window 1 that chunk's last column and chunks
+                // 4 g + 2, 4 g + 3 (2-byte stores where the two windows share a word)
                 const int row = 32 * sp + lane;
-                uint8_t *base = slot + row * 128;
-#pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
+                uint8_t *hb = slot + row * 128, *lb = hb + RC_P / 2;
+                auto choff = [&](int chunk) { return ((chunk ^ (row & 7)) & 7) << 4; };
+                if (hw == 0) {
                     uint32_t h[4], l[4];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float x0 = v[8 * qq + 2 * e], x1 = v[8 * qq + 2 * e + 1];
-                        const __half2 hh = __floats2half2_rn(x0, x1);
-                        const float2 hf = __half22float2(hh);
-                        const __half2 ll = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
-                        h[e] = *reinterpret_cast<const uint32_t *>(&hh);
-                        l[e] = *reinterpret_cast<const uint32_t *>(&ll);
+                    for (int e = 0; e < 4; ++e) split_h2(v[2 * e], v[2 * e + 1], h[e], l[e]);
+                    *reinterpret_cast<uint4 *>(hb + choff(4 * g)) = make_uint4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<uint4 *>(lb + choff(4 * g)) = make_uint4(l[0], l[1], l[2], l[3]);
+                    const int o = choff(4 * g + 1);
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) {
+                        split_h2(v[8 + 2 * e], v[9 + 2 * e], h[e], l[e]);
+                        *reinterpret_cast<uint32_t *>(hb + o + 4 * e) = h[e];
+                        *reinterpret_cast<uint32_t *>(lb + o + 4 * e) = l[e];
                     }
-                    const int off = (((4 * g + qq) ^ (row & 7)) & 7) << 4;
-                    *reinterpret_cast<uint4 *>(base + off) = make_uint4(h[0], h[1], h[2], h[3]);
-                    *reinterpret_cast<uint4 *>(base + RC_P / 2 + off) = make_uint4(l[0], l[1], l[2], l[3]);
+                    split_h2(v[14], 0.f, h[3], l[3]);
+                    *reinterpret_cast<uint16_t *>(hb + o + 12) = (uint16_t)(h[3] & 0xffffu);
+                    *reinterpret_cast<uint16_t *>(lb + o + 12) = (uint16_t)(l[3] & 0xffffu);
+                } else {
+                    uint32_t h[4], l[4];
+                    const int o = choff(4 * g + 1);
+                    split_h2(v[0], 0.f, h[0], l[0]);
+                    *reinterpret_cast<uint16_t *>(hb + o + 14) = (uint16_t)(h[0] & 0xffffu);
+                    *reinterpret_cast<uint16_t *>(lb + o + 14) = (uint16_t)(l[0] & 0xffffu);
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) split_h2(v[1 + 8 * q + 2 * e], v[2 + 8 * q + 2 * e], h[e], l[e]);
+                        *reinterpret_cast<uint4 *>(hb + choff(4 * g + 2 + q)) = make_uint4(h[0], h[1], h[2], h[3]);
+                        *reinterpret_cast<uint4 *>(lb + choff(4 * g + 2 + q)) = make_uint4(l[0], l[1], l[2], l[3]);
+                    }
                 }
             }
             // generic-proxy stores to the slot must be visible to tcgen05.mma and to the bulk copies
             fence_proxy_async();
             __syncwarp();
             if (lane == 0 && !fail) mbar_arrive(&pfull_bar[s]);
-            if (named_bar_or(1, 256, fail || *abort_v)) {
+            if (named_bar_or(1, 32 * RC_EPI, fail || *abort_v)) {
                 alive = false;
                 break;
             }
@@ -885,33 +925,34 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
                 }
             }
         }
-        // row sums of w~ per A model: the three lanes of a model, then the two column halves
+        // row sums of w~ per A model: the three lanes of a model, then one slot per column quarter
+        // (ew / 4), added in a fixed order below, so that the sums do not depend on warp timing
         float cs3 = csum + __shfl_down_sync(0xffffffffu, csum, 1) + __shfl_down_sync(0xffffffffu, csum, 2);
-        if (lane_ok && alpha == 0) atomicAdd(&dsum[la], cs3);
+        if (lane < 30 && alpha == 0) dpart[ew >> 2][la] = cs3;
         {  // every epilogue warp, stopped or not, meets the others here once
             const bool ok3 = alive && mbar_wait_sleep(&d2_bar, 0);
-            alive = !named_bar_or(1, 256, !ok3 || *abort_v);
+            alive = !named_bar_or(1, 32 * RC_EPI, !ok3 || *abort_v);
         }
         if (alive) {
             tc_fence_after();
-            // read the transposed sum out of TMEM: warp (sp, g) takes TMEM lanes 32 sp.. (atoms)
-            // and half g of each block's 128 columns (rows of the A tile); undo both scales
+            // read the transposed sum out of TMEM: warp (sp, q = ew / 4) takes TMEM lanes 32 sp..
+            // (atoms) and the q-th quarter of each block's 128 columns (rows of the A tile); undo
+            // both scales
             const float ix = exp2i(-kx), ip = exp2i(-kp);
             float *gbase = Gp + (sidx * Rpad + 128 * I) * (int64_t)Lp;
+            const int r0 = 32 * (ew >> 2);
             for (int bl = 0; bl < nb; ++bl) {
                 const int atom = (blk0 + bl) * RC_BLK + 32 * sp + lane;
+                float vv[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * sp) << 16) + RC_G2COL + (uint32_t)(bl * 128 + r0), vv);
+                if (atom < Lp) {
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int r0 = 64 * g + 32 * h;
-                    float vv[32];
-                    tmem_ld32(tmem + ((uint32_t)(32 * sp) << 16) + RC_G2COL + (uint32_t)(bl * 128 + r0), vv);
-                    if (atom < Lp) {
-#pragma unroll
-                        for (int jj = 0; jj < 32; ++jj) gbase[(int64_t)(r0 + jj) * Lp + atom] = -(vv[jj] * ix) * ip;
-                    }
+                    for (int jj = 0; jj < 32; ++jj) gbase[(int64_t)(r0 + jj) * Lp + atom] = -(vv[jj] * ix) * ip;
                 }
             }
-            if (etid < TC_MA) dp[dslice * Npad + a_base + etid] = lead ? dsum[etid] : 0.f;
+            if (etid < TC_MA)
+                dp[dslice * Npad + a_base + etid] =
+                    lead ? ((dpart[0][etid] + dpart[1][etid]) + dpart[2][etid]) + dpart[3][etid] : 0.f;
         } else {
             atomicExch(&abort_flag, 1);
         }
