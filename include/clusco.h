@@ -263,12 +263,11 @@ int clusco_crmsd_allpairs_backward_rot(const float *coords, int64_t N, int64_t L
  * followed by clusco_crmsd_allpairs_backward_rot of the weights grad_out (grad_coords), with the
  * same arguments, results and limits as those two calls made in turn. The adjoint's pre-pass
  * reads only coords and grad_out, so the call runs it on a stream of the library's own (one per
- * device, created on first use and kept until the process exits), forked from and joined back
- * into stream by events, beside the forward. grad_out must therefore be final when the call is
+ * host thread and device, created on the thread's first fused call and kept until the process
+ * exits), forked from and joined back into stream by events, beside the forward. grad_out must therefore be final when the call is
  * made (its values may not depend on this call's out). Every kernel is ordered after the work
- * already enqueued on stream, and every later work on stream after the call's. Each host thread
- * has its own side stream per device, so that calls from several threads never share one.
- * Workspace: CLUSCO_OP_STEP_ROT bytes (the two calls' workspaces,
+ * already enqueued on stream, and every later work on stream after the call's. Calls from
+ * several host threads never share a side stream. Workspace: CLUSCO_OP_STEP_ROT bytes (the two calls' workspaces,
  * each 256-byte aligned). No counterpart in the paper, which gives no gradient. */
 int clusco_crmsd_allpairs_step_rot(const float *coords, int64_t N, int64_t L, const float *grad_out, float *out,
                                    float *rot, float *grad_coords, int form, float eps, void *workspace,
@@ -282,9 +281,12 @@ int clusco_crmsd_allpairs_step_rot(const float *coords, int64_t N, int64_t L, co
  * the thread's first fused call, kept until the process exits), forked from and joined back into
  * stream by events, beside the forward. grad_out must therefore be final when the call is made (its
  * values may not depend on this call's out). Every kernel is ordered after the work already
- * enqueued on stream, and every later work on stream after the call's. Workspace: CLUSCO_OP_STEP
- * bytes (the two calls' workspaces, each 256-byte aligned). No counterpart in the paper, which
- * gives no gradient. */
+ * enqueued on stream, and every later work on stream after the call's. With a workspace given,
+ * the call can be captured into a CUDA graph from stream (the fork and the join become edges of
+ * the graph); while that capture is open the thread's side stream belongs to it, so the thread
+ * makes no uncaptured fused call until the capture ends. Workspace: CLUSCO_OP_STEP bytes (the
+ * two calls' workspaces, each 256-byte aligned). No counterpart in the paper, which gives no
+ * gradient. */
 int clusco_crmsd_allpairs_step(const float *coords, int64_t N, int64_t L, const float *grad_out, float *out,
                                float *grad_coords, int form, float eps, void *workspace, size_t workspace_bytes,
                                void *stream);

@@ -191,6 +191,36 @@ def test_fused_step_equals_the_two_calls(N, L):
         assert d <= 1e-6
 
 
+def test_fused_step_in_a_cuda_graph():
+    """The fused step captured into a CUDA graph from a torch stream (the side stream's fork and
+    join become graph edges) and replayed twice gives the uncaptured call's matrix and gradient
+    bit for bit. The ensemble has no near-duplicate pair, whose FP64 terms are added with float
+    atomics in any order."""
+    N, L = 400, 500
+    e = E.decoy_ensemble(N, L, 2, (1.0, 8.0), 4242)
+    X = torch.from_numpy(e.coords).cuda()
+    w = torch.from_numpy(E.weights(N * (N - 1) // 2, 4243)).cuda()
+    ws = torch.empty(clusco.workspace_bytes(clusco.OP_STEP, N, L), dtype=torch.uint8, device="cuda")
+    out0, g0 = clusco.crmsd_allpairs_step(X, w, clusco.FORM_BF16_EXACT2, 1e-6, workspace=ws)
+    assert clusco.sync_status() == 0
+    assert float(out0.min()) >= 0.5  # no pair takes the near-duplicate path
+    out, g = torch.empty_like(out0), torch.empty_like(g0)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=st):
+        clusco.crmsd_allpairs_step(X, w, clusco.FORM_BF16_EXACT2, 1e-6, out=out, grad_coords=g, workspace=ws,
+                                   stream=st)
+    for _ in range(2):
+        out.zero_()
+        g.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, out0)
+        assert torch.equal(g, g0)
+    assert clusco.sync_status() == 0
+
+
 def test_fused_step_argument_errors():
     X = torch.zeros((4, 8, 3), device="cuda")
     w = torch.ones(6, device="cuda")
