@@ -21,9 +21,11 @@
 //   warp 1 (MMA): GEMM1 of an owned tile: H = X_I X_J^T in three FP16 passes (hi.hi into
 //     columns 0..63, hi.lo + lo.hi into 64..127 of one 128-column accumulator: A_hi against
 //     the stacked [X_J,hi; X_J,lo] is one N = 128 MMA, A_lo against X_J,hi one N = 64 MMA);
-//   warp 18 (TMA and MMA): the transposed parts X_J^T of the CTA's atom blocks (128 atoms x the
-//     tile's 64 rows, 2-stage ring) and GEMM2 of every tile: sum^T += X_J^T P^T per atom block
-//     (M = 128 atoms, N = 128 rows of the A tile, K = the tile's 64 rows, three FP16 passes);
+//   warp 19 (TMA): the transposed parts X_J^T of the CTA's atom blocks (128 atoms x the tile's
+//     64 rows), hi and lo halves in a 4-stage ring of half blocks, up to three ahead;
+//   warp 18 (MMA): GEMM2 of every tile: sum^T += X_J^T P^T per atom block (M = 128 atoms,
+//     N = 128 rows of the A tile, K = the tile's 64 rows, three FP16 passes: the hi half against
+//     P_hi and P_lo, then the lo half against P_hi);
 //   warps 2-17 (epilogue; four per TMEM lane quadrant, each the quadrant's 10 A models against 5
 //     of the tile's 20 B models, two pairs per lane on the paired FP32 instructions): for owned
 //     tiles, read the covariance out of tensor memory (then hand it back to GEMM1), assemble each
@@ -61,21 +63,22 @@
 
 namespace clusco {
 
-// warp 0 covariance TMA, warp 1 covariance MMA (GEMM1), warps 2-17 epilogue, warp 18 X^T TMA and
-// contraction MMA (GEMM2)
-constexpr int RC_THREADS = 608;
+// warp 0 covariance TMA, warp 1 covariance MMA (GEMM1), warps 2-17 epilogue, warp 18 contraction
+// MMA (GEMM2), warp 19 X^T TMA
+constexpr int RC_THREADS = 640;
 constexpr int RC_G2WARP = 18;
+constexpr int RC_XWARP = 19;
 constexpr int RC_EPI = 16;  // epilogue warps: 4 per TMEM lane quadrant, 5 B models of a tile each
 constexpr int RC_STAGES = 2;                          // GEMM1 ring
 constexpr uint32_t RC_STAGE = 2 * 16384 + 2 * 8192;   // A_hi, A_lo (128 rows), B_hi, B_lo (64 rows) x 64 FP16
 constexpr uint32_t RC_P = 2 * 16384;                  // operand P: hi, lo parts of 128 rows x 64 FP16
-constexpr int RC_XSTAGES = 2;                         // X_J^T ring
-constexpr uint32_t RC_XBUF = 2 * 16384;               // X_J^T: hi, lo parts of 128 atoms x 64 FP16
+constexpr int RC_XSTAGES = 4;                         // X_J^T ring of half blocks
+constexpr uint32_t RC_XHALF = 16384;                  // X_J^T hi or lo part of 128 atoms x 64 FP16
 constexpr int RC_BLK = 128;                           // atoms per accumulator block (GEMM2 M)
 constexpr int RC_MAXQ = 3;                            // accumulator blocks per CTA
 constexpr int RC_MAXLP = 1024;
 constexpr uint32_t RC_G2COL = 128;                    // first TMEM column of the transposed sum
-constexpr size_t RC_SMEM = 1024 + RC_STAGES * RC_STAGE + 2 * RC_P + RC_XSTAGES * RC_XBUF;
+constexpr size_t RC_SMEM = 1024 + RC_STAGES * RC_STAGE + 2 * RC_P + RC_XSTAGES * RC_XHALF;
 static_assert(RC_SMEM + 1024 <= 227 * 1024, "shared memory per CTA");
 static_assert((RC_MAXLP / RC_BLK + RC_MAXQ - 1) / RC_MAXQ <= 4, "the operand slots' barriers assume clusters of <= 4");
 
@@ -448,7 +451,7 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
     __shared__ __align__(8) uint64_t pfull_bar[2];           // an owned tile's operand is written (8 arrivals)
     __shared__ __align__(8) uint64_t prx_bar[2];             // a peer's operand has landed (1 arrival + bytes)
     __shared__ __align__(8) uint64_t pfree_bar[2][2];        // every CTA finished GEMM2 of a tile (CS arrivals)
-    __shared__ __align__(8) uint64_t xfull_bar[RC_XSTAGES];  // an X^T block landed
+    __shared__ __align__(8) uint64_t xfull_bar[RC_XSTAGES];  // an X^T half block landed
     __shared__ __align__(8) uint64_t xempty_bar[RC_XSTAGES]; // GEMM2 has finished reading it
     __shared__ __align__(8) uint64_t d2_bar;                 // every GEMM2 MMA of this CTA has completed
     __shared__ __align__(8) uint64_t g1end_bar;              // every GEMM1 MMA of this CTA has completed
@@ -462,7 +465,7 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
     uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint8_t *RING = smem;
     uint8_t *PS = smem + RC_STAGES * RC_STAGE;  // two operand slots of RC_P bytes
-    uint8_t *XT = PS + 2 * RC_P;                // RC_XSTAGES X^T blocks of RC_XBUF bytes
+    uint8_t *XT = PS + 2 * RC_P;                // RC_XSTAGES X^T half blocks of RC_XHALF bytes
     const uint32_t ringbase = smem_u32(RING), pbase = smem_u32(PS), xtbase = smem_u32(XT);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t cl = blockIdx.x / C;  // the cluster (CS = C) or the group of C chunk CTAs
@@ -529,8 +532,8 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
     const int64_t nJ = J1 - J0;
     volatile int *abort_v = &abort_flag;
     auto owned = [&](int64_t j) { return CS == 1 || (int)(j % CS) == crank; };
-    // stages armed by the covariance producer (warp 0, lane 0) and by the contraction thread's X^T
-    // loads (warp 10, lane 0)
+    // stages armed by the covariance producer (warp 0, lane 0) and by the X^T producer (warp 19,
+    // lane 0)
     int64_t q1 = 0, cx = 0;
 
     if (warp == 0) {
@@ -562,18 +565,12 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
         }
         __syncwarp();
     } else if (warp == 1 || warp == RC_G2WARP) {
-        // ================= MMA issuers: covariance GEMM1 (warp 1), contraction GEMM2 (warp 10) =================
+        // ================= MMA issuers: covariance GEMM1 (warp 1), contraction GEMM2 (warp 18) =================
         // Two threads, so that GEMM1 of the next owned tile goes out as soon as the epilogue has read
         // the current covariance, whatever operand GEMM2 is waiting for; each thread's commits track
-        // its own MMAs, and they touch disjoint tensor memory and shared memory. The GEMM2 thread
-        // also loads the X^T blocks, one block ahead of its consumption (a ring of RC_XSTAGES).
+        // its own MMAs, and they touch disjoint tensor memory and shared memory.
         if (lane == 0) {
-            if (warp == RC_G2WARP) {
-                tma_prefetch_desc(&mapTh);
-                tma_prefetch_desc(&mapTl);
-            }
             int64_t q1 = 0, xc = 0, ko = 0, gd = 0, seen = 0;
-            const int64_t nxb = nJ * nb;  // X^T blocks of the sweep, tile-major
             int po0 = 0, po1 = 0;  // own operands written into slot 0 / 1
             int rx0 = 0, rx1 = 0;  // peer operands received into slot 0 / 1
             bool ok = true;
@@ -600,21 +597,6 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
                 }
                 mma_commit(&done1_bar);
             };
-            // arm X^T block t (tile t / nb, block t mod nb of this CTA's chunk) into stage t mod
-            // RC_XSTAGES, once GEMM2 has finished reading the stage's previous block
-            auto x_arm = [&](int64_t t) {
-                const int st = (int)(t % RC_XSTAGES);
-                if (t >= RC_XSTAGES && !mbar_wait_sleep(&xempty_bar[st], (uint32_t)(((t / RC_XSTAGES) - 1) & 1))) {
-                    ok = false;
-                    return;
-                }
-                // the tile's 64 operand rows x 128 atoms; atoms past Lp read as zeros
-                const int x = (int)(64 * (J0 + t / nb)), y = (blk0 + (int)(t % nb)) * RC_BLK;
-                mbar_arrive_expect_tx(&xfull_bar[st], RC_XBUF);
-                tma_load_2d(XT + st * RC_XBUF, &mapTh, &xfull_bar[st], x, y);
-                tma_load_2d(XT + st * RC_XBUF + RC_XBUF / 2, &mapTl, &xfull_bar[st], x, y);
-                cx = t + 1;
-            };
             auto g2 = [&](int64_t jj) {
                 const int s = (int)(jj & 1);
                 bool got;
@@ -639,26 +621,33 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
                 tc_fence_after();
                 const uint32_t pb = pbase + s * RC_P;
                 for (int bl = 0; bl < nb && ok; ++bl, ++xc) {
-                    const int st = (int)(xc % RC_XSTAGES);
-                    if (!mbar_wait(&xfull_bar[st], (uint32_t)((xc / RC_XSTAGES) & 1))) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t xb = xtbase + st * RC_XBUF;
                     const uint32_t d = tmem + RC_G2COL + (uint32_t)(bl * 128);
+                    // the block's hi half (X_J,hi against P_hi and P_lo), then its lo half (X_J,lo
+                    // against P_hi), each from its own stage of the ring
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const uint64_t xhi = desc_sw128(xb + 32 * k), xlo = desc_sw128(xb + RC_XBUF / 2 + 32 * k);
-                        const uint64_t phi = desc_sw128(pb + 32 * k), plo = desc_sw128(pb + RC_P / 2 + 32 * k);
-                        // each block's first MMA of the sweep starts its columns from zero
-                        mma_f16(d, xhi, phi, id128, (jj == 0 && k == 0) ? 0u : 1u);
-                        mma_f16(d, xhi, plo, id128, 1u);
-                        mma_f16(d, xlo, phi, id128, 1u);
+                    for (int part = 0; part < 2; ++part) {
+                        const int64_t hh = 2 * xc + part;
+                        const int st = (int)(hh % RC_XSTAGES);
+                        if (!mbar_wait(&xfull_bar[st], (uint32_t)((hh / RC_XSTAGES) & 1))) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t xb = xtbase + st * RC_XHALF;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const uint64_t xd = desc_sw128(xb + 32 * k);
+                            const uint64_t phi = desc_sw128(pb + 32 * k), plo = desc_sw128(pb + RC_P / 2 + 32 * k);
+                            if (part == 0) {
+                                // each block's first MMA of the sweep starts its columns from zero
+                                mma_f16(d, xd, phi, id128, (jj == 0 && k == 0) ? 0u : 1u);
+                                mma_f16(d, xd, plo, id128, 1u);
+                            } else {
+                                mma_f16(d, xd, phi, id128, 1u);
+                            }
+                        }
+                        mma_commit(&xempty_bar[st]);
                     }
-                    mma_commit(&xempty_bar[st]);
-                    // refill the stage the previous block used (its GEMM2 was committed a block ago)
-                    if (xc >= 1 && xc - 1 + RC_XSTAGES < nxb) x_arm(xc - 1 + RC_XSTAGES);
                 }
                 if (!ok) return;
                 uint64_t *pf = &pfree_bar[s][(jj >> 1) & 1];
@@ -680,7 +669,6 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
                     ++ko;
                 }
             } else {
-                for (int64_t t = 0; t < RC_XSTAGES && t < nxb && ok; ++t) x_arm(t);
                 for (int64_t j = 0; j < nJ && ok && !*abort_v; ++j) g2(j);
             }
             // also on abort: fires once everything this thread issued has completed
@@ -692,6 +680,32 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
                 g2_done = gd;
                 g2_seen = seen;
             }
+        }
+        __syncwarp();
+    } else if (warp == RC_XWARP) {
+        // ================= TMA producer: X^T half blocks of every tile =================
+        // half block h: block h / 2 of the sweep (tile h / (2 nb), atom block of this CTA's chunk),
+        // part h mod 2 (hi, lo), into stage h mod RC_XSTAGES once GEMM2 has finished reading the
+        // stage's previous half block; so up to three half blocks load while GEMM2 reads the fourth
+        if (lane == 0) {
+            tma_prefetch_desc(&mapTh);
+            tma_prefetch_desc(&mapTl);
+            const int64_t nxh = 2 * nJ * nb;
+            bool ok = true;
+            for (int64_t h = 0; h < nxh && ok && !*abort_v; ++h) {
+                const int st = (int)(h % RC_XSTAGES);
+                if (h >= RC_XSTAGES && !mbar_wait_sleep(&xempty_bar[st], (uint32_t)(((h / RC_XSTAGES) - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                // the tile's 64 operand rows x 128 atoms; atoms past Lp read as zeros
+                const int64_t t = h >> 1;
+                const int x = (int)(64 * (J0 + t / nb)), y = (blk0 + (int)(t % nb)) * RC_BLK;
+                mbar_arrive_expect_tx(&xfull_bar[st], RC_XHALF);
+                tma_load_2d(XT + st * RC_XHALF, (h & 1) ? &mapTl : &mapTh, &xfull_bar[st], x, y);
+                cx = h + 1;
+            }
+            if (!ok) atomicExch(&abort_flag, 1);
         }
         __syncwarp();
     } else {
@@ -965,7 +979,7 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
         if (warp == 0)
             for (int64_t r = (q1 > RC_STAGES ? q1 - RC_STAGES : 0); r < q1; ++r)
                 mbar_wait(&full_bar[r % RC_STAGES], (uint32_t)((r / RC_STAGES) & 1));
-        if (warp == RC_G2WARP)
+        if (warp == RC_XWARP)
             for (int64_t r = (cx > RC_XSTAGES ? cx - RC_XSTAGES : 0); r < cx; ++r)
                 mbar_wait(&xfull_bar[r % RC_XSTAGES], (uint32_t)((r / RC_XSTAGES) & 1));
     }
