@@ -768,38 +768,36 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
                 tc_fence_after();
                 // the window's 15 columns of hh | hl (columns 0..63) and of hl + lh (64..127); window 1
                 // starts at column 15, so it takes one column and the 16 from column 16
-                uint32_t u0[16], u1[16];
+                // one class at a time (16 registers in flight, not 32)
+                uint32_t u[16];
                 if (hw == 0) {
-                    tmem_ld16_issue(tcol, u0);
-                    tmem_ld16_issue(tcol + 64, u1);
+                    tmem_ld16_issue(tcol, u);
                     tmem_wait_ld();
-                    tmem_pin16(u0);
-                    tmem_pin16(u1);
+                    tmem_pin16(u);
 #pragma unroll
-                    for (int jj = 0; jj < 14; jj += 2) {
-                        const float2 t = add2(make_float2(__uint_as_float(u0[jj]), __uint_as_float(u0[jj + 1])),
-                                              make_float2(__uint_as_float(u1[jj]), __uint_as_float(u1[jj + 1])));
-                        V[jj] = t.x;
-                        V[jj + 1] = t.y;
-                    }
-                    V[14] = __uint_as_float(u0[14]) + __uint_as_float(u1[14]);
+                    for (int jj = 0; jj < 15; ++jj) V[jj] = __uint_as_float(u[jj]);
+                    tmem_ld16_issue(tcol + 64, u);
+                    tmem_wait_ld();
+                    tmem_pin16(u);
+#pragma unroll
+                    for (int jj = 0; jj < 15; ++jj) V[jj] += __uint_as_float(u[jj]);
                 } else {
-                    uint32_t e0 = tmem_ld1_issue(tcol + 15), e1 = tmem_ld1_issue(tcol + 79);
-                    tmem_ld16_issue(tcol + 16, u0);
-                    tmem_ld16_issue(tcol + 80, u1);
+                    uint32_t e0 = tmem_ld1_issue(tcol + 15);
+                    tmem_ld16_issue(tcol + 16, u);
                     tmem_wait_ld();
                     tmem_pin1(e0);
-                    tmem_pin1(e1);
-                    tmem_pin16(u0);
-                    tmem_pin16(u1);
-                    V[0] = __uint_as_float(e0) + __uint_as_float(e1);
+                    tmem_pin16(u);
+                    V[0] = __uint_as_float(e0);
 #pragma unroll
-                    for (int jj = 0; jj < 14; jj += 2) {
-                        const float2 t = add2(make_float2(__uint_as_float(u0[jj]), __uint_as_float(u0[jj + 1])),
-                                              make_float2(__uint_as_float(u1[jj]), __uint_as_float(u1[jj + 1])));
-                        V[jj + 1] = t.x;
-                        V[jj + 2] = t.y;
-                    }
+                    for (int jj = 0; jj < 14; ++jj) V[jj + 1] = __uint_as_float(u[jj]);
+                    e0 = tmem_ld1_issue(tcol + 79);
+                    tmem_ld16_issue(tcol + 80, u);
+                    tmem_wait_ld();
+                    tmem_pin1(e0);
+                    tmem_pin16(u);
+                    V[0] += __uint_as_float(e0);
+#pragma unroll
+                    for (int jj = 0; jj < 14; ++jj) V[jj + 1] += __uint_as_float(u[jj]);
                 }
             } else {
 #pragma unroll
@@ -955,13 +953,23 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
             const float ix = exp2i(-kx), ip = exp2i(-kp);
             float *gbase = Gp + (sidx * Rpad + 128 * I) * (int64_t)Lp;
             const int r0 = 32 * (ew >> 2);
+            // 16 columns at a time: a 32-column load here, with the sweep's state still live,
+            // made the register allocator spill inside the tile loop
+#pragma unroll 1
             for (int bl = 0; bl < nb; ++bl) {
                 const int atom = (blk0 + bl) * RC_BLK + 32 * sp + lane;
-                float vv[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * sp) << 16) + RC_G2COL + (uint32_t)(bl * 128 + r0), vv);
-                if (atom < Lp) {
+                float *gcol = gbase + (int64_t)r0 * Lp + atom;
+#pragma unroll 1
+                for (int hc = 0; hc < 32; hc += 16) {
+                    uint32_t vv[16];
+                    tmem_ld16_issue(tmem + ((uint32_t)(32 * sp) << 16) + RC_G2COL + (uint32_t)(bl * 128 + r0 + hc), vv);
+                    tmem_wait_ld();
+                    tmem_pin16(vv);
+                    if (atom < Lp) {
 #pragma unroll
-                    for (int jj = 0; jj < 32; ++jj) gbase[(int64_t)(r0 + jj) * Lp + atom] = -(vv[jj] * ix) * ip;
+                        for (int jj = 0; jj < 16; ++jj)
+                            gcol[(int64_t)(hc + jj) * Lp] = -(__uint_as_float(vv[jj]) * ix) * ip;
+                    }
                 }
             }
             if (etid < TC_MA)
