@@ -261,21 +261,6 @@ __global__ void __launch_bounds__(256) rc_split_kernel(const float *__restrict__
 // operations per instruction): the same steps as rc_rotation, so that each lane carries two
 // independent chains and half the instructions per pair. Selections, reciprocals and the
 // validity tests stay per pair.
-__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b)
-{
-    unsigned long long d;
-    asm("sub.rn.f32x2 %0, %1, %2;"
-        : "=l"(d)
-        : "l"(*reinterpret_cast<const unsigned long long *>(&a)), "l"(*reinterpret_cast<const unsigned long long *>(&b)));
-    return *reinterpret_cast<const float2 *>(&d);
-}
-// a b - c d
-__device__ __forceinline__ float2 dif2(float2 a, float2 b, float2 c, float2 d) { return sub2(mul2(a, b), mul2(c, d)); }
-
 // Horn's adjugate column for one of the two pairs (h = 0: .x, 1: .y): the column of the
 // largest diagonal entry, and whether that entry clears tol * lam^3.
 __device__ __forceinline__ bool horn_pick(const float (&d)[10], float lam, float tol, float q[4])

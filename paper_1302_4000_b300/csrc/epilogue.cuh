@@ -23,6 +23,23 @@
 #include <cuda_runtime.h>
 
 
+// Paired FP32 arithmetic: two IEEE operations (round to nearest) per instruction on the halves
+// of a float2, so that one lane carries two independent pairs.
+__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<const unsigned long long *>(&a)), "l"(*reinterpret_cast<const unsigned long long *>(&b)));
+    return *reinterpret_cast<const float2 *>(&d);
+}
+// a b - c d
+__device__ __forceinline__ float2 dif2(float2 a, float2 b, float2 c, float2 d) { return sub2(mul2(a, b), mul2(c, d)); }
+
 // The nine 2x2 minors of m (row-major), mn = {a01, a02, a12, b01, b02, b12, c01, c02, c12}:
 // a.. from rows 1,2, b.. from rows 0,2, c.. from rows 0,1; the digits name the columns.
 template <typename T>
@@ -422,6 +439,68 @@ __device__ __forceinline__ float crmsd_fast_fp32(const float H[9], float Ga, flo
     const float e = (deg || !(dP > 0.f)) ? __int_as_float(0x7f800000) : kq * 5.9604645e-8f * scale;
     *err_c2 = pos ? e : 0.0f;
     return pos ? sqrtf(fmaxf(scale * (1.0f - s), 0.0f)) : 0.0f;
+}
+
+// crmsd_fast_fp32 for two pairs at once, one in each half of a float2: the same steps on the
+// paired FP32 instructions, the cubic's start, the reciprocals and the square root per pair.
+__device__ __forceinline__ float2 crmsd_fast_fp32x2(const float2 H[9], float2 Ga, float2 Gb, float invL,
+                                                   float2 *err_c2)
+{
+    const float2 Gs = add2(Ga, Gb);
+    const bool posx = Gs.x > 0.0f, posy = Gs.y > 0.0f;
+    const float2 nrm = make_float2(__fdividef(2.0f, posx ? Gs.x : 1.0f), __fdividef(2.0f, posy ? Gs.y : 1.0f));
+    float2 m[9], mn[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m[k] = mul2(H[k], nrm);
+    mn[0] = dif2(m[3], m[7], m[4], m[6]);
+    mn[1] = dif2(m[3], m[8], m[5], m[6]);
+    mn[2] = dif2(m[4], m[8], m[5], m[7]);
+    mn[3] = dif2(m[0], m[7], m[1], m[6]);
+    mn[4] = dif2(m[0], m[8], m[2], m[6]);
+    mn[5] = dif2(m[1], m[8], m[2], m[7]);
+    mn[6] = dif2(m[0], m[4], m[1], m[3]);
+    mn[7] = dif2(m[0], m[5], m[2], m[3]);
+    mn[8] = dif2(m[1], m[5], m[2], m[4]);
+    const float2 det = fma2(m[2], mn[0], sub2(mul2(m[0], mn[2]), mul2(m[1], mn[1])));
+    float2 I2 = mul2(mn[0], mn[0]), I1 = mul2(m[0], m[0]);
+#pragma unroll
+    for (int k = 1; k < 9; ++k) {
+        I2 = fma2(mn[k], mn[k], I2);
+        I1 = fma2(m[k], m[k], I1);
+    }
+    // the cubic's start per pair, then two Newton steps on the quartic (see quartic_newton_f)
+    float2 s = make_float2(sigma_cubic_f(I1.x, det.x, I2.x), sigma_cubic_f(I1.y, det.y, I2.y));
+    const float2 c2 = mul2(bc2(-2.f), I1), c1 = mul2(bc2(-8.f), det);
+    const float2 c0 = fma2(I1, I1, mul2(bc2(-4.f), I2));
+    float2 dP = bc2(0.f);
+    bool degx = false, degy = false;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const float2 sq = mul2(s, s);
+        const float2 P = fma2(add2(sq, c2), sq, fma2(c1, s, c0));
+        dP = fma2(fma2(bc2(4.f), sq, mul2(bc2(2.f), c2)), s, c1);
+        const float2 lim = mul2(mul2(bc2(8e-3f), sq), s);
+        if (dP.x > lim.x)
+            s.x -= __fdividef(P.x, dP.x);
+        else
+            degx = true;
+        if (dP.y > lim.y)
+            s.y -= __fdividef(P.y, dP.y);
+        else
+            degy = true;
+    }
+    // the error bound of crmsd_fast_fp32
+    const float2 scale = mul2(Gs, bc2(invL));
+    const float2 sq = mul2(s, s);
+    const float2 adet = make_float2(fabsf(det.x), fabsf(det.y));
+    const float2 Q = fma2(fma2(bc2(2.f), I1, sq), sq, fma2(mul2(bc2(8.f), adet), s, mul2(I1, I1)));
+    const float2 kq = make_float2(CLUSCO_KERR_A + CLUSCO_KERR_B * __fdividef(Q.x, dP.x),
+                                  CLUSCO_KERR_A + CLUSCO_KERR_B * __fdividef(Q.y, dP.y));
+    const float2 e = mul2(mul2(kq, bc2(5.9604645e-8f)), scale);
+    err_c2->x = posx ? ((degx || !(dP.x > 0.f)) ? __int_as_float(0x7f800000) : e.x) : 0.0f;
+    err_c2->y = posy ? ((degy || !(dP.y > 0.f)) ? __int_as_float(0x7f800000) : e.y) : 0.0f;
+    const float2 d = fma2(scale, sub2(bc2(0.f), s), scale);  // scale (1 - s)
+    return make_float2(posx ? sqrtf(fmaxf(d.x, 0.0f)) : 0.0f, posy ? sqrtf(fmaxf(d.y, 0.0f)) : 0.0f);
 }
 
 // crmsd_fast_fp32 and the rotation of the same pair together: one set of minors serves I2,

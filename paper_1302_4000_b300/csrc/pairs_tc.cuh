@@ -481,68 +481,19 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                     tmem_ld32(trow + 0, V);
                 }
             }
-            // one round at a time (a compact loop: the fast path's code size, not its latency,
-            // limits this kernel)
-#pragma unroll 1
-            for (int r = 0; r < 4; ++r) {
-                float blk[9];
-                switch (r) {  // warp-uniform; compile-time column offsets in each case
-                    case 0: assemble_block(V, 0, alpha, mloc, blk); break;
-                    case 1: assemble_block(V, 1, alpha, mloc, blk); break;
-                    case 2: assemble_block(V, 2, alpha, mloc, blk); break;
-                    default: assemble_block(V, 3, alpha, mloc, blk); break;
-                }
-                float sv, ev;
-                float m[9], R[9];
-                bool okR = false;
-                const float cv = ROT ? crmsd_fast_rot_fp32(blk, Ga, Gb[0], invL, &sv, &ev, m, R, &okR)
-                                     : crmsd_fast_fp32(blk, Ga, Gb[0], invL, &sv, &ev);
-                const int64_t b = b0 + 3 * r;
-                if (ROT) {
-                    if (pok[0]) {
-                        // blk's rows are axes alpha, alpha + 1, alpha + 2: axis ax is row (ax - alpha) mod 3
-                        const int64_t ridx = rowbase + b;
-                        bool done = okR;
-                        if (!okR) {
-                            const unsigned long long slot = atomicAdd(fix_count, 1ull);
-                            if ((int64_t)slot < fix_cap) {
-                                RotFix *f = fix + slot;
-                                f->idx = ridx;
-#pragma unroll
-                                for (int ax = 0; ax < 3; ++ax) {
-                                    const int src = (ax + 3 - alpha) % 3;
-#pragma unroll
-                                    for (int be = 0; be < 3; ++be)
-                                        f->m[3 * ax + be] = sel3(src, m[be], m[3 + be], m[6 + be]);
-                                }
-                            } else {
-                                rotation_robust(m, R);  // the list is full: solve it here
-                                done = true;
-                            }
-                        }
-                        if (done) {
-                            float Rn[9];
-#pragma unroll
-                            for (int ax = 0; ax < 3; ++ax) {
-                                const int src = (ax + 3 - alpha) % 3;
-#pragma unroll
-                                for (int be = 0; be < 3; ++be) Rn[3 * ax + be] = sel3(src, R[be], R[3 + be], R[6 + be]);
-                            }
-                            store_rot(rot + ridx * ROT_STRIDE, Rn);
-                        }
-                    }
-                }
-                const bool flagged = LAYOUT == TC_EXACT2 && pok[0] && !(ev <= 2.f * CLUSCO_TOL_FAST * cv);
-                const float cfin = (isnan(Ga) || isnan(Gb[0])) ? __int_as_float(0x7fc00000) : cv;
+            // one pair's result: flag it for the refinement, or store it (dense) / stage it (threshold)
+            auto emit = [&](float cv, float ev, bool pk, float gbh, int64_t b) {
+                const bool flagged = LAYOUT == TC_EXACT2 && pk && !(ev <= 2.f * CLUSCO_TOL_FAST * cv);
+                const float cfin = (isnan(Ga) || isnan(gbh)) ? __int_as_float(0x7fc00000) : cv;
                 if (flagged) {
                     // the bound fails: refine_flagged_kernel writes (or keeps) this pair's value
                     const int64_t li = rowbase + b;
                     atomicOr(flags + (li >> 5), 1u << (li & 31));
-                } else if (!SPARSE && pok[0]) {
+                } else if (!SPARSE && pk) {
                     out[rowbase + b] = cfin;
                 }
                 if (SPARSE) {
-                    const bool keep = pok[0] && !flagged && cfin < sink.tau;
+                    const bool keep = pk && !flagged && cfin < sink.tau;
                     const unsigned m = __ballot_sync(0xffffffffu, keep);
                     if (m) {
                         if (keep) {
@@ -562,10 +513,90 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                         }
                     }
                 }
+            };
+            if constexpr (!ROT) {
+                // two rounds at a time (rounds 2 d and 2 d + 1 in the two halves of the paired FP32
+                // instructions): two independent pairs per lane, half the instructions per pair
+#pragma unroll 1
+                for (int d = 0; d < 2; ++d) {
+                    float bx[9], by[9];
+                    if (d == 0) {  // warp-uniform; compile-time column offsets in each branch
+                        assemble_block(V, 0, alpha, mloc, bx);
+                        assemble_block(V, 1, alpha, mloc, by);
+                    } else {
+                        assemble_block(V, 2, alpha, mloc, bx);
+                        assemble_block(V, 3, alpha, mloc, by);
+                    }
+                    float2 Hm[9];
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    Gb[i] = Gb[i + 1];
-                    pok[i] = pok[i + 1];
+                    for (int e = 0; e < 9; ++e) Hm[e] = make_float2(bx[e], by[e]);
+                    float2 ev;
+                    const float2 cv = crmsd_fast_fp32x2(Hm, make_float2(Ga, Ga), make_float2(Gb[0], Gb[1]), invL, &ev);
+                    emit(cv.x, ev.x, pok[0], Gb[0], b0 + 6 * d);
+                    emit(cv.y, ev.y, pok[1], Gb[1], b0 + 6 * d + 3);
+                    Gb[0] = Gb[2];
+                    Gb[1] = Gb[3];
+                    pok[0] = pok[2];
+                    pok[1] = pok[3];
+                }
+            } else {
+                // with rotations: one round at a time (a compact loop: the fast path's code size, not
+                // its latency, limits this kernel)
+#pragma unroll 1
+                for (int r = 0; r < 4; ++r) {
+                    float blk[9];
+                    switch (r) {  // warp-uniform; compile-time column offsets in each case
+                        case 0: assemble_block(V, 0, alpha, mloc, blk); break;
+                        case 1: assemble_block(V, 1, alpha, mloc, blk); break;
+                        case 2: assemble_block(V, 2, alpha, mloc, blk); break;
+                        default: assemble_block(V, 3, alpha, mloc, blk); break;
+                    }
+                    float sv, ev;
+                    float m[9], R[9];
+                    bool okR = false;
+                    const float cv = ROT ? crmsd_fast_rot_fp32(blk, Ga, Gb[0], invL, &sv, &ev, m, R, &okR)
+                                         : crmsd_fast_fp32(blk, Ga, Gb[0], invL, &sv, &ev);
+                    const int64_t b = b0 + 3 * r;
+                    if (ROT) {
+                        if (pok[0]) {
+                            // blk's rows are axes alpha, alpha + 1, alpha + 2: axis ax is row (ax - alpha) mod 3
+                            const int64_t ridx = rowbase + b;
+                            bool done = okR;
+                            if (!okR) {
+                                const unsigned long long slot = atomicAdd(fix_count, 1ull);
+                                if ((int64_t)slot < fix_cap) {
+                                    RotFix *f = fix + slot;
+                                    f->idx = ridx;
+#pragma unroll
+                                    for (int ax = 0; ax < 3; ++ax) {
+                                        const int src = (ax + 3 - alpha) % 3;
+#pragma unroll
+                                        for (int be = 0; be < 3; ++be)
+                                            f->m[3 * ax + be] = sel3(src, m[be], m[3 + be], m[6 + be]);
+                                    }
+                                } else {
+                                    rotation_robust(m, R);  // the list is full: solve it here
+                                    done = true;
+                                }
+                            }
+                            if (done) {
+                                float Rn[9];
+#pragma unroll
+                                for (int ax = 0; ax < 3; ++ax) {
+                                    const int src = (ax + 3 - alpha) % 3;
+#pragma unroll
+                                    for (int be = 0; be < 3; ++be) Rn[3 * ax + be] = sel3(src, R[be], R[3 + be], R[6 + be]);
+                                }
+                                store_rot(rot + ridx * ROT_STRIDE, Rn);
+                            }
+                        }
+                    }
+                    emit(cv, ev, pok[0], Gb[0], b);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        Gb[i] = Gb[i + 1];
+                        pok[i] = pok[i + 1];
+                    }
                 }
             }
             // the accumulator buffer is drained: hand it back to the MMA warp
