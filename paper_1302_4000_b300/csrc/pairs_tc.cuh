@@ -96,17 +96,21 @@ struct TcArgs {
 
 constexpr uint32_t STAGE_BYTES_BF16 = 2 * 16384 + 2 * 8192;  // A_h, A_l, B_h, B_l
 constexpr uint32_t STAGE_BYTES_TF32 = 16384 + 8192;          // A, B
-// Persistent forward kernel: 1 CTA per SM, warp 0 TMA, warp 1 MMA, warps 2-9 epilogue.
-#ifndef CLUSCO_FW_EGROUPS
-#define CLUSCO_FW_EGROUPS 1  // epilogue warp groups of 8; with 2, each group owns one TMEM buffer
-#endif
-constexpr int FW_EGROUPS = CLUSCO_FW_EGROUPS;
-constexpr int FW_THREADS = 64 + 256 * FW_EGROUPS;
-constexpr int FW_STAGES = FW_EGROUPS == 2 ? 2 : 3;
+// Persistent forward kernel: 1 CTA per SM, warp 0 TMA, warp 1 MMA, then the epilogue warps:
+// with WIN 16 (four per TMEM lane quadrant, each the quadrant's 10 A models against a 5-model
+// window of the tile's 20 B models), else 8 (two per quadrant, 10-model halves).
+__host__ __device__ constexpr int fw_epi(bool win) { return win ? 16 : 8; }
+__host__ __device__ constexpr int fw_threads(bool win) { return 64 + 32 * fw_epi(win); }
+// the 5-model windows pay off while the epilogue alone bounds the kernel; with more atoms per
+// pair the MMA stream takes a larger share and the extra warps cost more than they give
+// (0.495 -> 0.434 ms at 5,000 x 300, 1.734 -> 1.770 ms at 8,192 x 500 for the forward call)
+constexpr int64_t FW_WIN_MAXLP = 384;
+constexpr int FW_MAXEPI = 16;
+constexpr int FW_STAGES = 3;
 // threshold mode: per epilogue warp, a staging buffer of 64 kept pairs (global index, value),
 // published 32 at a time with one atomic
 constexpr int FW_SBUF = 64;
-constexpr size_t FW_SMEM = 1024 + FW_STAGES * STAGE_BYTES_BF16 + 8 * FW_EGROUPS * FW_SBUF * 12;
+constexpr size_t FW_SMEM = 1024 + FW_STAGES * STAGE_BYTES_BF16 + FW_MAXEPI * FW_SBUF * 12;
 static_assert(FW_SMEM <= 227 * 1024, "shared memory per CTA");
 
 __host__ __device__ __forceinline__ int64_t tc_row_start(int64_t I, int64_t TB) { return I * TB - I * (I - 1); }
@@ -201,6 +205,46 @@ __device__ __forceinline__ void assemble_block(const float V[32], int r, int alp
     assemble_from_cand(cand, alpha, mloc, blk);
 }
 
+// The 15 TMEM columns of a 5-model window of one warp's 32-column half (window 0: columns
+// 0..14, window 1: 15..29 of the half, starting at taddr), one region (digit class) of the
+// accumulator: window 1 takes one column and the 16 from column 16.
+__device__ __forceinline__ void ld_window(uint32_t taddr, int hw, float (&w)[15])
+{
+    uint32_t u[16];
+    if (hw == 0) {
+        tmem_ld16_issue(taddr, u);
+        tmem_wait_ld();
+        tmem_pin16(u);
+#pragma unroll
+        for (int j = 0; j < 15; ++j) w[j] = __uint_as_float(u[j]);
+    } else {
+        uint32_t e = tmem_ld1_issue(taddr + 15);
+        tmem_ld16_issue(taddr + 16, u);
+        tmem_wait_ld();
+        asm volatile("" : "+r"(e));
+        tmem_pin16(u);
+        w[0] = __uint_as_float(e);
+#pragma unroll
+        for (int j = 0; j < 14; ++j) w[j + 1] = __uint_as_float(u[j]);
+    }
+}
+
+// assemble_block on a 5-model window (15 columns): round r holds window models 3 r + t; a lane
+// whose model falls past the window gets a zero block (and has no pair).
+template <int r>
+__device__ __forceinline__ void assemble_window(const float (&V)[15], int alpha, int mloc, float blk[9])
+{
+    float cand[3][3];
+#pragma unroll
+    for (int al = 0; al < 3; ++al)
+#pragma unroll
+        for (int be = 0; be < 3; ++be) {
+            const int j = 9 * r + 3 * al + be;
+            cand[al][be] = (j < 15) ? V[j] : 0.f;
+        }
+    assemble_from_cand(cand, alpha, mloc, blk);
+}
+
 // The rotation of a rare block whose quartic root is (nearly) double (out of line): Jacobi
 // sweeps for a rank-deficient block (I2 ~ 0, where an FP32 Sigma is least accurate), else
 // Horn's adjugate with the block's Sigma, and Jacobi sweeps where that is degenerate too.
@@ -266,8 +310,8 @@ __global__ void __launch_bounds__(256) rot_fixup_kernel(const RotFix *__restrict
 // ROT: also write each pair's optimal rotation R_ab (b onto a, natural axis order, row-major)
 // to rot[(idx - out_base) * ROT_STRIDE ..], computed as dSigma/dM from the fast path's Sigma (Horn's
 // key matrix near a double root); the adjoint reads it instead of recomputing the covariance.
-template <int LAYOUT, bool ROT, bool SPARSE = false>
-__global__ void __launch_bounds__(FW_THREADS, 1)
+template <int LAYOUT, bool ROT, bool SPARSE = false, bool WIN = false>
+__global__ void __launch_bounds__(fw_threads(WIN), 1)
     pairs_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                     const float *__restrict__ scales, const float *__restrict__ G32,
                     int64_t N, int L, int nkb, int64_t Rpad, int64_t TA, int64_t TB, int64_t tile0, int64_t ntiles,
@@ -279,7 +323,7 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
     __shared__ __align__(8) uint64_t full_bar[FW_STAGES];   // ring: K block landed
     __shared__ __align__(8) uint64_t empty_bar[FW_STAGES];  // ring: K block consumed by the MMAs
     __shared__ __align__(8) uint64_t tfull_bar[2];          // accumulator buffer holds a finished tile
-    __shared__ __align__(8) uint64_t tempty_bar[2];         // the epilogue has drained the buffer (8 arrivals)
+    __shared__ __align__(8) uint64_t tempty_bar[2];         // the epilogue has drained the buffer (one arrival per epilogue warp)
     __shared__ __align__(8) uint64_t done_bar;              // every MMA this CTA issued has completed
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
@@ -303,7 +347,7 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull_bar[b], 1);
-            mbar_init(&tempty_bar[b], 8);
+            mbar_init(&tempty_bar[b], fw_epi(WIN));
         }
         mbar_init(&done_bar, 1);
         abort_flag = 0;
@@ -386,19 +430,19 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
         }
         __syncwarp();
     } else {
-        // ================= epilogue warps 2.. (FW_EGROUPS groups of 8) =================
-        // group gp takes the CTA's tiles k = gp, gp + FW_EGROUPS, ...; within a group warp w
-        // reads TMEM lanes 32 (w % 4) .. + 31 (its lane quadrant) and column half g
+        // ================= epilogue warps 2.. =================
+        // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its lane quadrant, the 10 A models of its
+        // rows); with rotations it takes column half g (10 B models), without them the 5-model
+        // window hw of that half (columns 32 g + 15 hw .. + 14)
         const int ew = warp - 2;
-        const int gp = ew >> 3;
-        const int sp = warp & 3, g = (ew & 7) >> 2;
+        const int sp = warp & 3, g = (ew >> 2) & 1, hw = WIN ? (ew >> 3) : 0;
         const int mloc = lane / 3, alpha = lane - 3 * (lane / 3);
         const float invL = 1.f / (float)L;
         float *const out = sink.out;
         const int64_t out_base = sink.out_base;
         // threshold mode: this warp's staging buffer of kept pairs (fill is warp-uniform)
         long long *sidx = reinterpret_cast<long long *>(smem + FW_STAGES * STAGE_BYTES_BF16) + ew * FW_SBUF;
-        float *sval = reinterpret_cast<float *>(smem + FW_STAGES * STAGE_BYTES_BF16 + 8 * 8 * FW_EGROUPS * FW_SBUF) +
+        float *sval = reinterpret_cast<float *>(smem + FW_STAGES * STAGE_BYTES_BF16 + 8 * FW_MAXEPI * FW_SBUF) +
                       ew * FW_SBUF;
         int fill = 0;
         auto publish = [&](int n) {  // the first n staged pairs to the list, one atomic
@@ -413,12 +457,121 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
             __syncwarp();
         };
 
-        const int64_t gstep = (int64_t)FW_EGROUPS * gridDim.x;
-        int64_t k = gp;
+        // one pair's result (li: its condensed index relative to the output's base): flag it for the
+        // refinement, or store it (dense) / stage it (threshold)
+        auto emit_pair = [&](float cv, float ev, bool pk, float Ga, float gbh, int64_t li) {
+            const bool flagged = LAYOUT == TC_EXACT2 && pk && !(ev <= 2.f * CLUSCO_TOL_FAST * cv);
+            const float cfin = (isnan(Ga) || isnan(gbh)) ? __int_as_float(0x7fc00000) : cv;
+            if (flagged) {
+                // the bound fails: refine_flagged_kernel writes (or keeps) this pair's value
+                atomicOr(flags + (li >> 5), 1u << (li & 31));
+            } else if (!SPARSE && pk) {
+                out[li] = cfin;
+            }
+            if (SPARSE) {
+                const bool keep = pk && !flagged && cfin < sink.tau;
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                if (m) {
+                    if (keep) {
+                        const int my = fill + __popc(m & ((1u << lane) - 1u));
+                        sidx[my] = li + out_base;
+                        sval[my] = cfin;
+                    }
+                    fill += __popc(m);
+                    if (fill >= 32) {
+                        publish(32);
+                        if (lane < fill - 32) {
+                            sidx[lane] = sidx[32 + lane];
+                            sval[lane] = sval[32 + lane];
+                        }
+                        __syncwarp();
+                        fill -= 32;
+                    }
+                }
+            }
+        };
+
+        const int64_t gstep = gridDim.x;
+        int64_t k = 0;
         int64_t I, J;
-        tc_decode(tile0 + blockIdx.x + (int64_t)gp * gridDim.x, TB, TA, &I, &J);
-        for (int64_t t = blockIdx.x + (int64_t)gp * gridDim.x; t < ntiles;
-             t += gstep, k += FW_EGROUPS, tc_advance(I, J, gstep, TB, TA)) {
+        tc_decode(tile0 + blockIdx.x, TB, TA, &I, &J);
+        for (int64_t t = blockIdx.x; t < ntiles; t += gstep, ++k, tc_advance(I, J, gstep, TB, TA)) {
+            if constexpr (WIN) {
+                // the window: B models J TC_MB + 10 g + 5 hw + t (rounds 0, 1: t = alpha, 3 + alpha)
+                const int64_t a = I * TC_MA + 10 * sp + mloc;
+                const int64_t b0 = J * TC_MB + 10 * g + 5 * hw + alpha;
+                const bool lane_ok = lane < 30 && a < N && a >= row_begin && a < row_end;
+                const int64_t rowbase = a * N - a * (a + 1) / 2 - a - 1 - out_base;  // condensed index - b
+                float srow0 = 1.f, Ga = 0.f;
+                if (lane_ok) {
+                    srow0 = scales[a * 3 + alpha];
+                    Ga = G32[a];
+                }
+                bool pok[2];
+                float Gb[2];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int64_t b = b0 + 3 * r;
+                    pok[r] = lane_ok && (3 * r + alpha) < 5 && b < N && a < b;
+                    Gb[r] = pok[r] ? __ldg(G32 + b) : 0.f;
+                }
+                const int buf = (int)(k & 1);
+                const bool okw = mbar_wait_sleep(&tfull_bar[buf], (uint32_t)((k >> 1) & 1));
+                if (__any_sync(0xffffffffu, !okw || *abort_v)) {
+                    atomicExch(&abort_flag, 1);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tcol = tmem + 256u * buf + ((uint32_t)(32 * sp) << 16) + (uint32_t)(32 * g);
+                float V[15];
+                {
+                    float w[15];
+                    if (LAYOUT == TC_EXACT2) {
+                        ld_window(tcol + 0, hw, w);
+#pragma unroll
+                        for (int j = 0; j < 15; ++j) V[j] = 65536.f * w[j];
+                        ld_window(tcol + 64, hw, w);
+#pragma unroll
+                        for (int j = 0; j < 15; ++j) V[j] = fmaf(256.f, w[j], V[j]);
+                        ld_window(tcol + 128, hw, w);
+#pragma unroll
+                        for (int j = 0; j < 15; ++j) V[j] = fmaf(256.f, w[j], V[j]);
+                        ld_window(tcol + 192, hw, w);
+#pragma unroll
+                        for (int j = 0; j < 15; ++j) V[j] += w[j];
+                        // column j of the window is (model J TC_MB + 10 g + 5 hw + j / 3, axis j % 3)
+                        const float cs = (lane < 15) ? __ldg(scales + (J * TC_MB + 10 * g + 5 * hw) * 3 + lane) : 1.f;
+#pragma unroll
+                        for (int j = 0; j < 15; ++j) V[j] *= srow0 * __shfl_sync(0xffffffffu, cs, j);
+                    } else if (LAYOUT == TC_BF16X3) {
+                        ld_window(tcol + 0, hw, V);
+                        ld_window(tcol + 64, hw, w);
+#pragma unroll
+                        for (int j = 0; j < 15; ++j) V[j] += w[j];
+                        ld_window(tcol + 128, hw, w);
+#pragma unroll
+                        for (int j = 0; j < 15; ++j) V[j] += w[j];
+                    } else {
+                        ld_window(tcol + 0, hw, V);
+                    }
+                }
+                // the accumulator buffer is read: hand it back to the MMA warp
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty_bar[buf]);
+                // rounds 0 and 1 of the window in the two halves of the paired FP32 instructions
+                float bx[9], by[9];
+                assemble_window<0>(V, alpha, mloc, bx);
+                assemble_window<1>(V, alpha, mloc, by);
+                float2 Hm[9];
+#pragma unroll
+                for (int e = 0; e < 9; ++e) Hm[e] = make_float2(bx[e], by[e]);
+                float2 ev;
+                const float2 cv = crmsd_fast_fp32x2(Hm, make_float2(Ga, Ga), make_float2(Gb[0], Gb[1]), invL, &ev);
+                emit_pair(cv.x, ev.x, pok[0], Ga, Gb[0], rowbase + b0);
+                emit_pair(cv.y, ev.y, pok[1], Ga, Gb[1], rowbase + b0 + 3);
+                continue;
+            }
             // lane (mloc, alpha): row = axis alpha of A model a; in round r its pair is (a, b0 + 3 r)
             const int64_t a = I * TC_MA + 10 * sp + mloc;
             const int64_t b0 = J * TC_MB + 10 * g + alpha;
@@ -481,38 +634,8 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                     tmem_ld32(trow + 0, V);
                 }
             }
-            // one pair's result: flag it for the refinement, or store it (dense) / stage it (threshold)
             auto emit = [&](float cv, float ev, bool pk, float gbh, int64_t b) {
-                const bool flagged = LAYOUT == TC_EXACT2 && pk && !(ev <= 2.f * CLUSCO_TOL_FAST * cv);
-                const float cfin = (isnan(Ga) || isnan(gbh)) ? __int_as_float(0x7fc00000) : cv;
-                if (flagged) {
-                    // the bound fails: refine_flagged_kernel writes (or keeps) this pair's value
-                    const int64_t li = rowbase + b;
-                    atomicOr(flags + (li >> 5), 1u << (li & 31));
-                } else if (!SPARSE && pk) {
-                    out[rowbase + b] = cfin;
-                }
-                if (SPARSE) {
-                    const bool keep = pk && !flagged && cfin < sink.tau;
-                    const unsigned m = __ballot_sync(0xffffffffu, keep);
-                    if (m) {
-                        if (keep) {
-                            const int my = fill + __popc(m & ((1u << lane) - 1u));
-                            sidx[my] = rowbase + b + out_base;
-                            sval[my] = cfin;
-                        }
-                        fill += __popc(m);
-                        if (fill >= 32) {
-                            publish(32);
-                            if (lane < fill - 32) {
-                                sidx[lane] = sidx[32 + lane];
-                                sval[lane] = sval[32 + lane];
-                            }
-                            __syncwarp();
-                            fill -= 32;
-                        }
-                    }
-                }
+                emit_pair(cv, ev, pk, Ga, gbh, rowbase + b);
             };
             if constexpr (!ROT) {
                 // two rounds at a time (rounds 2 d and 2 d + 1 in the two halves of the paired FP32
@@ -874,8 +997,10 @@ inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const bool win = !a.rot && a.Lp <= FW_WIN_MAXLP;
     auto kern = a.rot ? pairs_tc_kernel<LAYOUT, true, false>
-                      : (a.list ? pairs_tc_kernel<LAYOUT, false, true> : pairs_tc_kernel<LAYOUT, false, false>);
+                      : (a.list ? (win ? pairs_tc_kernel<LAYOUT, false, true, true> : pairs_tc_kernel<LAYOUT, false, true>)
+                                : (win ? pairs_tc_kernel<LAYOUT, false, false, true> : pairs_tc_kernel<LAYOUT, false, false>));
     PairSink sink;
     sink.out = a.out;
     sink.out_base = a.out_base;
@@ -914,7 +1039,7 @@ inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
             return CLUSCO_ECUDA;
         }
     }
-    kern<<<grid, FW_THREADS, FW_SMEM, st>>>(mA, mB, a.scales, a.G32, a.N, (int)a.L, nkb, a.Rpad, TA, TB, t0, nt,
+    kern<<<grid, fw_threads(win), FW_SMEM, st>>>(mA, mB, a.scales, a.G32, a.N, (int)a.L, nkb, a.Rpad, TA, TB, t0, nt,
                                              a.row_begin, a.row_end, sink, a.rot, a.fix, a.fix_count, a.fix_cap,
                                              a.flags);
     e = cudaGetLastError();
