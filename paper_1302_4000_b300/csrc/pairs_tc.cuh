@@ -634,6 +634,10 @@ __global__ void __launch_bounds__(fw_threads(WIN), 1)
                     tmem_ld32(trow + 0, V);
                 }
             }
+            // the accumulator buffer is read: hand it back to the MMA warp
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty_bar[buf]);
             auto emit = [&](float cv, float ev, bool pk, float gbh, int64_t b) {
                 emit_pair(cv, ev, pk, Ga, gbh, rowbase + b);
             };
@@ -722,10 +726,6 @@ __global__ void __launch_bounds__(fw_threads(WIN), 1)
                     }
                 }
             }
-            // the accumulator buffer is drained: hand it back to the MMA warp
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty_bar[buf]);
         }
         if (SPARSE && fill > 0) publish(fill);
     }
