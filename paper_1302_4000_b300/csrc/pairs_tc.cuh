@@ -858,12 +858,15 @@ __device__ __forceinline__ unsigned dp4a_uu(unsigned a, unsigned b, unsigned c)
 // so warps take single mask words (32 pairs) round-robin (loading 32 of their words at a
 // time); lanes split the atom quads of each pair, and pairs are batched 32 at a time so that
 // every FP64 instruction runs on 32 lanes.
-__global__ void __launch_bounds__(256, 2) refine_flagged_kernel(const int8_t *__restrict__ hplane,
-                                                                const uint8_t *__restrict__ lplane,
-                                                                const float *__restrict__ scales,
-                                                                const double *__restrict__ G64, int64_t N, int L,
-                                                                int Lp, int64_t npairs, int64_t out_base,
-                                                                const uint32_t *__restrict__ flags, PairSink sink)
+// MINB CTAs per SM: 2 keeps the FP64 Newton in registers; 3 (a few spills) hides more of the
+// gather latency, which pays once the flagged set is large (many pairs of long chains).
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) refine_flagged_kernel(const int8_t *__restrict__ hplane,
+                                                                   const uint8_t *__restrict__ lplane,
+                                                                   const float *__restrict__ scales,
+                                                                   const double *__restrict__ G64, int64_t N, int L,
+                                                                   int Lp, int64_t npairs, int64_t out_base,
+                                                                   const uint32_t *__restrict__ flags, PairSink sink)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -1045,11 +1048,16 @@ inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
     e = cudaGetLastError();
     prof_mark(PROF_PAIRS, st);
     if (e == cudaSuccess && LAYOUT == TC_EXACT2) {
-        // one wave (two CTAs per SM by the launch bound): with the few flagged pairs spread over
-        // many warps, a second wave only added its latency
-        refine_flagged_kernel<<<2 * (sms > 0 ? sms : 148), 256, 0, st>>>(a.hplane, a.lplane, a.scales, a.G64, a.N,
-                                                                          (int)a.L, (int)a.Lp, npairs, a.out_base,
-                                                                          a.flags, sink);
+        // one wave (MINB CTAs per SM by the launch bound): with the few flagged pairs spread over
+        // many warps, a second wave only added its latency. Three per SM from 2^33 pair-atoms up
+        // (8,192 x 500: 1.72 -> 1.68 ms for the whole forward), two below (5,000 x 300 lost 0.01 ms).
+        const int nsm = sms > 0 ? sms : 148;
+        if ((double)npairs * (double)a.Lp >= 8589934592.0)
+            refine_flagged_kernel<3><<<3 * nsm, 256, 0, st>>>(a.hplane, a.lplane, a.scales, a.G64, a.N, (int)a.L,
+                                                               (int)a.Lp, npairs, a.out_base, a.flags, sink);
+        else
+            refine_flagged_kernel<2><<<2 * nsm, 256, 0, st>>>(a.hplane, a.lplane, a.scales, a.G64, a.N, (int)a.L,
+                                                               (int)a.Lp, npairs, a.out_base, a.flags, sink);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && a.rot) {
