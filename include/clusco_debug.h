@@ -3,7 +3,8 @@
  * The debug library is the production source compiled with -DCLUSCO_DEBUG_HOOKS and a short
  * device wait limit (-DCLUSCO_WAIT_NS=200000000, 0.2 s); the production library (libclusco.so)
  * exports none of this. The hooks let tests reach two failure paths without faulting or hanging
- * a GPU: a bounded wait that gives up, and a near-duplicate queue that overflows.
+ * a GPU: a bounded wait that gives up, a near-duplicate queue that overflows, and lists of
+ * flagged pairs that overflow into the flag mask.
  */
 #ifndef CLUSCO_DEBUG_H
 #define CLUSCO_DEBUG_H
@@ -28,6 +29,13 @@ extern "C" {
  *     the default capacity, min(P, 2^22).
  * Returns CLUSCO_OK, CLUSCO_EINVAL (nd_cap < 0) or CLUSCO_ECUDA. */
 int clusco_debug_hooks(int skip_arrive, int64_t nd_cap);
+
+/* Capacity of each epilogue warp's list of flagged pairs in the exact-digit forward, for the
+ * calls that follow (process-wide): cap > 0 caps the lists at cap entries, so that the pairs
+ * past them take the refinement's mask path (results are unchanged); 0 restores the default
+ * (1/32 of the pairs, at least 2^16 entries, over all lists).
+ * Returns CLUSCO_OK or CLUSCO_EINVAL (cap < 0). */
+int clusco_debug_flag_list_cap(int cap);
 
 #ifdef __cplusplus
 }

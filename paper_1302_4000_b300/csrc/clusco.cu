@@ -86,8 +86,10 @@ struct PairsWs {
     int64_t Lp = 0, Npad = 0, Rpad = 0;
     // EXACT2: the 16-bit coordinates and the mask of pairs the fast path flags
     int8_t *hplane = nullptr;
-    uint8_t *lplane = nullptr;
+    int8_t *lplane = nullptr;
     uint32_t *flags = nullptr;
+    int2 *flist = nullptr;
+    int64_t flist_entries = 0;
     // rotation entry point only: the deferred-rotation list
     RotFix *fix = nullptr;
     unsigned long long *fix_count = nullptr;
@@ -132,8 +134,10 @@ PairsWs carve_pairs(void *base, int64_t N, int64_t L, int form, bool with_rot = 
         if (form == CLUSCO_FORM_BF16_EXACT2) {
             const int64_t P = N * (N - 1) / 2;
             w.hplane = c.take<int8_t>((size_t)(w.Rpad * w.Lp));
-            w.lplane = c.take<uint8_t>((size_t)(w.Rpad * w.Lp));
-            w.flags = c.take<uint32_t>((size_t)((P + 31) / 32));
+            w.lplane = c.take<int8_t>((size_t)(w.Rpad * w.Lp));
+            w.flags = c.take<uint32_t>((size_t)(flag_list_offset(P) + FL_MAXSLOTS));  // mask, list counts
+            w.flist_entries = flag_list_entries(P);
+            w.flist = c.take<int2>((size_t)w.flist_entries);
         }
         if (with_rot) {
             w.fix_cap = rotfix_cap(N);
@@ -293,6 +297,8 @@ int allpairs_impl(const float *coords, int64_t N, int64_t L, int64_t row_begin, 
         a.fix_count = w.fix_count;
         a.fix_cap = w.fix_cap;
         a.flags = w.flags;
+        a.flist = w.flist;
+        a.flist_entries = w.flist_entries;
         a.hplane = w.hplane;
         a.lplane = w.lplane;
         if (thr) {
@@ -701,6 +707,14 @@ int clusco_debug_hooks(int skip_arrive, int64_t nd_cap)
     const int v = skip_arrive ? 1 : 0;
     CUDA_TRY(cudaMemcpyToSymbol(g_debug_skip_arrive, &v, sizeof v));
     debug_nd_cap() = nd_cap;
+    return CLUSCO_OK;
+}
+
+int clusco_debug_flag_list_cap(int cap)
+{
+    g_last_error.clear();
+    if (cap < 0) return fail(CLUSCO_EINVAL, "cap=%d must be >= 0", cap);
+    debug_fl_cap() = cap;
     return CLUSCO_OK;
 }
 #endif

@@ -18,11 +18,18 @@ __device__ __forceinline__ void set_status(unsigned int bit) { atomicOr(&g_clusc
 // Test hooks, compiled into the separate debug library only (the production library has none):
 // g_debug_skip_arrive makes the forward's TMA producer of CTA 0 skip its first stage (no arrive,
 // no copy), so that the bounded waits give up and the status word reports the timeout;
-// debug_nd_cap() shrinks the adjoints' near-duplicate queues so that an overflow can be provoked.
+// debug_nd_cap() shrinks the adjoints' near-duplicate queues so that an overflow can be provoked;
+// debug_fl_cap() shrinks the exact-digit forward's per-warp lists of flagged pairs, so that the
+// refinement's path for the pairs past a list (the flag mask) can be exercised.
 __device__ int g_debug_skip_arrive;
 inline int64_t &debug_nd_cap()
 {
     static int64_t v = 0;
+    return v;
+}
+inline int &debug_fl_cap()
+{
+    static int v = 0;
     return v;
 }
 #endif

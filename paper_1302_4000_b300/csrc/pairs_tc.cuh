@@ -81,9 +81,12 @@ struct TcArgs {
     RotFix *fix = nullptr;            // deferred rotations (see RotFix)
     unsigned long long *fix_count = nullptr;
     int64_t fix_cap = 0;
-    uint32_t *flags = nullptr;  // EXACT2: one bit per output pair, set where the FP32 bound fails
+    uint32_t *flags = nullptr;  // EXACT2: one bit per output pair (flagged pairs past a warp's list),
+                                // then FL_MAXSLOTS list counts (flag_list_offset)
+    int2 *flist = nullptr;      // EXACT2: the flagged pairs (a, b), one list per epilogue warp
+    int64_t flist_entries = 0;  // capacity of flist over all warps
     int8_t *hplane = nullptr;   // EXACT2: the 16-bit fixed-point coordinates as bytes (h, l), for
-    uint8_t *lplane = nullptr;  // the refinement of flagged pairs
+    int8_t *lplane = nullptr;   // the refinement of flagged pairs
     // threshold mode (list != nullptr; no rotations): the pairs with c < tau instead of out
     long long *list = nullptr;
     float *vals = nullptr;
@@ -317,7 +320,8 @@ __global__ void __launch_bounds__(fw_threads(WIN), 1)
                     int64_t N, int L, int nkb, int64_t Rpad, int64_t TA, int64_t TB, int64_t tile0, int64_t ntiles,
                     int64_t row_begin, int64_t row_end, PairSink sink,
                     float *__restrict__ rot, RotFix *__restrict__ fix, unsigned long long *__restrict__ fix_count,
-                    int64_t fix_cap, uint32_t *__restrict__ flags)
+                    int64_t fix_cap, uint32_t *__restrict__ flags, int2 *__restrict__ flist,
+                    unsigned *__restrict__ fl_cnt, int fl_cap)
 {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[FW_STAGES];   // ring: K block landed
@@ -445,6 +449,10 @@ __global__ void __launch_bounds__(fw_threads(WIN), 1)
         float *sval = reinterpret_cast<float *>(smem + FW_STAGES * STAGE_BYTES_BF16 + 8 * FW_MAXEPI * FW_SBUF) +
                       ew * FW_SBUF;
         int fill = 0;
+        // EXACT2: this warp's list of flagged pairs (a, b); the ones past its capacity set their
+        // mask bit instead
+        int nfl = 0;
+        int2 *const myfl = flist + ((int64_t)blockIdx.x * FW_MAXEPI + ew) * fl_cap;
         auto publish = [&](int n) {  // the first n staged pairs to the list, one atomic
             __syncwarp();
             unsigned long long base = 0;
@@ -459,15 +467,24 @@ __global__ void __launch_bounds__(fw_threads(WIN), 1)
 
         // one pair's result (li: its condensed index relative to the output's base): flag it for the
         // refinement, or store it (dense) / stage it (threshold)
-        auto emit_pair = [&](float cv, float ev, bool pk, float Ga, float gbh, int64_t li) {
+        auto emit_pair = [&](float cv, float ev, bool pk, float Ga, float gbh, int64_t li, int64_t ia, int64_t ib) {
             const bool flagged = LAYOUT == TC_EXACT2 && pk && !(ev <= 2.f * CLUSCO_TOL_FAST * cv);
             const float cfin = (isnan(Ga) || isnan(gbh)) ? __int_as_float(0x7fc00000) : cv;
-            if (flagged) {
+            if constexpr (LAYOUT == TC_EXACT2) {
                 // the bound fails: refine_flagged_kernel writes (or keeps) this pair's value
-                atomicOr(flags + (li >> 5), 1u << (li & 31));
-            } else if (!SPARSE && pk) {
-                out[li] = cfin;
+                const unsigned fm = __ballot_sync(0xffffffffu, flagged);
+                if (fm) {
+                    const int pos = nfl + __popc(fm & ((1u << lane) - 1u));
+                    if (flagged) {
+                        if (pos < fl_cap)
+                            myfl[pos] = make_int2((int)ia, (int)ib);
+                        else
+                            atomicOr(flags + (li >> 5), 1u << (li & 31));
+                    }
+                    nfl += __popc(fm);
+                }
             }
+            if (!flagged && !SPARSE && pk) out[li] = cfin;
             if (SPARSE) {
                 const bool keep = pk && !flagged && cfin < sink.tau;
                 const unsigned m = __ballot_sync(0xffffffffu, keep);
@@ -568,8 +585,8 @@ __global__ void __launch_bounds__(fw_threads(WIN), 1)
                 for (int e = 0; e < 9; ++e) Hm[e] = make_float2(bx[e], by[e]);
                 float2 ev;
                 const float2 cv = crmsd_fast_fp32x2(Hm, make_float2(Ga, Ga), make_float2(Gb[0], Gb[1]), invL, &ev);
-                emit_pair(cv.x, ev.x, pok[0], Ga, Gb[0], rowbase + b0);
-                emit_pair(cv.y, ev.y, pok[1], Ga, Gb[1], rowbase + b0 + 3);
+                emit_pair(cv.x, ev.x, pok[0], Ga, Gb[0], rowbase + b0, a, b0);
+                emit_pair(cv.y, ev.y, pok[1], Ga, Gb[1], rowbase + b0 + 3, a, b0 + 3);
                 continue;
             }
             // lane (mloc, alpha): row = axis alpha of A model a; in round r its pair is (a, b0 + 3 r)
@@ -639,7 +656,7 @@ __global__ void __launch_bounds__(fw_threads(WIN), 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty_bar[buf]);
             auto emit = [&](float cv, float ev, bool pk, float gbh, int64_t b) {
-                emit_pair(cv, ev, pk, Ga, gbh, rowbase + b);
+                emit_pair(cv, ev, pk, Ga, gbh, rowbase + b, a, b);
             };
             if constexpr (!ROT) {
                 // two rounds at a time (rounds 2 d and 2 d + 1 in the two halves of the paired FP32
@@ -728,6 +745,7 @@ __global__ void __launch_bounds__(fw_threads(WIN), 1)
             }
         }
         if (SPARSE && fill > 0) publish(fill);
+        if (LAYOUT == TC_EXACT2 && lane == 0) fl_cnt[blockIdx.x * FW_MAXEPI + ew] = (unsigned)nfl;
     }
     tc_fence_before();
     __syncthreads();
@@ -820,69 +838,68 @@ __device__ __forceinline__ int64_t condensed_row(int64_t idx, int64_t N)
     return a;
 }
 
-// 4-way byte dot products with a 32-bit accumulator: signed x signed, signed x unsigned,
-// unsigned x signed, unsigned x unsigned bytes.
+// 4-way signed byte dot product with a 32-bit accumulator.
 __device__ __forceinline__ int dp4a_ss(int a, int b, int c)
 {
     int d;
     asm("dp4a.s32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
     return d;
 }
-__device__ __forceinline__ int dp4a_su(int a, int b, int c)
-{
-    int d;
-    asm("dp4a.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-    return d;
-}
-__device__ __forceinline__ int dp4a_us(int a, int b, int c)
-{
-    int d;
-    asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-    return d;
-}
-__device__ __forceinline__ unsigned dp4a_uu(unsigned a, unsigned b, unsigned c)
-{
-    unsigned d;
-    asm("dp4a.u32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-    return d;
-}
 
-// The pairs the fast path flagged (their bits set in flags, indices relative to out_base):
-// each one's covariance recomputed exactly from the 16-bit fixed-point coordinates
-// n = 256 h + l (byte planes, h signed and l unsigned; rows in the tensor-core layout, zero
-// past L) as three digit classes of nine sums, hh, hl + lh and ll, each an exact 32-bit
-// integer (4-way byte dot products over atom quads: per atom |hh| <= 2^14, |hl + lh| < 2^16,
-// ll < 2^16, so over L <= 1024 atoms every class stays below 2^26), then
-// H = 65536 hh + 256 (hl + lh) + ll in int64, scaled to FP64, and cRMSD by FP64 Newton from an
-// FP32 start (crmsd_refine_newton_fp64). Flagged pairs cluster (close decoys of one native),
-// so warps take single mask words (32 pairs) round-robin (loading 32 of their words at a
-// time); lanes split the atom quads of each pair, and pairs are batched 32 at a time so that
-// every FP64 instruction runs on 32 lanes.
-// MINB CTAs per SM: 2 keeps the FP64 Newton in registers; 3 (a few spills) hides more of the
-// gather latency, which pays once the flagged set is large (many pairs of long chains).
+// The flagged-pair lists of the exact-digit forward: one per epilogue warp slot (CTA x
+// FW_MAXEPI + warp), FL_MAXSLOTS slots at most, each of capacity flist_entries / slots; their
+// counts follow the flag mask (flag_list_offset words from its start, 16-byte aligned).
+constexpr int FL_MAXSLOTS = 4096;
+inline int64_t flag_list_offset(int64_t npairs) { return ((npairs + 31) / 32 + 3) / 4 * 4; }
+// list entries for a pair range: 1/32 of the pairs (the bench ensembles flag under 1 %), at
+// least 2^16
+inline int64_t flag_list_entries(int64_t npairs) { return std::max<int64_t>(npairs / 32, (int64_t)1 << 16); }
+
+// Minimum flagged pairs per refinement warp: fewer warps with fuller batches where the flagged
+// set is small (each batch costs its FP64 instructions whatever its fill).
+constexpr int REFINE_MIN_PAIRS = 16;
+
+// The pairs the fast path flagged: each one's covariance recomputed exactly from the 16-bit
+// fixed-point coordinates n = 256 h + l (byte planes, h and l signed; rows in the tensor-core
+// layout, zero past L) as three digit classes of nine sums, hh, hl + lh and ll, each an exact
+// 32-bit integer (signed 4-way byte dot products over atom quads: per atom |hh|, |ll| <= 2^14
+// and |hl + lh| <= 2^15, so over L <= 1024 atoms every class stays below 2^25 and each is
+// reduced across the warp on its own), then H = 65536 hh + 256 (hl + lh) + ll in int64, scaled
+// to FP64, and cRMSD by FP64 Newton from an FP32 start (crmsd_refine_newton_fp64). Lanes split
+// the atoms of each pair, and pairs are batched 32 at a time so that every FP64 instruction runs
+// on 32 lanes. The flagged pairs come as the forward's per-warp lists (fl_cnt[s] pairs in slot
+// s, the ones past fl_cap in the mask): each block scans the list counts; with F listed pairs,
+// warp g of the W' = min(W, ceil(F / REFINE_MIN_PAIRS)) working warps (interleaved across the
+// blocks, so across the SMs) takes ranks [g F / W', (g + 1) F / W') of the concatenated lists,
+// so the work is balanced however the flagged pairs cluster. Pairs past a list's capacity
+// (their mask bits) are taken after it, mask words round-robin over all warps.
 template <int MINB>
 __global__ void __launch_bounds__(256, MINB) refine_flagged_kernel(const int8_t *__restrict__ hplane,
-                                                                   const uint8_t *__restrict__ lplane,
+                                                                   const int8_t *__restrict__ lplane,
                                                                    const float *__restrict__ scales,
                                                                    const double *__restrict__ G64, int64_t N, int L,
                                                                    int Lp, int64_t npairs, int64_t out_base,
-                                                                   const uint32_t *__restrict__ flags, PairSink sink)
+                                                                   const uint32_t *__restrict__ flags,
+                                                                   const int2 *__restrict__ flist,
+                                                                   const unsigned *__restrict__ fl_cnt, int nslots,
+                                                                   int fl_cap, PairSink sink)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int64_t nwords = (npairs + 31) / 32;
-    const int nq = (L + 3) / 4;  // atom quads (bytes past L are zero)
-    const int rq = Lp / 4;       // quads per row
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const double invL = 1.0 / (double)L;
-    // this lane's batch slot: the pair's exact integer sums, its models and output index; the
-    // FP64 work waits for the batch, where every FP64 instruction serves 32 pairs
-    long long v[9];
-    int64_t sa = 0, sb = 0, oidx = -1;
+    // the warp's batch: slot j holds the j-th pair's models (lst) and its three exact class
+    // sums per covariance entry (sv: hh, then hl + lh, then ll); the FP64 work waits for the
+    // batch, where every FP64 instruction serves 32 pairs
+    __shared__ int2 lst[8][32];
+    __shared__ int sv[8][27][32];
+    __shared__ unsigned spre[FL_MAXSLOTS + 1];
     int cnt = 0;
     auto flush = [&]() {
+        __syncwarp();
         float c = 0.f;
+        int64_t oidx = 0;
         if (lane < cnt) {
+            const int64_t sa = lst[wib][lane].x, sb = lst[wib][lane].y;
+            oidx = condensed_idx(sa, sb, N) - out_base;
             float s3a[3], s3b[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -897,89 +914,154 @@ __global__ void __launch_bounds__(256, MINB) refine_flagged_kernel(const int8_t 
             double H[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
-                mf[k] = (float)v[k] * (s3a[k / 3] * s3b[k % 3]) * nrmf;
-                H[k] = (double)v[k] * ((double)s3a[k / 3] * (double)s3b[k % 3]);
+                const long long vk = 65536LL * sv[wib][k][lane] + 256LL * sv[wib][9 + k][lane] + sv[wib][18 + k][lane];
+                mf[k] = (float)vk * (s3a[k / 3] * s3b[k % 3]) * nrmf;
+                H[k] = (double)vk * ((double)s3a[k / 3] * (double)s3b[k % 3]);
             }
             c = crmsd_refine_newton_fp64(H, Ga, Gb, invL, sigma_hat_f32(mf));
             if (!sink.list) sink.out[oidx] = c;
         }
         if (sink.list) sink_append_warp(sink, lane < cnt && c < sink.tau, oidx + out_base, c);
+        __syncwarp();
         cnt = 0;
     };
-    // one flagged pair: its nine exact sums reduced across the warp into lane cnt's slot
-    auto pair = [&](int64_t li) {
-        const int64_t idx = li + out_base;
-        const int64_t a = condensed_row(idx, N);
-        const int64_t b = idx - condensed_idx(a, a + 1, N) + a + 1;
-        const int *ha = reinterpret_cast<const int *>(hplane + tc_row(a, 0) * Lp);
-        const unsigned *la = reinterpret_cast<const unsigned *>(lplane + tc_row(a, 0) * Lp);
-        const int *hb = reinterpret_cast<const int *>(hplane + tc_row(b, 0) * Lp);
-        const unsigned *lb = reinterpret_cast<const unsigned *>(lplane + tc_row(b, 0) * Lp);
-        int hh[9], hx[9];
-        unsigned ll[9];
+    // one flagged pair (a < b): its exact class sums reduced across the warp into slot cnt. Each
+    // lane takes 16 consecutive bytes (16 atoms) of each of the pair's twelve rows per 512-byte
+    // chunk, so a pair of L <= 512 atoms costs one round of twelve 16-byte loads
+    auto pair = [&](int64_t a, int64_t b) {
+        const int8_t *ha = hplane + tc_row(a, 0) * Lp;
+        const int8_t *la = lplane + tc_row(a, 0) * Lp;
+        const int8_t *hb = hplane + tc_row(b, 0) * Lp;
+        const int8_t *lb = lplane + tc_row(b, 0) * Lp;
+        int hh[9], hx[9], ll[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             hh[k] = 0;
             hx[k] = 0;
-            ll[k] = 0u;
+            ll[k] = 0;
         }
-#pragma unroll 4
-        for (int q = lane; q < nq; q += 32) {
-            int A[3], B[3];
-            unsigned Al[3], Bl[3];
+#pragma unroll 1
+        for (int o = 16 * lane; o < Lp; o += 512) {
+            int A[3][4], Al[3][4], B[3][4], Bl[3][4];
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
-                A[ax] = __ldg(ha + ax * rq + q);
-                Al[ax] = __ldg(la + ax * rq + q);
-                B[ax] = __ldg(hb + ax * rq + q);
-                Bl[ax] = __ldg(lb + ax * rq + q);
+                const int4 u = __ldg(reinterpret_cast<const int4 *>(ha + ax * Lp + o));
+                const int4 ul = __ldg(reinterpret_cast<const int4 *>(la + ax * Lp + o));
+                const int4 w = __ldg(reinterpret_cast<const int4 *>(hb + ax * Lp + o));
+                const int4 wl = __ldg(reinterpret_cast<const int4 *>(lb + ax * Lp + o));
+                A[ax][0] = u.x, A[ax][1] = u.y, A[ax][2] = u.z, A[ax][3] = u.w;
+                Al[ax][0] = ul.x, Al[ax][1] = ul.y, Al[ax][2] = ul.z, Al[ax][3] = ul.w;
+                B[ax][0] = w.x, B[ax][1] = w.y, B[ax][2] = w.z, B[ax][3] = w.w;
+                Bl[ax][0] = wl.x, Bl[ax][1] = wl.y, Bl[ax][2] = wl.z, Bl[ax][3] = wl.w;
             }
 #pragma unroll
-            for (int al = 0; al < 3; ++al)
+            for (int j = 0; j < 4; ++j)
 #pragma unroll
-                for (int be = 0; be < 3; ++be) {
-                    const int k = 3 * al + be;
-                    hh[k] = dp4a_ss(A[al], B[be], hh[k]);
-                    hx[k] = dp4a_us((int)Al[al], B[be], dp4a_su(A[al], (int)Bl[be], hx[k]));
-                    ll[k] = dp4a_uu(Al[al], Bl[be], ll[k]);
-                }
+                for (int al = 0; al < 3; ++al)
+#pragma unroll
+                    for (int be = 0; be < 3; ++be) {
+                        const int k = 3 * al + be;
+                        hh[k] = dp4a_ss(A[al][j], B[be][j], hh[k]);
+                        hx[k] = dp4a_ss(Al[al][j], B[be][j], dp4a_ss(A[al][j], Bl[be][j], hx[k]));
+                        ll[k] = dp4a_ss(Al[al][j], Bl[be][j], ll[k]);
+                    }
         }
         const int slot = cnt;
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-            // this lane's part of the sum, |t| < 2^36, reduced exactly as two 32-bit halves
-            const long long t = 65536LL * hh[k] + 256LL * hx[k] + (long long)ll[k];
-            const long long shi = __reduce_add_sync(0xffffffffu, (int)(t >> 24));
-            const long long slo = __reduce_add_sync(0xffffffffu, (int)(t & 0xFFFFFF));
-            if (lane == slot) v[k] = (shi << 24) + slo;
+            const int shh = __reduce_add_sync(0xffffffffu, hh[k]);
+            const int shx = __reduce_add_sync(0xffffffffu, hx[k]);
+            const int sll = __reduce_add_sync(0xffffffffu, ll[k]);
+            if (lane == k) {
+                sv[wib][k][slot] = shh;
+                sv[wib][9 + k][slot] = shx;
+                sv[wib][18 + k][slot] = sll;
+            }
         }
-        if (lane == slot) {
-            sa = a;
-            sb = b;
-            oidx = li;
-        }
+        if (lane == 0) lst[wib][slot] = make_int2((int)a, (int)b);
         if (++cnt == 32) flush();
     };
-    // mask words w0 + nwarps (32 it + j): lane j loads one word per iteration, so the scan
-    // issues 32 loads at a time yet keeps the round-robin assignment of words to warps
-    for (int64_t base = w0; base < nwords; base += 32 * nwarps) {
-        const int64_t wl = base + (int64_t)lane * nwarps;
+
+    // the list counts (each capped at fl_cap) and their exclusive prefix sums, per block
+    bool over = false;
+    {
+        const int per = (nslots + 255) / 256;
+        const int i0 = min((int)threadIdx.x * per, nslots), i1 = min(i0 + per, nslots);
+        unsigned loc = 0;
+        for (int i = i0; i < i1; ++i) {
+            const unsigned c = fl_cnt[i];
+            over |= c > (unsigned)fl_cap;
+            loc += min(c, (unsigned)fl_cap);
+        }
+        unsigned inc = loc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        __shared__ unsigned wtot[8];
+        if (lane == 31) wtot[wib] = inc;
+        __syncthreads();
+        unsigned run = inc - loc;
+        for (int w = 0; w < wib; ++w) run += wtot[w];
+        for (int i = i0; i < i1; ++i) {
+            spre[i] = run;
+            run += min(fl_cnt[i], (unsigned)fl_cap);
+        }
+        if (threadIdx.x == 255) spre[nslots] = run;
+        over = __syncthreads_or(over);
+    }
+    const unsigned F = spre[nslots];
+    const unsigned W = gridDim.x * (blockDim.x >> 5);
+    const unsigned Wf = max(1u, min(W, (F + REFINE_MIN_PAIRS - 1) / REFINE_MIN_PAIRS));
+    const unsigned g = wib * gridDim.x + blockIdx.x;
+    if (g < Wf) {
+        const unsigned r0 = (unsigned)((unsigned long long)g * F / Wf);
+        const unsigned r1 = (unsigned)((unsigned long long)(g + 1) * F / Wf);
+        for (unsigned r = r0; r < r1; r += 32) {
+            // lane j fetches the pair of rank r + j: its slot by bisection of the prefix sums
+            const unsigned rr = r + lane;
+            int2 e = make_int2(0, 0);
+            if (rr < r1) {
+                int lo = 0, hi = nslots;  // spre[lo] <= rr < spre[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (spre[mid] <= rr)
+                        lo = mid;
+                    else
+                        hi = mid;
+                }
+                e = flist[(int64_t)lo * fl_cap + (rr - spre[lo])];
+            }
+            const int n = (int)min(32u, r1 - r);
+            for (int j = 0; j < n; ++j) pair(__shfl_sync(0xffffffffu, e.x, j), __shfl_sync(0xffffffffu, e.y, j));
+        }
+        if (cnt) flush();
+    }
+    if (!over) return;
+    // pairs past a list's capacity: their mask bits, words w0 + W (32 it + j), lane j loading one
+    // word per iteration (32 loads at a time)
+    const int64_t nwords = (npairs + 31) / 32;
+    for (int64_t base = g; base < nwords; base += 32 * (int64_t)W) {
+        const int64_t wl = base + (int64_t)lane * W;
         uint32_t word = wl < nwords ? flags[wl] : 0u;
         if (wl == nwords - 1 && (npairs & 31)) word &= ~0u >> (32 - (int)(npairs & 31));
         uint32_t nz = __ballot_sync(0xffffffffu, word != 0u);
         while (nz) {
             const int src = __ffs(nz) - 1;
             nz &= nz - 1;
-            const int64_t wi = base + (int64_t)src * nwarps;
+            const int64_t wi = base + (int64_t)src * W;
             uint32_t wd = __shfl_sync(0xffffffffu, word, src);
             while (wd) {
                 const int bit = __ffs(wd) - 1;
                 wd &= wd - 1;
-                pair(wi * 32 + bit);
+                const int64_t idx = wi * 32 + bit + out_base;
+                const int64_t a = condensed_row(idx, N);
+                pair(a, idx - condensed_idx(a, a + 1, N) + a + 1);
             }
         }
     }
-    flush();
+    if (cnt) flush();
 }
 
 template <int LAYOUT>
@@ -1020,8 +1102,17 @@ inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
     // persistent: one CTA per SM, CTA x takes tiles x, x + grid, x + 2 grid, ...
     const unsigned grid = (unsigned)std::min<int64_t>(nt, sms > 0 ? sms : 148);
     const int64_t npairs = condensed_idx(a.row_end - 1, a.N - 1, a.N) + 1 - a.out_base;
+    if ((int64_t)grid * FW_MAXEPI > FL_MAXSLOTS) {
+        err = "more epilogue warps than flagged-pair list slots";
+        return CLUSCO_EUNSUPPORTED;
+    }
+    int fl_cap = a.flist ? (int)std::min<int64_t>(a.flist_entries / ((int64_t)grid * FW_MAXEPI), 1 << 30) : 0;
+#ifdef CLUSCO_DEBUG_HOOKS
+    if (debug_fl_cap() > 0) fl_cap = std::min(fl_cap, debug_fl_cap());
+#endif
     if (LAYOUT == TC_EXACT2) {
-        e = cudaMemsetAsync(a.flags, 0, (size_t)((npairs + 31) / 32) * sizeof(uint32_t), st);
+        // the mask and the list counts
+        e = cudaMemsetAsync(a.flags, 0, (size_t)(flag_list_offset(npairs) + FL_MAXSLOTS) * sizeof(uint32_t), st);
         if (e != cudaSuccess) {
             err = std::string("flag mask reset: ") + cudaGetErrorString(e);
             return CLUSCO_ECUDA;
@@ -1044,20 +1135,18 @@ inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
     }
     kern<<<grid, fw_threads(win), FW_SMEM, st>>>(mA, mB, a.scales, a.G32, a.N, (int)a.L, nkb, a.Rpad, TA, TB, t0, nt,
                                              a.row_begin, a.row_end, sink, a.rot, a.fix, a.fix_count, a.fix_cap,
-                                             a.flags);
+                                             a.flags, a.flist, a.flags ? a.flags + flag_list_offset(npairs) : nullptr,
+                                             fl_cap);
     e = cudaGetLastError();
     prof_mark(PROF_PAIRS, st);
     if (e == cudaSuccess && LAYOUT == TC_EXACT2) {
-        // one wave (MINB CTAs per SM by the launch bound): with the few flagged pairs spread over
-        // many warps, a second wave only added its latency. Three per SM from 2^33 pair-atoms up
-        // (8,192 x 500: 1.72 -> 1.68 ms for the whole forward), two below (5,000 x 300 lost 0.01 ms).
+        // one wave, two CTAs per SM (the launch bound keeps the FP64 Newton and a pair's twelve
+        // 16-byte loads in registers)
         const int nsm = sms > 0 ? sms : 148;
-        if ((double)npairs * (double)a.Lp >= 8589934592.0)
-            refine_flagged_kernel<3><<<3 * nsm, 256, 0, st>>>(a.hplane, a.lplane, a.scales, a.G64, a.N, (int)a.L,
-                                                               (int)a.Lp, npairs, a.out_base, a.flags, sink);
-        else
-            refine_flagged_kernel<2><<<2 * nsm, 256, 0, st>>>(a.hplane, a.lplane, a.scales, a.G64, a.N, (int)a.L,
-                                                               (int)a.Lp, npairs, a.out_base, a.flags, sink);
+        refine_flagged_kernel<2><<<2 * nsm, 256, 0, st>>>(a.hplane, a.lplane, a.scales, a.G64, a.N, (int)a.L,
+                                                           (int)a.Lp, npairs, a.out_base, a.flags, a.flist,
+                                                           a.flags + flag_list_offset(npairs), (int)grid * FW_MAXEPI,
+                                                           fl_cap, sink);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && a.rot) {

@@ -12,8 +12,9 @@
 //        row(a, axis) = 32*(a/10) + 3*(a%10) + axis.
 //    BF16_EXACT2: plane 0 = high digit h, plane 1 = low digit l of the 16-bit
 //      fixed point value n = round(x/s_axis), n = 256 h + l, |h|,|l| <= 128,
-//      s_axis = max|x_axis| / 32767 per model and axis; G from the same n
-//      (exact in int64), so G and the covariance describe the same points.
+//      s_axis = max|x_axis| / 32639 per model and axis (|n| <= 32639, so that the byte
+//      digits below are signed bytes too); G from the same n (exact in int64), so G and
+//      the covariance describe the same points.
 //    BF16X3: plane 0 = bf16(x), plane 1 = bf16(x - bf16(x)); G from hi + lo.
 //    TF32: one FP32 plane holding tf32-rounded x; G from those values.
 //    Optionally (xf != nullptr) the centred FP32 coordinates in the same row layout.
@@ -182,15 +183,16 @@ enum TcLayout { TC_EXACT2 = 0, TC_BF16X3 = 1, TC_TF32 = 2 };
 // tcgen05 operand planes. Grid: ceil(Npad40/8) blocks of 256 threads.
 // planes: element type bf16 (EXACT2, BF16X3; two planes) or float (TF32; one plane),
 // plane stride Rpad*Lp elements. hplane / lplane (EXACT2, optional): the same 16-bit
-// fixed-point coordinates as bytes, n = 256 h + l with h = n >> 8 signed and l = n & 255
-// unsigned, for the exact recomputation of flagged pairs with 4-way byte dot products.
+// fixed-point coordinates as signed bytes, n = 256 h + l with h = floor((n + 128) / 256) and
+// l = n - 256 h, both in [-128, 127] for |n| <= 32639, for the exact recomputation of flagged
+// pairs with signed 4-way byte dot products.
 template <int LAYOUT>
 __global__ void __launch_bounds__(256) prepass_tc_kernel(const float *__restrict__ coords, int64_t N, int L, int Lp,
                                                          int64_t Npad, int64_t Rpad, void *__restrict__ planes,
                                                          float *__restrict__ scales, double *__restrict__ G64,
                                                          float *__restrict__ G32, float *__restrict__ xf,
                                                          int8_t *__restrict__ hplane = nullptr,
-                                                         uint8_t *__restrict__ lplane = nullptr)
+                                                         int8_t *__restrict__ lplane = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const int64_t a = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -240,8 +242,8 @@ __global__ void __launch_bounds__(256) prepass_tc_kernel(const float *__restrict
     if (LAYOUT == TC_EXACT2) {
         for (int ax = 0; ax < 3; ++ax) {
             if (mx[ax] > 0.f && isfinite(mx[ax])) {
-                sc[ax] = mx[ax] / 32767.f;
-                inv[ax] = 32767.f / mx[ax];
+                sc[ax] = mx[ax] / 32639.f;
+                inv[ax] = 32639.f / mx[ax];
             }
         }
     }
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(256) prepass_tc_kernel(const float *__restrict
             if (xf) xf[off] = v;
             if (LAYOUT == TC_EXACT2) {
                 float n = rintf(v * inv[ax]);
-                n = fminf(fmaxf(n, -32767.f), 32767.f);
+                n = fminf(fmaxf(n, -32639.f), 32639.f);
                 if (!isfinite(v)) n = 0.f;
                 const float h = rintf(n * (1.f / 256.f));
                 const float l = n - 256.f * h;
@@ -262,8 +264,9 @@ __global__ void __launch_bounds__(256) prepass_tc_kernel(const float *__restrict
                 p1[off] = __float2bfloat16_rn(l);
                 const int ni = (int)n;
                 if (hplane) {
-                    hplane[off] = (int8_t)(ni >> 8);     // n = 256 h + l, h in [-128, 127]
-                    lplane[off] = (uint8_t)(ni & 255);  // l in [0, 255]
+                    const int hb = (ni + 128) >> 8;  // floor: n = 256 h + l, h and l in [-128, 127]
+                    hplane[off] = (int8_t)hb;
+                    lplane[off] = (int8_t)(ni - 256 * hb);
                 }
                 gi[ax] += (long long)ni * ni;
             } else if (LAYOUT == TC_BF16X3) {

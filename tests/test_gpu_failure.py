@@ -38,6 +38,9 @@ def dlib():
     lib = ctypes.CDLL(path)
     vp, i64, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t
     lib.clusco_debug_hooks.argtypes = [ctypes.c_int, i64]
+    lib.clusco_debug_flag_list_cap.argtypes = [ctypes.c_int]
+    lib.clusco_crmsd_allpairs_below.argtypes = [vp, i64, i64, ctypes.c_float, vp, vp, i64, vp, ctypes.c_int, vp,
+                                                sz, vp]
     lib.clusco_crmsd_allpairs.argtypes = [vp, i64, i64, vp, ctypes.c_int, vp, sz, vp]
     lib.clusco_crmsd_allpairs_backward.argtypes = [vp, i64, i64, vp, vp, vp, ctypes.c_float, ctypes.c_int, vp, sz,
                                                    vp]
@@ -45,6 +48,7 @@ def dlib():
     lib.clusco_last_error.restype = ctypes.c_char_p
     yield lib
     lib.clusco_debug_hooks(0, 0)
+    lib.clusco_debug_flag_list_cap(0)
 
 
 def test_skipped_arrive_times_out_and_the_context_survives(dlib):
@@ -104,3 +108,39 @@ def test_near_duplicate_queue_overflow_is_reported(dlib):
     rel = (torch.linalg.vector_norm((g - want).reshape(N, -1), dim=1)
            / torch.linalg.vector_norm(want.reshape(N, -1), dim=1).clamp_min(1e-30))
     assert float(rel.max()) <= 1e-5
+
+
+def test_flagged_list_overflow_takes_the_mask_path(dlib):
+    """The exact-digit forward lists its flagged pairs per epilogue warp; with the lists cut to one
+    or three entries, the pairs past them go through the flag mask instead (the refinement's
+    second path). The matrix, and the threshold list, are bit for bit the default library's."""
+    e = E.decoy_ensemble(1200, 500, 10, (0.1, 12.0), 31337)  # the bench recipe: ~0.7 % flagged
+    N, L = e.N, e.L
+    P = N * (N - 1) // 2
+    X = torch.from_numpy(e.coords).cuda()
+    good = clusco.crmsd_allpairs(X, clusco.FORM_BF16_EXACT2)
+    tau = 3.2
+    gl, gv = clusco.crmsd_pairs_below(X, tau, clusco.FORM_BF16_EXACT2)
+    assert clusco.sync_status() == 0
+    gorder = torch.argsort(gl)
+    for cap in (1, 3):
+        assert dlib.clusco_debug_flag_list_cap(cap) == 0
+        out = torch.full((P,), -1.0, device="cuda")
+        rc = dlib.clusco_crmsd_allpairs(X.data_ptr(), N, L, out.data_ptr(), clusco.FORM_BF16_EXACT2, None, 0, None)
+        assert rc == 0, dlib.clusco_last_error()
+        assert dlib.clusco_sync_status(None) == 0
+        assert torch.equal(out, good), cap
+        cap_l = gl.numel() + 64
+        lst = torch.empty(cap_l, dtype=torch.int64, device="cuda")
+        vals = torch.empty(cap_l, dtype=torch.float32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        rc = dlib.clusco_crmsd_allpairs_below(X.data_ptr(), N, L, ctypes.c_float(tau), lst.data_ptr(),
+                                              vals.data_ptr(), cap_l, cnt.data_ptr(), clusco.FORM_BF16_EXACT2, None,
+                                              0, None)
+        assert rc == 0, dlib.clusco_last_error()
+        assert dlib.clusco_sync_status(None) == 0
+        n = int(cnt.item())
+        assert n == gl.numel()
+        order = torch.argsort(lst[:n])
+        assert torch.equal(lst[:n][order], gl[gorder]) and torch.equal(vals[:n][order], gv[gorder])
+    assert dlib.clusco_debug_flag_list_cap(0) == 0
