@@ -21,8 +21,9 @@
 //    A_l B'^T -> cols [128,256) (lh | ll). Four digit-product classes, each an exact
 //    integer sum in FP32 (|digit| <= 128, L <= 1024 keeps every sum below 2^24).
 //    Epilogue: FP32 fast path; pairs whose FP32 error bound exceeds the fast-path
-//    tolerance get a bit in a mask and are recomputed after the sweep, exactly from the
-//    16-bit coordinates and in FP64 (refine_flagged_kernel).
+//    tolerance go to their epilogue warp's list (past its capacity: a bit in a mask) and are
+//    recomputed after the sweep, exactly from the 16-bit coordinates and in FP64
+//    (refine_flagged_kernel).
 //  BF16X3: planes hi, lo; A_h B'^T (hh | hl) and A_l B_h^T (lh); H = hh + hl + lh.
 //  TF32: one FP32 plane; A B^T with kind::tf32.
 #pragma once
