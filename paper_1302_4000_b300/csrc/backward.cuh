@@ -238,8 +238,17 @@ __global__ void __launch_bounds__(256, 1)
     }
 }
 
-// Direct FP64 residual path for near-duplicate pairs: one warp per queued pair (a < b).
-__global__ void __launch_bounds__(256) bwd_neardup_kernel(const float *__restrict__ coords, int64_t N, int L,
+// Direct FP64 path for near-duplicate pairs: one warp per queued pair (a < b), pairs spread
+// over the blocks first (so over the SMs). Centroids from per-lane compensated FP32 sums
+// (Neumaier: a running error term, so each lane's sum is exact to a few units of FP32
+// rounding squared) combined in FP64; the centred coordinates, G_A, G_B and the covariance in
+// FP64; the
+// rotation in FP64 (quartic Newton, Horn's adjugate, Jacobi where that vanishes); cRMSD from
+// L c^2 = G_A + G_B - 2 tr(R^T H) in FP64 (stationary in R, and the cancellation leaves ~1e-12
+// relative of G at FP64 rounding); then one more pass for the residuals a_i - R b_i in FP64
+// and the gradient terms: the b side b_i - R^T a_i = -R^T (a_i - R b_i) from the FP64
+// residual rounded to FP32 (accurate relative to the residual itself).
+__global__ void __launch_bounds__(256, 2) bwd_neardup_kernel(const float *__restrict__ coords, int64_t N, int L,
                                                           const float *__restrict__ wvec, float eps,
                                                           const long long *__restrict__ nd_list,
                                                           const unsigned long long *__restrict__ nd_count,
@@ -252,32 +261,44 @@ __global__ void __launch_bounds__(256) bwd_neardup_kernel(const float *__restric
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(CLUSCO_ST_BOUNDS);
         cnt = nd_cap;
     }
-    for (int64_t p = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); p < (int64_t)cnt; p += nwarps) {
+    for (int64_t p = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x; p < (int64_t)cnt; p += nwarps) {
         const int64_t a = nd_list[2 * p], b = nd_list[2 * p + 1];
         const float *xa = coords + a * (int64_t)L * 3;
         const float *xb = coords + b * (int64_t)L * 3;
-        double ma[3] = {0, 0, 0}, mb[3] = {0, 0, 0};
+        float fa[3] = {0.f, 0.f, 0.f}, fb[3] = {0.f, 0.f, 0.f}, ca[3] = {0.f, 0.f, 0.f}, cb[3] = {0.f, 0.f, 0.f};
+        auto acc = [](float &sum, float &comp, float x) {
+            const float t = sum + x;
+            comp += fabsf(sum) >= fabsf(x) ? (sum - t) + x : (x - t) + sum;
+            sum = t;
+        };
         for (int i = lane; i < L; i += 32)
+#pragma unroll
             for (int k = 0; k < 3; ++k) {
-                ma[k] += (double)xa[3 * i + k];
-                mb[k] += (double)xb[3 * i + k];
+                acc(fa[k], ca[k], xa[3 * i + k]);
+                acc(fb[k], cb[k], xb[3 * i + k]);
             }
+        double ma[3], mb[3];
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
-            ma[k] = warp_sum_d(ma[k]) / (double)L;
-            mb[k] = warp_sum_d(mb[k]) / (double)L;
+            ma[k] = warp_sum_d((double)fa[k] + (double)ca[k]) / (double)L;
+            mb[k] = warp_sum_d((double)fb[k] + (double)cb[k]) / (double)L;
         }
         double H[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, Ga = 0, Gb = 0;
         for (int i = lane; i < L; i += 32) {
             double u[3], v[3];
+#pragma unroll
             for (int k = 0; k < 3; ++k) {
                 u[k] = (double)xa[3 * i + k] - ma[k];
                 v[k] = (double)xb[3 * i + k] - mb[k];
-                Ga += u[k] * u[k];
-                Gb += v[k] * v[k];
+                Ga = fma(u[k], u[k], Ga);
+                Gb = fma(v[k], v[k], Gb);
             }
+#pragma unroll
             for (int r = 0; r < 3; ++r)
-                for (int c = 0; c < 3; ++c) H[3 * r + c] += u[r] * v[c];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) H[3 * r + c] = fma(u[r], v[c], H[3 * r + c]);
         }
+#pragma unroll
         for (int k = 0; k < 9; ++k) H[k] = warp_sum_d(H[k]);
         Ga = warp_sum_d(Ga);
         Gb = warp_sum_d(Gb);
@@ -286,6 +307,7 @@ __global__ void __launch_bounds__(256) bwd_neardup_kernel(const float *__restric
         if (Gs > 0.0) {
             double m[9];
             const double nrm = 2.0 / Gs;
+#pragma unroll
             for (int k = 0; k < 9; ++k) m[k] = H[k] * nrm;
             double I1, det, I2;
             invariants3(m, I1, det, I2);
@@ -294,23 +316,15 @@ __global__ void __launch_bounds__(256) bwd_neardup_kernel(const float *__restric
             if (deg) s = sigma_cubic_d(I1, det, I2);
             if (!horn_rotation(m, s, 1e-12, R)) rotation_jacobi4<double, 10>(m, R);
         }
-        // residuals r_i = a_i - R b_i; c from the residuals; coefficient with the guard
-        double rr = 0.0;
-        for (int i = lane; i < L; i += 32) {
-            double u[3], v[3];
-            for (int k = 0; k < 3; ++k) {
-                u[k] = (double)xa[3 * i + k] - ma[k];
-                v[k] = (double)xb[3 * i + k] - mb[k];
-            }
-            for (int r = 0; r < 3; ++r) {
-                const double e = u[r] - (R[3 * r] * v[0] + R[3 * r + 1] * v[1] + R[3 * r + 2] * v[2]);
-                rr += e * e;
-            }
-        }
-        rr = warp_sum_d(rr);
-        const double c = sqrt(rr / (double)L);
+        double tr = 0.0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) tr = fma(R[k], H[k], tr);
+        const double c = sqrt(fmax(Gs - 2.0 * tr, 0.0) / (double)L);
         const double w = (double)wvec[condensed_idx(a, b, N)];
-        const double coef = w / ((double)L * fmax(c, (double)eps));
+        const float coef = (float)(w / ((double)L * fmax(c, (double)eps)));
+        float Rf[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Rf[k] = (float)R[k];
         // a side: coef (a_i - R b_i); b side: coef (b_i - R^T a_i). Both sum to zero over atoms.
         // Added into the gradient with FP32 atomics (several queued pairs share a model): the
         // order of the additions, hence the last bits of the gradient rows of models with
@@ -319,15 +333,20 @@ __global__ void __launch_bounds__(256) bwd_neardup_kernel(const float *__restric
         // tolerance of the adjoint.
         for (int i = lane; i < L; i += 32) {
             double u[3], v[3];
+#pragma unroll
             for (int k = 0; k < 3; ++k) {
                 u[k] = (double)xa[3 * i + k] - ma[k];
                 v[k] = (double)xb[3 * i + k] - mb[k];
             }
+            float ea[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                ea[r] = (float)fma(-R[3 * r + 2], v[2], fma(-R[3 * r + 1], v[1], fma(-R[3 * r], v[0], u[r])));
+#pragma unroll
             for (int r = 0; r < 3; ++r) {
-                const double ea = u[r] - (R[3 * r] * v[0] + R[3 * r + 1] * v[1] + R[3 * r + 2] * v[2]);
-                const double eb = v[r] - (R[r] * u[0] + R[3 + r] * u[1] + R[6 + r] * u[2]);
-                atomicAdd(grad + (a * (int64_t)L + i) * 3 + r, (float)(coef * ea));
-                atomicAdd(grad + (b * (int64_t)L + i) * 3 + r, (float)(coef * eb));
+                const float eb = -fmaf(Rf[6 + r], ea[2], fmaf(Rf[3 + r], ea[1], Rf[r] * ea[0]));
+                atomicAdd(grad + (a * (int64_t)L + i) * 3 + r, coef * ea[r]);
+                atomicAdd(grad + (b * (int64_t)L + i) * 3 + r, coef * eb);
             }
         }
     }
