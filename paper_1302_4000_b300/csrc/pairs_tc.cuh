@@ -7,13 +7,14 @@
 // the 3x3 covariance blocks of its 800 model pairs. Only tiles with pairs a < b exist
 // (upper triangle: B-tile J >= 2 I).
 //
-// Pipeline (persistent: one CTA per SM, CTA x takes tiles x, x + grid, ...; 10 warps):
-// warp 0 lane 0 streams 64-column K blocks of the A and B tiles into a 3-stage
-// shared-memory ring with TMA (128-byte swizzle); warp 1 lane 0 issues tcgen05.mma into
-// one of two 256-column TMEM accumulator buffers, so that the MMAs of tile k + 1 run while
-// warps 2-9 drain tile k: tcgen05.ld of their 32 TMEM lanes x 32 columns, assembly of each
-// 3x3 block across the three lanes of a model with warp shuffles, eq. 2 in the normalised
-// frame, condensed FP32 store (or the threshold list). No covariance reaches global memory.
+// Pipeline (persistent: one CTA per SM, CTA x takes tiles x, x + grid, ...; 10 warps, or 18
+// with the 5-model windows below): warp 0 lane 0 streams 64-column K blocks of the A and B
+// tiles into a 3-stage shared-memory ring with TMA (128-byte swizzle); warp 1 lane 0 issues
+// tcgen05.mma into one of two 256-column TMEM accumulator buffers, so that the MMAs of tile
+// k + 1 run while the epilogue warps (8, or 16 on windows) drain tile k: tcgen05.ld of their
+// 32 TMEM lanes and columns, assembly of each 3x3 block across the three lanes of a model with
+// warp shuffles, eq. 2 in the normalised frame, condensed FP32 store (or the threshold list).
+// No covariance reaches global memory.
 //
 // Forms:
 //  EXACT2: planes h, l of 16-bit fixed point (n = 256 h + l). Per 16-wide K step two
