@@ -69,6 +69,7 @@ __device__ __forceinline__ void model_centroid_absmax(const float *__restrict__ 
     float s0 = 0.f, s1 = 0.f, s2 = 0.f;
     float lo[3] = {3.4e38f, 3.4e38f, 3.4e38f}, hi[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
     bool ok = true;
+#pragma unroll 4
     for (int i = lane; i < L; i += 32) {
         const float v0 = x[3 * i + 0], v1 = x[3 * i + 1], v2 = x[3 * i + 2];
         ok = ok && isfinite(v0) && isfinite(v1) && isfinite(v2);
@@ -249,6 +250,7 @@ __global__ void __launch_bounds__(256) prepass_tc_kernel(const float *__restrict
     }
     long long gi[3] = {0, 0, 0};
     double gd = 0.0;
+#pragma unroll 4
     for (int i = lane; i < Lp; i += 32) {
         for (int ax = 0; ax < 3; ++ax) {
             const int64_t off = (r0 + ax) * Lp + i;
