@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(fw_threads(WIN), 1)
         // EXACT2: this warp's list of flagged pairs (a, b); the ones past its capacity set their
         // mask bit instead
         int nfl = 0;
-        int2 *const myfl = flist + ((int64_t)blockIdx.x * FW_MAXEPI + ew) * fl_cap;
+        int2 *const myfl = flist ? flist + ((int64_t)blockIdx.x * FW_MAXEPI + ew) * fl_cap : nullptr;
         auto publish = [&](int n) {  // the first n staged pairs to the list, one atomic
             __syncwarp();
             unsigned long long base = 0;
@@ -875,8 +875,9 @@ constexpr int REFINE_MIN_PAIRS = 16;
 // blocks, so across the SMs) takes ranks [g F / W', (g + 1) F / W') of the concatenated lists,
 // so the work is balanced however the flagged pairs cluster. Pairs past a list's capacity
 // (their mask bits) are taken after it, mask words round-robin over all warps.
-template <int MINB>
-__global__ void __launch_bounds__(256, MINB) refine_flagged_kernel(const int8_t *__restrict__ hplane,
+// Two CTAs per SM (the launch bound keeps the FP64 Newton and a pair's twelve 16-byte loads in
+// 128 registers); three would cap them at 80, and the loads would spill.
+__global__ void __launch_bounds__(256, 2) refine_flagged_kernel(const int8_t *__restrict__ hplane,
                                                                    const int8_t *__restrict__ lplane,
                                                                    const float *__restrict__ scales,
                                                                    const double *__restrict__ G64, int64_t N, int L,
@@ -1142,13 +1143,12 @@ inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
     e = cudaGetLastError();
     prof_mark(PROF_PAIRS, st);
     if (e == cudaSuccess && LAYOUT == TC_EXACT2) {
-        // one wave, two CTAs per SM (the launch bound keeps the FP64 Newton and a pair's twelve
-        // 16-byte loads in registers)
+        // one wave of two CTAs per SM
         const int nsm = sms > 0 ? sms : 148;
-        refine_flagged_kernel<2><<<2 * nsm, 256, 0, st>>>(a.hplane, a.lplane, a.scales, a.G64, a.N, (int)a.L,
-                                                           (int)a.Lp, npairs, a.out_base, a.flags, a.flist,
-                                                           a.flags + flag_list_offset(npairs), (int)grid * FW_MAXEPI,
-                                                           fl_cap, sink);
+        refine_flagged_kernel<<<2 * nsm, 256, 0, st>>>(a.hplane, a.lplane, a.scales, a.G64, a.N, (int)a.L,
+                                                        (int)a.Lp, npairs, a.out_base, a.flags, a.flist,
+                                                        a.flags + flag_list_offset(npairs), (int)grid * FW_MAXEPI,
+                                                        fl_cap, sink);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && a.rot) {
