@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(fw_threads(WIN), 1)
         // EXACT2: this warp's list of flagged pairs (a, b); the ones past its capacity set their
         // mask bit instead
         int nfl = 0;
-        int2 *const myfl = flist ? flist + ((int64_t)blockIdx.x * FW_MAXEPI + ew) * fl_cap : nullptr;
+        int2 *const myfl = flist ? flist + ((int64_t)blockIdx.x * fw_epi(WIN) + ew) * fl_cap : nullptr;
         auto publish = [&](int n) {  // the first n staged pairs to the list, one atomic
             __syncwarp();
             unsigned long long base = 0;
@@ -747,7 +747,7 @@ __global__ void __launch_bounds__(fw_threads(WIN), 1)
             }
         }
         if (SPARSE && fill > 0) publish(fill);
-        if (LAYOUT == TC_EXACT2 && lane == 0) fl_cnt[blockIdx.x * FW_MAXEPI + ew] = (unsigned)nfl;
+        if (LAYOUT == TC_EXACT2 && lane == 0) fl_cnt[blockIdx.x * fw_epi(WIN) + ew] = (unsigned)nfl;
     }
     tc_fence_before();
     __syncthreads();
@@ -848,9 +848,9 @@ __device__ __forceinline__ int dp4a_ss(int a, int b, int c)
     return d;
 }
 
-// The flagged-pair lists of the exact-digit forward: one per epilogue warp slot (CTA x
-// FW_MAXEPI + warp), FL_MAXSLOTS slots at most, each of capacity flist_entries / slots; their
-// counts follow the flag mask (flag_list_offset words from its start, 16-byte aligned).
+// The flagged-pair lists of the exact-digit forward: one per epilogue warp (slot CTA x epilogue
+// warps per CTA + warp), FL_MAXSLOTS slots at most, each of capacity flist_entries / slots;
+// their counts follow the flag mask (flag_list_offset words from its start, 16-byte aligned).
 constexpr int FL_MAXSLOTS = 4096;
 inline int64_t flag_list_offset(int64_t npairs) { return ((npairs + 31) / 32 + 3) / 4 * 4; }
 // list entries for a pair range: 1/32 of the pairs (the bench ensembles flag under 1 %), at
@@ -1105,11 +1105,12 @@ inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
     // persistent: one CTA per SM, CTA x takes tiles x, x + grid, x + 2 grid, ...
     const unsigned grid = (unsigned)std::min<int64_t>(nt, sms > 0 ? sms : 148);
     const int64_t npairs = condensed_idx(a.row_end - 1, a.N - 1, a.N) + 1 - a.out_base;
-    if ((int64_t)grid * FW_MAXEPI > FL_MAXSLOTS) {
+    const int64_t nslots = (int64_t)grid * fw_epi(win);  // one flagged-pair list per epilogue warp
+    if (nslots > FL_MAXSLOTS) {
         err = "more epilogue warps than flagged-pair list slots";
         return CLUSCO_EUNSUPPORTED;
     }
-    int fl_cap = a.flist ? (int)std::min<int64_t>(a.flist_entries / ((int64_t)grid * FW_MAXEPI), 1 << 30) : 0;
+    int fl_cap = a.flist ? (int)std::min<int64_t>(a.flist_entries / nslots, 1 << 30) : 0;
 #ifdef CLUSCO_DEBUG_HOOKS
     if (debug_fl_cap() > 0) fl_cap = std::min(fl_cap, debug_fl_cap());
 #endif
@@ -1147,7 +1148,7 @@ inline int launch_tc(const TcArgs &a, cudaStream_t st, std::string &err)
         const int nsm = sms > 0 ? sms : 148;
         refine_flagged_kernel<<<2 * nsm, 256, 0, st>>>(a.hplane, a.lplane, a.scales, a.G64, a.N, (int)a.L,
                                                         (int)a.Lp, npairs, a.out_base, a.flags, a.flist,
-                                                        a.flags + flag_list_offset(npairs), (int)grid * FW_MAXEPI,
+                                                        a.flags + flag_list_offset(npairs), (int)nslots,
                                                         fl_cap, sink);
         e = cudaGetLastError();
     }
