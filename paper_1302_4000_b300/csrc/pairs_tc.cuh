@@ -854,8 +854,12 @@ __device__ __forceinline__ int dp4a_ss(int a, int b, int c)
 constexpr int FL_MAXSLOTS = 4096;
 inline int64_t flag_list_offset(int64_t npairs) { return ((npairs + 31) / 32 + 3) / 4 * 4; }
 // list entries for a pair range: 1/32 of the pairs (the bench ensembles flag under 1 %), at
-// least 2^16
-inline int64_t flag_list_entries(int64_t npairs) { return std::max<int64_t>(npairs / 32, (int64_t)1 << 16); }
+// least 2^16 and at most 2^27 (1 GiB of workspace; past that, and past a list's share, the
+// pairs take the mask path), so that the counts and their prefix sums stay below 2^32
+inline int64_t flag_list_entries(int64_t npairs)
+{
+    return std::min<int64_t>(std::max<int64_t>(npairs / 32, (int64_t)1 << 16), (int64_t)1 << 27);
+}
 
 // Minimum flagged pairs per refinement warp: fewer warps with fuller batches where the flagged
 // set is small (each batch costs its FP64 instructions whatever its fill).
